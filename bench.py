@@ -1,0 +1,390 @@
+"""Benchmark of the batched mapping step (RMGS-SLAM §III-C global Gaussian-map
+optimisation) on GB300.
+
+Workload (default): 2M Gaussians, SH degree 3, from the synthetic LiDAR generator along a
+200 m closed loop; 8 keyframes per step with uneven resolutions (2 x each of 640x480,
+960x540, 1280x720, 1280x1024, fx = 0.7 W), 4 sampled from the recent window (last 10% of
+the loop) and 4 from the history; targets are renders of a perturbed copy of the map.
+One step = project + tile sort + composite with the fused L1 loss + backward (incl. pose
+twists) + masked Adam, all views in each launch.
+
+Prints one JSON line (see the keys below).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIZES = [(640, 480), (640, 480), (960, 540), (960, 540), (1280, 720), (1280, 720), (1280, 1024), (1280, 1024)]
+METRIC = "fwd+bwd render Mpix/s and iters/s at 2M Gaussians; secs-to-PSNR learned vs plain"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=3)
+    return ap.parse_args()
+
+
+def make_workload(n, seed, rank=0):
+    import synth
+    sc = synth.lidar_scene(seed=seed + 17 * rank, n=n, sh_degree=3, kind="loop")
+    rng = np.random.default_rng(seed + 1000 + rank)
+    n_pose = len(sc.meta["traj_pos"])
+    recent0 = int(0.9 * n_pose)
+    idx = list(rng.integers(recent0, n_pose, 4)) + list(rng.integers(0, recent0, 4))
+    cams = synth.trajectory_cameras(sc, SIZES, idx, fx_per_width=0.7)
+    gt = synth.perturbed(sc, seed + 2000 + rank)
+    return sc, gt, cams
+
+
+def workload_config(args):
+    return {"workload": "batched keyframe step: 2M Gaussians SH3 (LiDAR loop scene), 8 views "
+                        "2x{640x480,960x540,1280x720,1280x1024}, fused fwd+bwd+Adam",
+            "n_gaussians": args.n, "views": len(SIZES), "pixels_per_step": sum(w * h for w, h in SIZES),
+            "tile": args.tile, "chunk": args.chunk,
+            "l2": "inputs larger than L2 (params+grads+Adam state ~1.9 GB, pair lists ~0.5 GB)"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                try:
+                    rows.append((float(p[1]), float(p[2]), p[5:9]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r) if x.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+# oracle (CPU) timing: bounded sample of the same workload
+# ------------------------------------------------------------------------------------------
+
+def crop_camera(cam, w, h):
+    c = dict(cam)
+    c["cx"] = cam["cx"] - (cam["width"] - w) / 2
+    c["cy"] = cam["cy"] - (cam["height"] - h) / 2
+    c["width"], c["height"] = w, h
+    return c
+
+
+def oracle_sample(sc, cams, targets, crop=(64, 48)):
+    """One oracle 'step' on a pixel sample: projection of every Gaussian into the cropped
+    view 0, brute-force render + L1 loss + backward of the crop, masked Adam over every
+    parameter.  Returns (seconds, pixels, threads)."""
+    import oracle
+    cam = crop_camera(cams[0], *crop)
+    H, W = crop[1], crop[0]
+    full = cams[0]
+    y0 = (full["height"] - H) // 2
+    x0 = (full["width"] - W) // 2
+    tg = {"rgb": targets[0]["rgb"][:, y0:y0 + H, x0:x0 + W], "depth": targets[0]["depth"][y0:y0 + H, x0:x0 + W],
+          "mask": np.ones((H, W), np.uint8)}
+    t0 = time.perf_counter()
+    out = oracle.loss_and_grads(sc, [cam], [tg])
+    planes = sc.planes()
+    zeros = np.zeros_like(planes, dtype=np.float64)
+    oracle.adam(planes, out["grads"], zeros, zeros, None, step=1)
+    dt = time.perf_counter() - t0
+    return dt, W * H, os.cpu_count()
+
+
+def cpu_baseline_line(sc, cams, targets, budget_s=20.0):
+    dt, px, thr = oracle_sample(sc, cams, targets, (32, 24))
+    # scale the crop so the sample takes about budget_s
+    per_px = dt / px
+    side = int(max(32, min(256, math.sqrt(max(1.0, budget_s / per_px) * 4 / 3))))
+    w, h = side, max(24, side * 3 // 4)
+    dt, px, thr = oracle_sample(sc, cams, targets, (w, h))
+    return {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": thr, "kind": "oracle",
+            "sample": f"{w}x{h} crop of view 0 (1280-wide class) with all {sc.n} Gaussians projected, "
+                      f"brute-force render + L1 + backward + Adam over all parameters, FP64, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+def run_gpu(args, rank, world):
+    import torch
+
+    import paper_2604_12942_gb300 as gs
+    dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
+    torch.cuda.set_device(dev)
+    sc, gt, cams = make_workload(args.n, args.seed, rank)
+    opts = gs.default_opts(tile=args.tile, chunk=args.chunk)
+    n = sc.n
+    # pair capacity: measure the ground truth's pairs once, add headroom
+    probe = gs.Workspace(n, cams, opts, 1 << 20)
+    gt_planes = torch.as_tensor(gt.planes(), device=dev).contiguous()
+    probe.project(gt_planes, 3)
+    probe.bin_sort()
+    need = int(probe.counters().n_pairs)
+    cap = int(need * 1.5) + (1 << 20)
+    del probe
+    ws = gs.Workspace(n, cams, opts, cap)
+    P = ws.layout.total_pixels
+    trgb = torch.empty(3 * P, device=dev)
+    tdep = torch.empty(P, device=dev)
+    ws.project(gt_planes, 3)
+    ws.bin_sort()
+    ws.render_fwd(trgb, tdep)
+    torch.cuda.synchronize()
+    del gt_planes, ws
+    step = gs.MappingStep(torch.as_tensor(sc.planes(), device=dev).contiguous(), 3, cams, opts, max_pairs=cap)
+    stages = ["project", "bin_sort", "render_fwd", "render_bwd", "adam"]
+    st = torch.cuda.current_stream()
+
+    def one(evs=None):
+        w = step.ws
+        if evs: evs[0].record(st)
+        w.project(step.planes, 3)
+        if evs: evs[1].record(st)
+        w.bin_sort()
+        if evs: evs[2].record(st)
+        w.render_fwd(step.rgb, step.depth, None, trgb, tdep, None, step.dl_drgb, step.dl_ddepth, step.loss)
+        if evs: evs[3].record(st)
+        w.render_bwd(step.planes, 3, step.grads, step.dl_drgb, step.dl_ddepth, None)
+        if evs: evs[4].record(st)
+        step.t += 1
+        gs.adam_step(step.planes, step.grads, step.m, step.v, 3, step.t, step.lr, None, w.visible())
+        if evs: evs[5].record(st)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    c = step.ws.counters()
+    if c.status != 0:
+        raise RuntimeError(f"device status {c.status} (pairs {c.n_pairs}, capacity {cap})")
+    n_pairs = int(c.n_pairs)
+    loss0 = float(step.loss[-1])
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(dev.index) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(st)
+        for k in range(args.steps):
+            one(evs[k])
+        t1.record(st)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
+                for i, s in enumerate(stages)}
+    c = step.ws.counters()
+    # end-to-end through the public API: targets uploaded from pinned host memory every
+    # step and the loss read back
+    h_rgb = trgb.cpu().pin_memory()
+    h_dep = tdep.cpu().pin_memory()
+    h_loss = torch.empty(len(cams) + 1).pin_memory()
+    d_rgb = torch.empty_like(trgb)
+    d_dep = torch.empty_like(tdep)
+    e_steps = max(3, args.steps // 2)
+    for _ in range(2):
+        d_rgb.copy_(h_rgb, non_blocking=True); d_dep.copy_(h_dep, non_blocking=True)
+        step(d_rgb, d_dep)
+        h_loss.copy_(step.loss, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(e_steps):
+        d_rgb.copy_(h_rgb, non_blocking=True)
+        d_dep.copy_(h_dep, non_blocking=True)
+        step(d_rgb, d_dep)
+        h_loss.copy_(step.loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e_dt = (time.perf_counter() - e0) / e_steps
+    px = sum(w * h for w, h in SIZES)
+    return dict(total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=float(step.loss[-1]),
+                clocks=clk.summary(), e2e_s=e_dt, px=px, h2d=int(h_rgb.numel() * 4 + h_dep.numel() * 4),
+                d2h=int(h_loss.numel() * 4), sc=sc, cams=cams, trgb=trgb, tdep=tdep, n=n,
+                kernels=kernels_per_step(step.ws.layout))
+
+
+def kernels_per_step(L):
+    tiles = L.total_tiles
+    tb = 0
+    while (1 << tb) < tiles:
+        tb += 1
+    passes = 4 + (tb + 7) // 8
+    # project: views + project; bin_sort: views + 3 scan + emit + 3 per pass + ranges;
+    # fwd: views + count + composite + finalize; bwd: views + composite bwd + projection bwd; adam
+    return 2 + (1 + 3 + 1 + 3 * passes + 1) + 4 + 3 + 1
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        dist.init_process_group("nccl")
+    r = run_gpu(args, rank, world)
+    total_ms = r["total_ms"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t)
+    ms_step = total_ms / args.steps
+    mpix = world * r["px"] * args.steps / (total_ms / 1e3) / 1e6
+    if rank != 0:
+        return
+    pk, pk_kind = peaks()
+    stage = r["stage_ms"]
+    dom = max(stage, key=stage.get)
+    roof = roofline(dom, stage, r, pk, pk_kind)
+    line = {
+        "metric": METRIC, "value": round(mpix, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "iters_per_s": round(1e3 / ms_step, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args),
+        "stage_ms": {k: round(v, 4) for k, v in stage.items()}, "n_pairs": r["n_pairs"],
+        "loss": [round(r["loss0"], 6), round(r["loss_end"], 6)],
+        "roofline": roof, "clocks": r["clocks"],
+        "e2e": {"value": round(r["px"] / r["e2e_s"] / 1e6, 2), "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["kernels"] * args.steps,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        tg = [{"rgb": t[0].cpu().numpy(), "depth": t[1].cpu().numpy()} for t in
+              zip(__import__("paper_2604_12942_gb300").unpack_rgb(r["trgb"], r["cams"]),
+                  __import__("paper_2604_12942_gb300").unpack_plane(r["tdep"], r["cams"]))]
+        line["cpu_baseline"] = cpu_baseline_line(r["sc"], r["cams"], tg)
+    print(json.dumps(line), flush=True)
+
+
+def roofline(dom, stage, r, pk, pk_kind):
+    """Bound and achieved fraction of the dominant stage (see the design doc for the per-unit
+    algorithmic work)."""
+    n, V, P = r["n"], len(SIZES), r["n_pairs"]
+    hbm = pk["hbm_gbs"]
+    if dom in ("project", "adam", "bin_sort"):
+        if dom == "project":
+            byts = 236 * n + V * n * 4 + 0.3 * V * n * 48    # params once, touched, records of visible
+        elif dom == "adam":
+            byts = 32 * 59 * n
+        else:
+            byts = P * (12 + 6 * 32) + V * n * 12
+        ach = byts / (stage[dom] * 1e-3) / 1e9
+        return {"bound": "hbm", "stage": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": None, "peak_kind": pk_kind}
+    # compositing: FP32 ALU bound
+    fp32 = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "stage": dom, "achieved": None, "peak": round(fp32, 1), "unit": "TFLOP/s",
+            "frac": None, "traffic": None, "peak_kind": pk_kind + " clock x 152 SM x 128 FP32 lanes x 2"}
+
+
+def run_reference(args):
+    import synth  # noqa: F401
+    sc, gt, cams = make_workload(args.n, args.seed)
+    # targets: the oracle cannot render the full views in bounded time; use the perturbed
+    # copy's oracle render of the sampled crop only
+    import oracle
+    crop = (32, 24)
+    cam = crop_camera(cams[0], *crop)
+    pr = oracle.project(gt, cam)
+    im = oracle.render(pr, cam)
+    tg_full = [{"rgb": np.zeros((3, cams[0]["height"], cams[0]["width"])),
+                "depth": np.zeros((cams[0]["height"], cams[0]["width"]))}]
+    H, W = crop[1], crop[0]
+    y0 = (cams[0]["height"] - H) // 2
+    x0 = (cams[0]["width"] - W) // 2
+    tg_full[0]["rgb"][:, y0:y0 + H, x0:x0 + W] = im["C"]
+    tg_full[0]["depth"][y0:y0 + H, x0:x0 + W] = im["D"]
+    times = []
+    for k in range(args.warmup + args.steps):
+        dt, px, thr = oracle_sample(sc, cams, tg_full, crop)
+        if k >= args.warmup:
+            times.append(dt)
+    val = px * len(times) / sum(times) / 1e6
+    sample = f"{crop[0]}x{crop[1]} crop of view 0 with all {sc.n} Gaussians projected, FP64 oracle step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": thr, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

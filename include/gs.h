@@ -1,0 +1,216 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) differentiable 3D-Gaussian-splatting mapping step.
+ *
+ * The step is the global Gaussian-map optimisation of RMGS-SLAM (arXiv 2604.12942, §III-C):
+ * Gaussians + keyframe poses/intrinsics + target images -> rendered colour and depth, an
+ * L1 photometric + depth loss, its gradients (to every Gaussian parameter and to each
+ * keyframe's SE(3) pose) and a masked Adam update of the "visible and unfrozen" Gaussians.
+ *
+ * Conventions shared by every entry point
+ *   - All tensor arguments are DEVICE pointers unless stated otherwise; the caller owns and
+ *     allocates every buffer, including the workspace sized by gs_workspace_size().  The
+ *     library never allocates device memory and never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Every call
+ *     is asynchronous on that stream; host-side argument errors are returned synchronously,
+ *     device-side conditions (pair-capacity overflow, timeouts) are written to the status
+ *     word of the workspace and read with gs_read_counters() after the stream is synced.
+ *   - Camera arrays (gs_camera*, n_views = L->n_views entries) are HOST memory.  Their poses
+ *     and intrinsics are copied into the workspace by each call (a by-value kernel argument,
+ *     so calls can be captured in a CUDA graph); image sizes must match the layout's.
+ *   - Gaussian parameters are structure-of-arrays float32 planes, each plane contiguous
+ *     over the n Gaussians: means [3][n], log_scales [3][n], quats [4][n] (w, x, y, z,
+ *     unnormalised), opacity_logits [n], sh [3K][n] with K = (sh_degree+1)^2 and plane
+ *     k*3 + c holding SH coefficient k of colour channel c.
+ *   - Images of the n_views views are packed one after another in view order; view v starts
+ *     at pixel offset pix_off(v) = sum_{u<v} W_u H_u.  Colour is planar: channel c of view v
+ *     is the W_v*H_v plane at rgb + 3*pix_off(v) + c*W_v*H_v.  Depth, T, masks: one plane
+ *     per view at + pix_off(v).  Row-major, pixel (x, y) at y*W + x, sampled at its centre
+ *     (x + 0.5, y + 0.5).
+ *   - Functions return GS_OK or an error; gs_last_error() gives a message (thread-local).
+ *
+ * Readings of the paper's "standard differentiable Gaussian splatting" (§III-C), fixed by
+ * gs_render_opts (defaults from gs_default_opts):
+ *   alpha = min(alpha_max, o * exp(-q/2)), q = d^T Sigma'^-1 d; fragments with
+ *   alpha < alpha_min are skipped; when T * (1 - alpha) < T_min the fragment is not added
+ *   and the pixel stops.  C = sum_i c_i alpha_i T_i + T_final * bg, and depth
+ *   D = sum_i z_i alpha_i T_i with the same weights (§III-C depth equation), z_i the
+ *   camera-frame depth of the Gaussian centre.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,  /* bad pointer, size, view count, tile size, ... */
+    GS_ERR_CUDA = 2,         /* a CUDA runtime call failed (message in gs_last_error) */
+    GS_ERR_CAPACITY = 3,     /* more (tile, Gaussian) pairs than the workspace holds */
+    GS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    GS_ERR_NONFINITE = 5,    /* a non-finite value was detected */
+    GS_ERR_UNSUPPORTED = 6   /* a valid request this build does not implement */
+} gs_status;
+
+#define GS_MAX_VIEWS 32
+#define GS_MAX_SH_DEGREE 3
+
+/* Pinhole keyframe camera.  R_cw, t_cw map world to camera (row-major): p_c = R_cw p + t_cw,
+ * camera looking along +z with +x right and +y down; u = fx x/z + cx, v = fy y/z + cy. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R_cw[9];
+    float t_cw[3];
+} gs_camera;
+
+/* The Gaussian map (§III-B: one Gaussian per LiDAR point with mean, log-space scale,
+ * rotation quaternion, opacity and SH colour).  Device planes as described above. */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;      /* 0..3 */
+    float *means;           /* [3][n] */
+    float *log_scales;      /* [3][n] */
+    float *quats;           /* [4][n] */
+    float *opacity_logits;  /* [n]    */
+    float *sh;              /* [3K][n] */
+} gs_gaussians;
+
+/* Compositing constants, loss weights (§III-C total-loss equation, SSIM weight 0) and the
+ * kernel shape.  tile: 8 or 16 (pixels per tile side); chunk: Gaussians staged per
+ * shared-memory batch, one of 32, 64, 128, 256. */
+typedef struct {
+    float near_z;       /* cull if z <= near_z (default 0.2 m) */
+    float dilation;     /* added to the 2-D covariance diagonal (default 0.3 px^2) */
+    float alpha_min;    /* default 1/255 */
+    float alpha_max;    /* default 0.99 */
+    float T_min;        /* default 1e-4 */
+    float clamp_fov;    /* x/z, y/z clamp inside the EWA Jacobian, x tan(half fov) (1.3) */
+    float bg[3];        /* background colour (default black) */
+    float lambda_rgb;   /* default 1 */
+    float lambda_depth; /* default 0.1 */
+    int32_t tile;       /* default 16 */
+    int32_t chunk;      /* default 64 */
+} gs_render_opts;
+
+/* Byte offsets of the workspace regions (all 256-byte aligned) -- exposed so callers and
+ * tests can inspect intermediate state; the layout is an implementation detail otherwise. */
+typedef struct {
+    size_t views;        /* internal per-view table */
+    size_t counters;     /* gs_counters-compatible block: status, n_pairs, ... */
+    size_t loss_acc;     /* double [n_views][2] masked L1 sums, uint32 [n_views][2] counts */
+    size_t proj;         /* [n_views*n] records of 12 floats: (u, v, z, opacity),
+                            (A', B', C', radius bits), (r, g, b, 0); A', B', C' are the
+                            inverse 2-D covariance scaled so that alpha = o * 2^(A'dx^2 +
+                            B'dx dy + C'dy^2) */
+    size_t touched;      /* uint32 [n_views*n] tiles covered */
+    size_t offsets;      /* uint32 [n_views*n] exclusive scan of touched */
+    size_t scan_tmp;     /* uint32 scratch of the scan */
+    size_t keys0, keys1; /* uint64 [max_pairs] ping-pong: (global tile << 32) | bits(z) */
+    size_t vals0, vals1; /* uint32 [max_pairs] ping-pong: view * n + Gaussian index */
+    size_t sort_tmp;     /* uint32 scratch of the radix sort */
+    size_t ranges;       /* uint32 [total_tiles][2] [first, last+1) in the sorted pairs */
+    size_t T_final;      /* float [total_pixels] */
+    size_t n_contrib;    /* uint32 [total_pixels] tile-list position after the last added */
+    size_t grad2d;       /* [n_views*n] records of 12 floats (screen-space gradient sums) */
+    size_t visible;      /* uint8 [n]: 1 if the Gaussian covers a tile of any view */
+    size_t total;        /* workspace bytes */
+    int32_t sorted_buf;  /* 0 or 1: which ping-pong buffer holds the sorted pairs */
+    int32_t total_tiles;
+    int64_t total_pixels;
+    int64_t max_pairs;
+    int64_t n;           /* Gaussians the workspace was laid out for */
+    int32_t n_views;
+    int32_t tile;
+} gs_ws_layout;
+
+/* Device-side counters copied back by gs_read_counters. */
+typedef struct {
+    uint32_t status;     /* gs_status of the device work since the last reset */
+    uint32_t reserved;
+    uint64_t n_pairs;    /* (tile, Gaussian) pairs of the last gs_bin_sort */
+} gs_counters;
+
+void gs_default_opts(gs_render_opts *opts);
+const char *gs_last_error(void);
+const char *gs_version(void);
+
+/* Workspace size and layout for n Gaussians seen by n_views cameras (host array) with at
+ * most max_pairs (tile, Gaussian) pairs.  The layout is a plain host-side descriptor: the
+ * caller computes it once per (n, views, image sizes, tile, max_pairs) and passes it, with
+ * a device buffer of at least layout.total bytes (256-byte aligned), to every stage call.
+ * gs_workspace_size returns 0 on invalid arguments. */
+size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera *cams,
+                         const gs_render_opts *opts, int64_t max_pairs);
+gs_status gs_workspace_layout(int64_t n, int32_t n_views, const gs_camera *cams,
+                              const gs_render_opts *opts, int64_t max_pairs, gs_ws_layout *out);
+
+/* Copies the device counters into *out (host memory); synchronises `stream`. */
+gs_status gs_read_counters(const gs_ws_layout *L, const void *ws, gs_counters *out, void *stream);
+
+/* a1 -- EWA projection with SH colour (§III-C "standard differentiable Gaussian splatting";
+ * tile-based rasterizer of §II-A).  For every view v and Gaussian i: q = q/|q| -> R,
+ * Sigma = R S S^T R^T with S = diag(exp(log_scale)); p_c = R_cw mu + t_cw, culled if
+ * z <= near_z; Sigma' = J R_cw Sigma R_cw^T J^T + dilation*I with the perspective
+ * Jacobian J at (x/z, y/z) clamped to +-clamp_fov*(W/2)/fx (resp. H, fy); o =
+ * sigmoid(logit), culled if o < alpha_min; radius = ceil(sqrt(2 ln(o/alpha_min)
+ * lambda_max(Sigma'))); rgb = max(0, sum_k sh_k Y_k(dir) + 0.5), dir = normalize(mu -
+ * camera centre).  Writes the proj, touched and visible regions of the workspace. */
+gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, const gs_render_opts *opts,
+                     const gs_ws_layout *L, void *ws, void *stream);
+
+/* a2-a4 -- Tile binning, (tile, depth) radix sort and tile ranges (§II-A tile-based
+ * rasterizer).  A record with radius r covers tiles x in [floor((u-r)/T), floor((u+r)/T)]
+ * (same for y), clamped to the view's grid, computed in FP32 exactly as written.  Pair key
+ * = ((tile_offset(v) + ty*tiles_x + tx) << 32) | float_bits(z), value = v*n + i, emitted in
+ * ascending (v, i) then row-major tile order and sorted stably by key.  If the pairs exceed
+ * max_pairs the status word becomes GS_ERR_CAPACITY, n_pairs holds the required count and
+ * the later stages of the step do nothing. */
+gs_status gs_bin_sort(const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L,
+                      void *ws, void *stream);
+
+/* a5 -- Front-to-back compositing of colour and depth (§III-C, depth equation) with the
+ * fused L1 loss (§III-C loss equations, SSIM weight 0).  Outputs (packed per view, see
+ * above): out_rgb [3*P], out_depth [P]; out_T [P] (final transmittance) may be NULL.
+ * When target_rgb is non-NULL the loss is evaluated:
+ *   L = 1/V sum_v [ lambda_rgb/|M_v| sum_{x in M_v} ||C - C~||_1
+ *                 + lambda_depth/|M_v,D| sum_{x in M_v,D} |D - D~| ]
+ * where M_v = {mask != 0} (mask may be NULL = all ones) and M_v,D = M_v and {D~ > 0};
+ * dl_drgb [3*P] / dl_ddepth [P] receive dL/dC and dL/dD (sign(0) = 0) and loss_out (device,
+ * n_views + 1 floats) the per-view terms and their mean.  target_depth may be NULL (no
+ * depth term). */
+gs_status gs_render_fwd(const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L,
+                        void *ws, float *out_rgb, float *out_depth, float *out_T,
+                        const float *target_rgb, const float *target_depth, const uint8_t *mask,
+                        float *dl_drgb, float *dl_ddepth, float *loss_out, void *stream);
+
+/* a6-a7 -- Analytic backward of gs_render_fwd and gs_project for upstream per-pixel
+ * gradients dl_drgb [3*P], dl_ddepth [P] (dl_ddepth may be NULL).  Transmittance is
+ * recomputed back to front from the stored final T (T_i = T_{i+1} / (1 - alpha_i)); no
+ * per-fragment state is stored.  Gradients are ADDED to `grads` (same layout as g) and, if
+ * grad_twist is non-NULL, to grad_twist [n_views][6]: the derivative w.r.t. the twist
+ * xi = (rho, phi) of a left perturbation T_cw <- Exp(xi) T_cw of each view's pose. */
+gs_status gs_render_bwd(const gs_gaussians *g, const gs_camera *cams, const gs_render_opts *opts,
+                        const gs_ws_layout *L, void *ws, const float *dl_drgb,
+                        const float *dl_ddepth, gs_gaussians *grads, float *grad_twist,
+                        void *stream);
+
+/* a8 -- Fused masked Adam (§III-C: visible and unfrozen Gaussians are refined by a sparse
+ * gradient-based optimiser; only the most recent segments are updated).  Row i is updated
+ * iff (update_mask == NULL or update_mask[i]) and (visible == NULL or visible[i]);
+ * other rows keep p, m and v unchanged.  m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr_group * m_hat / (sqrt(v_hat) + eps) with bias correction by `step` (>= 1).
+ * lr[6]: means, log-scales, quats, opacity, SH DC, SH rest.  Zeroes every gradient row
+ * afterwards. */
+gs_status gs_adam_step(gs_gaussians *params, gs_gaussians *grads, gs_gaussians *m, gs_gaussians *v,
+                       const uint8_t *update_mask, const uint8_t *visible, const float lr[6],
+                       float b1, float b2, float eps, int64_t step, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -1,0 +1,11 @@
+"""GB300-native (sm_103a) differentiable 3D Gaussian splatting mapping step of RMGS-SLAM
+(arXiv 2604.12942, §III-C): EWA projection with SH colour, (tile, depth) radix sort,
+front-to-back compositing of colour and depth, L1 photometric + depth loss, analytic
+backward including keyframe SE(3) pose twists, and a masked Adam step -- hand-written CUDA
+behind the C ABI of include/gs.h, driven from PyTorch device memory and streams.
+"""
+from .core import (LR_DEFAULT, MappingStep, StepResult, Workspace, adam_step, camera_array, default_opts,
+                   gaussians_struct, n_planes, pack_plane, pack_rgb, pixel_offsets, unpack_plane, unpack_rgb)
+
+__all__ = ["LR_DEFAULT", "MappingStep", "StepResult", "Workspace", "adam_step", "camera_array", "default_opts",
+           "gaussians_struct", "n_planes", "pack_plane", "pack_rgb", "pixel_offsets", "unpack_plane", "unpack_rgb"]

@@ -1,0 +1,100 @@
+"""ctypes view of include/gs.h: the structures and the entry points of libgs.so.
+
+Argument marshalling only -- every step of the mapping step runs in the CUDA kernels of
+libgs.so.  Loading fails loudly if the library has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libgs.so")
+
+MAX_VIEWS = 32
+STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_CAPACITY", 4: "GS_ERR_TIMEOUT",
+          5: "GS_ERR_NONFINITE", 6: "GS_ERR_UNSUPPORTED"}
+
+
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("R_cw", C.c_float * 9), ("t_cw", C.c_float * 3)]
+
+
+class Gaussians(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("means", C.c_void_p), ("log_scales", C.c_void_p),
+                ("quats", C.c_void_p), ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("near_z", C.c_float), ("dilation", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
+                ("T_min", C.c_float), ("clamp_fov", C.c_float), ("bg", C.c_float * 3), ("lambda_rgb", C.c_float),
+                ("lambda_depth", C.c_float), ("tile", C.c_int32), ("chunk", C.c_int32)]
+
+
+class WsLayout(C.Structure):
+    _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "touched", "offsets", "scan_tmp",
+                                          "keys0", "keys1", "vals0", "vals1", "sort_tmp", "ranges", "T_final",
+                                          "n_contrib", "grad2d", "visible", "total")] + \
+               [("sorted_buf", C.c_int32), ("total_tiles", C.c_int32), ("total_pixels", C.c_int64),
+                ("max_pairs", C.c_int64), ("n", C.c_int64), ("n_views", C.c_int32), ("tile", C.c_int32)]
+
+
+class Counters(C.Structure):
+    _fields_ = [("status", C.c_uint32), ("reserved", C.c_uint32), ("n_pairs", C.c_uint64)]
+
+
+class GsError(RuntimeError):
+    pass
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (argtypes, restype)
+_SIGS = {
+    "gs_default_opts": ([C.POINTER(RenderOpts)], None),
+    "gs_last_error": ([], C.c_char_p),
+    "gs_version": ([], C.c_char_p),
+    "gs_workspace_size": ([C.c_int64, C.c_int32, C.POINTER(Camera), C.POINTER(RenderOpts), C.c_int64], C.c_size_t),
+    "gs_workspace_layout": ([C.c_int64, C.c_int32, C.POINTER(Camera), C.POINTER(RenderOpts), C.c_int64,
+                             C.POINTER(WsLayout)], C.c_int),
+    "gs_read_counters": ([C.POINTER(WsLayout), C.c_void_p, C.POINTER(Counters), C.c_void_p], C.c_int),
+    "gs_project": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p,
+                    C.c_void_p], C.c_int),
+    "gs_bin_sort": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.c_void_p], C.c_int),
+    "gs_render_fwd": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p] + [C.c_void_p] * 3 +
+                      [C.c_void_p] * 3 + [C.c_void_p] * 3 + [C.c_void_p], C.c_int),
+    "gs_render_bwd": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p,
+                       C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p], C.c_int),
+    "gs_adam_step": ([C.POINTER(Gaussians)] * 4 + [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.c_float, C.c_float,
+                                                   C.c_float, C.c_int64, C.c_void_p], C.c_int),
+}
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def lib(path: str | None = None):
+    """The loaded libgs.so.  Raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise GsError(f"libgs.so not built ({p}); run __graft_entry__.build() -- there is no CPU fallback")
+            L = C.CDLL(p)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str = ""):
+    if status != 0:
+        msg = lib().gs_last_error().decode(errors="replace")
+        raise GsError(f"{what}: {STATUS.get(status, status)}: {msg}")

@@ -1,0 +1,217 @@
+"""Python binding of libgs.so (include/gs.h) over PyTorch device memory and streams.
+
+Marshalling only: tensors become device pointers, camera dicts become gs_camera structs,
+and each method calls one C entry point on the current CUDA stream.  The mapping step of
+RMGS-SLAM §III-C (projection, tile sort, compositing of colour and depth, L1 loss, analytic
+backward incl. pose twists, masked Adam) runs entirely in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+PARAM_GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def n_planes(sh_degree: int) -> int:
+    return 11 + 3 * (sh_degree + 1) ** 2
+
+
+def default_opts(**kw) -> N.RenderOpts:
+    o = N.RenderOpts()
+    N.lib().gs_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "bg":
+            o.bg = (C.c_float * 3)(*v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def camera_array(cams) -> C.Array:
+    arr = (N.Camera * len(cams))()
+    for c, d in zip(arr, cams):
+        c.width, c.height = int(d["width"]), int(d["height"])
+        c.fx, c.fy, c.cx, c.cy = float(d["fx"]), float(d["fy"]), float(d["cx"]), float(d["cy"])
+        c.R_cw = (C.c_float * 9)(*np.asarray(d["R"], dtype=np.float64).reshape(-1).tolist())
+        c.t_cw = (C.c_float * 3)(*np.asarray(d["t"], dtype=np.float64).reshape(-1).tolist())
+    return arr
+
+
+def gaussians_struct(planes: torch.Tensor, sh_degree: int) -> N.Gaussians:
+    """gs_gaussians pointing into a packed [11 + 3K, n] float32 CUDA tensor."""
+    assert planes.is_cuda and planes.dtype == torch.float32 and planes.is_contiguous()
+    P, n = planes.shape
+    assert P == n_planes(sh_degree), (P, sh_degree)
+    base = planes.data_ptr()
+    row = 4 * n
+    return N.Gaussians(n, sh_degree, base, base + 3 * row, base + 6 * row, base + 10 * row, base + 11 * row)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def pixel_offsets(cams):
+    off = [0]
+    for c in cams:
+        off.append(off[-1] + int(c["width"]) * int(c["height"]))
+    return off
+
+
+def pack_rgb(images, device="cuda") -> torch.Tensor:
+    """Per-view [3, H, W] arrays -> the packed planar colour buffer of gs.h."""
+    return torch.cat([torch.as_tensor(np.ascontiguousarray(im), dtype=torch.float32).reshape(-1)
+                      for im in images]).to(device)
+
+
+def pack_plane(planes, dtype=torch.float32, device="cuda") -> torch.Tensor:
+    return torch.cat([torch.as_tensor(np.ascontiguousarray(p)).to(dtype).reshape(-1) for p in planes]).to(device)
+
+
+def unpack_rgb(buf: torch.Tensor, cams):
+    off = pixel_offsets(cams)
+    return [buf[3 * off[v]:3 * off[v + 1]].reshape(3, c["height"], c["width"]) for v, c in enumerate(cams)]
+
+
+def unpack_plane(buf: torch.Tensor, cams):
+    off = pixel_offsets(cams)
+    return [buf[off[v]:off[v + 1]].reshape(c["height"], c["width"]) for v, c in enumerate(cams)]
+
+
+class Workspace:
+    """A device workspace laid out for (n Gaussians, these cameras' image sizes, tile,
+    max_pairs) plus the host-side gs_ws_layout descriptor."""
+
+    def __init__(self, n, cams, opts: N.RenderOpts, max_pairs, device="cuda"):
+        self.cams_c = camera_array(cams)
+        self.cams = cams
+        self.opts = opts
+        self.layout = N.WsLayout()
+        N.check(N.lib().gs_workspace_layout(int(n), len(cams), self.cams_c, C.byref(opts), int(max_pairs),
+                                            C.byref(self.layout)), "gs_workspace_layout")
+        self.buf = torch.empty(int(self.layout.total), dtype=torch.uint8, device=device)
+        assert self.buf.data_ptr() % 256 == 0
+        self.n = int(n)
+        self.V = len(cams)
+
+    def set_cameras(self, cams):
+        """New poses (same image sizes) for the next calls."""
+        self.cams_c = camera_array(cams)
+        self.cams = cams
+
+    def region(self, name, dtype, count):
+        off = getattr(self.layout, name)
+        nbytes = count * torch.empty((), dtype=dtype).element_size()
+        return self.buf[off:off + nbytes].view(dtype)
+
+    # -- stage calls -----------------------------------------------------------------------
+    def project(self, planes, sh_degree):
+        g = gaussians_struct(planes, sh_degree)
+        N.check(N.lib().gs_project(C.byref(g), self.cams_c, C.byref(self.opts), C.byref(self.layout),
+                                   _ptr(self.buf), _stream()), "gs_project")
+
+    def bin_sort(self):
+        N.check(N.lib().gs_bin_sort(self.cams_c, C.byref(self.opts), C.byref(self.layout), _ptr(self.buf), _stream()),
+                "gs_bin_sort")
+
+    def render_fwd(self, out_rgb, out_depth, out_T=None, target_rgb=None, target_depth=None, mask=None,
+                   dl_drgb=None, dl_ddepth=None, loss_out=None):
+        N.check(N.lib().gs_render_fwd(self.cams_c, C.byref(self.opts), C.byref(self.layout), _ptr(self.buf),
+                                      _ptr(out_rgb), _ptr(out_depth), _ptr(out_T), _ptr(target_rgb),
+                                      _ptr(target_depth), _ptr(mask), _ptr(dl_drgb), _ptr(dl_ddepth),
+                                      _ptr(loss_out), _stream()), "gs_render_fwd")
+
+    def render_bwd(self, planes, sh_degree, grad_planes, dl_drgb, dl_ddepth=None, grad_twist=None):
+        g = gaussians_struct(planes, sh_degree)
+        gg = gaussians_struct(grad_planes, sh_degree)
+        N.check(N.lib().gs_render_bwd(C.byref(g), self.cams_c, C.byref(self.opts), C.byref(self.layout),
+                                      _ptr(self.buf), _ptr(dl_drgb), _ptr(dl_ddepth), C.byref(gg),
+                                      _ptr(grad_twist), _stream()), "gs_render_bwd")
+
+    def counters(self) -> N.Counters:
+        c = N.Counters()
+        N.check(N.lib().gs_read_counters(C.byref(self.layout), _ptr(self.buf), C.byref(c), _stream()),
+                "gs_read_counters")
+        return c
+
+    # -- views of intermediate state (for tests) ------------------------------------------
+    def sorted_pairs(self, n_pairs):
+        L = self.layout
+        kname, vname = ("keys1", "vals1") if L.sorted_buf else ("keys0", "vals0")
+        return self.region(kname, torch.int64, n_pairs), self.region(vname, torch.int32, n_pairs)
+
+    def visible(self):
+        return self.region("visible", torch.uint8, self.n)
+
+
+def adam_step(planes, grads, m, v, sh_degree, step, lr, update_mask=None, visible=None, b1=0.9, b2=0.999,
+              eps=1e-15):
+    gp, gg, gm, gv = (gaussians_struct(t, sh_degree) for t in (planes, grads, m, v))
+    lrs = (C.c_float * 6)(*lr)
+    N.check(N.lib().gs_adam_step(C.byref(gp), C.byref(gg), C.byref(gm), C.byref(gv), _ptr(update_mask),
+                                 _ptr(visible), lrs, b1, b2, eps, int(step), _stream()), "gs_adam_step")
+
+
+LR_DEFAULT = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 1.25e-4)
+
+
+@dataclass
+class StepResult:
+    loss: torch.Tensor          # [V + 1] device: per-view terms and their mean
+    rgb: torch.Tensor
+    depth: torch.Tensor
+    n_pairs: int | None = None
+
+
+class MappingStep:
+    """One optimisation step of the Gaussian map over a batch of keyframes: project, tile
+    sort, composite with the fused L1 loss, backward (with pose twists) and masked Adam --
+    each stage one C call, all views of the batch in each launch."""
+
+    def __init__(self, planes: torch.Tensor, sh_degree: int, cams, opts: N.RenderOpts | None = None,
+                 max_pairs: int | None = None, lr=LR_DEFAULT):
+        self.planes = planes
+        self.sh_degree = sh_degree
+        self.opts = opts or default_opts()
+        n = planes.shape[1]
+        self.ws = Workspace(n, cams, self.opts, max_pairs or max(1 << 20, 64 * n * len(cams)), planes.device)
+        P = self.ws.layout.total_pixels
+        dev = planes.device
+        self.grads = torch.zeros_like(planes)
+        self.m = torch.zeros_like(planes)
+        self.v = torch.zeros_like(planes)
+        self.rgb = torch.empty(3 * P, device=dev)
+        self.depth = torch.empty(P, device=dev)
+        self.dl_drgb = torch.empty(3 * P, device=dev)
+        self.dl_ddepth = torch.empty(P, device=dev)
+        self.loss = torch.zeros(len(cams) + 1, device=dev)
+        self.twist = torch.zeros(len(cams), 6, device=dev)
+        self.lr = lr
+        self.t = 0
+
+    def __call__(self, target_rgb, target_depth=None, mask=None, update_mask=None, optimize=True,
+                 with_twist=False) -> StepResult:
+        ws = self.ws
+        ws.project(self.planes, self.sh_degree)
+        ws.bin_sort()
+        ws.render_fwd(self.rgb, self.depth, None, target_rgb, target_depth, mask, self.dl_drgb,
+                      self.dl_ddepth if target_depth is not None else None, self.loss)
+        if with_twist:
+            self.twist.zero_()
+        ws.render_bwd(self.planes, self.sh_degree, self.grads, self.dl_drgb,
+                      self.dl_ddepth if target_depth is not None else None, self.twist if with_twist else None)
+        if optimize:
+            self.t += 1
+            adam_step(self.planes, self.grads, self.m, self.v, self.sh_degree, self.t, self.lr, update_mask,
+                      ws.visible())
+        return StepResult(self.loss, self.rgb, self.depth)

@@ -1,0 +1,451 @@
+// extern "C" entry points declared in include/gs.h: argument checks, workspace layout and
+// the launch sequence of each stage.  Host code only; all arithmetic of the step runs in
+// the kernels of project.cu, binsort.cu, render.cu and adam.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+static thread_local std::string g_err;
+
+static gs_status fail(gs_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define GS_CUDA(call)                                                                           \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(GS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Geometry {
+    int total_tiles = 0;
+    int64_t total_pixels = 0;
+    View views[GS_MAX_VIEWS];
+    int64_t pix[GS_MAX_VIEWS];
+};
+
+static gs_status check_opts(const gs_render_opts* o) {
+    if (!o) return fail(GS_ERR_INVALID_ARG, "opts is NULL");
+    if (o->tile != 8 && o->tile != 16) return fail(GS_ERR_INVALID_ARG, "tile must be 8 or 16 (got %d)", o->tile);
+    if (o->chunk != 32 && o->chunk != 64 && o->chunk != 128 && o->chunk != 256)
+        return fail(GS_ERR_INVALID_ARG, "chunk must be 32, 64, 128 or 256 (got %d)", o->chunk);
+    if (!(o->alpha_min > 0.f) || !(o->alpha_max <= 1.f) || !(o->alpha_min < o->alpha_max))
+        return fail(GS_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max <= 1");
+    if (!(o->T_min >= 0.f) || !(o->near_z >= 0.f) || !(o->dilation >= 0.f) || !(o->clamp_fov > 0.f))
+        return fail(GS_ERR_INVALID_ARG, "invalid compositing constants");
+    return GS_OK;
+}
+
+static gs_status make_geometry(int32_t n_views, const gs_camera* cams, const gs_render_opts* o, Geometry& G) {
+    if (n_views < 1 || n_views > GS_MAX_VIEWS)
+        return fail(GS_ERR_INVALID_ARG, "n_views must be in [1, %d] (got %d)", GS_MAX_VIEWS, n_views);
+    if (!cams) return fail(GS_ERR_INVALID_ARG, "cams is NULL");
+    gs_status s = check_opts(o);
+    if (s != GS_OK) return s;
+    int64_t toff = 0, poff = 0;
+    for (int v = 0; v < n_views; v++) {
+        const gs_camera& c = cams[v];
+        if (c.width <= 0 || c.height <= 0 || c.width > 16384 || c.height > 16384)
+            return fail(GS_ERR_INVALID_ARG, "view %d: bad size %dx%d", v, c.width, c.height);
+        if (!(c.fx > 0.f) || !(c.fy > 0.f)) return fail(GS_ERR_INVALID_ARG, "view %d: focal lengths must be > 0", v);
+        View& V = G.views[v];
+        memset(&V, 0, sizeof(V));
+        V.W = c.width;
+        V.H = c.height;
+        V.tiles_x = (c.width + o->tile - 1) / o->tile;
+        V.tiles_y = (c.height + o->tile - 1) / o->tile;
+        V.n_tiles = V.tiles_x * V.tiles_y;
+        V.tile_off = (int32_t)toff;
+        V.pix_off = poff;
+        V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy;
+        memcpy(V.R, c.R_cw, sizeof(V.R));
+        memcpy(V.t, c.t_cw, sizeof(V.t));
+        for (int i = 0; i < 3; i++)
+            V.cw[i] = -(c.R_cw[0 * 3 + i] * c.t_cw[0] + c.R_cw[1 * 3 + i] * c.t_cw[1] + c.R_cw[2 * 3 + i] * c.t_cw[2]);
+        V.limx = o->clamp_fov * (0.5f * (float)c.width) / c.fx;
+        V.limy = o->clamp_fov * (0.5f * (float)c.height) / c.fy;
+        G.pix[v] = (int64_t)c.width * c.height;
+        toff += V.n_tiles;
+        poff += G.pix[v];
+    }
+    if (toff > (int64_t)1 << 30) return fail(GS_ERR_INVALID_ARG, "too many tiles");
+    G.total_tiles = (int)toff;
+    G.total_pixels = poff;
+    return GS_OK;
+}
+
+static int tile_bits(int total_tiles) {
+    int b = 0;
+    while (b < 31 && ((int64_t)1 << b) < total_tiles) b++;
+    return b;
+}
+
+static int sort_passes(int total_tiles, int* shifts) {
+    int np = 0;
+    for (int s = 0; s < 32; s += 8) shifts[np++] = s;
+    const int tb = tile_bits(total_tiles);
+    for (int s = 0; s < tb; s += 8) shifts[np++] = 32 + s;
+    return np;
+}
+
+static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const gs_render_opts* o, int64_t max_pairs,
+                        gs_ws_layout& L, Geometry& G) {
+    if (n < 0) return fail(GS_ERR_INVALID_ARG, "n must be >= 0");
+    if (max_pairs < 0 || max_pairs > (int64_t)0xFFFFFFFFll) return fail(GS_ERR_INVALID_ARG, "max_pairs out of range");
+    gs_status s = make_geometry(n_views, cams, o, G);
+    if (s != GS_OK) return s;
+    const int64_t VN = (int64_t)n_views * n;
+    if (VN >= (int64_t)0xFFFFFFFFll) return fail(GS_ERR_INVALID_ARG, "n_views * n must be < 2^32");
+    memset(&L, 0, sizeof(L));
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t r = off; off = align256(off + bytes); return r; };
+    L.views = take(sizeof(View) * GS_MAX_VIEWS);
+    L.counters = take(sizeof(Counters));
+    L.loss_acc = take(sizeof(double) * 2 * GS_MAX_VIEWS + sizeof(uint32_t) * 2 * GS_MAX_VIEWS);
+    L.proj = take(sizeof(float) * 12 * (size_t)VN);
+    L.touched = take(sizeof(uint32_t) * (size_t)VN);
+    L.offsets = take(sizeof(uint32_t) * (size_t)VN);
+    L.scan_tmp = take(sizeof(uint32_t) * ((size_t)VN / kScanBlock + 2));
+    L.keys0 = take(sizeof(unsigned long long) * (size_t)max_pairs);
+    L.keys1 = take(sizeof(unsigned long long) * (size_t)max_pairs);
+    L.vals0 = take(sizeof(uint32_t) * (size_t)max_pairs);
+    L.vals1 = take(sizeof(uint32_t) * (size_t)max_pairs);
+    L.sort_tmp = take(sizeof(uint32_t) * ((size_t)kSortBins * 4096 + kSortBins));
+    L.ranges = take(sizeof(uint32_t) * 2 * (size_t)G.total_tiles);
+    L.T_final = take(sizeof(float) * (size_t)G.total_pixels);
+    L.n_contrib = take(sizeof(uint32_t) * (size_t)G.total_pixels);
+    L.grad2d = take(sizeof(float) * 12 * (size_t)VN);
+    L.visible = take((size_t)n);
+    L.total = off;
+    int shifts[16];
+    L.sorted_buf = sort_passes(G.total_tiles, shifts) & 1;
+    L.total_tiles = G.total_tiles;
+    L.total_pixels = G.total_pixels;
+    L.max_pairs = max_pairs;
+    L.n = n;
+    L.n_views = n_views;
+    L.tile = o->tile;
+    return GS_OK;
+}
+
+template <typename T>
+static T* at(void* ws, size_t off) { return reinterpret_cast<T*>(reinterpret_cast<char*>(ws) + off); }
+
+static Opts to_opts(const gs_render_opts* o) {
+    Opts r;
+    r.near_z = o->near_z; r.dilation = o->dilation; r.alpha_min = o->alpha_min; r.alpha_max = o->alpha_max;
+    r.T_min = o->T_min; r.clamp_fov = o->clamp_fov;
+    r.bg0 = o->bg[0]; r.bg1 = o->bg[1]; r.bg2 = o->bg[2];
+    r.lambda_rgb = o->lambda_rgb; r.lambda_depth = o->lambda_depth;
+    r.tile = o->tile; r.chunk = o->chunk;
+    return r;
+}
+
+struct ViewsParam {
+    int n;
+    View v[GS_MAX_VIEWS];
+};
+
+__global__ void setup_views_kernel(View* dst, const __grid_constant__ ViewsParam p) {
+    for (int i = threadIdx.x; i < p.n; i += blockDim.x) dst[i] = p.v[i];
+}
+
+static gs_status upload_views(void* ws, const gs_ws_layout& L, const Geometry& G, int n_views, cudaStream_t st) {
+    ViewsParam p;
+    memset(&p, 0, sizeof(p));
+    p.n = n_views;
+    memcpy(p.v, G.views, sizeof(View) * n_views);
+    setup_views_kernel<<<1, 32, 0, st>>>(at<View>(ws, L.views), p);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+static gs_status check_ws(const void* ws, const gs_ws_layout* L) {
+    if (!L) return fail(GS_ERR_INVALID_ARG, "layout is NULL");
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return fail(GS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return GS_OK;
+}
+
+static gs_status check_gaussians(const gs_gaussians* g, bool need) {
+    if (!g) return fail(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0) return fail(GS_ERR_INVALID_ARG, "n must be >= 0");
+    if (g->sh_degree < 0 || g->sh_degree > GS_MAX_SH_DEGREE) return fail(GS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (need && g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return fail(GS_ERR_INVALID_ARG, "a parameter plane pointer is NULL");
+    return GS_OK;
+}
+
+// Geometry of the cameras, checked against the layout the workspace was made for.
+static gs_status geometry_for(const gs_ws_layout* L, const gs_camera* cams, const gs_render_opts* opts, Geometry& G) {
+    gs_status s = make_geometry(L->n_views, cams, opts, G);
+    if (s != GS_OK) return s;
+    if (G.total_tiles != L->total_tiles || G.total_pixels != L->total_pixels || opts->tile != L->tile)
+        return fail(GS_ERR_INVALID_ARG, "cameras / tile size do not match the workspace layout");
+    return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+const char* gs_last_error(void) { return g_err.c_str(); }
+const char* gs_version(void) { return "gs-gb300 0.1 (sm_103a)"; }
+
+void gs_default_opts(gs_render_opts* o) {
+    if (!o) return;
+    o->near_z = 0.2f;
+    o->dilation = 0.3f;
+    o->alpha_min = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->T_min = 1e-4f;
+    o->clamp_fov = 1.3f;
+    o->bg[0] = o->bg[1] = o->bg[2] = 0.f;
+    o->lambda_rgb = 1.0f;
+    o->lambda_depth = 0.1f;
+    o->tile = 16;
+    o->chunk = 64;
+}
+
+size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams, const gs_render_opts* opts,
+                         int64_t max_pairs) {
+    gs_ws_layout L;
+    Geometry G;
+    if (layout(n, n_views, cams, opts, max_pairs, L, G) != GS_OK) return 0;
+    return L.total;
+}
+
+gs_status gs_workspace_layout(int64_t n, int32_t n_views, const gs_camera* cams, const gs_render_opts* opts,
+                              int64_t max_pairs, gs_ws_layout* out) {
+    if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
+    Geometry G;
+    return layout(n, n_views, cams, opts, max_pairs, *out, G);
+}
+
+gs_status gs_read_counters(const gs_ws_layout* L, const void* ws, gs_counters* out, void* stream) {
+    if (!ws || !out || !L) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    Counters c;
+    GS_CUDA(cudaMemcpyAsync(&c, at<Counters>(const_cast<void*>(ws), L->counters), sizeof(c), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    out->status = c.status;
+    out->reserved = 0;
+    out->n_pairs = c.n_pairs;
+    return GS_OK;
+}
+
+gs_status gs_project(const gs_gaussians* g, const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L,
+                     void* ws, void* stream) {
+    gs_status s = check_gaussians(g, true);
+    if (s != GS_OK) return s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    if (g->n != L->n) return fail(GS_ERR_INVALID_ARG, "n = %lld does not match the layout (%lld)", (long long)g->n, (long long)L->n);
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    GS_CUDA(cudaMemsetAsync(at<Counters>(ws, L->counters), 0, sizeof(Counters), st));
+    ProjectArgs a;
+    a.n = g->n;
+    a.n_views = L->n_views;
+    a.views = at<View>(ws, L->views);
+    a.op = to_opts(opts);
+    a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats; a.logits = g->opacity_logits; a.sh = g->sh;
+    a.proj = at<float4>(ws, L->proj);
+    a.touched = at<uint32_t>(ws, L->touched);
+    a.visible = at<uint8_t>(ws, L->visible);
+    GS_CUDA(launch_project(a, g->sh_degree, st));
+    return GS_OK;
+}
+
+gs_status gs_bin_sort(const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L, void* ws, void* stream) {
+    gs_status s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    Counters* cnt = at<Counters>(ws, L->counters);
+    BinArgs b;
+    b.n = L->n;
+    b.n_views = L->n_views;
+    b.views = at<View>(ws, L->views);
+    b.tile = opts->tile;
+    b.max_pairs = L->max_pairs;
+    b.proj = at<float4>(ws, L->proj);
+    b.touched = at<uint32_t>(ws, L->touched);
+    b.offsets = at<uint32_t>(ws, L->offsets);
+    b.scan_tmp = at<uint32_t>(ws, L->scan_tmp);
+    b.keys = at<unsigned long long>(ws, L->keys0);
+    b.vals = at<uint32_t>(ws, L->vals0);
+    b.counters = cnt;
+    GS_CUDA(launch_bin(b, st));
+    SortArgs sa;
+    sa.keys[0] = at<unsigned long long>(ws, L->keys0);
+    sa.keys[1] = at<unsigned long long>(ws, L->keys1);
+    sa.vals[0] = at<uint32_t>(ws, L->vals0);
+    sa.vals[1] = at<uint32_t>(ws, L->vals1);
+    sa.grid = sort_grid();
+    if (sa.grid > 4096) sa.grid = 4096;
+    sa.hist = at<uint32_t>(ws, L->sort_tmp);
+    sa.digit_tot = sa.hist + (size_t)kSortBins * 4096;
+    sa.counters = cnt;
+    int shifts[16];
+    const int np = sort_passes(G.total_tiles, shifts);
+    GS_CUDA(launch_sort(sa, np, shifts, st));
+    GS_CUDA(cudaMemsetAsync(at<uint32_t>(ws, L->ranges), 0, sizeof(uint32_t) * 2 * (size_t)G.total_tiles, st));
+    RangeArgs r;
+    r.keys = sa.keys[np & 1];
+    r.ranges = at<uint2>(ws, L->ranges);
+    r.counters = cnt;
+    GS_CUDA(launch_ranges(r, G.total_tiles, st));
+    return GS_OK;
+}
+
+gs_status gs_render_fwd(const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                        float* out_rgb, float* out_depth, float* out_T, const float* target_rgb,
+                        const float* target_depth, const uint8_t* mask, float* dl_drgb, float* dl_ddepth,
+                        float* loss_out, void* stream) {
+    gs_status s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    if (!out_rgb || !out_depth) return fail(GS_ERR_INVALID_ARG, "out_rgb and out_depth are required");
+    if (target_rgb && (!dl_drgb || !loss_out)) return fail(GS_ERR_INVALID_ARG, "the loss needs dl_drgb and loss_out");
+    if (target_depth && !target_rgb) return fail(GS_ERR_INVALID_ARG, "target_depth needs target_rgb");
+    if (target_depth && !dl_ddepth) return fail(GS_ERR_INVALID_ARG, "the depth loss needs dl_ddepth");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    double* sums = at<double>(ws, L->loss_acc);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(sums + 2 * GS_MAX_VIEWS);
+    if (target_rgb) {
+        GS_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 2 * GS_MAX_VIEWS + sizeof(uint32_t) * 2 * GS_MAX_VIEWS, st));
+        GS_CUDA(launch_loss_count(at<View>(ws, L->views), L->n_views, G.pix, target_depth, mask, counts, st));
+    }
+    FwdArgs a;
+    a.n_views = L->n_views;
+    a.views = at<View>(ws, L->views);
+    a.op = to_opts(opts);
+    a.proj = at<float4>(ws, L->proj);
+    a.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
+    a.ranges = at<uint2>(ws, L->ranges);
+    a.counters = at<Counters>(ws, L->counters);
+    a.T_final = at<float>(ws, L->T_final);
+    a.n_contrib = at<uint32_t>(ws, L->n_contrib);
+    a.out_rgb = out_rgb;
+    a.out_depth = out_depth;
+    a.out_T = out_T;
+    a.tgt_rgb = target_rgb;
+    a.tgt_depth = target_depth;
+    a.mask = mask;
+    a.dl_drgb = target_rgb ? dl_drgb : nullptr;
+    a.dl_ddepth = target_rgb ? dl_ddepth : nullptr;
+    a.loss_sums = sums;
+    a.loss_counts = counts;
+    GS_CUDA(launch_render_fwd(a, G.total_tiles, st));
+    if (target_rgb)
+        GS_CUDA(launch_loss_finalize(sums, counts, L->n_views, opts->lambda_rgb, opts->lambda_depth,
+                                     target_depth != nullptr, loss_out, st));
+    return GS_OK;
+}
+
+gs_status gs_render_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L,
+                        void* ws, const float* dl_drgb, const float* dl_ddepth, gs_gaussians* grads, float* grad_twist,
+                        void* stream) {
+    gs_status s = check_gaussians(g, true);
+    if (s != GS_OK) return s;
+    if ((s = check_gaussians(grads, true)) != GS_OK) return s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    if (g->n != L->n || grads->n != L->n || grads->sh_degree != g->sh_degree)
+        return fail(GS_ERR_INVALID_ARG, "gaussians / grads do not match the layout");
+    if (!dl_drgb) return fail(GS_ERR_INVALID_ARG, "dl_drgb is required");
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    const int64_t VN = (int64_t)L->n_views * L->n;
+    GS_CUDA(cudaMemsetAsync(at<float>(ws, L->grad2d), 0, sizeof(float) * 12 * (size_t)VN, st));
+    BwdArgs b;
+    b.n_views = L->n_views;
+    b.views = at<View>(ws, L->views);
+    b.op = to_opts(opts);
+    b.proj = at<float4>(ws, L->proj);
+    b.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
+    b.ranges = at<uint2>(ws, L->ranges);
+    b.counters = at<Counters>(ws, L->counters);
+    b.T_final = at<float>(ws, L->T_final);
+    b.n_contrib = at<uint32_t>(ws, L->n_contrib);
+    b.dl_drgb = dl_drgb;
+    b.dl_ddepth = dl_ddepth;
+    b.grad2d = at<float4>(ws, L->grad2d);
+    GS_CUDA(launch_render_bwd(b, G.total_tiles, st));
+    ProjectBwdArgs p;
+    p.n = L->n;
+    p.n_views = L->n_views;
+    p.views = at<View>(ws, L->views);
+    p.op = to_opts(opts);
+    p.means = g->means; p.log_scales = g->log_scales; p.quats = g->quats; p.logits = g->opacity_logits; p.sh = g->sh;
+    p.touched = at<uint32_t>(ws, L->touched);
+    p.grad2d = at<float4>(ws, L->grad2d);
+    p.g_means = grads->means; p.g_log_scales = grads->log_scales; p.g_quats = grads->quats;
+    p.g_logits = grads->opacity_logits; p.g_sh = grads->sh;
+    p.grad_twist = grad_twist;
+    GS_CUDA(launch_project_bwd(p, g->sh_degree, st));
+    return GS_OK;
+}
+
+gs_status gs_adam_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
+                       const uint8_t* update_mask, const uint8_t* visible, const float lr[6], float b1, float b2,
+                       float eps, int64_t step, void* stream) {
+    gs_status s;
+    gs_gaussians* all[4] = {params, grads, m, v};
+    for (auto* x : all)
+        if ((s = check_gaussians(x, true)) != GS_OK) return s;
+    for (auto* x : all)
+        if (x->n != params->n || x->sh_degree != params->sh_degree)
+            return fail(GS_ERR_INVALID_ARG, "params / grads / m / v differ in n or sh_degree");
+    if (!lr) return fail(GS_ERR_INVALID_ARG, "lr is NULL");
+    if (step < 1) return fail(GS_ERR_INVALID_ARG, "step must be >= 1");
+    if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps >= 0.f))
+        return fail(GS_ERR_INVALID_ARG, "need 0 <= b1, b2 < 1 and eps >= 0");
+    const int K = (params->sh_degree + 1) * (params->sh_degree + 1);
+    AdamArgs a;
+    a.n = params->n;
+    a.n_planes = 11 + 3 * K;
+    gs_gaussians* src[4] = {params, grads, m, v};
+    float** dst[4] = {a.p, a.g, a.m, a.v};
+    for (int k = 0; k < 4; k++) {
+        dst[k][0] = src[k]->means;
+        dst[k][1] = src[k]->log_scales;
+        dst[k][2] = src[k]->quats;
+        dst[k][3] = src[k]->opacity_logits;
+        dst[k][4] = src[k]->sh;
+    }
+    a.planes_of[0] = 3; a.planes_of[1] = 3; a.planes_of[2] = 4; a.planes_of[3] = 1; a.planes_of[4] = 3 * K;
+    a.update_mask = update_mask;
+    a.visible = visible;
+    for (int k = 0; k < 6; k++) a.lr[k] = lr[k];
+    a.b1 = b1; a.b2 = b2; a.eps = eps;
+    a.bc1 = (float)(1.0 - pow((double)b1, (double)step));
+    a.bc2 = (float)(1.0 - pow((double)b2, (double)step));
+    GS_CUDA(launch_adam(a, (cudaStream_t)stream));
+    return GS_OK;
+}
+
+}  // extern "C"

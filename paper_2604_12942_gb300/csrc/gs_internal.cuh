@@ -1,0 +1,281 @@
+// Internal device-side definitions of the sm_103a 3DGS mapping-step library.
+// The math here follows §III-C of RMGS-SLAM (standard differentiable Gaussian splatting,
+// depth composited with the colour weights) under the readings documented in gs.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr float kLn2 = 0.69314718055994530942f;
+constexpr float kLog2e = 1.44269504088896340736f;
+constexpr int kSortBins = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;                     // per thread per chunk
+constexpr int kSortChunk = kSortThreads * kSortItems;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+// Per-view table held in the workspace.
+struct View {
+    int32_t W, H, tiles_x, tiles_y;
+    int32_t tile_off, n_tiles;
+    int64_t pix_off;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float cw[3];          // camera centre -R^T t
+    float limx, limy;     // clamp of x/z, y/z in the Jacobian
+};
+
+struct Counters {
+    uint32_t status;
+    uint32_t reserved;
+    unsigned long long n_pairs;
+    uint32_t n_chunks;    // radix-sort chunk count (device-computed)
+    uint32_t pad[3];
+};
+
+struct Opts {
+    float near_z, dilation, alpha_min, alpha_max, T_min, clamp_fov;
+    float bg0, bg1, bg2;
+    float lambda_rgb, lambda_depth;
+    int tile, chunk;
+};
+
+__device__ __forceinline__ void set_status(Counters* c, uint32_t s) { atomicCAS(&c->status, 0u, s); }
+
+// ---------------------------------------------------------------------------------------
+// Compositing exponent: alpha = o * 2^e with e = A' dx^2 + C' dy^2 + B' dx dy, where
+// (A', B', C') = -log2(e) * (A/2, B, C/2) for the inverse covariance [[A, B], [B, C]].
+// The forward and the backward kernels call exactly this sequence of correctly rounded
+// operations, so both take the same skip / stop decisions.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float frag_exponent(float dx, float dy, float A, float B, float C) {
+    float e = __fmul_rn(__fmul_rn(A, dx), dx);
+    e = __fmaf_rn(__fmul_rn(C, dy), dy, e);
+    e = __fmaf_rn(__fmul_rn(B, dx), dy, e);
+    return e;
+}
+
+// 2^x by the hardware ex2 instruction (flush-to-zero for tiny results).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Tiles covered along one axis by centre c and integer radius r: [floor((c-r)/T),
+// floor((c+r)/T)] clamped to [0, n-1]; false if empty.  FP32, correctly rounded, as gs.h
+// defines it.
+__device__ __forceinline__ bool tile_span(float c, int r, int tile, int n, int& lo, int& hi) {
+    const float rf = (float)r;
+    const float tf = (float)tile;
+    float a = floorf(__fdiv_rn(__fsub_rn(c, rf), tf));
+    float b = floorf(__fdiv_rn(__fadd_rn(c, rf), tf));
+    if (!(b >= 0.0f) || !(a <= (float)(n - 1))) return false;
+    a = fmaxf(a, 0.0f);
+    b = fminf(b, (float)(n - 1));
+    lo = (int)a;
+    hi = (int)b;
+    return hi >= lo;
+}
+
+// ---------------------------------------------------------------------------------------
+// Real spherical harmonics, degree <= 3 (orthonormal, Condon-Shortley phase).
+// ---------------------------------------------------------------------------------------
+constexpr float SH0 = 0.28209479177387814f;
+constexpr float SH1 = 0.48860251190291992f;
+constexpr float SH2a = 1.09254843059207907f;
+constexpr float SH2b = 0.31539156525252005f;
+constexpr float SH2c = 0.54627421529603959f;
+constexpr float SH3a = 0.59004358992664352f;
+constexpr float SH3b = 2.89061144264055405f;
+constexpr float SH3c = 0.45704579946446573f;
+constexpr float SH3d = 0.37317633259011540f;
+constexpr float SH3e = 1.44530572132027702f;
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = SH0;
+    if (DEG >= 1) {
+        Y[1] = -SH1 * y;
+        Y[2] = SH1 * z;
+        Y[3] = -SH1 * x;
+    }
+    if (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = SH2a * x * y;
+        Y[5] = -SH2a * y * z;
+        Y[6] = SH2b * (2.f * zz - xx - yy);
+        Y[7] = -SH2a * x * z;
+        Y[8] = SH2c * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -SH3a * y * (3.f * xx - yy);
+            Y[10] = SH3b * x * y * z;
+            Y[11] = -SH3c * y * (4.f * zz - xx - yy);
+            Y[12] = SH3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -SH3c * x * (4.f * zz - xx - yy);
+            Y[14] = SH3e * z * (xx - yy);
+            Y[15] = -SH3a * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+// g += w_k * grad Y_k for every k (gradients of the polynomial forms above).
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad_acc(float x, float y, float z, const float* w, float& gx,
+                                                  float& gy, float& gz) {
+    if (DEG >= 1) {
+        gy += -SH1 * w[1];
+        gz += SH1 * w[2];
+        gx += -SH1 * w[3];
+    }
+    if (DEG >= 2) {
+        gx += SH2a * y * w[4];
+        gy += SH2a * x * w[4];
+        gy += -SH2a * z * w[5];
+        gz += -SH2a * y * w[5];
+        gx += -2.f * SH2b * x * w[6];
+        gy += -2.f * SH2b * y * w[6];
+        gz += 4.f * SH2b * z * w[6];
+        gx += -SH2a * z * w[7];
+        gz += -SH2a * x * w[7];
+        gx += 2.f * SH2c * x * w[8];
+        gy += -2.f * SH2c * y * w[8];
+        if (DEG >= 3) {
+            const float xx = x * x, yy = y * y, zz = z * z;
+            gx += -6.f * SH3a * x * y * w[9];
+            gy += -3.f * SH3a * (xx - yy) * w[9];
+            gx += SH3b * y * z * w[10];
+            gy += SH3b * x * z * w[10];
+            gz += SH3b * x * y * w[10];
+            gx += 2.f * SH3c * x * y * w[11];
+            gy += -SH3c * (4.f * zz - xx - 3.f * yy) * w[11];
+            gz += -8.f * SH3c * y * z * w[11];
+            gx += -6.f * SH3d * x * z * w[12];
+            gy += -6.f * SH3d * y * z * w[12];
+            gz += SH3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+            gx += -SH3c * (4.f * zz - 3.f * xx - yy) * w[13];
+            gy += 2.f * SH3c * x * y * w[13];
+            gz += -8.f * SH3c * x * z * w[13];
+            gx += 2.f * SH3e * x * z * w[14];
+            gy += -2.f * SH3e * y * z * w[14];
+            gz += SH3e * (xx - yy) * w[14];
+            gx += -3.f * SH3a * (xx - yy) * w[15];
+            gy += 6.f * SH3a * x * y * w[15];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Gaussian geometry: world covariance Sigma = M M^T with M = R(q/|q|) diag(exp(s)).
+// ---------------------------------------------------------------------------------------
+struct Cov3 {
+    float qn[4], qinv;   // normalised quaternion, 1/|q|
+    float Rq[9];
+    float s[3];
+    float M[9];
+    float S[6];          // Sigma: xx, xy, xz, yy, yz, zz
+};
+
+__device__ __forceinline__ void cov3_forward(const float* q, const float* ls, Cov3& c) {
+    const float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    c.qinv = rsqrtf(n2);
+    const float w = q[0] * c.qinv, x = q[1] * c.qinv, y = q[2] * c.qinv, z = q[3] * c.qinv;
+    c.qn[0] = w; c.qn[1] = x; c.qn[2] = y; c.qn[3] = z;
+    c.Rq[0] = 1.f - 2.f * (y * y + z * z); c.Rq[1] = 2.f * (x * y - w * z); c.Rq[2] = 2.f * (x * z + w * y);
+    c.Rq[3] = 2.f * (x * y + w * z); c.Rq[4] = 1.f - 2.f * (x * x + z * z); c.Rq[5] = 2.f * (y * z - w * x);
+    c.Rq[6] = 2.f * (x * z - w * y); c.Rq[7] = 2.f * (y * z + w * x); c.Rq[8] = 1.f - 2.f * (x * x + y * y);
+#pragma unroll
+    for (int k = 0; k < 3; k++) c.s[k] = expf(ls[k]);
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) c.M[r * 3 + k] = c.Rq[r * 3 + k] * c.s[k];
+    const float* M = c.M;
+    c.S[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    c.S[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    c.S[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    c.S[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    c.S[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    c.S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+}
+
+// Per-view projection of one Gaussian (everything the backward needs again).
+struct ProjV {
+    bool culled;
+    float pc[3];
+    float tx, ty;
+    bool clx, cly;
+    float J00, J02, J11, J12;   // J = [[J00, 0, J02], [0, J11, J12]]
+    float T[6];                 // J W, 2x3 row-major
+    float a, b, c;              // dilated 2-D covariance
+    float det;
+    float o;
+    float u, v;
+    int radius;
+};
+
+__device__ __forceinline__ void project_view(const float* mu, const Cov3& cv, float logit, const View& V,
+                                             const Opts& op, ProjV& P) {
+    // Every field is computed (no early exit) so the backward, which recomputes this for
+    // the pairs the forward kept, never reads an unset value.
+    const float* W = V.R;
+    P.pc[0] = W[0] * mu[0] + W[1] * mu[1] + W[2] * mu[2] + V.t[0];
+    P.pc[1] = W[3] * mu[0] + W[4] * mu[1] + W[5] * mu[2] + V.t[1];
+    P.pc[2] = W[6] * mu[0] + W[7] * mu[1] + W[8] * mu[2] + V.t[2];
+    const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
+    const bool front = z > op.near_z;
+    const float iz = 1.0f / (front ? z : 1.0f);
+    const float rx = x * iz, ry = y * iz;
+    P.tx = fminf(V.limx, fmaxf(-V.limx, rx));
+    P.ty = fminf(V.limy, fmaxf(-V.limy, ry));
+    P.clx = (rx < -V.limx) || (rx > V.limx);
+    P.cly = (ry < -V.limy) || (ry > V.limy);
+    P.J00 = V.fx * iz;
+    P.J02 = -V.fx * P.tx * iz;
+    P.J11 = V.fy * iz;
+    P.J12 = -V.fy * P.ty * iz;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        P.T[k] = P.J00 * W[k] + P.J02 * W[6 + k];
+        P.T[3 + k] = P.J11 * W[3 + k] + P.J12 * W[6 + k];
+    }
+    // T Sigma (2x3) then (T Sigma) T^T
+    const float* S = cv.S;
+    float TS[6];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const float* t = &P.T[3 * r];
+        TS[3 * r + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
+        TS[3 * r + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
+        TS[3 * r + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+    }
+    P.a = TS[0] * P.T[0] + TS[1] * P.T[1] + TS[2] * P.T[2] + op.dilation;
+    P.b = TS[0] * P.T[3] + TS[1] * P.T[4] + TS[2] * P.T[5];
+    P.c = TS[3] * P.T[3] + TS[4] * P.T[4] + TS[5] * P.T[5] + op.dilation;
+    P.det = P.a * P.c - P.b * P.b;
+    P.o = 1.0f / (1.0f + expf(-logit));
+    const bool opaque = P.o >= op.alpha_min;
+    const float hd = 0.5f * (P.a - P.c);
+    const float lmax = 0.5f * (P.a + P.c) + sqrtf(hd * hd + P.b * P.b);
+    const float r2 = 2.0f * logf(fmaxf(P.o, op.alpha_min) / op.alpha_min) * lmax;
+    P.radius = (front && P.det > 0.f && opaque && r2 > 0.f) ? (int)ceilf(sqrtf(r2)) : 0;
+    P.u = V.fx * x * iz + V.cx;
+    P.v = V.fy * y * iz + V.cy;
+    P.culled = !(front && P.det > 0.f && opaque && P.radius > 0);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace gs

@@ -1,0 +1,306 @@
+// a1 and a7: per-Gaussian EWA projection with SH colour, and its backward (chain rule to
+// the Gaussian parameters and to each view's SE(3) pose twist).
+// RMGS-SLAM §III-C ("standard differentiable Gaussian splatting"); gs.h documents the
+// readings (near plane, dilation, Jacobian clamp, opacity-aware radius, SH convention).
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+template <int DEG>
+__global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int64_t n = a.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float mu[3], ls[3], q[4], sh[3 * K];
+#pragma unroll
+    for (int k = 0; k < 3; k++) { mu[k] = __ldg(a.means + k * n + i); ls[k] = __ldg(a.log_scales + k * n + i); }
+#pragma unroll
+    for (int k = 0; k < 4; k++) q[k] = __ldg(a.quats + k * n + i);
+    const float logit = __ldg(a.logits + i);
+#pragma unroll
+    for (int k = 0; k < 3 * K; k++) sh[k] = __ldg(a.sh + k * n + i);
+    Cov3 cv;
+    cov3_forward(q, ls, cv);
+    const Opts op = a.op;
+    bool vis = false;
+    for (int v = 0; v < a.n_views; v++) {
+        const View& V = a.views[v];
+        const int64_t idx = (int64_t)v * n + i;
+        ProjV P;
+        project_view(mu, cv, logit, V, op, P);
+        uint32_t touched = 0;
+        if (!P.culled) {
+            int x0, x1, y0, y1;
+            if (tile_span(P.u, P.radius, op.tile, V.tiles_x, x0, x1) &&
+                tile_span(P.v, P.radius, op.tile, V.tiles_y, y0, y1))
+                touched = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+        }
+        if (touched) {
+            const float idet = 1.0f / P.det;
+            const float A = P.c * idet, B = -P.b * idet, C = P.a * idet;
+            // colour along the viewing direction
+            float d[3] = {mu[0] - V.cw[0], mu[1] - V.cw[1], mu[2] - V.cw[2]};
+            const float rn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            float Y[16];
+            sh_basis<DEG>(d[0] * rn, d[1] * rn, d[2] * rn, Y);
+            float rgb[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float s = 0.5f;
+#pragma unroll
+                for (int k = 0; k < K; k++) s += sh[k * 3 + c] * Y[k];
+                rgb[c] = fmaxf(s, 0.0f);
+            }
+            float4* rec = a.proj + 3 * idx;
+            rec[0] = make_float4(P.u, P.v, P.pc[2], P.o);
+            rec[1] = make_float4(-0.5f * kLog2e * A, -kLog2e * B, -0.5f * kLog2e * C, __int_as_float(P.radius));
+            rec[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+            vis = true;
+        }
+        a.touched[idx] = touched;
+    }
+    a.visible[i] = vis ? 1 : 0;
+}
+
+// Backward of the projection.  Screen-space sums per (view, Gaussian) come from the
+// backward compositing kernel (see render.cu for their definition):
+//   r0 = (sum h (2A'dx + B'dy), sum h (B'dx + 2C'dy), sum h dx^2, sum h dx dy)
+//   r1 = (sum h dy^2, dL/do, dL/dz, 0), r2 = (dL/dr, dL/dg, dL/db, 0)
+// with h = dL/dalpha * o * G.  Pose: xi = (rho, phi), T_cw <- Exp(xi) T_cw, so
+// dp_c = rho + phi x p_c, dW = [phi]x W and the camera centre moves by -W^T rho.
+template <int DEG>
+__global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdArgs a) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    __shared__ float s_tw[GS_MAX_VIEWS * 6];
+    for (int t = threadIdx.x; t < a.n_views * 6; t += blockDim.x) s_tw[t] = 0.f;
+    __syncthreads();
+    const int64_t n = a.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < n;
+    const int64_t ii = live ? i : 0;
+    float mu[3], ls[3], q[4], sh[3 * K];
+#pragma unroll
+    for (int k = 0; k < 3; k++) { mu[k] = __ldg(a.means + k * n + ii); ls[k] = __ldg(a.log_scales + k * n + ii); }
+#pragma unroll
+    for (int k = 0; k < 4; k++) q[k] = __ldg(a.quats + k * n + ii);
+    const float logit = __ldg(a.logits + ii);
+#pragma unroll
+    for (int k = 0; k < 3 * K; k++) sh[k] = __ldg(a.sh + k * n + ii);
+    Cov3 cv;
+    cov3_forward(q, ls, cv);
+    const Opts op = a.op;
+    float g_mu[3] = {0, 0, 0};
+    float gS[6] = {0, 0, 0, 0, 0, 0};   // dL/dSigma as a symmetric matrix: xx xy xz yy yz zz
+    float g_o = 0.f;
+    float g_sh[3 * K];
+#pragma unroll
+    for (int k = 0; k < 3 * K; k++) g_sh[k] = 0.f;
+    const int lane = threadIdx.x & 31;
+    for (int v = 0; v < a.n_views; v++) {
+        const View& V = a.views[v];
+        const int64_t idx = (int64_t)v * n + ii;
+        const bool act = live && a.touched[idx] != 0;
+        float tw[6] = {0, 0, 0, 0, 0, 0};
+        if (act) {
+            ProjV P;
+            project_view(mu, cv, logit, V, op, P);
+            const float4* gr = a.grad2d + 3 * idx;
+            const float4 r0 = gr[0], r1 = gr[1], r2 = gr[2];
+            const float* W = V.R;
+            // screen-space gradients
+            const float gu = -kLn2 * r0.x, gv = -kLn2 * r0.y;
+            const float gA = -0.5f * r0.z, gB = -r0.w, gC = -0.5f * r1.x;
+            g_o += r1.y;
+            float g_pc[3] = {0.f, 0.f, r1.z};
+            // conic = inverse(cov), cov = [[a, b], [b, c]]
+            const float pa = P.a, pb = P.b, pc = P.c;
+            const float id2 = 1.0f / (P.det * P.det);
+            const float ga = (-pc * pc * gA + pb * pc * gB - pb * pb * gC) * id2;
+            const float gb = (2.f * pb * pc * gA - (pa * pc + pb * pb) * gB + 2.f * pa * pb * gC) * id2;
+            const float gc = (-pb * pb * gA + pa * pb * gB - pa * pa * gC) * id2;
+            const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
+            // T Sigma
+            const float* S = cv.S;
+            float TS[6];
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const float* t = &P.T[3 * r];
+                TS[3 * r + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
+                TS[3 * r + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
+                TS[3 * r + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+            }
+            // g_T = 2 G T Sigma
+            float gT[6];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                gT[k] = 2.f * (G00 * TS[k] + G01 * TS[3 + k]);
+                gT[3 + k] = 2.f * (G01 * TS[k] + G11 * TS[3 + k]);
+            }
+            // g_Sigma += T^T G T
+            {
+                float GT[6];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    GT[k] = G00 * P.T[k] + G01 * P.T[3 + k];
+                    GT[3 + k] = G01 * P.T[k] + G11 * P.T[3 + k];
+                }
+                gS[0] += P.T[0] * GT[0] + P.T[3] * GT[3];
+                gS[1] += P.T[0] * GT[1] + P.T[3] * GT[4];
+                gS[2] += P.T[0] * GT[2] + P.T[3] * GT[5];
+                gS[3] += P.T[1] * GT[1] + P.T[4] * GT[4];
+                gS[4] += P.T[1] * GT[2] + P.T[4] * GT[5];
+                gS[5] += P.T[2] * GT[2] + P.T[5] * GT[5];
+            }
+            // T = J W : g_J = g_T W^T, g_W = J^T g_T
+            const float gJ00 = gT[0] * W[0] + gT[1] * W[1] + gT[2] * W[2];
+            const float gJ02 = gT[0] * W[6] + gT[1] * W[7] + gT[2] * W[8];
+            const float gJ11 = gT[3] * W[3] + gT[4] * W[4] + gT[5] * W[5];
+            const float gJ12 = gT[3] * W[6] + gT[4] * W[7] + gT[5] * W[8];
+            float gW[9];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                gW[k] = P.J00 * gT[k];
+                gW[3 + k] = P.J11 * gT[3 + k];
+                gW[6 + k] = P.J02 * gT[k] + P.J12 * gT[3 + k];
+            }
+            const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
+            const float iz = 1.0f / z, iz2 = iz * iz;
+            const float fx = V.fx, fy = V.fy;
+            const float dtx_dx = P.clx ? 0.f : iz, dtx_dz = P.clx ? 0.f : -x * iz2;
+            const float dty_dy = P.cly ? 0.f : iz, dty_dz = P.cly ? 0.f : -y * iz2;
+            g_pc[2] += -gJ00 * fx * iz2 - gJ11 * fy * iz2;
+            g_pc[2] += gJ02 * (fx * P.tx * iz2 - fx * iz * dtx_dz);
+            g_pc[0] += gJ02 * (-fx * iz * dtx_dx);
+            g_pc[2] += gJ12 * (fy * P.ty * iz2 - fy * iz * dty_dz);
+            g_pc[1] += gJ12 * (-fy * iz * dty_dy);
+            g_pc[0] += gu * fx * iz;
+            g_pc[1] += gv * fy * iz;
+            g_pc[2] += -(gu * fx * x + gv * fy * y) * iz2;
+#pragma unroll
+            for (int k = 0; k < 3; k++) g_mu[k] += W[k] * g_pc[0] + W[3 + k] * g_pc[1] + W[6 + k] * g_pc[2];
+            // pose: rho <- g_pc, phi <- p_c x g_pc + vee(g_W W^T)
+            tw[0] = g_pc[0]; tw[1] = g_pc[1]; tw[2] = g_pc[2];
+            tw[3] = y * g_pc[2] - z * g_pc[1];
+            tw[4] = z * g_pc[0] - x * g_pc[2];
+            tw[5] = x * g_pc[1] - y * g_pc[0];
+            {
+                // A = g_W W^T; need A21 - A12, A02 - A20, A10 - A01
+                auto Arc = [&](int r, int c) { return gW[3 * r] * W[3 * c] + gW[3 * r + 1] * W[3 * c + 1] + gW[3 * r + 2] * W[3 * c + 2]; };
+                tw[3] += Arc(2, 1) - Arc(1, 2);
+                tw[4] += Arc(0, 2) - Arc(2, 0);
+                tw[5] += Arc(1, 0) - Arc(0, 1);
+            }
+            // SH colour: rgb_c = max(0, sum_k sh_kc Y_k(dir) + 0.5), dir = (mu - cw)/|mu - cw|
+            float d[3] = {mu[0] - V.cw[0], mu[1] - V.cw[1], mu[2] - V.cw[2]};
+            const float rn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const float dir[3] = {d[0] * rn, d[1] * rn, d[2] * rn};
+            float Y[16];
+            sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
+            const float grgb[3] = {r2.x, r2.y, r2.z};
+            float wk[16];
+#pragma unroll
+            for (int k = 0; k < K; k++) wk[k] = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float s = 0.5f;
+#pragma unroll
+                for (int k = 0; k < K; k++) s += sh[k * 3 + c] * Y[k];
+                if (s < 0.f) continue;   // clamped channel: no gradient
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    g_sh[k * 3 + c] += grgb[c] * Y[k];
+                    wk[k] += grgb[c] * sh[k * 3 + c];
+                }
+            }
+            if (DEG > 0) {
+                float gd[3] = {0.f, 0.f, 0.f};
+                sh_basis_grad_acc<DEG>(dir[0], dir[1], dir[2], wk, gd[0], gd[1], gd[2]);
+                const float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
+#pragma unroll
+                for (int k = 0; k < 3; k++) gd[k] = (gd[k] - dir[k] * dd) * rn;
+#pragma unroll
+                for (int k = 0; k < 3; k++) g_mu[k] += gd[k];
+#pragma unroll
+                for (int r = 0; r < 3; r++) tw[r] += W[3 * r] * gd[0] + W[3 * r + 1] * gd[1] + W[3 * r + 2] * gd[2];
+            }
+        }
+        if (a.grad_twist) {
+            if (__any_sync(0xffffffffu, act)) {
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    const float s = warp_sum(tw[k]);
+                    if (lane == 0) atomicAdd(&s_tw[v * 6 + k], s);
+                }
+            }
+        }
+    }
+    if (live) {
+        // Sigma = M M^T -> g_M = 2 gSigma M (symmetric gSigma); M = Rq diag(s)
+        const float Gs[9] = {gS[0], gS[1], gS[2], gS[1], gS[3], gS[4], gS[2], gS[4], gS[5]};
+        float gM[9];
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                gM[3 * r + c] = 2.f * (Gs[3 * r] * cv.M[c] + Gs[3 * r + 1] * cv.M[3 + c] + Gs[3 * r + 2] * cv.M[6 + c]);
+        float gls[3], gR[9];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            gls[c] = (cv.Rq[c] * gM[c] + cv.Rq[3 + c] * gM[3 + c] + cv.Rq[6 + c] * gM[6 + c]) * cv.s[c];
+#pragma unroll
+            for (int r = 0; r < 3; r++) gR[3 * r + c] = gM[3 * r + c] * cv.s[c];
+        }
+        const float w = cv.qn[0], x = cv.qn[1], y = cv.qn[2], z = cv.qn[3];
+        float gq[4];
+        gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+        gq[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.f * x * gR[8]);
+        gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.f * y * gR[8]);
+        gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
+        const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+        const float qn[4] = {w, x, y, z};
+        const float o = 1.0f / (1.0f + expf(-logit));
+#pragma unroll
+        for (int k = 0; k < 3; k++) a.g_means[k * n + i] += g_mu[k];
+#pragma unroll
+        for (int k = 0; k < 3; k++) a.g_log_scales[k * n + i] += gls[k];
+#pragma unroll
+        for (int k = 0; k < 4; k++) a.g_quats[k * n + i] += (gq[k] - qn[k] * dq) * cv.qinv;
+        a.g_logits[i] += g_o * o * (1.f - o);
+#pragma unroll
+        for (int k = 0; k < 3 * K; k++) a.g_sh[k * n + i] += g_sh[k];
+    }
+    if (a.grad_twist) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < a.n_views * 6; t += blockDim.x)
+            if (s_tw[t] != 0.f) atomicAdd(&a.grad_twist[t], s_tw[t]);
+    }
+}
+
+cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st) {
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
+    if (blocks == 0) return cudaSuccess;
+    switch (deg) {
+        case 0: project_kernel<0><<<blocks, threads, 0, st>>>(a); break;
+        case 1: project_kernel<1><<<blocks, threads, 0, st>>>(a); break;
+        case 2: project_kernel<2><<<blocks, threads, 0, st>>>(a); break;
+        default: project_kernel<3><<<blocks, threads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st) {
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
+    if (blocks == 0) return cudaSuccess;
+    switch (deg) {
+        case 0: project_bwd_kernel<0><<<blocks, threads, 0, st>>>(a); break;
+        case 1: project_bwd_kernel<1><<<blocks, threads, 0, st>>>(a); break;
+        case 2: project_bwd_kernel<2><<<blocks, threads, 0, st>>>(a); break;
+        default: project_bwd_kernel<3><<<blocks, threads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,392 @@
+// a5-a6: front-to-back compositing of colour and depth with the fused L1 loss, and its
+// backward with transmittance recomputed back to front.  RMGS-SLAM §III-C: colour by
+// standard alpha compositing, depth D = sum z_i T_i alpha_i with the same weights, loss
+// lambda_rgb L_rgb + lambda_depth L_depth over the mask (SSIM weight 0).
+//
+// One CTA per (view, tile) work item, one thread per pixel.  The tile's depth-sorted pair
+// list is walked in chunks staged in shared memory (records gathered once per chunk by
+// the whole CTA); the inner loop then reads broadcast shared memory only.
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+__device__ __forceinline__ int view_of_tile(const View* views, int n_views, int gt) {
+    int v = 0;
+    while (v + 1 < n_views && views[v + 1].tile_off <= gt) v++;
+    return v;
+}
+
+// ----------------------------------------------------------------------------------------
+// Loss normalisers: |M_v| and |M_v and D~ > 0| per view.
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) loss_count_kernel(const View* views, const float* tgt_depth,
+                                                         const uint8_t* mask, uint32_t* counts) {
+    const int v = blockIdx.y;
+    const View& V = views[v];
+    const int64_t P = (int64_t)V.W * V.H;
+    uint32_t cm = 0, cd = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = V.pix_off + p;
+        const bool in = mask ? mask[g] != 0 : true;
+        cm += in;
+        cd += (in && tgt_depth && tgt_depth[g] > 0.f);
+    }
+    cm = warp_sum(cm);
+    cd = warp_sum(cd);
+    if ((threadIdx.x & 31) == 0) {
+        if (cm) atomicAdd(&counts[2 * v], cm);
+        if (cd) atomicAdd(&counts[2 * v + 1], cd);
+    }
+}
+
+cudaError_t launch_loss_count(const View* views, int n_views, const int64_t* pix_counts_host, const float* tgt_depth,
+                              const uint8_t* mask, uint32_t* counts, cudaStream_t st) {
+    int64_t mx = 0;
+    for (int v = 0; v < n_views; v++) mx = pix_counts_host[v] > mx ? pix_counts_host[v] : mx;
+    int bx = (int)((mx + 255) / 256);
+    if (bx > 256) bx = 256;
+    if (bx < 1) bx = 1;
+    loss_count_kernel<<<dim3(bx, n_views), 256, 0, st>>>(views, tgt_depth, mask, counts);
+    return cudaGetLastError();
+}
+
+__global__ void loss_finalize_kernel(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
+                                     float lambda_depth, int has_depth, float* loss_out) {
+    if (threadIdx.x != 0) return;
+    double tot = 0;
+    for (int v = 0; v < n_views; v++) {
+        const double cm = counts[2 * v], cd = counts[2 * v + 1];
+        double l = cm > 0 ? lambda_rgb * sums[2 * v] / cm : 0.0;
+        if (has_depth && cd > 0) l += lambda_depth * sums[2 * v + 1] / cd;
+        loss_out[v] = (float)l;
+        tot += l;
+    }
+    loss_out[n_views] = (float)(tot / n_views);
+}
+
+cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
+                                 float lambda_depth, int has_depth, float* loss_out, cudaStream_t st) {
+    loss_finalize_kernel<<<1, 32, 0, st>>>(sums, counts, n_views, lambda_rgb, lambda_depth, has_depth, loss_out);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------
+// Forward compositing.
+// ----------------------------------------------------------------------------------------
+template <int TILE, int CHUNK>
+__global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(FwdArgs a) {
+    constexpr int NT = TILE * TILE;
+    __shared__ float2 s_uv[CHUNK];
+    __shared__ float4 s_co[CHUNK];   // A', B', C', opacity
+    __shared__ float4 s_cz[CHUNK];   // r, g, b, z
+    __shared__ double s_red[2][NT / 32];
+    if (a.counters->status != 0) return;
+    const int gt = blockIdx.x;
+    const int v = view_of_tile(a.views, a.n_views, gt);
+    const View& V = a.views[v];
+    const int lt = gt - V.tile_off;
+    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+    const int x = tx * TILE + (threadIdx.x % TILE), y = ty * TILE + (threadIdx.x / TILE);
+    const bool inside = x < V.W && y < V.H;
+    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const uint2 rg = a.ranges[gt];
+    const int n = (int)(rg.y - rg.x);
+    const float amin = a.op.alpha_min, amax = a.op.alpha_max, tmin = a.op.T_min;
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (int base = 0; base < n; base += CHUNK) {
+        if (__syncthreads_count(!done) == 0) break;
+        for (int k = threadIdx.x; k < CHUNK; k += NT) {
+            const int j = base + k;
+            if (j < n) {
+                const uint32_t gid = a.vals[rg.x + j];
+                const float4* r = a.proj + 3 * (size_t)gid;
+                const float4 f0 = __ldg(r), f1 = __ldg(r + 1), f2 = __ldg(r + 2);
+                s_uv[k] = make_float2(f0.x, f0.y);
+                s_co[k] = make_float4(f1.x, f1.y, f1.z, f0.w);
+                s_cz[k] = make_float4(f2.x, f2.y, f2.z, f0.z);
+            }
+        }
+        __syncthreads();
+        if (!done) {
+            const int m = min(CHUNK, n - base);
+            for (int k = 0; k < m; k++) {
+                const float2 uv = s_uv[k];
+                const float4 co = s_co[k];
+                const float dx = px - uv.x, dy = py - uv.y;
+                const float G = ex2_approx(frag_exponent(dx, dy, co.x, co.y, co.z));
+                const float alpha = fminf(amax, co.w * G);
+                if (alpha < amin) continue;
+                const float test_T = T * (1.f - alpha);
+                if (test_T < tmin) {
+                    done = true;
+                    break;
+                }
+                const float w = alpha * T;
+                const float4 cz = s_cz[k];
+                c0 = fmaf(w, cz.x, c0);
+                c1 = fmaf(w, cz.y, c1);
+                c2 = fmaf(w, cz.z, c2);
+                dep = fmaf(w, cz.w, dep);
+                T = test_T;
+                last = (uint32_t)(base + k + 1);
+            }
+        }
+    }
+    double lr = 0.0, ld = 0.0;
+    if (inside) {
+        const int64_t P = (int64_t)V.W * V.H;
+        const int64_t p = (int64_t)y * V.W + x;
+        const int64_t g = V.pix_off + p;
+        const float o0 = c0 + T * a.op.bg0, o1 = c1 + T * a.op.bg1, o2 = c2 + T * a.op.bg2;
+        float* rgb = a.out_rgb + 3 * V.pix_off;
+        rgb[p] = o0;
+        rgb[P + p] = o1;
+        rgb[2 * P + p] = o2;
+        a.out_depth[g] = dep;
+        if (a.out_T) a.out_T[g] = T;
+        a.T_final[g] = T;
+        a.n_contrib[g] = last;
+        if (a.tgt_rgb) {
+            const bool in = a.mask ? a.mask[g] != 0 : true;
+            const float cm = (float)a.loss_counts[2 * v], cd = (float)a.loss_counts[2 * v + 1];
+            const float inv_v = 1.0f / (float)a.n_views;
+            const float krgb = (in && cm > 0.f) ? a.op.lambda_rgb * inv_v / cm : 0.f;
+            const float* t = a.tgt_rgb + 3 * V.pix_off;
+            const float r0 = o0 - t[p], r1 = o1 - t[P + p], r2 = o2 - t[2 * P + p];
+            float* dl = a.dl_drgb + 3 * V.pix_off;
+            dl[p] = krgb * (float)((r0 > 0.f) - (r0 < 0.f));
+            dl[P + p] = krgb * (float)((r1 > 0.f) - (r1 < 0.f));
+            dl[2 * P + p] = krgb * (float)((r2 > 0.f) - (r2 < 0.f));
+            if (in) lr = (double)fabsf(r0) + (double)fabsf(r1) + (double)fabsf(r2);
+            if (a.dl_ddepth) {
+                const float td = a.tgt_depth ? a.tgt_depth[g] : 0.f;
+                const bool ind = in && td > 0.f;
+                const float kd = (ind && cd > 0.f) ? a.op.lambda_depth * inv_v / cd : 0.f;
+                const float rd = dep - td;
+                a.dl_ddepth[g] = kd * (float)((rd > 0.f) - (rd < 0.f));
+                if (ind) ld = (double)fabsf(rd);
+            }
+        }
+    }
+    if (a.tgt_rgb) {
+        // block reduction of the two L1 sums, one atomic per CTA
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lr += __shfl_xor_sync(0xffffffffu, lr, o);
+            ld += __shfl_xor_sync(0xffffffffu, ld, o);
+        }
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) { s_red[0][w] = lr; s_red[1][w] = ld; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sr = 0, sd = 0;
+            for (int k = 0; k < NT / 32; k++) { sr += s_red[0][k]; sd += s_red[1][k]; }
+            if (sr != 0.0) atomicAdd(&a.loss_sums[2 * v], sr);
+            if (sd != 0.0) atomicAdd(&a.loss_sums[2 * v + 1], sd);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// Backward compositing.
+//
+// For a pixel with upstream gradients g_C (3) and g_D, walking its contributing fragments
+// back to front with T_i = T_{i+1} / (1 - alpha_i):
+//   w_i = alpha_i T_i;  dL/dc_i = g_C w_i;  dL/dz_i = g_D w_i
+//   dL/dalpha_i = T_i (g_C.c_i + g_D z_i) - S_i / (1 - alpha_i)
+// with S_i = g_C.bg T_final + sum_{j>i} (g_C.c_j + g_D z_j) w_j (one running scalar).
+// If o G < alpha_max (the clamp is inactive), alpha = o 2^e gives dalpha/do = G and
+// dalpha/de = ln2 o G.  Per (view, Gaussian) the kernel accumulates, with h = dL/dalpha o G:
+//   r0 = (sum h (2A'dx + B'dy), sum h (B'dx + 2C'dy), sum h dx^2, sum h dx dy)
+//   r1 = (sum h dy^2, sum dL/dalpha G, sum g_D w, 0), r2 = (sum g_C w, 0)
+// and the projection backward applies the constant factors (ln2, -log2 e / 2, ...).
+// Lanes of a warp walk the same list position; their 10 values are summed with a
+// transpose-reduce (16 shuffles) and written by 10 lanes with one atomic each.
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ void warp_transpose_reduce10(float (&v)[16], float& out) {
+    const int lane = threadIdx.x & 31;
+    // 16 -> 8 (partner lane ^ 16)
+    {
+        const bool hi = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const float mine = hi ? v[8 + k] : v[k];
+            const float other = hi ? v[k] : v[8 + k];
+            v[k] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+        }
+    }
+    {
+        const bool hi = lane & 8;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float mine = hi ? v[4 + k] : v[k];
+            const float other = hi ? v[k] : v[4 + k];
+            v[k] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+        }
+    }
+    {
+        const bool hi = lane & 4;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const float mine = hi ? v[2 + k] : v[k];
+            const float other = hi ? v[k] : v[2 + k];
+            v[k] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
+        }
+    }
+    {
+        const bool hi = lane & 2;
+        const float mine = hi ? v[1] : v[0];
+        const float other = hi ? v[0] : v[1];
+        v[0] = mine + __shfl_xor_sync(0xffffffffu, other, 2);
+    }
+    out = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    // lane l now holds the warp total of value index l >> 1
+}
+
+template <int TILE, int CHUNK>
+__global__ void __launch_bounds__(TILE* TILE) render_bwd_kernel(BwdArgs a) {
+    constexpr int NT = TILE * TILE;
+    __shared__ float2 s_uv[CHUNK];
+    __shared__ float4 s_co[CHUNK];
+    __shared__ float4 s_cz[CHUNK];
+    __shared__ uint32_t s_id[CHUNK];
+    __shared__ uint32_t s_max;
+    if (a.counters->status != 0) return;
+    const int gt = blockIdx.x;
+    const int v = view_of_tile(a.views, a.n_views, gt);
+    const View& V = a.views[v];
+    const int lt = gt - V.tile_off;
+    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+    const int x = tx * TILE + (threadIdx.x % TILE), y = ty * TILE + (threadIdx.x / TILE);
+    const bool inside = x < V.W && y < V.H;
+    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const uint2 rg = a.ranges[gt];
+    const float amin = a.op.alpha_min, amax = a.op.alpha_max;
+    float T = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gd = 0.f;
+    uint32_t last = 0;
+    if (inside) {
+        const int64_t P = (int64_t)V.W * V.H;
+        const int64_t p = (int64_t)y * V.W + x;
+        const int64_t g = V.pix_off + p;
+        T = a.T_final[g];
+        last = a.n_contrib[g];
+        const float* d = a.dl_drgb + 3 * V.pix_off;
+        gc0 = d[p];
+        gc1 = d[P + p];
+        gc2 = d[2 * P + p];
+        gd = a.dl_ddepth ? a.dl_ddepth[g] : 0.f;
+        if (gc0 == 0.f && gc1 == 0.f && gc2 == 0.f && gd == 0.f) last = 0;
+    }
+    float S = (gc0 * a.op.bg0 + gc1 * a.op.bg1 + gc2 * a.op.bg2) * T;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
+    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_max, wmax);
+    __syncthreads();
+    const int top_all = (int)s_max;
+    const int lane = threadIdx.x & 31;
+    for (int top = top_all; top > 0; top -= CHUNK) {
+        const int lo = max(0, top - CHUNK);
+        __syncthreads();
+        for (int k = threadIdx.x; k < top - lo; k += NT) {
+            const uint32_t gid = a.vals[rg.x + lo + k];
+            const float4* r = a.proj + 3 * (size_t)gid;
+            const float4 f0 = __ldg(r), f1 = __ldg(r + 1), f2 = __ldg(r + 2);
+            s_uv[k] = make_float2(f0.x, f0.y);
+            s_co[k] = make_float4(f1.x, f1.y, f1.z, f0.w);
+            s_cz[k] = make_float4(f2.x, f2.y, f2.z, f0.z);
+            s_id[k] = gid;
+        }
+        __syncthreads();
+        // highest list position any lane of this warp still needs
+        const uint32_t wtop = __reduce_max_sync(0xffffffffu, last);
+        const int jstart = min(top, (int)wtop) - 1;
+        for (int j = jstart; j >= lo; j--) {
+            const int k = j - lo;
+            float val[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) val[q] = 0.f;
+            bool contrib = false;
+            if ((uint32_t)j < last) {
+                const float2 uv = s_uv[k];
+                const float4 co = s_co[k];
+                const float dx = px - uv.x, dy = py - uv.y;
+                const float G = ex2_approx(frag_exponent(dx, dy, co.x, co.y, co.z));
+                const float a0 = co.w * G;
+                const float alpha = fminf(amax, a0);
+                if (alpha >= amin) {
+                    contrib = true;
+                    const float om = 1.f - alpha;
+                    const float rom = __frcp_rn(om);
+                    T = T * rom;
+                    const float w = alpha * T;
+                    const float4 cz = s_cz[k];
+                    const float gcz = gc0 * cz.x + gc1 * cz.y + gc2 * cz.z + gd * cz.w;
+                    const float dLda = T * gcz - S * rom;
+                    S = fmaf(gcz, w, S);
+                    val[7] = gc0 * w;
+                    val[8] = gc1 * w;
+                    val[9] = gc2 * w;
+                    val[6] = gd * w;
+                    if (a0 < amax) {
+                        const float h = dLda * a0;
+                        val[0] = h * (2.f * co.x * dx + co.y * dy);
+                        val[1] = h * (co.y * dx + 2.f * co.z * dy);
+                        val[2] = h * dx * dx;
+                        val[3] = h * dx * dy;
+                        val[4] = h * dy * dy;
+                        val[5] = dLda * G;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                float tot;
+                warp_transpose_reduce10(val, tot);
+                const int idx = lane >> 1;
+                if ((lane & 1) == 0 && idx < 10) {
+                    float* rec = reinterpret_cast<float*>(a.grad2d + 3 * (size_t)s_id[k]);
+                    // value index -> record slot: 0..6 -> 0..6, 7..9 -> 8..10
+                    atomicAdd(rec + (idx < 7 ? idx : idx + 1), tot);
+                }
+            }
+        }
+    }
+}
+
+template <int TILE>
+static cudaError_t launch_fwd_t(const FwdArgs& a, int total_tiles, int chunk, cudaStream_t st) {
+    switch (chunk) {
+        case 32: render_fwd_kernel<TILE, 32><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+        case 64: render_fwd_kernel<TILE, 64><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+        case 128: render_fwd_kernel<TILE, 128><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+        default: render_fwd_kernel<TILE, 256><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int TILE>
+static cudaError_t launch_bwd_t(const BwdArgs& a, int total_tiles, int chunk, cudaStream_t st) {
+    switch (chunk) {
+        case 32: render_bwd_kernel<TILE, 32><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+        case 64: render_bwd_kernel<TILE, 64><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+        case 128: render_bwd_kernel<TILE, 128><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+        default: render_bwd_kernel<TILE, 256><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_fwd(const FwdArgs& a, int total_tiles, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    return a.op.tile == 8 ? launch_fwd_t<8>(a, total_tiles, a.op.chunk, st)
+                          : launch_fwd_t<16>(a, total_tiles, a.op.chunk, st);
+}
+
+cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    return a.op.tile == 8 ? launch_bwd_t<8>(a, total_tiles, a.op.chunk, st)
+                          : launch_bwd_t<16>(a, total_tiles, a.op.chunk, st);
+}
+
+}  // namespace gs
