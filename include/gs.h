@@ -210,6 +210,25 @@ gs_status gs_adam_step(gs_gaussians *params, gs_gaussians *grads, gs_gaussians *
                        const uint8_t *update_mask, const uint8_t *visible, const float lr[6],
                        float b1, float b2, float eps, int64_t step, void *stream);
 
+/* Allocation-free sort (the paper has no counterpart; it is a service of this library).
+ * Stable LSD radix sort of n (key, value) pairs by the low key_bits bits of the key (8 bits
+ * per pass), the same sort gs_bin_sort applies to its (tile, depth) pairs, for callers that
+ * cannot allocate device memory -- e.g. code running under a no-allocation policy, inside
+ * a host callback, or as a plug-in of an application that owns all device allocations.
+ * Its scratch is a fixed array inside the library (about 13 MB per device, held by every
+ * GPU that loads the library until the process exits), so a call sorts at most 1048576
+ * pairs; larger n returns GS_ERR_INVALID_ARG.  The call allocates nothing.
+ *   keys_in [n], vals_in [n]   device input, not modified
+ *   keys_out [n], vals_out [n] device output; must not alias the inputs
+ * The first call on a device (with that device current) looks up the scratch address with
+ * cudaGetSymbolAddress, which can load the library's device code; make that first call
+ * before any stream capture.  All calls share the scratch and it keeps the previous call's
+ * contents, so calls that may overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. */
+gs_status gs_sort_pairs_noalloc(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n,
+                                int32_t key_bits, uint64_t *keys_out, uint32_t *vals_out,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

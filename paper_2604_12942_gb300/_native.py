@@ -68,6 +68,8 @@ _SIGS = {
                       [C.c_void_p] * 3 + [C.c_void_p] * 3 + [C.c_void_p], C.c_int),
     "gs_render_bwd": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p,
                        C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p], C.c_int),
+    "gs_sort_pairs_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
+                              C.c_int),
     "gs_adam_step": ([C.POINTER(Gaussians)] * 4 + [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.c_float, C.c_float,
                                                    C.c_float, C.c_int64, C.c_void_p], C.c_int),
 }

@@ -199,6 +199,9 @@ static gs_status geometry_for(const gs_ws_layout* L, const gs_camera* cams, cons
     return GS_OK;
 }
 
+// Error recording for entry points defined in other translation units.
+gs_status record_error(gs_status s, const char* msg) { return fail(s, "%s", msg); }
+
 }  // namespace gs
 
 using namespace gs;
