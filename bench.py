@@ -37,8 +37,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--n", type=int, default=2_000_000)
-    ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--tile", type=int, default=0, help="8 or 16; 0 = autotune")
+    ap.add_argument("--chunk", type=int, default=0, help="32, 64, 128 or 256; 0 = autotune")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=3)
     return ap.parse_args()
@@ -178,17 +179,16 @@ def run_gpu(args, rank, world):
     dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
     torch.cuda.set_device(dev)
     sc, gt, cams = make_workload(args.n, args.seed, rank)
-    opts = gs.default_opts(tile=args.tile, chunk=args.chunk)
     n = sc.n
-    # pair capacity: measure the ground truth's pairs once, add headroom
-    probe = gs.Workspace(n, cams, opts, 1 << 20)
+    # pair capacity: measure the ground truth's pairs once at the smaller tile, add headroom
+    probe = gs.Workspace(n, cams, gs.default_opts(tile=8), 1 << 20)
     gt_planes = torch.as_tensor(gt.planes(), device=dev).contiguous()
     probe.project(gt_planes, 3)
     probe.bin_sort()
     need = int(probe.counters().n_pairs)
     cap = int(need * 1.5) + (1 << 20)
     del probe
-    ws = gs.Workspace(n, cams, opts, cap)
+    ws = gs.Workspace(n, cams, gs.default_opts(), cap)
     P = ws.layout.total_pixels
     trgb = torch.empty(3 * P, device=dev)
     tdep = torch.empty(P, device=dev)
@@ -197,7 +197,19 @@ def run_gpu(args, rank, world):
     ws.render_fwd(trgb, tdep)
     torch.cuda.synchronize()
     del gt_planes, ws
-    step = gs.MappingStep(torch.as_tensor(sc.planes(), device=dev).contiguous(), 3, cams, opts, max_pairs=cap)
+    planes0 = torch.as_tensor(sc.planes(), device=dev).contiguous()
+    tune = None
+    if args.tile == 0 or args.chunk == 0:
+        from paper_2604_12942_gb300 import autotune
+        key = autotune.cache_key(torch.cuda.get_device_name(dev), n, SIZES, 3)
+        tiles = (args.tile,) if args.tile else autotune.TILES
+        chunks = (args.chunk,) if args.chunk else autotune.CHUNKS
+        ch = autotune.tune(lambda t, c: autotune.time_mapping_step(planes0, 3, cams, (trgb, tdep), t, c, cap),
+                           key, [(t, c) for t in tiles for c in chunks], force=args.retune)
+        args.tile, args.chunk = ch.tile, ch.chunk
+        tune = {"tile": ch.tile, "chunk": ch.chunk, "ms_per_step": round(ch.ms, 4), "table": ch.table, "key": key}
+    opts = gs.default_opts(tile=args.tile, chunk=args.chunk)
+    step = gs.MappingStep(planes0, 3, cams, opts, max_pairs=cap)
     stages = ["project", "bin_sort", "render_fwd", "render_bwd", "adam"]
     st = torch.cuda.current_stream()
 
@@ -266,6 +278,7 @@ def run_gpu(args, rank, world):
     e_dt = (time.perf_counter() - e0) / e_steps
     px = sum(w * h for w, h in SIZES)
     return dict(total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=float(step.loss[-1]),
+                tune=tune,
                 clocks=clk.summary(), e2e_s=e_dt, px=px, h2d=int(h_rgb.numel() * 4 + h_dep.numel() * 4),
                 d2h=int(h_loss.numel() * 4), sc=sc, cams=cams, trgb=trgb, tdep=tdep, n=n,
                 kernels=kernels_per_step(step.ws.layout))
@@ -323,6 +336,7 @@ def main():
         "e2e": {"value": round(r["px"] / r["e2e_s"] / 1e6, 2), "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["kernels"] * args.steps,
+        "autotune": r["tune"],
     }
     if not args.no_cpu_baseline and world == 1:
         tg = [{"rgb": t[0].cpu().numpy(), "depth": t[1].cpu().numpy()} for t in

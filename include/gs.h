@@ -104,9 +104,9 @@ typedef struct {
     size_t counters;     /* gs_counters-compatible block: status, n_pairs, ... */
     size_t loss_acc;     /* double [n_views][2] masked L1 sums, uint32 [n_views][2] counts */
     size_t proj;         /* [n_views*n] records of 12 floats: (u, v, z, opacity),
-                            (A', B', C', radius bits), (r, g, b, 0); A', B', C' are the
-                            inverse 2-D covariance scaled so that alpha = o * 2^(A'dx^2 +
-                            B'dx dy + C'dy^2) */
+                            (a, b, c, rx bits), (r, g, b, ry bits); (a, b, c) is the inverse
+                            2-D covariance times -log2(e)/2, so alpha = o * 2^(a dx^2 +
+                            2 b dx dy + c dy^2); rx, ry are the box half-extents (int32) */
     size_t touched;      /* uint32 [n_views*n] tiles covered */
     size_t offsets;      /* uint32 [n_views*n] exclusive scan of touched */
     size_t scan_tmp;     /* uint32 scratch of the scan */
@@ -157,15 +157,17 @@ gs_status gs_read_counters(const gs_ws_layout *L, const void *ws, gs_counters *o
  * Sigma = R S S^T R^T with S = diag(exp(log_scale)); p_c = R_cw mu + t_cw, culled if
  * z <= near_z; Sigma' = J R_cw Sigma R_cw^T J^T + dilation*I with the perspective
  * Jacobian J at (x/z, y/z) clamped to +-clamp_fov*(W/2)/fx (resp. H, fy); o =
- * sigmoid(logit), culled if o < alpha_min; radius = ceil(sqrt(2 ln(o/alpha_min)
- * lambda_max(Sigma'))); rgb = max(0, sum_k sh_k Y_k(dir) + 0.5), dir = normalize(mu -
- * camera centre).  Writes the proj, touched and visible regions of the workspace. */
+ * sigmoid(logit), culled if o < alpha_min; rgb = max(0, sum_k sh_k Y_k(dir) + 0.5),
+ * dir = normalize(mu - camera centre); box half-extents rx = ceil(sqrt(tau Sigma'_xx)), ry = ceil(sqrt(tau
+ * Sigma'_yy)), tau = 2 ln(o/alpha_min) (the bounding box of the ellipse outside which
+ * alpha < alpha_min).  Writes the proj, touched and visible regions of the workspace. */
 gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, const gs_render_opts *opts,
                      const gs_ws_layout *L, void *ws, void *stream);
 
 /* a2-a4 -- Tile binning, (tile, depth) radix sort and tile ranges (§II-A tile-based
- * rasterizer).  A record with radius r covers tiles x in [floor((u-r)/T), floor((u+r)/T)]
- * (same for y), clamped to the view's grid, computed in FP32 exactly as written.  Pair key
+ * rasterizer).  A record with box half-extents rx, ry covers tiles x in
+ * [floor((u-rx)/T), floor((u+rx)/T)] and y in [floor((v-ry)/T), floor((v+ry)/T)], clamped to
+ * the view's grid, computed in FP32 exactly as written.  Pair key
  * = ((tile_offset(v) + ty*tiles_x + tx) << 32) | float_bits(z), value = v*n + i, emitted in
  * ascending (v, i) then row-major tile order and sorted stably by key.  If the pairs exceed
  * max_pairs the status word becomes GS_ERR_CAPACITY, n_pairs holds the required count and

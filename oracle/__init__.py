@@ -52,7 +52,7 @@ class _Opts(C.Structure):
 class _Proj(C.Structure):
     _fields_ = [("visible", C.c_void_p), ("u", C.c_void_p), ("v", C.c_void_p), ("z", C.c_void_p),
                 ("cov2d", C.c_void_p), ("conic", C.c_void_p), ("opacity", C.c_void_p),
-                ("rgb", C.c_void_p), ("radius", C.c_void_p), ("fragile", C.c_void_p)]
+                ("rgb", C.c_void_p), ("rx", C.c_void_p), ("ry", C.c_void_p), ("fragile", C.c_void_p)]
 
 
 def lib():
@@ -73,7 +73,7 @@ def lib():
             L.or_project_backward.argtypes = [i64, i32, vp, vp, vp, vp, vp, C.POINTER(_Cam),
                                               C.POINTER(_Opts), vp, vp, vp]
             L.or_adam.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, dbl, dbl, dbl, i64]
-            L.or_bin_view.argtypes = [i64, vp, vp, vp, vp, i32, i32, i32, i64, i64, vp, vp, vp]
+            L.or_bin_view.argtypes = [i64, vp, vp, vp, vp, vp, i32, i32, i32, i64, i64, vp, vp, vp]
             L.or_bin_view.restype = i64
             L.or_sort_pairs.argtypes = [i64, vp, vp]
             L.or_tile_ranges.argtypes = [i64, vp, i64, vp]
@@ -133,9 +133,10 @@ def project(scene, cam, opts: Opts = Opts()):
     n = scene.n
     out = dict(visible=np.zeros(n, np.int32), u=np.zeros(n), v=np.zeros(n), z=np.zeros(n),
                cov2d=np.zeros(3 * n), conic=np.zeros(3 * n), opacity=np.zeros(n),
-               rgb=np.zeros(3 * n), radius=np.zeros(n, np.int32), fragile=np.zeros(n, np.int32))
+               rgb=np.zeros(3 * n), rx=np.zeros(n, np.int32), ry=np.zeros(n, np.int32),
+               fragile=np.zeros(n, np.int32))
     pr = _Proj(*[_p(out[k]).value for k in ("visible", "u", "v", "z", "cov2d", "conic", "opacity",
-                                              "rgb", "radius", "fragile")])
+                                              "rgb", "rx", "ry", "fragile")])
     ps = _params(scene)
     lib().or_project(n, scene.sh_degree, *[_p(a) for a in ps], C.byref(_cam(cam)), C.byref(opts.c()),
                      C.byref(pr))
@@ -150,7 +151,7 @@ def _proj_struct(pr):
     for k in ("cov2d", "conic", "rgb"):
         assert pr[k].flags.c_contiguous
     return _Proj(*[_p(pr[k]).value for k in ("visible", "u", "v", "z", "cov2d", "conic", "opacity",
-                                              "rgb", "radius", "fragile")])
+                                              "rgb", "rx", "ry", "fragile")])
 
 
 def render(pr, cam, opts: Opts = Opts(), margin=1e-4, use_square=True):
@@ -265,12 +266,13 @@ def bin_views(items, cams, tile):
         W, H = cam["width"], cam["height"]
         n = it["u"].shape[0]
         u = np.ascontiguousarray(it["u"], np.float32); v = np.ascontiguousarray(it["v"], np.float32)
-        z = np.ascontiguousarray(it["z"], np.float32); r = np.ascontiguousarray(it["radius"], np.int32)
+        z = np.ascontiguousarray(it["z"], np.float32)
+        rx = np.ascontiguousarray(it["rx"], np.int32); ry = np.ascontiguousarray(it["ry"], np.int32)
         touched = np.zeros(n, np.uint32)
-        P = lib().or_bin_view(n, _p(u), _p(v), _p(z), _p(r), W, H, tile, tile_off, idx_off, None, None,
-                              _p(touched))
+        P = lib().or_bin_view(n, _p(u), _p(v), _p(z), _p(rx), _p(ry), W, H, tile, tile_off, idx_off, None,
+                              None, _p(touched))
         keys = np.zeros(P, np.uint64); vals = np.zeros(P, np.uint32)
-        lib().or_bin_view(n, _p(u), _p(v), _p(z), _p(r), W, H, tile, tile_off, idx_off, _p(keys),
+        lib().or_bin_view(n, _p(u), _p(v), _p(z), _p(rx), _p(ry), W, H, tile, tile_off, idx_off, _p(keys),
                           _p(vals), None)
         keys_l.append(keys); vals_l.append(vals); touched_l.append(touched)
         nt = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)

@@ -25,8 +25,9 @@
  *   if T*(1-alpha) < T_min the fragment is not added and the pixel stops.  Pixel (x, y) is
  *   sampled at (x+0.5, y+0.5).  The 2-D covariance gets `dilation` on its diagonal.  x/z and
  *   y/z inside the Jacobian are clamped to +-clamp_fov * (W/2)/fx (resp. H, fy).  A
- *   Gaussian is culled when z <= near_z, det <= 0 or o < alpha_min.  Its screen radius is
- *   ceil(sqrt(2 ln(o/alpha_min) * lambda_max)), the distance beyond which alpha < alpha_min.
+ *   Gaussian is culled when z <= near_z, det <= 0 or o < alpha_min.  Its screen box has
+ *   half-extents ceil(sqrt(tau Sigma'_xx)), ceil(sqrt(tau Sigma'_yy)), tau = 2 ln(o/alpha_min):
+ *   the bounding box of the ellipse outside which alpha < alpha_min.
  *   rgb = max(0, sum_k sh_k Y_k(dir) + 0.5) with dir = normalize(mu - camera centre).
  */
 #include <math.h>
@@ -57,7 +58,7 @@ typedef struct {
     double *conic;     /* [3n] inverse of cov2d, (A, B, C) */
     double *opacity;   /* sigmoid(logit) */
     double *rgb;       /* [3n] */
-    int32_t *radius;   /* ceil of the alpha_min radius, 0 if culled */
+    int32_t *rx, *ry;  /* half-extents (px) of the alpha >= alpha_min box, 0 if culled */
     int32_t *fragile;  /* 1 if a cull decision lies within a relative 1e-5 of its threshold */
 } or_proj;
 
@@ -184,8 +185,8 @@ typedef struct {
     double dirraw[3], dnorm, dir[3];
     double Y[16], rgb_pre[3], rgb[3];
     int rgb_clamped[3];
-    double radius_real;
-    int32_t radius;
+    double tau;            /* 2 ln(o / alpha_min): alpha >= alpha_min  <=>  d^T conic d <= tau */
+    int32_t rx, ry;
 } proj1;
 
 static void project_one(const double *mu, const double *ls, const double *q, double logit,
@@ -240,12 +241,12 @@ static void project_one(const double *mu, const double *ls, const double *q, dou
     P->o = 1.0 / (1.0 + exp(-logit));
     if (fabs(P->o - opt->alpha_min) <= 1e-5 * opt->alpha_min) P->fragile = 1;
     if (P->o < opt->alpha_min) { P->culled = 1; return; }
-    /* screen radius: alpha >= alpha_min only within sqrt(2 ln(o/alpha_min) lambda_max) */
-    const double mid = 0.5 * (cov[0] + cov[3]);
-    const double lmax = mid + sqrt(fmax(0.0, mid * mid - P->det));
-    P->radius_real = sqrt(2.0 * log(P->o / opt->alpha_min) * lmax);
-    P->radius = (int32_t)ceil(P->radius_real);
-    if (P->radius <= 0) { P->culled = 1; return; }
+    /* alpha >= alpha_min only inside the ellipse d^T conic d <= tau; its bounding box has
+     * half-extents sqrt(tau * cov_xx) and sqrt(tau * cov_yy) (support function of an ellipse) */
+    P->tau = 2.0 * log(P->o / opt->alpha_min);
+    P->rx = (int32_t)ceil(sqrt(P->tau * cov[0]));
+    P->ry = (int32_t)ceil(sqrt(P->tau * cov[3]));
+    if (P->rx <= 0 || P->ry <= 0) { P->culled = 1; return; }
     P->u = cam->fx * x / z + cam->cx;
     P->v = cam->fy * y / z + cam->cy;
     /* SH colour along the viewing direction */
@@ -286,7 +287,8 @@ void or_project(int64_t n, int deg, const double *means, const double *log_scale
         project_one(mu, s, q, lg, shc, deg, cam, opt, &P);
         out->fragile[i] = P.fragile;
         out->visible[i] = !P.culled;
-        out->radius[i] = P.culled ? 0 : P.radius;
+        out->rx[i] = P.culled ? 0 : P.rx;
+        out->ry[i] = P.culled ? 0 : P.ry;
         out->u[i] = P.u; out->v[i] = P.v; out->z[i] = P.pc[2];
         out->opacity[i] = P.o;
         for (int k = 0; k < 3; k++) {
@@ -341,8 +343,8 @@ static double frag_alpha(const or_proj *pr, int64_t g, double px, double py, con
  * this pixel (alpha vs alpha_min, T(1-alpha) vs T_min, alpha vs the alpha_max clamp, the
  * depth order of two added neighbours, a cull decision of an added Gaussian) lies within a
  * relative `margin` of its threshold, so that a correct FP32 implementation may take the
- * other branch.  Gaussians whose screen square does not contain the pixel centre are
- * skipped: outside the square alpha < alpha_min by construction of the radius (tested). */
+ * other branch.  Gaussians whose screen box (half-extents rx, ry) does not contain the pixel
+ * centre are skipped: outside the box alpha < alpha_min by construction (tested). */
 void or_render(int64_t n, const or_proj *pr, const or_camera *cam, const or_opts *opt,
                double margin, int use_square, double *C, double *D, double *T_out,
                int32_t *n_frag, int32_t *fragile_px) {
@@ -360,8 +362,7 @@ void or_render(int64_t n, const or_proj *pr, const or_camera *cam, const or_opts
             for (int64_t k = 0; k < m; k++) {
                 const int64_t g = order[k];
                 if (use_square) {
-                    const double r = pr->radius[g];
-                    if (fabs(cx - pr->u[g]) > r + 1e-9 || fabs(cy - pr->v[g]) > r + 1e-9) continue;
+                    if (fabs(cx - pr->u[g]) > pr->rx[g] + 1e-9 || fabs(cy - pr->v[g]) > pr->ry[g] + 1e-9) continue;
                 }
                 double a0;
                 const double a = frag_alpha(pr, g, cx, cy, opt, NULL, NULL, NULL, &a0);
@@ -465,8 +466,7 @@ void or_render_backward(int64_t n, const or_proj *pr, const or_camera *cam, cons
                 for (int64_t k = 0; k < m; k++) {
                     const int64_t g = order[k];
                     if (use_square) {
-                        const double r = pr->radius[g];
-                        if (fabs(cx - pr->u[g]) > r + 1e-9 || fabs(cy - pr->v[g]) > r + 1e-9) continue;
+                        if (fabs(cx - pr->u[g]) > pr->rx[g] + 1e-9 || fabs(cy - pr->v[g]) > pr->ry[g] + 1e-9) continue;
                     }
                     double G, dx, dy, a0;
                     const double a = frag_alpha(pr, g, cx, cy, opt, &G, &dx, &dy, &a0);
@@ -680,9 +680,9 @@ void or_adam(int64_t n, int n_planes, double *p, const double *g, double *m, dou
 /* ------------------------------------------------------------------------------------ */
 /* Binning: (tile, depth) keys.  Inputs are the FP32 screen-space records; every         */
 /* decision is taken in FP32 exactly as defined here, so the keys are unique bits.       */
-/*   covered tiles: x in [floor((u - r)/T), floor((u + r)/T)] clamped to the grid, same  */
-/*   for y; key = ((tile_offset + ty*tiles_x + tx) << 32) | bits(z); value = idx_offset + i */
-/* Emission order is i ascending, tiles row-major.                                       */
+/*   covered tiles: x in [floor((u - rx)/T), floor((u + rx)/T)] clamped to the grid,     */
+/*   y likewise with ry; key = ((tile_offset + ty*tiles_x + tx) << 32) | bits(z);        */
+/*   value = idx_offset + i.  Emission order is i ascending, tiles row-major.            */
 /* ------------------------------------------------------------------------------------ */
 static int tile_span(float c, int32_t r, int tile, int ntiles, int *lo, int *hi) {
     const float rf = (float)r;
@@ -697,16 +697,16 @@ static int tile_span(float c, int32_t r, int tile, int ntiles, int *lo, int *hi)
     return *hi >= *lo;
 }
 
-int64_t or_bin_view(int64_t n, const float *u, const float *v, const float *z,
-                    const int32_t *radius, int W, int H, int tile, int64_t tile_offset,
-                    int64_t idx_offset, uint64_t *keys, uint32_t *vals, uint32_t *touched) {
+int64_t or_bin_view(int64_t n, const float *u, const float *v, const float *z, const int32_t *rx,
+                    const int32_t *ry, int W, int H, int tile, int64_t tile_offset, int64_t idx_offset,
+                    uint64_t *keys, uint32_t *vals, uint32_t *touched) {
     const int tx_n = (W + tile - 1) / tile, ty_n = (H + tile - 1) / tile;
     int64_t P = 0;
     for (int64_t i = 0; i < n; i++) {
         int x0, x1, y0, y1;
         uint32_t cnt = 0;
-        if (radius[i] > 0 && tile_span(u[i], radius[i], tile, tx_n, &x0, &x1) &&
-            tile_span(v[i], radius[i], tile, ty_n, &y0, &y1)) {
+        if (rx[i] > 0 && ry[i] > 0 && tile_span(u[i], rx[i], tile, tx_n, &x0, &x1) &&
+            tile_span(v[i], ry[i], tile, ty_n, &y0, &y1)) {
             uint32_t zb;
             memcpy(&zb, &z[i], 4);
             for (int ty = y0; ty <= y1; ty++)

@@ -112,10 +112,10 @@ __global__ void __launch_bounds__(256) emit_kernel(BinArgs a) {
         const int v = (int)(idx / a.n);
         const View& V = a.views[v];
         const float4 r0 = a.proj[3 * idx];
-        const float4 r1 = a.proj[3 * idx + 1];
-        const int radius = __float_as_int(r1.w);
+        const int rx = __float_as_int(a.proj[3 * idx + 1].w);
+        const int ry = __float_as_int(a.proj[3 * idx + 2].w);
         int x0, x1, y0, y1;
-        if (!tile_span(r0.x, radius, a.tile, V.tiles_x, x0, x1) || !tile_span(r0.y, radius, a.tile, V.tiles_y, y0, y1))
+        if (!tile_span(r0.x, rx, a.tile, V.tiles_x, x0, x1) || !tile_span(r0.y, ry, a.tile, V.tiles_y, y0, y1))
             continue;
         const unsigned long long zb = (unsigned long long)__float_as_uint(r0.z);
         uint32_t off = a.offsets[idx];
@@ -154,19 +154,26 @@ __device__ __forceinline__ void chunk_span(const Counters* c, int grid, int b, i
 }
 
 __global__ void __launch_bounds__(kSortThreads) sort_upsweep_kernel(SortArgs a, int in_buf, int shift) {
-    __shared__ uint32_t h[kSortBins];
+    // one private histogram per warp keeps shared-memory atomics on a digit to one warp
+    __shared__ uint32_t h[kSortThreads / 32][kSortBins];
     if (a.counters->status != 0) return;
-    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) h[d] = 0;
+    for (int t = threadIdx.x; t < (kSortThreads / 32) * kSortBins; t += blockDim.x) (&h[0][0])[t] = 0;
     __syncthreads();
     int64_t lo, hi;
     chunk_span(a.counters, a.grid, blockIdx.x, lo, hi);
     const unsigned long long* keys = a.keys[in_buf];
+    uint32_t* hw = h[threadIdx.x >> 5];
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
         const uint32_t d = (uint32_t)(keys[j] >> shift) & (kSortBins - 1);
-        atomicAdd(&h[d], 1u);
+        atomicAdd(&hw[d], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) a.hist[(int64_t)d * a.grid + blockIdx.x] = h[d];
+    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; w++) s += h[w][d];
+        a.hist[(int64_t)d * a.grid + blockIdx.x] = s;
+    }
 }
 
 // One block of 1024 threads: per digit (one warp per 8 digits) exclusive prefix over the

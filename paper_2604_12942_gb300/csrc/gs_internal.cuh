@@ -50,22 +50,38 @@ struct Opts {
 __device__ __forceinline__ void set_status(Counters* c, uint32_t s) { atomicCAS(&c->status, 0u, s); }
 
 // ---------------------------------------------------------------------------------------
-// Compositing exponent: alpha = o * 2^e with e = A' dx^2 + C' dy^2 + B' dx dy, where
-// (A', B', C') = -log2(e) * (A/2, B, C/2) for the inverse covariance [[A, B], [B, C]].
-// The forward and the backward kernels call exactly this sequence of correctly rounded
-// operations, so both take the same skip / stop decisions.
+// Compositing exponent.  The record stores the inverse 2-D covariance [[A, B], [B, C]]
+// scaled by k = -log2(e)/2, (a, b, c) = k (A, B, C), so that alpha = o * 2^e with
+//   h_x = a dx + b dy,  h_y = b dx + c dy,  e = dx h_x + dy h_y  (= -q/2 * log2(e)).
+// (h_x, h_y) is also -1/2 of de/d(u, v), which the backward reuses.  The forward and the
+// backward kernels call exactly this sequence of correctly rounded operations, so both take
+// the same skip / stop decisions.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ float frag_exponent(float dx, float dy, float A, float B, float C) {
-    float e = __fmul_rn(__fmul_rn(A, dx), dx);
-    e = __fmaf_rn(__fmul_rn(C, dy), dy, e);
-    e = __fmaf_rn(__fmul_rn(B, dx), dy, e);
-    return e;
+struct FragE {
+    float hx, hy, e;
+};
+
+__device__ __forceinline__ FragE frag_exponent(float dx, float dy, float a, float b, float c) {
+    FragE f;
+    f.hx = __fmaf_rn(a, dx, __fmul_rn(b, dy));
+    f.hy = __fmaf_rn(c, dy, __fmul_rn(b, dx));
+    f.e = __fmaf_rn(dx, f.hx, __fmul_rn(dy, f.hy));
+    return f;
 }
+
+constexpr float kConicScale = -0.5f * kLog2e;
 
 // 2^x by the hardware ex2 instruction (flush-to-zero for tiny results).
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/x by the hardware rcp instruction.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
@@ -218,7 +234,7 @@ struct ProjV {
     float det;
     float o;
     float u, v;
-    int radius;
+    int rx, ry;          // half-extents of the alpha >= alpha_min box (pixels)
 };
 
 __device__ __forceinline__ void project_view(const float* mu, const Cov3& cv, float logit, const View& V,
@@ -262,13 +278,15 @@ __device__ __forceinline__ void project_view(const float* mu, const Cov3& cv, fl
     P.det = P.a * P.c - P.b * P.b;
     P.o = 1.0f / (1.0f + expf(-logit));
     const bool opaque = P.o >= op.alpha_min;
-    const float hd = 0.5f * (P.a - P.c);
-    const float lmax = 0.5f * (P.a + P.c) + sqrtf(hd * hd + P.b * P.b);
-    const float r2 = 2.0f * logf(fmaxf(P.o, op.alpha_min) / op.alpha_min) * lmax;
-    P.radius = (front && P.det > 0.f && opaque && r2 > 0.f) ? (int)ceilf(sqrtf(r2)) : 0;
+    // alpha >= alpha_min only inside d^T Sigma'^-1 d <= tau, tau = 2 ln(o / alpha_min), whose
+    // bounding box has half-extents sqrt(tau Sigma'_xx), sqrt(tau Sigma'_yy)
+    const float tau = 2.0f * logf(fmaxf(P.o, op.alpha_min) / op.alpha_min);
+    const bool ok = front && P.det > 0.f && opaque && tau > 0.f;
+    P.rx = ok ? (int)ceilf(fminf(sqrtf(tau * P.a), 1e9f)) : 0;
+    P.ry = ok ? (int)ceilf(fminf(sqrtf(tau * P.c), 1e9f)) : 0;
     P.u = V.fx * x * iz + V.cx;
     P.v = V.fy * y * iz + V.cy;
-    P.culled = !(front && P.det > 0.f && opaque && P.radius > 0);
+    P.culled = !(ok && P.rx > 0 && P.ry > 0);
 }
 
 template <typename T>

@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
         uint32_t touched = 0;
         if (!P.culled) {
             int x0, x1, y0, y1;
-            if (tile_span(P.u, P.radius, op.tile, V.tiles_x, x0, x1) &&
-                tile_span(P.v, P.radius, op.tile, V.tiles_y, y0, y1))
+            if (tile_span(P.u, P.rx, op.tile, V.tiles_x, x0, x1) &&
+                tile_span(P.v, P.ry, op.tile, V.tiles_y, y0, y1))
                 touched = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
         }
         if (touched) {
@@ -54,8 +54,8 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
             }
             float4* rec = a.proj + 3 * idx;
             rec[0] = make_float4(P.u, P.v, P.pc[2], P.o);
-            rec[1] = make_float4(-0.5f * kLog2e * A, -kLog2e * B, -0.5f * kLog2e * C, __int_as_float(P.radius));
-            rec[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+            rec[1] = make_float4(kConicScale * A, kConicScale * B, kConicScale * C, __int_as_float(P.rx));
+            rec[2] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(P.ry));
             vis = true;
         }
         a.touched[idx] = touched;
@@ -65,12 +65,15 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 
 // Backward of the projection.  Screen-space sums per (view, Gaussian) come from the
 // backward compositing kernel (see render.cu for their definition):
-//   r0 = (sum h (2A'dx + B'dy), sum h (B'dx + 2C'dy), sum h dx^2, sum h dx dy)
+//   r0 = (sum h h_x, sum h h_y, sum h dx^2, sum h dx dy)
 //   r1 = (sum h dy^2, dL/do, dL/dz, 0), r2 = (dL/dr, dL/dg, dL/db, 0)
-// with h = dL/dalpha * o * G.  Pose: xi = (rho, phi), T_cw <- Exp(xi) T_cw, so
+// with h = dL/dalpha * o * G and e = dx h_x + dy h_y.  Since dalpha/de = ln2 o G and
+// de/du = -2 h_x, de/dv = -2 h_y, de/dA = k dx^2, de/dB = 2 k dx dy, de/dC = k dy^2
+// (k = -log2(e)/2, ln2 log2(e) = 1): dL/du = -2 ln2 r0.x, dL/dv = -2 ln2 r0.y,
+// dL/dA = -r0.z / 2, dL/dB = -r0.w, dL/dC = -r1.x / 2.  Pose: xi = (rho, phi), T_cw <- Exp(xi) T_cw, so
 // dp_c = rho + phi x p_c, dW = [phi]x W and the camera centre moves by -W^T rho.
 template <int DEG>
-__global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdArgs a) {
+__global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdArgs a) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ float s_tw[GS_MAX_VIEWS * 6];
     for (int t = threadIdx.x; t < a.n_views * 6; t += blockDim.x) s_tw[t] = 0.f;
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(ProjectBwdArgs a) {
             const float4 r0 = gr[0], r1 = gr[1], r2 = gr[2];
             const float* W = V.R;
             // screen-space gradients
-            const float gu = -kLn2 * r0.x, gv = -kLn2 * r0.y;
+            const float gu = -2.f * kLn2 * r0.x, gv = -2.f * kLn2 * r0.y;
             const float gA = -0.5f * r0.z, gB = -r0.w, gC = -0.5f * r1.x;
             g_o += r1.y;
             float g_pc[3] = {0.f, 0.f, r1.z};

@@ -3,7 +3,7 @@
 // standard alpha compositing, depth D = sum z_i T_i alpha_i with the same weights, loss
 // lambda_rgb L_rgb + lambda_depth L_depth over the mask (SSIM weight 0).
 //
-// One CTA per (view, tile) work item, one thread per pixel.  The tile's depth-sorted pair
+// One CTA per (view, tile) work item, one or two pixels per thread.  The tile's depth-sorted pair
 // list is walked in chunks staged in shared memory (records gathered once per chunk by
 // the whole CTA); the inner loop then reads broadcast shared memory only.
 #include "gs_kernels.cuh"
@@ -71,14 +71,73 @@ cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int
 }
 
 // ----------------------------------------------------------------------------------------
+// Work decomposition shared by the forward and the backward compositing kernels.
+//
+// A CTA owns one (view, tile) item.  Each warp owns an 8 x (4 PPT) pixel sub-region of the
+// tile and each lane PPT pixels of it, (x, y + 4q) for q < PPT with x = lane % 8,
+// y = lane / 8.  The CTA stages CHUNK records of the tile's list in shared memory; every
+// warp then walks the chunk and skips, warp-uniformly, every Gaussian whose
+// alpha >= alpha_min box misses its sub-region (outside the box alpha < alpha_min, so
+// nothing is lost).  The forward uses one pixel per thread (its per-fragment work is small,
+// occupancy matters more); the backward two, which halves its warp reductions per pixel.
+// ----------------------------------------------------------------------------------------
+constexpr int kFwdPPT = 1;
+constexpr int kBwdPPT = 2;
+
+template <int TILE, int PPT>
+struct TileMap {
+    static constexpr int NT = TILE * TILE / PPT;    // threads per CTA
+    static constexpr int WX = TILE / 8;             // warp regions per tile row
+    static constexpr int RH = 4 * PPT;              // warp region height
+};
+
+// Bit r of the result is set when the record's alpha >= alpha_min box overlaps warp region
+// r of the tile whose top-left pixel is (X0, Y0).  Computed once per staged record by the
+// thread that stages it; warps then test one bit per fragment.
+template <int TILE, int PPT>
+__device__ __forceinline__ uint32_t region_mask(float u, float v, float rx, float ry, float X0, float Y0) {
+    using TM = TileMap<TILE, PPT>;
+    uint32_t cols = 0, rows = 0;
+#pragma unroll
+    for (int c = 0; c < TM::WX; c++) {
+        const float x0 = X0 + 8.f * c;
+        if (u - rx <= x0 + 7.5f && u + rx >= x0 + 0.5f) cols |= 1u << c;
+    }
+#pragma unroll
+    for (int r = 0; r < TILE / TM::RH; r++) {
+        const float y0 = Y0 + (float)(TM::RH * r);
+        if (v - ry <= y0 + ((float)TM::RH - 0.5f) && v + ry >= y0 + 0.5f) rows |= 1u << r;
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int r = 0; r < TILE / TM::RH; r++)
+        if (rows & (1u << r)) m |= cols << (r * TM::WX);
+    return m;
+}
+
+__device__ __forceinline__ void load_record(const float4* proj, uint32_t gid, float2& uv, float4& co, float4& cz,
+                                            float& rx, float& ry) {
+    const float4* r = proj + 3 * (size_t)gid;
+    const float4 f0 = __ldg(r), f1 = __ldg(r + 1), f2 = __ldg(r + 2);
+    uv = make_float2(f0.x, f0.y);
+    co = make_float4(f1.x, f1.y, f1.z, f0.w);
+    cz = make_float4(f2.x, f2.y, f2.z, f0.z);
+    rx = (float)__float_as_int(f1.w);
+    ry = (float)__float_as_int(f2.w);
+}
+
+// ----------------------------------------------------------------------------------------
 // Forward compositing.
 // ----------------------------------------------------------------------------------------
 template <int TILE, int CHUNK>
-__global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(FwdArgs a) {
-    constexpr int NT = TILE * TILE;
+__global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(FwdArgs a) {
+    constexpr int kPPT = kFwdPPT;
+    using TM = TileMap<TILE, kPPT>;
+    constexpr int NT = TM::NT;
     __shared__ float2 s_uv[CHUNK];
-    __shared__ float4 s_co[CHUNK];   // A', B', C', opacity
+    __shared__ float4 s_co[CHUNK];   // a, b, c, opacity
     __shared__ float4 s_cz[CHUNK];   // r, g, b, z
+    __shared__ uint32_t s_mask[CHUNK];
     __shared__ double s_red[2][NT / 32];
     if (a.counters->status != 0) return;
     const int gt = blockIdx.x;
@@ -86,68 +145,86 @@ __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(FwdArgs a) {
     const View& V = a.views[v];
     const int lt = gt - V.tile_off;
     const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-    const int x = tx * TILE + (threadIdx.x % TILE), y = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = x < V.W && y < V.H;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int rx0 = tx * TILE + (w % TM::WX) * 8, ry0 = ty * TILE + (w / TM::WX) * TM::RH;
+    int x[kPPT], y[kPPT];
+    bool inside[kPPT], done[kPPT];
+    float T[kPPT], c0[kPPT], c1[kPPT], c2[kPPT], dep[kPPT];
+    uint32_t last[kPPT];
+#pragma unroll
+    for (int q = 0; q < kPPT; q++) {
+        x[q] = rx0 + (lane & 7);
+        y[q] = ry0 + (lane >> 3) + 4 * q;
+        inside[q] = x[q] < V.W && y[q] < V.H;
+        done[q] = !inside[q];
+        T[q] = 1.f; c0[q] = c1[q] = c2[q] = dep[q] = 0.f;
+        last[q] = 0;
+    }
     const uint2 rg = a.ranges[gt];
     const int n = (int)(rg.y - rg.x);
     const float amin = a.op.alpha_min, amax = a.op.alpha_max, tmin = a.op.T_min;
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
     for (int base = 0; base < n; base += CHUNK) {
-        if (__syncthreads_count(!done) == 0) break;
+        bool alive = false;
+#pragma unroll
+        for (int q = 0; q < kPPT; q++) alive |= !done[q];
+        if (__syncthreads_count(alive) == 0) break;
         for (int k = threadIdx.x; k < CHUNK; k += NT) {
             const int j = base + k;
             if (j < n) {
-                const uint32_t gid = a.vals[rg.x + j];
-                const float4* r = a.proj + 3 * (size_t)gid;
-                const float4 f0 = __ldg(r), f1 = __ldg(r + 1), f2 = __ldg(r + 2);
-                s_uv[k] = make_float2(f0.x, f0.y);
-                s_co[k] = make_float4(f1.x, f1.y, f1.z, f0.w);
-                s_cz[k] = make_float4(f2.x, f2.y, f2.z, f0.z);
+                float2 uv;
+                float rxf, ryf;
+                load_record(a.proj, a.vals[rg.x + j], uv, s_co[k], s_cz[k], rxf, ryf);
+                s_uv[k] = uv;
+                s_mask[k] = region_mask<TILE, kPPT>(uv.x, uv.y, rxf, ryf, (float)(tx * TILE), (float)(ty * TILE));
             }
         }
         __syncthreads();
-        if (!done) {
+        if (__any_sync(0xffffffffu, alive)) {
             const int m = min(CHUNK, n - base);
             for (int k = 0; k < m; k++) {
+                if (!((s_mask[k] >> w) & 1u)) continue;
                 const float2 uv = s_uv[k];
                 const float4 co = s_co[k];
-                const float dx = px - uv.x, dy = py - uv.y;
-                const float G = ex2_approx(frag_exponent(dx, dy, co.x, co.y, co.z));
-                const float alpha = fminf(amax, co.w * G);
-                if (alpha < amin) continue;
-                const float test_T = T * (1.f - alpha);
-                if (test_T < tmin) {
-                    done = true;
-                    break;
+#pragma unroll
+                for (int q = 0; q < kPPT; q++) {
+                    if (done[q]) continue;
+                    const float dx = ((float)x[q] + 0.5f) - uv.x, dy = ((float)y[q] + 0.5f) - uv.y;
+                    const float G = ex2_approx(frag_exponent(dx, dy, co.x, co.y, co.z).e);
+                    const float alpha = fminf(amax, co.w * G);
+                    if (alpha < amin) continue;
+                    const float test_T = T[q] * (1.f - alpha);
+                    if (test_T < tmin) {
+                        done[q] = true;
+                        continue;
+                    }
+                    const float wgt = alpha * T[q];
+                    const float4 cz = s_cz[k];
+                    c0[q] = fmaf(wgt, cz.x, c0[q]);
+                    c1[q] = fmaf(wgt, cz.y, c1[q]);
+                    c2[q] = fmaf(wgt, cz.z, c2[q]);
+                    dep[q] = fmaf(wgt, cz.w, dep[q]);
+                    T[q] = test_T;
+                    last[q] = (uint32_t)(base + k + 1);
                 }
-                const float w = alpha * T;
-                const float4 cz = s_cz[k];
-                c0 = fmaf(w, cz.x, c0);
-                c1 = fmaf(w, cz.y, c1);
-                c2 = fmaf(w, cz.z, c2);
-                dep = fmaf(w, cz.w, dep);
-                T = test_T;
-                last = (uint32_t)(base + k + 1);
             }
         }
     }
     double lr = 0.0, ld = 0.0;
-    if (inside) {
+#pragma unroll
+    for (int q = 0; q < kPPT; q++) {
+        if (!inside[q]) continue;
         const int64_t P = (int64_t)V.W * V.H;
-        const int64_t p = (int64_t)y * V.W + x;
+        const int64_t p = (int64_t)y[q] * V.W + x[q];
         const int64_t g = V.pix_off + p;
-        const float o0 = c0 + T * a.op.bg0, o1 = c1 + T * a.op.bg1, o2 = c2 + T * a.op.bg2;
+        const float o0 = c0[q] + T[q] * a.op.bg0, o1 = c1[q] + T[q] * a.op.bg1, o2 = c2[q] + T[q] * a.op.bg2;
         float* rgb = a.out_rgb + 3 * V.pix_off;
         rgb[p] = o0;
         rgb[P + p] = o1;
         rgb[2 * P + p] = o2;
-        a.out_depth[g] = dep;
-        if (a.out_T) a.out_T[g] = T;
-        a.T_final[g] = T;
-        a.n_contrib[g] = last;
+        a.out_depth[g] = dep[q];
+        if (a.out_T) a.out_T[g] = T[q];
+        a.T_final[g] = T[q];
+        a.n_contrib[g] = last[q];
         if (a.tgt_rgb) {
             const bool in = a.mask ? a.mask[g] != 0 : true;
             const float cm = (float)a.loss_counts[2 * v], cd = (float)a.loss_counts[2 * v + 1];
@@ -159,14 +236,14 @@ __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(FwdArgs a) {
             dl[p] = krgb * (float)((r0 > 0.f) - (r0 < 0.f));
             dl[P + p] = krgb * (float)((r1 > 0.f) - (r1 < 0.f));
             dl[2 * P + p] = krgb * (float)((r2 > 0.f) - (r2 < 0.f));
-            if (in) lr = (double)fabsf(r0) + (double)fabsf(r1) + (double)fabsf(r2);
+            if (in) lr += (double)fabsf(r0) + (double)fabsf(r1) + (double)fabsf(r2);
             if (a.dl_ddepth) {
                 const float td = a.tgt_depth ? a.tgt_depth[g] : 0.f;
                 const bool ind = in && td > 0.f;
                 const float kd = (ind && cd > 0.f) ? a.op.lambda_depth * inv_v / cd : 0.f;
-                const float rd = dep - td;
+                const float rd = dep[q] - td;
                 a.dl_ddepth[g] = kd * (float)((rd > 0.f) - (rd < 0.f));
-                if (ind) ld = (double)fabsf(rd);
+                if (ind) ld += (double)fabsf(rd);
             }
         }
     }
@@ -177,8 +254,7 @@ __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(FwdArgs a) {
             lr += __shfl_xor_sync(0xffffffffu, lr, o);
             ld += __shfl_xor_sync(0xffffffffu, ld, o);
         }
-        const int w = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0) { s_red[0][w] = lr; s_red[1][w] = ld; }
+        if (lane == 0) { s_red[0][w] = lr; s_red[1][w] = ld; }
         __syncthreads();
         if (threadIdx.x == 0) {
             double sr = 0, sd = 0;
@@ -199,15 +275,14 @@ __global__ void __launch_bounds__(TILE* TILE) render_fwd_kernel(FwdArgs a) {
 // with S_i = g_C.bg T_final + sum_{j>i} (g_C.c_j + g_D z_j) w_j (one running scalar).
 // If o G < alpha_max (the clamp is inactive), alpha = o 2^e gives dalpha/do = G and
 // dalpha/de = ln2 o G.  Per (view, Gaussian) the kernel accumulates, with h = dL/dalpha o G:
-//   r0 = (sum h (2A'dx + B'dy), sum h (B'dx + 2C'dy), sum h dx^2, sum h dx dy)
+//   r0 = (sum h h_x, sum h h_y, sum h dx^2, sum h dx dy)
 //   r1 = (sum h dy^2, sum dL/dalpha G, sum g_D w, 0), r2 = (sum g_C w, 0)
-// and the projection backward applies the constant factors (ln2, -log2 e / 2, ...).
-// Lanes of a warp walk the same list position; their 10 values are summed with a
-// transpose-reduce (16 shuffles) and written by 10 lanes with one atomic each.
+// (h_x, h_y from frag_exponent) and the projection backward applies the constant factors.
+// A lane first sums its two pixels; the warp's 10 sums are then reduced with a transpose
+// reduction (16 shuffles) and written by 10 lanes with one atomic each.
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ void warp_transpose_reduce10(float (&v)[16], float& out) {
     const int lane = threadIdx.x & 31;
-    // 16 -> 8 (partner lane ^ 16)
     {
         const bool hi = lane & 16;
 #pragma unroll
@@ -246,12 +321,15 @@ __device__ __forceinline__ void warp_transpose_reduce10(float (&v)[16], float& o
 }
 
 template <int TILE, int CHUNK>
-__global__ void __launch_bounds__(TILE* TILE) render_bwd_kernel(BwdArgs a) {
-    constexpr int NT = TILE * TILE;
+__global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(BwdArgs a) {
+    constexpr int kPPT = kBwdPPT;
+    using TM = TileMap<TILE, kPPT>;
+    constexpr int NT = TM::NT;
     __shared__ float2 s_uv[CHUNK];
     __shared__ float4 s_co[CHUNK];
     __shared__ float4 s_cz[CHUNK];
     __shared__ uint32_t s_id[CHUNK];
+    __shared__ uint32_t s_mask[CHUNK];
     __shared__ uint32_t s_max;
     if (a.counters->status != 0) return;
     const int gt = blockIdx.x;
@@ -259,86 +337,95 @@ __global__ void __launch_bounds__(TILE* TILE) render_bwd_kernel(BwdArgs a) {
     const View& V = a.views[v];
     const int lt = gt - V.tile_off;
     const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-    const int x = tx * TILE + (threadIdx.x % TILE), y = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = x < V.W && y < V.H;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int rx0 = tx * TILE + (w % TM::WX) * 8, ry0 = ty * TILE + (w / TM::WX) * TM::RH;
     const uint2 rg = a.ranges[gt];
     const float amin = a.op.alpha_min, amax = a.op.alpha_max;
-    float T = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gd = 0.f;
-    uint32_t last = 0;
-    if (inside) {
-        const int64_t P = (int64_t)V.W * V.H;
-        const int64_t p = (int64_t)y * V.W + x;
-        const int64_t g = V.pix_off + p;
-        T = a.T_final[g];
-        last = a.n_contrib[g];
-        const float* d = a.dl_drgb + 3 * V.pix_off;
-        gc0 = d[p];
-        gc1 = d[P + p];
-        gc2 = d[2 * P + p];
-        gd = a.dl_ddepth ? a.dl_ddepth[g] : 0.f;
-        if (gc0 == 0.f && gc1 == 0.f && gc2 == 0.f && gd == 0.f) last = 0;
+    float px[kPPT], py[kPPT], T[kPPT], S[kPPT], gc0[kPPT], gc1[kPPT], gc2[kPPT], gd[kPPT];
+    uint32_t last[kPPT];
+    uint32_t mylast = 0;
+#pragma unroll
+    for (int q = 0; q < kPPT; q++) {
+        const int xi = rx0 + (lane & 7), yi = ry0 + (lane >> 3) + 4 * q;
+        px[q] = (float)xi + 0.5f;
+        py[q] = (float)yi + 0.5f;
+        T[q] = 0.f; gc0[q] = gc1[q] = gc2[q] = gd[q] = 0.f;
+        last[q] = 0;
+        if (xi < V.W && yi < V.H) {
+            const int64_t P = (int64_t)V.W * V.H;
+            const int64_t p = (int64_t)yi * V.W + xi;
+            const int64_t g = V.pix_off + p;
+            T[q] = a.T_final[g];
+            last[q] = a.n_contrib[g];
+            const float* d = a.dl_drgb + 3 * V.pix_off;
+            gc0[q] = d[p];
+            gc1[q] = d[P + p];
+            gc2[q] = d[2 * P + p];
+            gd[q] = a.dl_ddepth ? a.dl_ddepth[g] : 0.f;
+            if (gc0[q] == 0.f && gc1[q] == 0.f && gc2[q] == 0.f && gd[q] == 0.f) last[q] = 0;
+        }
+        S[q] = (gc0[q] * a.op.bg0 + gc1[q] * a.op.bg1 + gc2[q] * a.op.bg2) * T[q];
+        mylast = max(mylast, last[q]);
     }
-    float S = (gc0 * a.op.bg0 + gc1 * a.op.bg1 + gc2 * a.op.bg2) * T;
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
-    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&s_max, wmax);
+    const uint32_t wtop = __reduce_max_sync(0xffffffffu, mylast);
+    if (lane == 0 && wtop) atomicMax(&s_max, wtop);
     __syncthreads();
     const int top_all = (int)s_max;
-    const int lane = threadIdx.x & 31;
     for (int top = top_all; top > 0; top -= CHUNK) {
         const int lo = max(0, top - CHUNK);
         __syncthreads();
         for (int k = threadIdx.x; k < top - lo; k += NT) {
             const uint32_t gid = a.vals[rg.x + lo + k];
-            const float4* r = a.proj + 3 * (size_t)gid;
-            const float4 f0 = __ldg(r), f1 = __ldg(r + 1), f2 = __ldg(r + 2);
-            s_uv[k] = make_float2(f0.x, f0.y);
-            s_co[k] = make_float4(f1.x, f1.y, f1.z, f0.w);
-            s_cz[k] = make_float4(f2.x, f2.y, f2.z, f0.z);
+            float2 uv;
+            float rxf, ryf;
+            load_record(a.proj, gid, uv, s_co[k], s_cz[k], rxf, ryf);
+            s_uv[k] = uv;
+            s_mask[k] = region_mask<TILE, kPPT>(uv.x, uv.y, rxf, ryf, (float)(tx * TILE), (float)(ty * TILE));
             s_id[k] = gid;
         }
         __syncthreads();
-        // highest list position any lane of this warp still needs
-        const uint32_t wtop = __reduce_max_sync(0xffffffffu, last);
         const int jstart = min(top, (int)wtop) - 1;
         for (int j = jstart; j >= lo; j--) {
             const int k = j - lo;
+            if (!((s_mask[k] >> w) & 1u)) continue;
+            const float2 bx = s_uv[k];
+            const float4 co = s_co[k];
             float val[16];
 #pragma unroll
             for (int q = 0; q < 16; q++) val[q] = 0.f;
             bool contrib = false;
-            if ((uint32_t)j < last) {
-                const float2 uv = s_uv[k];
-                const float4 co = s_co[k];
-                const float dx = px - uv.x, dy = py - uv.y;
-                const float G = ex2_approx(frag_exponent(dx, dy, co.x, co.y, co.z));
+#pragma unroll
+            for (int q = 0; q < kPPT; q++) {
+                if ((uint32_t)j >= last[q]) continue;
+                const float dx = px[q] - bx.x, dy = py[q] - bx.y;
+                const FragE fe = frag_exponent(dx, dy, co.x, co.y, co.z);
+                const float G = ex2_approx(fe.e);
                 const float a0 = co.w * G;
                 const float alpha = fminf(amax, a0);
-                if (alpha >= amin) {
-                    contrib = true;
-                    const float om = 1.f - alpha;
-                    const float rom = __frcp_rn(om);
-                    T = T * rom;
-                    const float w = alpha * T;
-                    const float4 cz = s_cz[k];
-                    const float gcz = gc0 * cz.x + gc1 * cz.y + gc2 * cz.z + gd * cz.w;
-                    const float dLda = T * gcz - S * rom;
-                    S = fmaf(gcz, w, S);
-                    val[7] = gc0 * w;
-                    val[8] = gc1 * w;
-                    val[9] = gc2 * w;
-                    val[6] = gd * w;
-                    if (a0 < amax) {
-                        const float h = dLda * a0;
-                        val[0] = h * (2.f * co.x * dx + co.y * dy);
-                        val[1] = h * (co.y * dx + 2.f * co.z * dy);
-                        val[2] = h * dx * dx;
-                        val[3] = h * dx * dy;
-                        val[4] = h * dy * dy;
-                        val[5] = dLda * G;
-                    }
+                if (alpha < amin) continue;
+                contrib = true;
+                const float rom = rcp_approx(1.f - alpha);
+                T[q] = T[q] * rom;
+                const float wgt = alpha * T[q];
+                const float4 cz = s_cz[k];
+                const float gcz = gc0[q] * cz.x + gc1[q] * cz.y + gc2[q] * cz.z + gd[q] * cz.w;
+                const float dLda = T[q] * gcz - S[q] * rom;
+                S[q] = fmaf(gcz, wgt, S[q]);
+                val[7] = fmaf(gc0[q], wgt, val[7]);
+                val[8] = fmaf(gc1[q], wgt, val[8]);
+                val[9] = fmaf(gc2[q], wgt, val[9]);
+                val[6] = fmaf(gd[q], wgt, val[6]);
+                if (a0 < amax) {
+                    const float h = dLda * a0;
+                    const float hdx = h * dx;
+                    val[0] = fmaf(h, fe.hx, val[0]);
+                    val[1] = fmaf(h, fe.hy, val[1]);
+                    val[2] = fmaf(hdx, dx, val[2]);
+                    val[3] = fmaf(hdx, dy, val[3]);
+                    val[4] = fmaf(h * dy, dy, val[4]);
+                    val[5] = fmaf(dLda, G, val[5]);
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
@@ -358,10 +445,10 @@ __global__ void __launch_bounds__(TILE* TILE) render_bwd_kernel(BwdArgs a) {
 template <int TILE>
 static cudaError_t launch_fwd_t(const FwdArgs& a, int total_tiles, int chunk, cudaStream_t st) {
     switch (chunk) {
-        case 32: render_fwd_kernel<TILE, 32><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
-        case 64: render_fwd_kernel<TILE, 64><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
-        case 128: render_fwd_kernel<TILE, 128><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
-        default: render_fwd_kernel<TILE, 256><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+        case 32: render_fwd_kernel<TILE, 32><<<total_tiles, TileMap<TILE, kFwdPPT>::NT, 0, st>>>(a); break;
+        case 64: render_fwd_kernel<TILE, 64><<<total_tiles, TileMap<TILE, kFwdPPT>::NT, 0, st>>>(a); break;
+        case 128: render_fwd_kernel<TILE, 128><<<total_tiles, TileMap<TILE, kFwdPPT>::NT, 0, st>>>(a); break;
+        default: render_fwd_kernel<TILE, 256><<<total_tiles, TileMap<TILE, kFwdPPT>::NT, 0, st>>>(a); break;
     }
     return cudaGetLastError();
 }
@@ -369,10 +456,10 @@ static cudaError_t launch_fwd_t(const FwdArgs& a, int total_tiles, int chunk, cu
 template <int TILE>
 static cudaError_t launch_bwd_t(const BwdArgs& a, int total_tiles, int chunk, cudaStream_t st) {
     switch (chunk) {
-        case 32: render_bwd_kernel<TILE, 32><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
-        case 64: render_bwd_kernel<TILE, 64><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
-        case 128: render_bwd_kernel<TILE, 128><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
-        default: render_bwd_kernel<TILE, 256><<<total_tiles, TILE * TILE, 0, st>>>(a); break;
+        case 32: render_bwd_kernel<TILE, 32><<<total_tiles, TileMap<TILE, kBwdPPT>::NT, 0, st>>>(a); break;
+        case 64: render_bwd_kernel<TILE, 64><<<total_tiles, TileMap<TILE, kBwdPPT>::NT, 0, st>>>(a); break;
+        case 128: render_bwd_kernel<TILE, 128><<<total_tiles, TileMap<TILE, kBwdPPT>::NT, 0, st>>>(a); break;
+        default: render_bwd_kernel<TILE, 256><<<total_tiles, TileMap<TILE, kBwdPPT>::NT, 0, st>>>(a); break;
     }
     return cudaGetLastError();
 }

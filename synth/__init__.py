@@ -342,18 +342,22 @@ def trajectory_cameras(scene: Scene, sizes, idx, fx_per_width=0.7, pitch_deg=5.0
 def random_projected_items(seed, cams, n, radius_max=48, zero_frac=0.2, tie_frac=0.3,
                            margin=60.0):
     """Synthetic per-(view, Gaussian) screen-space records for binning tests: float32 centre
-    (u, v) uniform over the image +- margin, integer radius (0 for a fraction), float32
-    depth with deliberate exact ties.  Returns a list (one per view) of dicts."""
+    (u, v) uniform over the image +- margin, integer half-extents rx, ry (both 0 for a
+    fraction), float32 depth with deliberate exact ties.  Returns a list (one per view) of
+    dicts."""
     rng = np.random.default_rng(seed)
     out = []
     for c in cams:
         W, H = c["width"], c["height"]
         u = rng.uniform(-margin, W + margin, n).astype(np.float32)
         v = rng.uniform(-margin, H + margin, n).astype(np.float32)
-        r = np.minimum(rng.geometric(0.12, n), radius_max).astype(np.int32)
-        r[rng.uniform(0, 1, n) < zero_frac] = 0
+        rx = np.minimum(rng.geometric(0.12, n), radius_max).astype(np.int32)
+        ry = np.minimum(rng.geometric(0.12, n), radius_max).astype(np.int32)
+        zero = rng.uniform(0, 1, n) < zero_frac
+        rx[zero] = 0
+        ry[zero] = 0
         z = rng.uniform(0.2, 80.0, n).astype(np.float32)
         tie = rng.uniform(0, 1, n) < tie_frac
         z[tie] = np.float32(np.round(rng.uniform(0.5, 5.0, int(tie.sum())), 1))
-        out.append(dict(u=u, v=v, z=z, radius=r))
+        out.append(dict(u=u, v=v, z=z, rx=rx, ry=ry))
     return out

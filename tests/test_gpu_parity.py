@@ -72,15 +72,16 @@ def test_project_matches_oracle(deg):
         np.testing.assert_allclose(r[:, 1], pr["v"][sel], atol=2e-3, rtol=0)
         np.testing.assert_allclose(r[:, 2], pr["z"][sel], rtol=2e-6)
         np.testing.assert_allclose(r[:, 3], pr["opacity"][sel], rtol=2e-6)
-        # conic from the scaled record: (A', B', C') = -log2(e) (A/2, B, C/2)
-        l2e = 1.0 / math.log(2.0)
-        conic = np.stack([r[:, 4] / (-0.5 * l2e), r[:, 5] / -l2e, r[:, 6] / (-0.5 * l2e)], 1)
+        # conic from the scaled record: (a, b, c) = -log2(e)/2 (A, B, C)
+        k = -0.5 / math.log(2.0)
+        conic = r[:, 4:7] / k
         scale = np.abs(pr["conic"][sel]).max(1, keepdims=True)
         assert np.max(np.abs(conic - pr["conic"][sel]) / scale) < 2e-4
         np.testing.assert_allclose(r[:, 8:11], pr["rgb"][sel], atol=2e-5)
-        rad = np.ascontiguousarray(r[:, 7]).view(np.int32)
-        assert np.all(np.abs(rad - pr["radius"][sel]) <= 1)
-        assert np.mean(rad == pr["radius"][sel]) > 0.99
+        for col, key in ((7, "rx"), (11, "ry")):
+            rad = np.ascontiguousarray(r[:, col]).view(np.int32)
+            assert np.all(np.abs(rad - pr[key][sel]) <= 1)
+            assert np.mean(rad == pr[key][sel]) > 0.99
 
 
 # ----------------------------------------------------------------------------------------
@@ -97,7 +98,8 @@ def _bin_case(cams, n, tile, seed, radius_max=48):
     rec = np.zeros((V, n, 12), np.float32)
     for v, it in enumerate(items):
         rec[v, :, 0] = it["u"]; rec[v, :, 1] = it["v"]; rec[v, :, 2] = it["z"]; rec[v, :, 3] = 0.5
-        rec[v, :, 7] = it["radius"].view(np.float32)
+        rec[v, :, 7] = it["rx"].view(np.float32)
+        rec[v, :, 11] = it["ry"].view(np.float32)
     ws.region("proj", torch.float32, 12 * V * n).copy_(torch.as_tensor(rec.reshape(-1)))
     ws.region("touched", torch.int32, V * n).copy_(torch.as_tensor(ref["touched"].astype(np.int32)))
     ws.region("counters", torch.int32, 8).zero_()
@@ -121,7 +123,7 @@ def test_bin_sort_bit_exact_small(tile):
 def test_bin_sort_bit_exact_multichunk():
     """More than 2.5M pairs: every block of the sort grid owns several chunks, ragged tail."""
     cams = [synth.camera(1280, 720, 900.0), synth.camera(640, 480, 500.0)]
-    P = _bin_case(cams, 200_000, 8, seed=4, radius_max=64)
+    P = _bin_case(cams, 300_000, 8, seed=4, radius_max=64)
     assert P > 2_500_000
 
 

@@ -86,7 +86,7 @@ def test_projection_on_axis_isotropic_closed_form():
     assert pr["u"][0] == pytest.approx(160.0) and pr["v"][0] == pytest.approx(120.0)
     o = 1 / (1 + math.exp(-2.0))
     r = math.ceil(math.sqrt(2 * math.log(255 * o) * var))
-    assert pr["radius"][0] == r
+    assert pr["rx"][0] == r and pr["ry"][0] == r
     np.testing.assert_allclose(pr["rgb"][0], [0.2, 0.6, 0.9], rtol=1e-13)
 
 
@@ -211,10 +211,11 @@ def test_depth_order_swaps_contributions():
     np.testing.assert_allclose(B["C"][:, px[0], px[1]], c2 * b2 + c1 * b1 * (1 - b2), atol=1e-12)
 
 
-def test_radius_square_bounds_every_kept_fragment():
-    """Outside a Gaussian's screen square alpha < alpha_min, so restricting each pixel to
-    the Gaussians whose square contains it changes nothing (the tiled GPU path relies on
-    this): brute force over all Gaussians equals the restricted form exactly."""
+def test_screen_box_bounds_every_kept_fragment():
+    """Outside a Gaussian's screen box (half-extents rx, ry) alpha < alpha_min, so
+    restricting each pixel to the Gaussians whose box contains it changes nothing (the tiled
+    GPU path relies on this): brute force over all Gaussians equals the restricted form
+    exactly, and alpha just outside each box edge is below alpha_min."""
     sc = synth.uniform_box_scene(4, 400, sh_degree=1)
     cam = synth.camera(80, 60, 70.0)
     pr = oracle.project(sc, cam)
@@ -223,11 +224,16 @@ def test_radius_square_bounds_every_kept_fragment():
     for k in ("C", "D", "T"):
         np.testing.assert_array_equal(a[k], b[k])
     # and directly: alpha at pixel centres just outside the square
-    for g in np.nonzero(pr["visible"])[0][:100]:
-        r = pr["radius"][g]
-        for dx, dy in ((r + 0.01, 0), (0, -r - 0.01), (r + 0.01, r + 0.01)):
-            A, B, Cq = pr["conic"][g]
-            q = A * dx * dx + 2 * B * dx * dy + Cq * dy * dy
+    for g in np.nonzero(pr["visible"])[0][:200]:
+        rx, ry = pr["rx"][g], pr["ry"][g]
+        A, B, Cq = pr["conic"][g]
+        # the largest alpha on the lines x = +-(rx + eps), y = +-(ry + eps) (closed-form minimum
+        # of the quadratic form along each line) stays below alpha_min
+        for dx in (rx + 0.01, -rx - 0.01):
+            q = dx * dx * (A - B * B / Cq)
+            assert pr["opacity"][g] * math.exp(-0.5 * q) < 1 / 255
+        for dy in (ry + 0.01, -ry - 0.01):
+            q = dy * dy * (Cq - B * B / A)
             assert pr["opacity"][g] * math.exp(-0.5 * q) < 1 / 255
 
 
@@ -389,19 +395,18 @@ def test_binning_sort_and_ranges():
         tiles = (b["sorted_keys"] >> np.uint64(32)).astype(np.int64)
         counts = np.bincount(tiles, minlength=b["n_tiles"])
         np.testing.assert_array_equal(b["ranges"][:, 1] - b["ranges"][:, 0], counts)
-        # conservative coverage: every pixel centre within the square of an item lies in an
+        # conservative coverage: every pixel centre within the box of an item lies in an
         # emitted tile of that item (brute force over pixels)
         off = 0
         toff = 0
         for it, cam in zip(items, cams):
             W, H = cam["width"], cam["height"]
             tx = (W + tile - 1) // tile
-            sel = np.nonzero(it["radius"] > 0)[0][:200]
+            sel = np.nonzero(it["rx"] > 0)[0][:200]
             for i in sel:
                 emitted = set((b["keys"][b["vals"] == off + i] >> np.uint64(32)).astype(np.int64) - toff)
-                r = it["radius"][i]
                 xs = np.arange(W) + 0.5; ys = np.arange(H) + 0.5
-                X = xs[np.abs(xs - it["u"][i]) <= r]; Y = ys[np.abs(ys - it["v"][i]) <= r]
+                X = xs[np.abs(xs - it["u"][i]) <= it["rx"][i]]; Y = ys[np.abs(ys - it["v"][i]) <= it["ry"][i]]
                 need = {int(y // tile) * tx + int(x // tile) for y in Y for x in X}
                 assert need <= emitted
             off += it["u"].shape[0]

@@ -35,7 +35,8 @@ def _regular_sort(items, cams, tile):
     rec = np.zeros((V, n, 12), np.float32)
     for v, it in enumerate(items):
         rec[v, :, 0] = it["u"]; rec[v, :, 1] = it["v"]; rec[v, :, 2] = it["z"]
-        rec[v, :, 7] = it["radius"].view(np.float32)
+        rec[v, :, 7] = it["rx"].view(np.float32)
+        rec[v, :, 11] = it["ry"].view(np.float32)
     ws.region("proj", torch.float32, 12 * V * n).copy_(torch.as_tensor(rec.reshape(-1)))
     ws.region("touched", torch.int32, V * n).copy_(torch.as_tensor(ref["touched"].astype(np.int32)))
     ws.region("counters", torch.int32, 8).zero_()
