@@ -213,30 +213,33 @@ def run_gpu(args, rank, world):
     stages = ["project", "bin_sort", "render_fwd", "render_bwd", "adam"]
     st = torch.cuda.current_stream()
 
-    def one(evs=None):
+    # per-stage breakdown: the same step as separate C calls, events between them
+    def staged(evs):
         w = step.ws
-        if evs: evs[0].record(st)
+        evs[0].record(st)
         w.project(step.planes, 3)
-        if evs: evs[1].record(st)
+        evs[1].record(st)
         w.bin_sort()
-        if evs: evs[2].record(st)
+        evs[2].record(st)
         w.render_fwd(step.rgb, step.depth, None, trgb, tdep, None, step.dl_drgb, step.dl_ddepth, step.loss)
-        if evs: evs[3].record(st)
+        evs[3].record(st)
         w.render_bwd(step.planes, 3, step.grads, step.dl_drgb, step.dl_ddepth, None)
-        if evs: evs[4].record(st)
-        step.t += 1
-        gs.adam_step(step.planes, step.grads, step.m, step.v, 3, step.t, step.lr, None, w.visible())
-        if evs: evs[5].record(st)
+        evs[4].record(st)
+        gs.adam_step(step.planes, step.grads, step.m, step.v, 3, 1, step.lr, None, w.visible())
+        evs[5].record(st)
 
+    # headline: the batched step captured once as a CUDA graph and replayed
+    for _ in range(2):
+        step(trgb, tdep)
+    step.capture(trgb, tdep)
     for _ in range(args.warmup):
-        one()
+        step.replay()
     torch.cuda.synchronize()
     c = step.ws.counters()
     if c.status != 0:
         raise RuntimeError(f"device status {c.status} (pairs {c.n_pairs}, capacity {cap})")
     n_pairs = int(c.n_pairs)
     loss0 = float(step.loss[-1])
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -245,18 +248,21 @@ def run_gpu(args, rank, world):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(st)
-        for k in range(args.steps):
-            one(evs[k])
+        for _ in range(args.steps):
+            step.replay()
         t1.record(st)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     total_ms = t0.elapsed_time(t1)
-    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
-                for i, s in enumerate(stages)}
-    c = step.ws.counters()
-    # end-to-end through the public API: targets uploaded from pinned host memory every
-    # step and the loss read back
+    loss_end = float(step.loss[-1])
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(max(3, args.steps // 2))]
+    for e in evs:
+        staged(e)
+    torch.cuda.synchronize()
+    stage_ms = {s: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, s in enumerate(stages)}
+    # end-to-end through the public API (eager gs_step): targets uploaded from pinned host
+    # memory every step and the loss read back
     h_rgb = trgb.cpu().pin_memory()
     h_dep = tdep.cpu().pin_memory()
     h_loss = torch.empty(len(cams) + 1).pin_memory()
@@ -276,23 +282,40 @@ def run_gpu(args, rank, world):
         h_loss.copy_(step.loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e_dt = (time.perf_counter() - e0) / e_steps
+    # what the end-to-end time is made of: the eager step on the device, the target upload
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(st)
+    for _ in range(e_steps):
+        step(trgb, tdep)
+    eb.record(st)
+    torch.cuda.synchronize()
+    eager_ms = ea.elapsed_time(eb) / e_steps
+    ea.record(st)
+    d_rgb.copy_(h_rgb, non_blocking=True)
+    d_dep.copy_(h_dep, non_blocking=True)
+    eb.record(st)
+    torch.cuda.synchronize()
+    h2d_ms = ea.elapsed_time(eb)
     px = sum(w * h for w, h in SIZES)
-    return dict(total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=float(step.loss[-1]),
-                tune=tune,
+    adam_steps = int(step.ws.counters().adam_step)
+    step.release()
+    return dict(total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=loss_end,
+                tune=tune, adam_steps=adam_steps, eager_ms=eager_ms, h2d_ms=h2d_ms,
                 clocks=clk.summary(), e2e_s=e_dt, px=px, h2d=int(h_rgb.numel() * 4 + h_dep.numel() * 4),
                 d2h=int(h_loss.numel() * 4), sc=sc, cams=cams, trgb=trgb, tdep=tdep, n=n,
                 kernels=kernels_per_step(step.ws.layout))
 
 
 def kernels_per_step(L):
+    """Kernels one gs_step launches (the graph replays exactly these)."""
     tiles = L.total_tiles
     tb = 0
     while (1 << tb) < tiles:
         tb += 1
     passes = 4 + (tb + 7) // 8
-    # project: views + project; bin_sort: views + 3 scan + emit + 3 per pass + ranges;
-    # fwd: views + count + composite + finalize; bwd: views + composite bwd + projection bwd; adam
-    return 2 + (1 + 3 + 1 + 3 * passes + 1) + 4 + 3 + 1
+    # view table, project, 3 scan + emit, 3 per radix pass, ranges, loss count + composite +
+    # loss finalize, composite backward + projection backward, Adam counter + Adam
+    return 1 + 1 + 4 + 3 * passes + 1 + 3 + 2 + 2
 
 
 def main():
@@ -334,8 +357,9 @@ def main():
         "loss": [round(r["loss0"], 6), round(r["loss_end"], 6)],
         "roofline": roof, "clocks": r["clocks"],
         "e2e": {"value": round(r["px"] / r["e2e_s"] / 1e6, 2), "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
-                "d2h_bytes_per_step": r["d2h"]},
-        "gpu_launches": r["kernels"] * args.steps,
+                "d2h_bytes_per_step": r["d2h"], "ms_per_step": round(1e3 * r["e2e_s"], 3),
+                "eager_device_ms_per_step": round(r["eager_ms"], 3), "h2d_ms_per_step": round(r["h2d_ms"], 3)},
+        "gpu_launches": r["kernels"] * args.steps, "timed": "CUDA-graph replay of gs_step",
         "autotune": r["tune"],
     }
     if not args.no_cpu_baseline and world == 1:

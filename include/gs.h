@@ -133,7 +133,26 @@ typedef struct {
     uint32_t status;     /* gs_status of the device work since the last reset */
     uint32_t reserved;
     uint64_t n_pairs;    /* (tile, Gaussian) pairs of the last gs_bin_sort */
+    uint64_t adam_step;  /* Adam steps taken by gs_step / a captured graph */
 } gs_counters;
+
+/* Inputs and outputs of one batched step (gs_step / gs_graph_create).  Device pointers,
+ * packed per view as for gs_render_fwd. */
+typedef struct {
+    const float *target_rgb;    /* [3*P] required */
+    const float *target_depth;  /* [P] or NULL (no depth term) */
+    const uint8_t *mask;        /* [P] or NULL (all pixels) */
+    float *out_rgb, *out_depth; /* [3*P], [P] rendered colour and depth */
+    float *dl_drgb, *dl_ddepth; /* [3*P], [P] dL/dC, dL/dD (dl_ddepth needed with target_depth) */
+    float *loss_out;            /* [n_views + 1] per-view loss terms and their mean */
+    float *grad_twist;          /* [n_views][6] or NULL; zeroed, then the pose gradients */
+    const uint8_t *update_mask; /* [n] or NULL: rows allowed to change (unfrozen segments) */
+    float lr[6];                /* means, log-scales, quats, opacity, SH DC, SH rest */
+    float b1, b2, eps;
+    int32_t optimize;           /* 0: stop after the backward (gradients left in grads) */
+} gs_step_io;
+
+typedef struct gs_graph_s *gs_graph;
 
 void gs_default_opts(gs_render_opts *opts);
 const char *gs_last_error(void);
@@ -151,6 +170,9 @@ gs_status gs_workspace_layout(int64_t n, int32_t n_views, const gs_camera *cams,
 
 /* Copies the device counters into *out (host memory); synchronises `stream`. */
 gs_status gs_read_counters(const gs_ws_layout *L, const void *ws, gs_counters *out, void *stream);
+/* Clears the device counters (status, pair count, the Adam step of gs_step).  Call once after
+ * allocating a workspace (asynchronous on `stream`). */
+gs_status gs_workspace_init(const gs_ws_layout *L, void *ws, void *stream);
 
 /* a1 -- EWA projection with SH colour (§III-C "standard differentiable Gaussian splatting";
  * tile-based rasterizer of §II-A).  For every view v and Gaussian i: q = q/|q| -> R,
@@ -211,6 +233,29 @@ gs_status gs_render_bwd(const gs_gaussians *g, const gs_camera *cams, const gs_r
 gs_status gs_adam_step(gs_gaussians *params, gs_gaussians *grads, gs_gaussians *m, gs_gaussians *v,
                        const uint8_t *update_mask, const uint8_t *visible, const float lr[6],
                        float b1, float b2, float eps, int64_t step, void *stream);
+
+/* a9 -- The batched mapping step (§III-C: each iteration samples keyframes from the recent and
+ * history windows and updates the visible, unfrozen Gaussians): gs_project, gs_bin_sort,
+ * gs_render_fwd with the fused L1 loss, gs_render_bwd and, if io->optimize, the masked Adam
+ * step, for every view of the batch, on one stream without host synchronisation.  Gradients
+ * are accumulated into `grads` and zeroed again by the Adam step.  The Adam step counter is a
+ * device counter in the workspace (gs_workspace_init sets it to 0), so the sequence can be
+ * captured once and replayed. */
+gs_status gs_step(gs_gaussians *params, gs_gaussians *grads, gs_gaussians *m, gs_gaussians *v,
+                  const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L, void *ws,
+                  const gs_step_io *io, void *stream);
+
+/* CUDA graph of one gs_step, captured on `stream` (must not be the legacy default stream).
+ * All pointers are baked into the graph; write new targets into the same buffers.  New poses
+ * (same image sizes) go in with gs_graph_set_cameras, which rewrites the by-value camera
+ * argument of the captured view-table upload -- no re-capture.  The handle owns only host
+ * and driver objects; gs_graph_destroy releases them. */
+gs_status gs_graph_create(gs_graph *out, gs_gaussians *params, gs_gaussians *grads, gs_gaussians *m,
+                          gs_gaussians *v, const gs_camera *cams, const gs_render_opts *opts,
+                          const gs_ws_layout *L, void *ws, const gs_step_io *io, void *stream);
+gs_status gs_graph_launch(gs_graph g, void *stream);
+gs_status gs_graph_set_cameras(gs_graph g, const gs_camera *cams);
+gs_status gs_graph_destroy(gs_graph g);
 
 /* Allocation-free sort (the paper has no counterpart; it is a service of this library).
  * Stable LSD radix sort of n (key, value) pairs by the low key_bits bits of the key (8 bits

@@ -42,7 +42,15 @@ class WsLayout(C.Structure):
 
 
 class Counters(C.Structure):
-    _fields_ = [("status", C.c_uint32), ("reserved", C.c_uint32), ("n_pairs", C.c_uint64)]
+    _fields_ = [("status", C.c_uint32), ("reserved", C.c_uint32), ("n_pairs", C.c_uint64), ("adam_step", C.c_uint64)]
+
+
+class StepIO(C.Structure):
+    _fields_ = [("target_rgb", C.c_void_p), ("target_depth", C.c_void_p), ("mask", C.c_void_p),
+                ("out_rgb", C.c_void_p), ("out_depth", C.c_void_p), ("dl_drgb", C.c_void_p), ("dl_ddepth", C.c_void_p),
+                ("loss_out", C.c_void_p), ("grad_twist", C.c_void_p), ("update_mask", C.c_void_p),
+                ("lr", C.c_float * 6), ("b1", C.c_float), ("b2", C.c_float), ("eps", C.c_float),
+                ("optimize", C.c_int32)]
 
 
 class GsError(RuntimeError):
@@ -61,6 +69,15 @@ _SIGS = {
     "gs_workspace_layout": ([C.c_int64, C.c_int32, C.POINTER(Camera), C.POINTER(RenderOpts), C.c_int64,
                              C.POINTER(WsLayout)], C.c_int),
     "gs_read_counters": ([C.POINTER(WsLayout), C.c_void_p, C.POINTER(Counters), C.c_void_p], C.c_int),
+    "gs_workspace_init": ([C.POINTER(WsLayout), C.c_void_p, C.c_void_p], C.c_int),
+    "gs_step": ([C.POINTER(Gaussians)] * 4 + [C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout),
+                                              C.c_void_p, C.POINTER(StepIO), C.c_void_p], C.c_int),
+    "gs_graph_create": ([C.POINTER(C.c_void_p)] + [C.POINTER(Gaussians)] * 4 +
+                        [C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.POINTER(StepIO),
+                         C.c_void_p], C.c_int),
+    "gs_graph_launch": ([C.c_void_p, C.c_void_p], C.c_int),
+    "gs_graph_set_cameras": ([C.c_void_p, C.POINTER(Camera)], C.c_int),
+    "gs_graph_destroy": ([C.c_void_p], C.c_int),
     "gs_project": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p,
                     C.c_void_p], C.c_int),
     "gs_bin_sort": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.c_void_p], C.c_int),

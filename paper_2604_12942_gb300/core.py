@@ -103,6 +103,7 @@ class Workspace:
         assert self.buf.data_ptr() % 256 == 0
         self.n = int(n)
         self.V = len(cams)
+        N.check(N.lib().gs_workspace_init(C.byref(self.layout), _ptr(self.buf), _stream()), "gs_workspace_init")
 
     def set_cameras(self, cams):
         """New poses (same image sizes) for the next calls."""
@@ -170,16 +171,17 @@ class StepResult:
     loss: torch.Tensor          # [V + 1] device: per-view terms and their mean
     rgb: torch.Tensor
     depth: torch.Tensor
-    n_pairs: int | None = None
 
 
 class MappingStep:
-    """One optimisation step of the Gaussian map over a batch of keyframes: project, tile
-    sort, composite with the fused L1 loss, backward (with pose twists) and masked Adam --
-    each stage one C call, all views of the batch in each launch."""
+    """One optimisation step of the Gaussian map over a batch of keyframes (gs_step): project,
+    tile sort, composite with the fused L1 loss, backward (with pose twists) and masked Adam,
+    all views of the batch in each launch, one C call.  `capture()` records the step as a
+    CUDA graph (gs_graph_create) and `replay()` launches it; `set_cameras()` changes the
+    poses of a captured graph without re-capturing."""
 
     def __init__(self, planes: torch.Tensor, sh_degree: int, cams, opts: N.RenderOpts | None = None,
-                 max_pairs: int | None = None, lr=LR_DEFAULT):
+                 max_pairs: int | None = None, lr=LR_DEFAULT, b1=0.9, b2=0.999, eps=1e-15):
         self.planes = planes
         self.sh_degree = sh_degree
         self.opts = opts or default_opts()
@@ -196,22 +198,66 @@ class MappingStep:
         self.dl_ddepth = torch.empty(P, device=dev)
         self.loss = torch.zeros(len(cams) + 1, device=dev)
         self.twist = torch.zeros(len(cams), 6, device=dev)
-        self.lr = lr
-        self.t = 0
+        self.lr, self.b1, self.b2, self.eps = tuple(lr), b1, b2, eps
+        self._structs = [gaussians_struct(t, sh_degree) for t in (self.planes, self.grads, self.m, self.v)]
+        self.graph = None
+        self._graph_io = None
+
+    def _io(self, target_rgb, target_depth, mask, update_mask, optimize, with_twist):
+        io = N.StepIO()
+        io.target_rgb, io.target_depth = target_rgb.data_ptr(), (target_depth.data_ptr() if target_depth is not None else None)
+        io.mask = mask.data_ptr() if mask is not None else None
+        io.out_rgb, io.out_depth = self.rgb.data_ptr(), self.depth.data_ptr()
+        io.dl_drgb, io.dl_ddepth = self.dl_drgb.data_ptr(), self.dl_ddepth.data_ptr()
+        io.loss_out = self.loss.data_ptr()
+        io.grad_twist = self.twist.data_ptr() if with_twist else None
+        io.update_mask = update_mask.data_ptr() if update_mask is not None else None
+        io.lr = (C.c_float * 6)(*self.lr)
+        io.b1, io.b2, io.eps = self.b1, self.b2, self.eps
+        io.optimize = 1 if optimize else 0
+        return io
 
     def __call__(self, target_rgb, target_depth=None, mask=None, update_mask=None, optimize=True,
                  with_twist=False) -> StepResult:
-        ws = self.ws
-        ws.project(self.planes, self.sh_degree)
-        ws.bin_sort()
-        ws.render_fwd(self.rgb, self.depth, None, target_rgb, target_depth, mask, self.dl_drgb,
-                      self.dl_ddepth if target_depth is not None else None, self.loss)
-        if with_twist:
-            self.twist.zero_()
-        ws.render_bwd(self.planes, self.sh_degree, self.grads, self.dl_drgb,
-                      self.dl_ddepth if target_depth is not None else None, self.twist if with_twist else None)
-        if optimize:
-            self.t += 1
-            adam_step(self.planes, self.grads, self.m, self.v, self.sh_degree, self.t, self.lr, update_mask,
-                      ws.visible())
+        io = self._io(target_rgb, target_depth, mask, update_mask, optimize, with_twist)
+        gp, gg, gm, gv = self._structs
+        N.check(N.lib().gs_step(C.byref(gp), C.byref(gg), C.byref(gm), C.byref(gv), self.ws.cams_c,
+                                C.byref(self.opts), C.byref(self.ws.layout), _ptr(self.ws.buf), C.byref(io), _stream()),
+                "gs_step")
         return StepResult(self.loss, self.rgb, self.depth)
+
+    def capture(self, target_rgb, target_depth=None, mask=None, update_mask=None, optimize=True, with_twist=False):
+        """Record one step as a CUDA graph (inputs are read from these buffers at replay)."""
+        self.release()
+        io = self._io(target_rgb, target_depth, mask, update_mask, optimize, with_twist)
+        self._graph_io = (io, target_rgb, target_depth, mask, update_mask)
+        side = torch.cuda.Stream(device=self.planes.device)
+        side.wait_stream(torch.cuda.current_stream())
+        h = C.c_void_p()
+        gp, gg, gm, gv = self._structs
+        N.check(N.lib().gs_graph_create(C.byref(h), C.byref(gp), C.byref(gg), C.byref(gm), C.byref(gv),
+                                        self.ws.cams_c, C.byref(self.opts), C.byref(self.ws.layout), _ptr(self.ws.buf),
+                                        C.byref(io), C.c_void_p(side.cuda_stream)), "gs_graph_create")
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = h
+
+    def replay(self) -> StepResult:
+        N.check(N.lib().gs_graph_launch(self.graph, _stream()), "gs_graph_launch")
+        return StepResult(self.loss, self.rgb, self.depth)
+
+    def set_cameras(self, cams):
+        """New poses (same image sizes) for the eager step and for a captured graph."""
+        self.ws.set_cameras(cams)
+        if self.graph is not None:
+            N.check(N.lib().gs_graph_set_cameras(self.graph, self.ws.cams_c), "gs_graph_set_cameras")
+
+    def release(self):
+        if self.graph is not None:
+            N.lib().gs_graph_destroy(self.graph)
+            self.graph = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass

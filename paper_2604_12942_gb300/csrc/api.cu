@@ -199,6 +199,238 @@ static gs_status geometry_for(const gs_ws_layout* L, const gs_camera* cams, cons
     return GS_OK;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Stage runners: launch sequences without argument checks or camera upload.  The public
+// entry points (and gs_step) validate, upload the view table, then call these.
+// ---------------------------------------------------------------------------------------
+static cudaError_t run_project(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                               cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(at<Counters>(ws, L->counters), 0, kCountersResetBytes, st);
+    if (e != cudaSuccess) return e;
+    ProjectArgs a;
+    a.n = g->n;
+    a.n_views = L->n_views;
+    a.views = at<View>(ws, L->views);
+    a.op = to_opts(opts);
+    a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats; a.logits = g->opacity_logits; a.sh = g->sh;
+    a.proj = at<float4>(ws, L->proj);
+    a.touched = at<uint32_t>(ws, L->touched);
+    a.visible = at<uint8_t>(ws, L->visible);
+    return launch_project(a, g->sh_degree, st);
+}
+
+static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* L, void* ws, cudaStream_t st) {
+    Counters* cnt = at<Counters>(ws, L->counters);
+    BinArgs b;
+    b.n = L->n;
+    b.n_views = L->n_views;
+    b.views = at<View>(ws, L->views);
+    b.tile = opts->tile;
+    b.max_pairs = L->max_pairs;
+    b.proj = at<float4>(ws, L->proj);
+    b.touched = at<uint32_t>(ws, L->touched);
+    b.offsets = at<uint32_t>(ws, L->offsets);
+    b.scan_tmp = at<uint32_t>(ws, L->scan_tmp);
+    b.keys = at<unsigned long long>(ws, L->keys0);
+    b.vals = at<uint32_t>(ws, L->vals0);
+    b.counters = cnt;
+    cudaError_t e = launch_bin(b, st);
+    if (e != cudaSuccess) return e;
+    SortArgs sa;
+    sa.keys[0] = at<unsigned long long>(ws, L->keys0);
+    sa.keys[1] = at<unsigned long long>(ws, L->keys1);
+    sa.vals[0] = at<uint32_t>(ws, L->vals0);
+    sa.vals[1] = at<uint32_t>(ws, L->vals1);
+    sa.grid = sort_grid();
+    if (sa.grid > 4096) sa.grid = 4096;
+    sa.hist = at<uint32_t>(ws, L->sort_tmp);
+    sa.digit_tot = sa.hist + (size_t)kSortBins * 4096;
+    sa.counters = cnt;
+    int shifts[16];
+    const int np = sort_passes(L->total_tiles, shifts);
+    if ((e = launch_sort(sa, np, shifts, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(at<uint32_t>(ws, L->ranges), 0, sizeof(uint32_t) * 2 * (size_t)L->total_tiles, st)) !=
+        cudaSuccess)
+        return e;
+    RangeArgs r;
+    r.keys = sa.keys[np & 1];
+    r.ranges = at<uint2>(ws, L->ranges);
+    r.counters = cnt;
+    return launch_ranges(r, L->total_tiles, st);
+}
+
+static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
+                           float* out_rgb, float* out_depth, float* out_T, const float* target_rgb,
+                           const float* target_depth, const uint8_t* mask, float* dl_drgb, float* dl_ddepth,
+                           float* loss_out, cudaStream_t st) {
+    double* sums = at<double>(ws, L->loss_acc);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(sums + 2 * GS_MAX_VIEWS);
+    cudaError_t e;
+    if (target_rgb) {
+        if ((e = cudaMemsetAsync(sums, 0, sizeof(double) * 2 * GS_MAX_VIEWS + sizeof(uint32_t) * 2 * GS_MAX_VIEWS, st)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_loss_count(at<View>(ws, L->views), L->n_views, G.pix, target_depth, mask, counts, st)) !=
+            cudaSuccess)
+            return e;
+    }
+    FwdArgs a;
+    a.n_views = L->n_views;
+    a.views = at<View>(ws, L->views);
+    a.op = to_opts(opts);
+    a.proj = at<float4>(ws, L->proj);
+    a.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
+    a.ranges = at<uint2>(ws, L->ranges);
+    a.counters = at<Counters>(ws, L->counters);
+    a.T_final = at<float>(ws, L->T_final);
+    a.n_contrib = at<uint32_t>(ws, L->n_contrib);
+    a.out_rgb = out_rgb;
+    a.out_depth = out_depth;
+    a.out_T = out_T;
+    a.tgt_rgb = target_rgb;
+    a.tgt_depth = target_depth;
+    a.mask = mask;
+    a.dl_drgb = target_rgb ? dl_drgb : nullptr;
+    a.dl_ddepth = target_rgb ? dl_ddepth : nullptr;
+    a.loss_sums = sums;
+    a.loss_counts = counts;
+    if ((e = launch_render_fwd(a, L->total_tiles, st)) != cudaSuccess) return e;
+    if (target_rgb)
+        return launch_loss_finalize(sums, counts, L->n_views, opts->lambda_rgb, opts->lambda_depth,
+                                    target_depth != nullptr, loss_out, st);
+    return cudaSuccess;
+}
+
+static cudaError_t run_bwd(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                           const float* dl_drgb, const float* dl_ddepth, gs_gaussians* grads, float* grad_twist,
+                           cudaStream_t st) {
+    const int64_t VN = (int64_t)L->n_views * L->n;
+    cudaError_t e = cudaMemsetAsync(at<float>(ws, L->grad2d), 0, sizeof(float) * 12 * (size_t)VN, st);
+    if (e != cudaSuccess) return e;
+    BwdArgs b;
+    b.n_views = L->n_views;
+    b.views = at<View>(ws, L->views);
+    b.op = to_opts(opts);
+    b.proj = at<float4>(ws, L->proj);
+    b.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
+    b.ranges = at<uint2>(ws, L->ranges);
+    b.counters = at<Counters>(ws, L->counters);
+    b.T_final = at<float>(ws, L->T_final);
+    b.n_contrib = at<uint32_t>(ws, L->n_contrib);
+    b.dl_drgb = dl_drgb;
+    b.dl_ddepth = dl_ddepth;
+    b.grad2d = at<float4>(ws, L->grad2d);
+    if ((e = launch_render_bwd(b, L->total_tiles, st)) != cudaSuccess) return e;
+    ProjectBwdArgs p;
+    p.n = L->n;
+    p.n_views = L->n_views;
+    p.views = at<View>(ws, L->views);
+    p.op = to_opts(opts);
+    p.means = g->means; p.log_scales = g->log_scales; p.quats = g->quats; p.logits = g->opacity_logits; p.sh = g->sh;
+    p.touched = at<uint32_t>(ws, L->touched);
+    p.grad2d = at<float4>(ws, L->grad2d);
+    p.g_means = grads->means; p.g_log_scales = grads->log_scales; p.g_quats = grads->quats;
+    p.g_logits = grads->opacity_logits; p.g_sh = grads->sh;
+    p.grad_twist = grad_twist;
+    return launch_project_bwd(p, g->sh_degree, st);
+}
+
+static gs_status check_adam(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
+                            const float* lr, float b1, float b2, float eps) {
+    gs_status s;
+    gs_gaussians* all[4] = {params, grads, m, v};
+    for (auto* x : all)
+        if ((s = check_gaussians(x, true)) != GS_OK) return s;
+    for (auto* x : all)
+        if (x->n != params->n || x->sh_degree != params->sh_degree)
+            return fail(GS_ERR_INVALID_ARG, "params / grads / m / v differ in n or sh_degree");
+    if (!lr) return fail(GS_ERR_INVALID_ARG, "lr is NULL");
+    if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps >= 0.f))
+        return fail(GS_ERR_INVALID_ARG, "need 0 <= b1, b2 < 1 and eps >= 0");
+    return GS_OK;
+}
+
+static cudaError_t run_adam(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
+                            const uint8_t* update_mask, const uint8_t* visible, const float* lr, float b1, float b2,
+                            float eps, int64_t step, const Counters* step_dev, cudaStream_t st) {
+    const int K = (params->sh_degree + 1) * (params->sh_degree + 1);
+    AdamArgs a;
+    a.n = params->n;
+    a.n_planes = 11 + 3 * K;
+    gs_gaussians* src[4] = {params, grads, m, v};
+    float** dst[4] = {a.p, a.g, a.m, a.v};
+    for (int k = 0; k < 4; k++) {
+        dst[k][0] = src[k]->means;
+        dst[k][1] = src[k]->log_scales;
+        dst[k][2] = src[k]->quats;
+        dst[k][3] = src[k]->opacity_logits;
+        dst[k][4] = src[k]->sh;
+    }
+    a.planes_of[0] = 3; a.planes_of[1] = 3; a.planes_of[2] = 4; a.planes_of[3] = 1; a.planes_of[4] = 3 * K;
+    a.update_mask = update_mask;
+    a.visible = visible;
+    for (int k = 0; k < 6; k++) a.lr[k] = lr[k];
+    a.b1 = b1; a.b2 = b2; a.eps = eps;
+    a.bc1 = step > 0 ? (float)(1.0 - pow((double)b1, (double)step)) : 1.f;
+    a.bc2 = step > 0 ? (float)(1.0 - pow((double)b2, (double)step)) : 1.f;
+    a.step_dev = step_dev;
+    return launch_adam(a, st);
+}
+
+static gs_status check_step_io(const gs_step_io* io) {
+    if (!io) return fail(GS_ERR_INVALID_ARG, "io is NULL");
+    if (!io->target_rgb || !io->out_rgb || !io->out_depth || !io->dl_drgb || !io->loss_out)
+        return fail(GS_ERR_INVALID_ARG, "target_rgb, out_rgb, out_depth, dl_drgb and loss_out are required");
+    if (io->target_depth && !io->dl_ddepth) return fail(GS_ERR_INVALID_ARG, "the depth loss needs dl_ddepth");
+    return GS_OK;
+}
+
+// The whole step on one stream (no host synchronisation, capturable).
+static gs_status run_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
+                          const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
+                          const gs_step_io* io, cudaStream_t st) {
+    gs_status s;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    GS_CUDA(run_project(params, opts, L, ws, st));
+    GS_CUDA(run_bin_sort(opts, L, ws, st));
+    GS_CUDA(run_fwd(opts, L, G, ws, io->out_rgb, io->out_depth, nullptr, io->target_rgb, io->target_depth, io->mask,
+                    io->dl_drgb, io->target_depth ? io->dl_ddepth : nullptr, io->loss_out, st));
+    if (io->grad_twist) GS_CUDA(cudaMemsetAsync(io->grad_twist, 0, sizeof(float) * 6 * L->n_views, st));
+    GS_CUDA(run_bwd(params, opts, L, ws, io->dl_drgb, io->target_depth ? io->dl_ddepth : nullptr, grads,
+                    io->grad_twist, st));
+    if (io->optimize) {
+        Counters* c = at<Counters>(ws, L->counters);
+        GS_CUDA(launch_adam_step_counter(c, io->b1, io->b2, st));
+        GS_CUDA(run_adam(params, grads, m, v, io->update_mask, at<uint8_t>(ws, L->visible), io->lr, io->b1, io->b2,
+                         io->eps, 0, c, st));
+    }
+    return GS_OK;
+}
+
+static gs_status check_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
+                            const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                            const gs_step_io* io, Geometry& G) {
+    gs_status s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    if ((s = check_step_io(io)) != GS_OK) return s;
+    if ((s = check_adam(params, grads, m, v, io->lr, io->b1, io->b2, io->eps)) != GS_OK) return s;
+    if (params->n != L->n) return fail(GS_ERR_INVALID_ARG, "n does not match the layout");
+    return geometry_for(L, cams, opts, G);
+}
+
+// Captured step: the graph, its executable and the node of the view-table upload, whose
+// by-value camera argument gs_graph_set_cameras rewrites.
+struct GraphState {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t views_node = nullptr;
+    cudaKernelNodeParams views_params;
+    gs_render_opts opts;
+    gs_ws_layout layout;
+    void* ws = nullptr;
+};
+
 // Error recording for entry points defined in other translation units.
 gs_status record_error(gs_status s, const char* msg) { return fail(s, "%s", msg); }
 
@@ -250,6 +482,14 @@ gs_status gs_read_counters(const gs_ws_layout* L, const void* ws, gs_counters* o
     out->status = c.status;
     out->reserved = 0;
     out->n_pairs = c.n_pairs;
+    out->adam_step = c.adam_step;
+    return GS_OK;
+}
+
+gs_status gs_workspace_init(const gs_ws_layout* L, void* ws, void* stream) {
+    gs_status s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    GS_CUDA(cudaMemsetAsync(at<Counters>(ws, L->counters), 0, sizeof(Counters), (cudaStream_t)stream));
     return GS_OK;
 }
 
@@ -263,17 +503,7 @@ gs_status gs_project(const gs_gaussians* g, const gs_camera* cams, const gs_rend
     if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
-    GS_CUDA(cudaMemsetAsync(at<Counters>(ws, L->counters), 0, sizeof(Counters), st));
-    ProjectArgs a;
-    a.n = g->n;
-    a.n_views = L->n_views;
-    a.views = at<View>(ws, L->views);
-    a.op = to_opts(opts);
-    a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats; a.logits = g->opacity_logits; a.sh = g->sh;
-    a.proj = at<float4>(ws, L->proj);
-    a.touched = at<uint32_t>(ws, L->touched);
-    a.visible = at<uint8_t>(ws, L->visible);
-    GS_CUDA(launch_project(a, g->sh_degree, st));
+    GS_CUDA(run_project(g, opts, L, ws, st));
     return GS_OK;
 }
 
@@ -284,40 +514,7 @@ gs_status gs_bin_sort(const gs_camera* cams, const gs_render_opts* opts, const g
     if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
-    Counters* cnt = at<Counters>(ws, L->counters);
-    BinArgs b;
-    b.n = L->n;
-    b.n_views = L->n_views;
-    b.views = at<View>(ws, L->views);
-    b.tile = opts->tile;
-    b.max_pairs = L->max_pairs;
-    b.proj = at<float4>(ws, L->proj);
-    b.touched = at<uint32_t>(ws, L->touched);
-    b.offsets = at<uint32_t>(ws, L->offsets);
-    b.scan_tmp = at<uint32_t>(ws, L->scan_tmp);
-    b.keys = at<unsigned long long>(ws, L->keys0);
-    b.vals = at<uint32_t>(ws, L->vals0);
-    b.counters = cnt;
-    GS_CUDA(launch_bin(b, st));
-    SortArgs sa;
-    sa.keys[0] = at<unsigned long long>(ws, L->keys0);
-    sa.keys[1] = at<unsigned long long>(ws, L->keys1);
-    sa.vals[0] = at<uint32_t>(ws, L->vals0);
-    sa.vals[1] = at<uint32_t>(ws, L->vals1);
-    sa.grid = sort_grid();
-    if (sa.grid > 4096) sa.grid = 4096;
-    sa.hist = at<uint32_t>(ws, L->sort_tmp);
-    sa.digit_tot = sa.hist + (size_t)kSortBins * 4096;
-    sa.counters = cnt;
-    int shifts[16];
-    const int np = sort_passes(G.total_tiles, shifts);
-    GS_CUDA(launch_sort(sa, np, shifts, st));
-    GS_CUDA(cudaMemsetAsync(at<uint32_t>(ws, L->ranges), 0, sizeof(uint32_t) * 2 * (size_t)G.total_tiles, st));
-    RangeArgs r;
-    r.keys = sa.keys[np & 1];
-    r.ranges = at<uint2>(ws, L->ranges);
-    r.counters = cnt;
-    GS_CUDA(launch_ranges(r, G.total_tiles, st));
+    GS_CUDA(run_bin_sort(opts, L, ws, st));
     return GS_OK;
 }
 
@@ -335,36 +532,8 @@ gs_status gs_render_fwd(const gs_camera* cams, const gs_render_opts* opts, const
     if (target_depth && !dl_ddepth) return fail(GS_ERR_INVALID_ARG, "the depth loss needs dl_ddepth");
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
-    double* sums = at<double>(ws, L->loss_acc);
-    uint32_t* counts = reinterpret_cast<uint32_t*>(sums + 2 * GS_MAX_VIEWS);
-    if (target_rgb) {
-        GS_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 2 * GS_MAX_VIEWS + sizeof(uint32_t) * 2 * GS_MAX_VIEWS, st));
-        GS_CUDA(launch_loss_count(at<View>(ws, L->views), L->n_views, G.pix, target_depth, mask, counts, st));
-    }
-    FwdArgs a;
-    a.n_views = L->n_views;
-    a.views = at<View>(ws, L->views);
-    a.op = to_opts(opts);
-    a.proj = at<float4>(ws, L->proj);
-    a.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
-    a.ranges = at<uint2>(ws, L->ranges);
-    a.counters = at<Counters>(ws, L->counters);
-    a.T_final = at<float>(ws, L->T_final);
-    a.n_contrib = at<uint32_t>(ws, L->n_contrib);
-    a.out_rgb = out_rgb;
-    a.out_depth = out_depth;
-    a.out_T = out_T;
-    a.tgt_rgb = target_rgb;
-    a.tgt_depth = target_depth;
-    a.mask = mask;
-    a.dl_drgb = target_rgb ? dl_drgb : nullptr;
-    a.dl_ddepth = target_rgb ? dl_ddepth : nullptr;
-    a.loss_sums = sums;
-    a.loss_counts = counts;
-    GS_CUDA(launch_render_fwd(a, G.total_tiles, st));
-    if (target_rgb)
-        GS_CUDA(launch_loss_finalize(sums, counts, L->n_views, opts->lambda_rgb, opts->lambda_depth,
-                                     target_depth != nullptr, loss_out, st));
+    GS_CUDA(run_fwd(opts, L, G, ws, out_rgb, out_depth, out_T, target_rgb, target_depth, mask, dl_drgb, dl_ddepth,
+                    loss_out, st));
     return GS_OK;
 }
 
@@ -382,34 +551,7 @@ gs_status gs_render_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_r
     if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
-    const int64_t VN = (int64_t)L->n_views * L->n;
-    GS_CUDA(cudaMemsetAsync(at<float>(ws, L->grad2d), 0, sizeof(float) * 12 * (size_t)VN, st));
-    BwdArgs b;
-    b.n_views = L->n_views;
-    b.views = at<View>(ws, L->views);
-    b.op = to_opts(opts);
-    b.proj = at<float4>(ws, L->proj);
-    b.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
-    b.ranges = at<uint2>(ws, L->ranges);
-    b.counters = at<Counters>(ws, L->counters);
-    b.T_final = at<float>(ws, L->T_final);
-    b.n_contrib = at<uint32_t>(ws, L->n_contrib);
-    b.dl_drgb = dl_drgb;
-    b.dl_ddepth = dl_ddepth;
-    b.grad2d = at<float4>(ws, L->grad2d);
-    GS_CUDA(launch_render_bwd(b, G.total_tiles, st));
-    ProjectBwdArgs p;
-    p.n = L->n;
-    p.n_views = L->n_views;
-    p.views = at<View>(ws, L->views);
-    p.op = to_opts(opts);
-    p.means = g->means; p.log_scales = g->log_scales; p.quats = g->quats; p.logits = g->opacity_logits; p.sh = g->sh;
-    p.touched = at<uint32_t>(ws, L->touched);
-    p.grad2d = at<float4>(ws, L->grad2d);
-    p.g_means = grads->means; p.g_log_scales = grads->log_scales; p.g_quats = grads->quats;
-    p.g_logits = grads->opacity_logits; p.g_sh = grads->sh;
-    p.grad_twist = grad_twist;
-    GS_CUDA(launch_project_bwd(p, g->sh_degree, st));
+    GS_CUDA(run_bwd(g, opts, L, ws, dl_drgb, dl_ddepth, grads, grad_twist, st));
     return GS_OK;
 }
 
@@ -417,37 +559,101 @@ gs_status gs_adam_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* 
                        const uint8_t* update_mask, const uint8_t* visible, const float lr[6], float b1, float b2,
                        float eps, int64_t step, void* stream) {
     gs_status s;
-    gs_gaussians* all[4] = {params, grads, m, v};
-    for (auto* x : all)
-        if ((s = check_gaussians(x, true)) != GS_OK) return s;
-    for (auto* x : all)
-        if (x->n != params->n || x->sh_degree != params->sh_degree)
-            return fail(GS_ERR_INVALID_ARG, "params / grads / m / v differ in n or sh_degree");
-    if (!lr) return fail(GS_ERR_INVALID_ARG, "lr is NULL");
+    if ((s = check_adam(params, grads, m, v, lr, b1, b2, eps)) != GS_OK) return s;
     if (step < 1) return fail(GS_ERR_INVALID_ARG, "step must be >= 1");
-    if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps >= 0.f))
-        return fail(GS_ERR_INVALID_ARG, "need 0 <= b1, b2 < 1 and eps >= 0");
-    const int K = (params->sh_degree + 1) * (params->sh_degree + 1);
-    AdamArgs a;
-    a.n = params->n;
-    a.n_planes = 11 + 3 * K;
-    gs_gaussians* src[4] = {params, grads, m, v};
-    float** dst[4] = {a.p, a.g, a.m, a.v};
-    for (int k = 0; k < 4; k++) {
-        dst[k][0] = src[k]->means;
-        dst[k][1] = src[k]->log_scales;
-        dst[k][2] = src[k]->quats;
-        dst[k][3] = src[k]->opacity_logits;
-        dst[k][4] = src[k]->sh;
+    GS_CUDA(run_adam(params, grads, m, v, update_mask, visible, lr, b1, b2, eps, step, nullptr, (cudaStream_t)stream));
+    return GS_OK;
+}
+
+gs_status gs_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v, const gs_camera* cams,
+                  const gs_render_opts* opts, const gs_ws_layout* L, void* ws, const gs_step_io* io, void* stream) {
+    Geometry G;
+    gs_status s = check_step(params, grads, m, v, cams, opts, L, ws, io, G);
+    if (s != GS_OK) return s;
+    return run_step(params, grads, m, v, opts, L, G, ws, io, (cudaStream_t)stream);
+}
+
+gs_status gs_graph_create(gs_graph* out, gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
+                          const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                          const gs_step_io* io, void* stream) {
+    if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!stream) return fail(GS_ERR_INVALID_ARG, "capture needs a non-default stream");
+    Geometry G;
+    gs_status s = check_step(params, grads, m, v, cams, opts, L, ws, io, G);
+    if (s != GS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    GraphState* gst = new GraphState();
+    gst->opts = *opts;
+    gst->layout = *L;
+    gst->ws = ws;
+    GS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    s = run_step(params, grads, m, v, opts, L, G, ws, io, st);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    if (s != GS_OK || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        delete gst;
+        return s != GS_OK ? s : fail(GS_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ec));
     }
-    a.planes_of[0] = 3; a.planes_of[1] = 3; a.planes_of[2] = 4; a.planes_of[3] = 1; a.planes_of[4] = 3 * K;
-    a.update_mask = update_mask;
-    a.visible = visible;
-    for (int k = 0; k < 6; k++) a.lr[k] = lr[k];
-    a.b1 = b1; a.b2 = b2; a.eps = eps;
-    a.bc1 = (float)(1.0 - pow((double)b1, (double)step));
-    a.bc2 = (float)(1.0 - pow((double)b2, (double)step));
-    GS_CUDA(launch_adam(a, (cudaStream_t)stream));
+    gst->graph = graph;
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    cudaGraphNode_t* nodes = new cudaGraphNode_t[nn ? nn : 1];
+    cudaGraphGetNodes(graph, nodes, &nn);
+    for (size_t i = 0; i < nn; i++) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(nodes[i], &kp) != cudaSuccess) continue;
+        if (kp.func == reinterpret_cast<void*>(setup_views_kernel)) {
+            gst->views_node = nodes[i];
+            gst->views_params = kp;
+        }
+    }
+    delete[] nodes;
+    const cudaError_t ei = cudaGraphInstantiate(&gst->exec, graph, 0);
+    if (ei != cudaSuccess || !gst->views_node) {
+        cudaGraphDestroy(graph);
+        delete gst;
+        return fail(GS_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    }
+    *out = reinterpret_cast<gs_graph>(gst);
+    return GS_OK;
+}
+
+gs_status gs_graph_launch(gs_graph g, void* stream) {
+    if (!g) return fail(GS_ERR_INVALID_ARG, "graph is NULL");
+    GraphState* gst = reinterpret_cast<GraphState*>(g);
+    GS_CUDA(cudaGraphLaunch(gst->exec, (cudaStream_t)stream));
+    return GS_OK;
+}
+
+gs_status gs_graph_set_cameras(gs_graph g, const gs_camera* cams) {
+    if (!g) return fail(GS_ERR_INVALID_ARG, "graph is NULL");
+    GraphState* gst = reinterpret_cast<GraphState*>(g);
+    Geometry G;
+    gs_status s = geometry_for(&gst->layout, cams, &gst->opts, G);
+    if (s != GS_OK) return s;
+    ViewsParam p;
+    memset(&p, 0, sizeof(p));
+    p.n = gst->layout.n_views;
+    memcpy(p.v, G.views, sizeof(View) * p.n);
+    View* dst = at<View>(gst->ws, gst->layout.views);
+    void* args[2] = {&dst, &p};
+    cudaKernelNodeParams kp = gst->views_params;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    GS_CUDA(cudaGraphExecKernelNodeSetParams(gst->exec, gst->views_node, &kp));
+    return GS_OK;
+}
+
+gs_status gs_graph_destroy(gs_graph g) {
+    if (!g) return GS_OK;
+    GraphState* gst = reinterpret_cast<GraphState*>(g);
+    if (gst->exec) cudaGraphExecDestroy(gst->exec);
+    if (gst->graph) cudaGraphDestroy(gst->graph);
+    delete gst;
     return GS_OK;
 }
 

@@ -37,8 +37,11 @@ struct Counters {
     uint32_t reserved;
     unsigned long long n_pairs;
     uint32_t n_chunks;    // radix-sort chunk count (device-computed)
-    uint32_t pad[3];
+    uint32_t pad0;
+    unsigned long long adam_step;   // Adam step counter of gs_step (device-side, graph-safe)
+    float adam_bc1, adam_bc2;       // 1 - b1^t, 1 - b2^t for that step
 };
+constexpr size_t kCountersResetBytes = 16;   // status, reserved, n_pairs: cleared per step
 
 struct Opts {
     float near_z, dilation, alpha_min, alpha_max, T_min, clamp_fov;

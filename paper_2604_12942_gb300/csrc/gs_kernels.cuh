@@ -102,6 +102,7 @@ struct AdamArgs {
     const uint8_t* visible;
     float lr[6];
     float b1, b2, eps, bc1, bc2;
+    const Counters* step_dev;   // if set, bias corrections come from this device counter block
 };
 
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
@@ -116,6 +117,7 @@ cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int
                                  float lambda_depth, int has_depth, float* loss_out, cudaStream_t st);
 cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st);
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t st);
+cudaError_t launch_adam_step_counter(Counters* c, float b1, float b2, cudaStream_t st);
 cudaError_t launch_setup_views(View* dst, const View* src_host, int n_views, cudaStream_t st);
 
 int sort_grid();

@@ -1,0 +1,80 @@
+"""The batched step (gs_step) and its CUDA graph against the staged calls."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2604_12942_gb300 as gs
+import synth
+from tests.gpu_helpers import planes_of
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(seed=41, n=6000):
+    sc = synth.uniform_box_scene(seed, n, sh_degree=3)
+    cams = [synth.camera(160, 120, 150.0), synth.camera(97, 61, 80.0, t=[0.1, 0.0, 0.2])]
+    tg = synth.random_targets(seed + 1, cams)
+    trgb = gs.pack_rgb([t["rgb"] for t in tg])
+    td = gs.pack_plane([t["depth"] for t in tg])
+    return sc, cams, trgb, td
+
+
+def test_step_equals_staged_calls():
+    sc, cams, trgb, td = _setup()
+    step = gs.MappingStep(planes_of(sc), 3, cams)
+    step(trgb, td, optimize=False, with_twist=True)
+    ws = gs.Workspace(sc.n, cams, gs.default_opts(), step.ws.layout.max_pairs)
+    P = ws.layout.total_pixels
+    planes = planes_of(sc)
+    rgb = torch.zeros(3 * P, device="cuda"); dep = torch.zeros(P, device="cuda")
+    dl = torch.zeros(3 * P, device="cuda"); dld = torch.zeros(P, device="cuda")
+    loss = torch.zeros(len(cams) + 1, device="cuda")
+    grads = torch.zeros_like(planes); tw = torch.zeros(len(cams), 6, device="cuda")
+    ws.project(planes, 3)
+    ws.bin_sort()
+    ws.render_fwd(rgb, dep, None, trgb, td, None, dl, dld, loss)
+    ws.render_bwd(planes, 3, grads, dl, dld, tw)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, step.rgb) and torch.equal(dep, step.depth) and torch.equal(dl, step.dl_drgb)
+    assert torch.allclose(loss, step.loss, rtol=1e-6)
+    # gradients are sums of float atomics: equal up to the summation order
+    assert torch.allclose(grads, step.grads, rtol=1e-5, atol=1e-7 * float(grads.abs().max()))
+    assert torch.allclose(tw, step.twist, rtol=1e-4, atol=1e-6 * float(tw.abs().max()))
+
+
+def test_graph_replay_equals_eager_and_counts_adam_steps():
+    sc, cams, trgb, td = _setup(43)
+    eager = gs.MappingStep(planes_of(sc), 3, cams, lr=(1e-3, 1e-2, 1e-2, 5e-2, 1e-2, 1e-3))
+    graph = gs.MappingStep(planes_of(sc), 3, cams, lr=(1e-3, 1e-2, 1e-2, 5e-2, 1e-2, 1e-3))
+    losses_e, losses_g = [], []
+    for _ in range(4):
+        eager(trgb, td)
+        losses_e.append(float(eager.loss[-1]))
+    graph.capture(trgb, td)
+    for _ in range(4):
+        graph.replay()
+        losses_g.append(float(graph.loss[-1]))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(losses_g, losses_e, rtol=1e-4)
+    scale = float(eager.planes.abs().max())
+    assert torch.allclose(graph.planes, eager.planes, rtol=1e-4, atol=1e-5 * scale)
+    assert eager.ws.counters().adam_step == 4 and graph.ws.counters().adam_step == 4
+    assert losses_e[-1] < losses_e[0]
+    graph.release()
+
+
+def test_graph_set_cameras_matches_eager_with_new_poses():
+    sc, cams, trgb, td = _setup(45)
+    step = gs.MappingStep(planes_of(sc), 3, cams)
+    step.capture(trgb, td, optimize=False)
+    moved = [dict(c) for c in cams]
+    for c in moved:
+        c["t"] = np.asarray(c["t"], float) + np.array([0.05, -0.03, 0.1])
+    step.set_cameras(moved)
+    step.replay()
+    torch.cuda.synchronize()
+    ref = gs.MappingStep(planes_of(sc), 3, moved)
+    ref(trgb, td, optimize=False)
+    torch.cuda.synchronize()
+    assert torch.equal(step.rgb, ref.rgb) and torch.equal(step.depth, ref.depth)
+    step.release()
