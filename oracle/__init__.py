@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gs_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "voxel_pca.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libgs_oracle.so")
 _lock = threading.Lock()
@@ -30,10 +31,11 @@ def build(force: bool = False) -> str:
     """Compile gs_oracle.c into oracle/_build/libgs_oracle.so (gcc, -O2, OpenMP, no FP
     contraction so FP32 decisions are taken exactly as written)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(f)
+                                                     for f in _SRCS):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -77,6 +79,13 @@ def lib():
             L.or_bin_view.restype = i64
             L.or_sort_pairs.argtypes = [i64, vp, vp]
             L.or_tile_ranges.argtypes = [i64, vp, i64, vp]
+            L.or_jacobi3.argtypes = [vp, vp, vp]
+            L.or_eig_sorted.argtypes = [vp, vp, vp]
+            L.or_descriptor_cov.argtypes = [i64, vp, vp, vp, vp, i32, dbl, vp, vp]
+            L.or_voxel_key.argtypes = [vp, C.c_float]
+            L.or_voxel_key.restype = i64
+            L.or_voxel_pca.argtypes = [i64, vp, C.c_float, i32, dbl, dbl, dbl, dbl, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.or_voxel_pca.restype = i64
             _lib = L
     return _lib
 
@@ -286,3 +295,47 @@ def bin_views(items, cams, tile):
     lib().or_tile_ranges(skeys.shape[0], _p(skeys), tile_off, _p(ranges))
     return dict(keys=keys, vals=vals, touched=np.concatenate(touched_l), sorted_keys=skeys,
                 sorted_vals=svals, ranges=ranges, n_tiles=tile_off)
+
+
+# ----------------------------------------------------------------------------------------
+# Voxel-PCA geometric fitting (§III-A)
+# ----------------------------------------------------------------------------------------
+
+VOXEL_DEFAULTS = dict(voxel=0.5, min_pts=5, tau_p=2.5e-3, tau_l=10.0, sigma=0.02, tau_trace=1e-2)
+
+
+def voxel_pca(points, voxel=0.5, min_pts=5, tau_p=2.5e-3, tau_l=10.0, sigma=0.02, tau_trace=1e-2):
+    """Per-point voxel features of FP32 points [3, n] (see voxel_pca.c): lam [n, 3] ascending,
+    V [n, 9] row-major with columns v_min, v_mid, v_max, mu [n, 3], cls, reliable, npts,
+    has_feature (npts >= min_pts), vox (dense voxel index), trace, n_voxels."""
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    n = pts.shape[1]
+    out = dict(vox=np.zeros(n, np.int64), npts=np.zeros(n, np.int32), lam=np.zeros((n, 3)), V=np.zeros((n, 9)),
+               mu=np.zeros((n, 3)), cls=np.zeros(n, np.int32), reliable=np.zeros(n, np.int32), trace=np.zeros(n))
+    nv = lib().or_voxel_pca(n, _p(pts), voxel, min_pts, tau_p, tau_l, sigma, tau_trace, _p(out["vox"]),
+                            _p(out["npts"]), _p(out["lam"]), _p(out["V"]), _p(out["mu"]), _p(out["cls"]),
+                            _p(out["reliable"]), _p(out["trace"]))
+    out["n_voxels"] = int(nv)
+    out["has_feature"] = out["npts"] >= min_pts
+    return out
+
+
+def eig_sorted(C):
+    C = _f64(C).reshape(9)
+    lam = np.zeros(3); V = np.zeros(9)
+    lib().or_eig_sorted(_p(C), _p(lam), _p(V))
+    return lam, V.reshape(3, 3)
+
+
+def descriptor_cov(P, k, sigma=0.02):
+    """Sigma_g (6x6) and the per-point Jacobians J_i (N, 6, 3) of one voxel's points P [N, 3]."""
+    P = _f64(P)
+    N = P.shape[0]
+    mu = P.mean(0)
+    d = P - mu
+    C = d.T @ d / N
+    lam, V = eig_sorted(C)
+    Sg = np.zeros(36); J = np.zeros(18 * N)
+    lib().or_descriptor_cov(N, _p(np.ascontiguousarray(P)), _p(np.ascontiguousarray(mu)), _p(lam),
+                            _p(np.ascontiguousarray(V)), k, sigma, _p(Sg), _p(J))
+    return Sg.reshape(6, 6), J.reshape(N, 6, 3), lam, V
