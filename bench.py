@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--learned", action="store_true",
+                    help="secs-to-PSNR of learned init + batched views vs plain init + one view per step")
+    ap.add_argument("--learned-n", type=int, default=150_000)
+    ap.add_argument("--ref-iters", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -313,13 +317,58 @@ def kernels_per_step(L):
     while (1 << tb) < tiles:
         tb += 1
     passes = 4 + (tb + 7) // 8
-    # view table, project, 3 scan + emit, 3 per radix pass, ranges, loss count + composite +
-    # loss finalize, composite backward + projection backward, Adam counter + Adam
-    return 1 + 1 + 4 + 3 * passes + 1 + 3 + 2 + 2
+    # view table, project, 3 scan + emit, 3 per radix pass, ranges, 3 tile-order kernels,
+    # loss count + composite + loss finalize, composite backward + projection backward,
+    # Adam counter + Adam
+    return 1 + 1 + 4 + 3 * passes + 1 + 3 + 3 + 2 + 2
+
+
+def run_learned(args):
+    """Train the initialiser on pairs from the plain loop (scenes 10-12), then on held-out
+    scenes (20, 21) measure wall seconds to the held-out PSNR that plain init + one view per
+    step reaches after --ref-iters iterations, for plain init + 1 view and learned init + 8
+    views per step."""
+    import torch
+
+    from paper_2604_12942_gb300 import learned_init as li
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    x, y = li.training_pairs([10, 11, 12], args.learned_n, iters=200, views=8)
+    mlp, losses = li.train_mlp(x, y, epochs=40)
+    train_s = time.perf_counter() - t0
+    rows = []
+    for s in (20, 21):
+        sd = li.make_scene(s, args.learned_n)
+        plain0, _, _ = li.initial_map(sd, None)
+        target = li.final_psnr(plain0.clone(), sd, 1, args.ref_iters, seed=s)
+        sp, ip, _ = li.seconds_to_psnr(plain0.clone(), sd, 1, target, args.ref_iters + 500, seed=s)
+        learned0, _, branch = li.initial_map(sd, mlp)
+        sl, il, curve = li.seconds_to_psnr(learned0.clone(), sd, 8, target, args.ref_iters, seed=s)
+        # the two factors separately: plain init batched, learned init one view per step
+        spb, ipb, _ = li.seconds_to_psnr(plain0.clone(), sd, 8, target, args.ref_iters, seed=s)
+        sl1, il1, _ = li.seconds_to_psnr(learned0.clone(), sd, 1, target, args.ref_iters + 500, seed=s)
+        rows.append(dict(scene=s, target_psnr=round(target, 3), plain_s=round(sp, 3), plain_iters=ip,
+                         learned_s=round(sl, 3), learned_iters=il, plain_batched_s=round(spb, 3),
+                         plain_batched_iters=ipb, learned_single_s=round(sl1, 3), learned_single_iters=il1,
+                         model_branch_frac=round(float((branch == 2).float().mean()), 3)))
+    plain = float(np.mean([r["plain_s"] for r in rows]))
+    lrn = float(np.mean([r["learned_s"] for r in rows]))
+    print(json.dumps({
+        "metric": "secs-to-PSNR learned vs plain", "value": round(lrn, 3), "unit": "s", "higher_is_better": False,
+        "plain_value": round(plain, 3), "speedup": round(plain / lrn, 3) if lrn > 0 else None, "n_gpus": 1,
+        "dtype": "f32 (MLP bf16/f32-acc)", "data": "synthetic",
+        "config": {"workload": f"LiDAR line scenes, {args.learned_n} Gaussians SH1, 28 train + 4 held-out keyframes "
+                               f"320x240; MLP trained on 200-iteration pairs of scenes 10-12",
+                   "ref_iters": args.ref_iters, "train_pairs": int(x.shape[0]),
+                   "mlp_loss_first_last": [round(losses[0], 5), round(losses[-1], 5)], "train_s": round(train_s, 2)},
+        "scenes": rows}), flush=True)
 
 
 def main():
     args = parse()
+    if args.learned:
+        run_learned(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

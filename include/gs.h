@@ -118,6 +118,8 @@ typedef struct {
     size_t n_contrib;    /* uint32 [total_pixels] tile-list position after the last added */
     size_t grad2d;       /* [n_views*n] records of 12 floats (screen-space gradient sums) */
     size_t visible;      /* uint8 [n]: 1 if the Gaussian covers a tile of any view */
+    size_t tile_order;   /* uint32 [total_tiles]: compositing work order, largest pair count
+                            first (power-of-two buckets), then scratch */
     size_t total;        /* workspace bytes */
     int32_t sorted_buf;  /* 0 or 1: which ping-pong buffer holds the sorted pairs */
     int32_t total_tiles;
@@ -256,6 +258,77 @@ gs_status gs_graph_create(gs_graph *out, gs_gaussians *params, gs_gaussians *gra
 gs_status gs_graph_launch(gs_graph g, void *stream);
 gs_status gs_graph_set_cameras(gs_graph g, const gs_camera *cams);
 gs_status gs_graph_destroy(gs_graph g);
+
+/* ---------------------------------------------------------------------------------------
+ * The learned Gaussian initialiser (a10-a12).  RMGS-SLAM §III-B initialises one Gaussian per
+ * LiDAR point by a cascade -- a learned model where its prediction is valid, else the
+ * voxel-PCA prior (§III-A) where it is geometrically reliable, else an isotropic depth
+ * heuristic.  The paper's model (a pretrained feed-forward network) is not available; here
+ * it is a small MLP over the voxel-PCA features.
+ * --------------------------------------------------------------------------------------- */
+
+/* Voxel-PCA constants (§III-A; the paper fixes tau_p, tau_l but does not state them). */
+typedef struct {
+    float voxel;      /* voxel side (0.5 m) */
+    int32_t min_pts;  /* points needed for a feature (5) */
+    float tau_p;      /* planar if lambda_min < tau_p (2.5e-3 m^2) */
+    float tau_l;      /* else linear if lambda_max / lambda_min > tau_l (10) */
+    float sigma;      /* per-point noise, Sigma_i = sigma^2 I (0.02 m) */
+    float tau_trace;  /* reliable iff trace of the directional block of Sigma_g < tau_trace (1e-2) */
+} gs_pca_opts;
+
+/* a10 -- Voxel-PCA features (§III-A): points [3][n] (world, FP32) and colours [3][n] are
+ * grouped into voxels by key (floor(p/voxel) per axis, FP32, sorted with the radix sort); per
+ * voxel with >= min_pts points: mean, covariance, sorted eigen-decomposition (each eigenvector's
+ * largest component positive, v_max = v_min x v_mid), planar / linear / unreliable class and
+ * reliability from the descriptor covariance Sigma_g = sum_i J_i Sigma_i J_i^T.  Per point:
+ *   x_out [n][16] = [ln max(lambda, 1e-4) (3), V row-major (9), rgb (3), ln(d / fx)] (zero rows
+ *   without a feature), has_feature, reliable, s_pca [n][3] = ln sqrt(max(lambda, 1e-4)),
+ *   q_pca [n][4] (w, x, y, z; w >= 0) of V; depth [n] and inside [n]: among the n_frames host
+ *   cameras (the segment's loopframes / keyframes, <= 32) the closest one whose image the point
+ *   projects into gives d (the "closer view" of §III-B) and inside = 1; with none, d is the
+ *   depth in frames[0] and inside = 0; fx is frames[0].fx.  ws: gs_pca_workspace_size(n)
+ *   bytes, 256-aligned. */
+size_t gs_pca_workspace_size(int64_t n);
+gs_status gs_voxel_pca(const float *pts, const float *rgb, int64_t n, const gs_camera *frames,
+                       int32_t n_frames, const gs_pca_opts *opts, void *ws, size_t ws_bytes, float *x_out,
+                       uint8_t *has_feature, uint8_t *reliable, float *s_pca, float *q_pca,
+                       float *depth, uint8_t *inside, void *stream);
+
+/* a11 -- MLP inference y [n][16] = f(x [n][16]): 16 -> 128 -> 128 -> 128 -> 16 with GELU
+ * (erf form) after the hidden layers; BF16 weights (w_bf16 [36864] = W1 128x16 | W2 128x128 |
+ * W3 128x128 | W4 16x128, row-major [out][in]), FP32 biases [400] (b1 | b2 | b3 | b4), BF16
+ * input and hidden activations, FP32 accumulation (tensor cores).  Outputs 0..10 are the
+ * residuals: log-scale (3), quaternion (4), opacity logit (1), colour (3). */
+gs_status gs_mlp_infer(const uint16_t *w_bf16, const float *bias, const float *x, int64_t n,
+                       float *y, void *stream);
+
+/* a12 -- One training step on n (x, y_target) rows: forward, loss = mean over rows and the
+ * 11 used outputs of (y - y_target)^2, backward GEMMs (BF16 operands, FP32 accumulate), Adam
+ * on the FP32 master weights w_master [36864] and biases [400] (both updated in place), BF16
+ * copy into w_bf16.  grad_w [36864], grad_b [400] must be zero on entry and are zeroed again;
+ * adam_m, adam_v [37264] (weights then biases).  scratch: gs_mlp_train_scratch_size(n) bytes.
+ * loss_out (device float, may be NULL) receives the loss of this step's forward. */
+size_t gs_mlp_train_scratch_size(int64_t n);
+gs_status gs_mlp_train_step(float *w_master, uint16_t *w_bf16, float *bias, float *grad_w, float *grad_b,
+                            float *adam_m, float *adam_v, const float *x, const float *y_target,
+                            int64_t n, float lr, float b1, float b2, float eps, int64_t step,
+                            void *scratch, size_t scratch_bytes, float *loss_out, void *stream);
+
+/* Cascaded initialisation (§III-B equations): per point, the model branch where the MLP output
+ * y (may be NULL: no model) is valid -- the point has a feature, lies inside the loopframe,
+ * the outputs are finite and |log-scale residual| < 3 -- giving log-scale s_pca + dy,
+ * quaternion normalize(q_pca + dq), opacity logit logit(opacity_init) + do, colour rgb + dc;
+ * else the PCA branch where reliable: s_pca + log(beta), q_pca; else the heuristic ln(d/fx)
+ * isotropic with identity rotation.  beta = clamp(#(reliable and not valid) / n, 0.25, 1).
+ * Non-model branches take opacity_init; SH DC from the colour, higher SH zero.  Writes every
+ * plane of `out` (n Gaussians), branch [n] (2 model, 1 PCA, 0 heuristic; may be NULL) and
+ * beta_out (device float, may be NULL); count_tmp is one device uint32 of scratch. */
+gs_status gs_init_cascade(const float *pts, const float *rgb, int64_t n, const float *y,
+                          const uint8_t *has_feature, const uint8_t *reliable, const float *s_pca,
+                          const float *q_pca, const float *depth, const uint8_t *inside, float fx,
+                          float opacity_init, gs_gaussians *out, int32_t *branch,
+                          unsigned int *count_tmp, float *beta_out, void *stream);
 
 /* Allocation-free sort (the paper has no counterpart; it is a service of this library).
  * Stable LSD radix sort of n (key, value) pairs by the low key_bits bits of the key (8 bits

@@ -131,17 +131,28 @@ def quat_from_matrix(R):
     return q if q[0] >= 0 else -q
 
 
-def point_depth(points, cam):
-    """Camera-frame depth of each point ([3, n] world) in the loopframe camera, and whether it
-    projects inside the image at positive depth."""
-    R, t = np.asarray(cam["R"], np.float64), np.asarray(cam["t"], np.float64)
-    pc = R @ np.asarray(points, np.float64) + t[:, None]
-    z = pc[2]
-    with np.errstate(divide="ignore", invalid="ignore"):
-        u = cam["fx"] * pc[0] / z + cam["cx"]
-        v = cam["fy"] * pc[1] / z + cam["cy"]
-    inside = (z > 0) & (u >= 0) & (u < cam["width"]) & (v >= 0) & (v < cam["height"])
-    return z, inside
+def point_depth(points, cams):
+    """Per point ([3, n] world): the camera-frame depth in the closest of `cams` (a camera or a
+    list: the segment's loopframes / keyframes) whose image it projects into at positive
+    depth -- the closer view of §III-B -- and whether there is one; if none, the depth in the
+    first camera."""
+    cams = [cams] if isinstance(cams, dict) else list(cams)
+    n = np.asarray(points).shape[1]
+    best = np.full(n, np.inf)
+    first = None
+    for cam in cams:
+        R, t = np.asarray(cam["R"], np.float64), np.asarray(cam["t"], np.float64)
+        pc = R @ np.asarray(points, np.float64) + t[:, None]
+        z = pc[2]
+        if first is None:
+            first = z
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = cam["fx"] * pc[0] / z + cam["cx"]
+            v = cam["fy"] * pc[1] / z + cam["cy"]
+        ins = (z > 0) & (u >= 0) & (u < cam["width"]) & (v >= 0) & (v < cam["height"])
+        best = np.where(ins & (z < best), z, best)
+    inside = np.isfinite(best)
+    return np.where(inside, best, first), inside
 
 
 def features(pca, colours, depth, fx):

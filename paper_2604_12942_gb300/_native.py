@@ -36,7 +36,7 @@ class RenderOpts(C.Structure):
 class WsLayout(C.Structure):
     _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "touched", "offsets", "scan_tmp",
                                           "keys0", "keys1", "vals0", "vals1", "sort_tmp", "ranges", "T_final",
-                                          "n_contrib", "grad2d", "visible", "total")] + \
+                                          "n_contrib", "grad2d", "visible", "tile_order", "total")] + \
                [("sorted_buf", C.c_int32), ("total_tiles", C.c_int32), ("total_pixels", C.c_int64),
                 ("max_pairs", C.c_int64), ("n", C.c_int64), ("n_views", C.c_int32), ("tile", C.c_int32)]
 
@@ -51,6 +51,11 @@ class StepIO(C.Structure):
                 ("loss_out", C.c_void_p), ("grad_twist", C.c_void_p), ("update_mask", C.c_void_p),
                 ("lr", C.c_float * 6), ("b1", C.c_float), ("b2", C.c_float), ("eps", C.c_float),
                 ("optimize", C.c_int32)]
+
+
+class PcaOpts(C.Structure):
+    _fields_ = [("voxel", C.c_float), ("min_pts", C.c_int32), ("tau_p", C.c_float), ("tau_l", C.c_float),
+                ("sigma", C.c_float), ("tau_trace", C.c_float)]
 
 
 class GsError(RuntimeError):
@@ -87,6 +92,17 @@ _SIGS = {
                        C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p], C.c_int),
     "gs_sort_pairs_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
                               C.c_int),
+    "gs_pca_workspace_size": ([C.c_int64], C.c_size_t),
+    "gs_voxel_pca": ([C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(Camera), C.c_int32, C.POINTER(PcaOpts), C.c_void_p,
+                      C.c_size_t]
+                     + [C.c_void_p] * 7 + [C.c_void_p], C.c_int),
+    "gs_mlp_infer": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "gs_mlp_train_scratch_size": ([C.c_int64], C.c_size_t),
+    "gs_mlp_train_step": ([C.c_void_p] * 9 + [C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int64,
+                                               C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p], C.c_int),
+    "gs_init_cascade": ([C.c_void_p] * 2 + [C.c_int64] + [C.c_void_p] * 7 + [C.c_float, C.c_float, C.POINTER(Gaussians),
+                                                                          C.c_void_p, C.c_void_p, C.c_void_p,
+                                                                          C.c_void_p], C.c_int),
     "gs_adam_step": ([C.POINTER(Gaussians)] * 4 + [C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.c_float, C.c_float,
                                                    C.c_float, C.c_int64, C.c_void_p], C.c_int),
 }

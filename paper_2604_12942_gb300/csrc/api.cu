@@ -130,6 +130,7 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.n_contrib = take(sizeof(uint32_t) * (size_t)G.total_pixels);
     L.grad2d = take(sizeof(float) * 12 * (size_t)VN);
     L.visible = take((size_t)n);
+    L.tile_order = take(sizeof(uint32_t) * ((size_t)G.total_tiles + 2 * 34));
     L.total = off;
     int shifts[16];
     L.sorted_buf = sort_passes(G.total_tiles, shifts) & 1;
@@ -257,7 +258,9 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     r.keys = sa.keys[np & 1];
     r.ranges = at<uint2>(ws, L->ranges);
     r.counters = cnt;
-    return launch_ranges(r, L->total_tiles, st);
+    if ((e = launch_ranges(r, L->total_tiles, st)) != cudaSuccess) return e;
+    uint32_t* order = at<uint32_t>(ws, L->tile_order);
+    return launch_tile_order(r.ranges, L->total_tiles, order, order + L->total_tiles, cnt, st);
 }
 
 static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
@@ -282,6 +285,7 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
     a.proj = at<float4>(ws, L->proj);
     a.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
     a.ranges = at<uint2>(ws, L->ranges);
+    a.order = at<uint32_t>(ws, L->tile_order);
     a.counters = at<Counters>(ws, L->counters);
     a.T_final = at<float>(ws, L->T_final);
     a.n_contrib = at<uint32_t>(ws, L->n_contrib);
@@ -315,6 +319,7 @@ static cudaError_t run_bwd(const gs_gaussians* g, const gs_render_opts* opts, co
     b.proj = at<float4>(ws, L->proj);
     b.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
     b.ranges = at<uint2>(ws, L->ranges);
+    b.order = at<uint32_t>(ws, L->tile_order);
     b.counters = at<Counters>(ws, L->counters);
     b.T_final = at<float>(ws, L->T_final);
     b.n_contrib = at<uint32_t>(ws, L->n_contrib);

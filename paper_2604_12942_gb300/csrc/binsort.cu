@@ -130,12 +130,19 @@ __global__ void __launch_bounds__(256) emit_kernel(BinArgs a) {
     }
 }
 
+cudaError_t launch_exclusive_scan(const uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp, Counters* c,
+                                  int64_t max_total, cudaStream_t st) {
+    const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
+    if (nb > 0) scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, tmp);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(tmp, nb, c, max_total);
+    if (nb > 0) scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, n, tmp, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const BinArgs& a, cudaStream_t st) {
     const int64_t total = (int64_t)a.n_views * a.n;
-    const int nb = (int)((total + kScanBlock - 1) / kScanBlock);
-    if (nb > 0) scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(a.touched, total, a.scan_tmp);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(a.scan_tmp, nb, a.counters, a.max_pairs);
-    if (nb > 0) scan_down_kernel<<<nb, kScanThreads, 0, st>>>(a.touched, total, a.scan_tmp, a.offsets);
+    cudaError_t e = launch_exclusive_scan(a.touched, total, a.offsets, a.scan_tmp, a.counters, a.max_pairs, st);
+    if (e != cudaSuccess) return e;
     const int64_t eb64 = (total + 255) / 256;
     const int eb = (int)(eb64 < 152 * 32 ? eb64 : 152 * 32);
     if (eb > 0) emit_kernel<<<eb, 256, 0, st>>>(a);
@@ -368,6 +375,69 @@ __global__ void __launch_bounds__(256) ranges_kernel(RangeArgs a) {
 cudaError_t launch_ranges(const RangeArgs& a, int n_tiles, cudaStream_t st) {
     (void)n_tiles;
     ranges_kernel<<<sort_grid() * 4, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------
+// Work order of the compositing kernels: (view, tile) items by decreasing pair count, in
+// power-of-two buckets (bucket b holds counts in [2^(b-1), 2^b)), so that the largest tiles
+// are scheduled first and the tail of the launch is made of short items.
+// ----------------------------------------------------------------------------------------
+constexpr int kOrderBuckets = 34;
+
+__device__ __forceinline__ int order_bucket(uint2 r) {
+    const uint32_t c = r.y - r.x;
+    return c ? 33 - __clz(c) : 0;   // 0 = empty, 1..33
+}
+
+__global__ void tile_order_hist_kernel(const uint2* ranges, int n_tiles, uint32_t* cnt, const Counters* c) {
+    __shared__ uint32_t h[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    if (c->status == 0)
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
+            atomicAdd(&h[order_bucket(ranges[t])], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
+        if (h[b]) atomicAdd(&cnt[b], h[b]);
+}
+
+// cursor[b] = number of items in buckets above b (largest counts first)
+__global__ void tile_order_scan_kernel(const uint32_t* cnt, uint32_t* cursor) {
+    if (threadIdx.x != 0) return;
+    uint32_t run = 0;
+    for (int b = kOrderBuckets - 1; b >= 0; b--) {
+        cursor[b] = run;
+        run += cnt[b];
+    }
+}
+
+__global__ void tile_order_scatter_kernel(const uint2* ranges, int n_tiles, uint32_t* cursor, uint32_t* order,
+                                          const Counters* c) {
+    const int lane = threadIdx.x & 31;
+    for (int t0 = blockIdx.x * blockDim.x; t0 < n_tiles; t0 += gridDim.x * blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const bool ok = t < n_tiles;
+        const int b = ok ? (c->status == 0 ? order_bucket(ranges[t]) : 0) : kOrderBuckets;
+        // one atomic per bucket per warp
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (ok && lane == leader) base = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (ok) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
+    }
+}
+
+cudaError_t launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, uint32_t* tmp, const Counters* c,
+                              cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(uint32_t) * 2 * kOrderBuckets, st);
+    if (e != cudaSuccess) return e;
+    const int blocks = (n_tiles + 255) / 256 < 1024 ? (n_tiles + 255) / 256 : 1024;
+    tile_order_hist_kernel<<<blocks, 256, 0, st>>>(ranges, n_tiles, tmp, c);
+    tile_order_scan_kernel<<<1, 32, 0, st>>>(tmp, tmp + kOrderBuckets);
+    tile_order_scatter_kernel<<<blocks, 256, 0, st>>>(ranges, n_tiles, tmp + kOrderBuckets, order, c);
     return cudaGetLastError();
 }
 

@@ -65,6 +65,7 @@ struct FwdArgs {
     const float4* proj;
     const uint32_t* vals;
     const uint2* ranges;
+    const uint32_t* order;     // work order of the (view, tile) items, or null (identity)
     const Counters* counters;
     float* T_final;
     uint32_t* n_contrib;
@@ -83,6 +84,7 @@ struct BwdArgs {
     const float4* proj;
     const uint32_t* vals;
     const uint2* ranges;
+    const uint32_t* order;
     const Counters* counters;
     const float* T_final;
     const uint32_t* n_contrib;
@@ -108,8 +110,14 @@ struct AdamArgs {
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_bin(const BinArgs& a, cudaStream_t st);
+// Exclusive scan of n uint32 values; the total goes to c->n_pairs (status GS_ERR_CAPACITY if it
+// exceeds max_total).  tmp holds n / 4096 + 2 values.
+cudaError_t launch_exclusive_scan(const uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp, Counters* c,
+                                  int64_t max_total, cudaStream_t st);
 cudaError_t launch_sort(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st);
 cudaError_t launch_ranges(const RangeArgs& a, int n_tiles, cudaStream_t st);
+cudaError_t launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, uint32_t* tmp, const Counters* c,
+                              cudaStream_t st);
 cudaError_t launch_loss_count(const View* views, int n_views, const int64_t* pix_counts_host,
                               const float* tgt_depth, const uint8_t* mask, uint32_t* counts, cudaStream_t st);
 cudaError_t launch_render_fwd(const FwdArgs& a, int total_tiles, cudaStream_t st);

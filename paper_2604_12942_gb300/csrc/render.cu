@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
     __shared__ uint32_t s_mask[CHUNK];
     __shared__ double s_red[2][NT / 32];
     if (a.counters->status != 0) return;
-    const int gt = blockIdx.x;
+    const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     const int v = view_of_tile(a.views, a.n_views, gt);
     const View& V = a.views[v];
     const int lt = gt - V.tile_off;
@@ -278,46 +278,53 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
 //   r0 = (sum h h_x, sum h h_y, sum h dx^2, sum h dx dy)
 //   r1 = (sum h dy^2, sum dL/dalpha G, sum g_D w, 0), r2 = (sum g_C w, 0)
 // (h_x, h_y from frag_exponent) and the projection backward applies the constant factors.
-// A lane first sums its two pixels; the warp's 10 sums are then reduced with a transpose
-// reduction (16 shuffles) and written by 10 lanes with one atomic each.
+// A lane first sums its two pixels; the warp's 10 sums are then reduced (warp_reduce10) and
+// written by 10 lanes with one atomic each.
 // ----------------------------------------------------------------------------------------
-__device__ __forceinline__ void warp_transpose_reduce10(float (&v)[16], float& out) {
+// Warp sums of 10 per-lane values by transpose reductions: values 0..7 halve their count at
+// each of the lane-xor 16, 8, 4 exchanges and finish with two butterflies (lane l ends with
+// the total of value (l >> 2) & 7); values 8..9 take one exchange and four butterflies (lane
+// l ends with value 8 + (l >> 4)).  44 shuffle / select / add instructions instead of 62 for
+// a 16-padded transpose.
+__device__ __forceinline__ void warp_reduce10(float (&v)[10], float& out8, float& out2) {
     const int lane = threadIdx.x & 31;
     {
         const bool hi = lane & 16;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const float mine = hi ? v[8 + k] : v[k];
-            const float other = hi ? v[k] : v[8 + k];
+        for (int k = 0; k < 4; k++) {
+            const float mine = hi ? v[4 + k] : v[k];
+            const float other = hi ? v[k] : v[4 + k];
             v[k] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
         }
     }
     {
         const bool hi = lane & 8;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float mine = hi ? v[4 + k] : v[k];
-            const float other = hi ? v[k] : v[4 + k];
+        for (int k = 0; k < 2; k++) {
+            const float mine = hi ? v[2 + k] : v[k];
+            const float other = hi ? v[k] : v[2 + k];
             v[k] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
         }
     }
     {
         const bool hi = lane & 4;
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const float mine = hi ? v[2 + k] : v[k];
-            const float other = hi ? v[k] : v[2 + k];
-            v[k] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
-        }
-    }
-    {
-        const bool hi = lane & 2;
         const float mine = hi ? v[1] : v[0];
         const float other = hi ? v[0] : v[1];
-        v[0] = mine + __shfl_xor_sync(0xffffffffu, other, 2);
+        v[0] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
     }
-    out = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-    // lane l now holds the warp total of value index l >> 1
+    float a = v[0];
+    a += __shfl_xor_sync(0xffffffffu, a, 2);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    out8 = a;
+    const bool hi = lane & 16;
+    const float mine = hi ? v[9] : v[8];
+    const float other = hi ? v[8] : v[9];
+    float b = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+    b += __shfl_xor_sync(0xffffffffu, b, 8);
+    b += __shfl_xor_sync(0xffffffffu, b, 4);
+    b += __shfl_xor_sync(0xffffffffu, b, 2);
+    b += __shfl_xor_sync(0xffffffffu, b, 1);
+    out2 = b;
 }
 
 template <int TILE, int CHUNK>
@@ -332,7 +339,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
     __shared__ uint32_t s_mask[CHUNK];
     __shared__ uint32_t s_max;
     if (a.counters->status != 0) return;
-    const int gt = blockIdx.x;
+    const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     const int v = view_of_tile(a.views, a.n_views, gt);
     const View& V = a.views[v];
     const int lt = gt - V.tile_off;
@@ -392,9 +399,9 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
             if (!((s_mask[k] >> w) & 1u)) continue;
             const float2 bx = s_uv[k];
             const float4 co = s_co[k];
-            float val[16];
+            float val[10];
 #pragma unroll
-            for (int q = 0; q < 16; q++) val[q] = 0.f;
+            for (int q = 0; q < 10; q++) val[q] = 0.f;
             bool contrib = false;
 #pragma unroll
             for (int q = 0; q < kPPT; q++) {
@@ -429,14 +436,15 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                float tot;
-                warp_transpose_reduce10(val, tot);
-                const int idx = lane >> 1;
-                if ((lane & 1) == 0 && idx < 10) {
-                    float* rec = reinterpret_cast<float*>(a.grad2d + 3 * (size_t)s_id[k]);
-                    // value index -> record slot: 0..6 -> 0..6, 7..9 -> 8..10
-                    atomicAdd(rec + (idx < 7 ? idx : idx + 1), tot);
+                float t8, t2;
+                warp_reduce10(val, t8, t2);
+                float* rec = reinterpret_cast<float*>(a.grad2d + 3 * (size_t)s_id[k]);
+                // value index -> record slot: 0..6 -> 0..6, 7..9 -> 8..10
+                if ((lane & 3) == 0) {
+                    const int idx = lane >> 2;
+                    atomicAdd(rec + (idx < 7 ? idx : idx + 1), t8);
                 }
+                if ((lane & 15) == 0) atomicAdd(rec + 9 + (lane >> 4), t2);
             }
         }
     }

@@ -45,7 +45,7 @@ def test_layout_is_aligned_and_consistent(native):
         o = gs.default_opts(tile=tile)
         L = native.WsLayout()
         assert native.lib().gs_workspace_layout(1000, 2, gs.camera_array(cams), C.byref(o), 5000, C.byref(L)) == 0
-        offs = [getattr(L, f) for f, _ in native.WsLayout._fields_[:17]]
+        offs = [getattr(L, f) for f, _ in native.WsLayout._fields_[:18]]
         assert all(x % 256 == 0 for x in offs)
         assert offs == sorted(offs) and L.total >= offs[-1]
         tiles = sum(((c["width"] + tile - 1) // tile) * ((c["height"] + tile - 1) // tile) for c in cams)
