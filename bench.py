@@ -65,7 +65,6 @@ def workload_config(args):
     return {"workload": "batched keyframe step: 2M Gaussians SH3 (LiDAR loop scene), 8 views "
                         "2x{640x480,960x540,1280x720,1280x1024}, fused fwd+bwd+Adam",
             "n_gaussians": args.n, "views": len(SIZES), "pixels_per_step": sum(w * h for w, h in SIZES),
-            "tile": args.tile, "chunk": args.chunk,
             "l2": "inputs larger than L2 (params+grads+Adam state ~1.9 GB, pair lists ~0.5 GB)"}
 
 
@@ -214,7 +213,7 @@ def run_gpu(args, rank, world):
         tune = {"tile": ch.tile, "chunk": ch.chunk, "ms_per_step": round(ch.ms, 4), "table": ch.table, "key": key}
     opts = gs.default_opts(tile=args.tile, chunk=args.chunk)
     step = gs.MappingStep(planes0, 3, cams, opts, max_pairs=cap)
-    stages = ["project", "bin_sort", "render_fwd", "render_bwd", "adam"]
+    stages = ["project", "bin_sort", "render_fwd", "composite_bwd", "project_bwd_adam"]
     st = torch.cuda.current_stream()
 
     # per-stage breakdown: the same step as separate C calls, events between them
@@ -227,9 +226,9 @@ def run_gpu(args, rank, world):
         evs[2].record(st)
         w.render_fwd(step.rgb, step.depth, None, trgb, tdep, None, step.dl_drgb, step.dl_ddepth, step.loss)
         evs[3].record(st)
-        w.render_bwd(step.planes, 3, step.grads, step.dl_drgb, step.dl_ddepth, None)
+        w.composite_bwd(step.dl_drgb, step.dl_ddepth)
         evs[4].record(st)
-        gs.adam_step(step.planes, step.grads, step.m, step.v, 3, 1, step.lr, None, w.visible())
+        w.project_bwd_adam(step.planes, 3, step.m, step.v, 1, step.lr)
         evs[5].record(st)
 
     # headline: the batched step captured once as a CUDA graph and replayed
@@ -260,11 +259,18 @@ def run_gpu(args, rank, world):
         dist.barrier()
     total_ms = t0.elapsed_time(t1)
     loss_end = float(step.loss[-1])
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(max(3, args.steps // 2))]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(max(3, args.steps // 2))]
     for e in evs:
         staged(e)
     torch.cuda.synchronize()
     stage_ms = {s: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, s in enumerate(stages)}
+    cnt = step.ws.counters()
+    work = dict(n=n, views=len(cams), pairs=int(cnt.n_pairs), frag_fwd_eval=int(cnt.frag_fwd_eval),
+                frag_fwd_add=int(cnt.frag_fwd_add), frag_bwd_eval=int(cnt.frag_bwd_eval),
+                frag_bwd_add=int(cnt.frag_bwd_add), visits_fwd=int(cnt.visits_fwd), visits_bwd=int(cnt.visits_bwd),
+                visible_entries=int(cnt.n_entries), visible_gaussians=int(step.ws.visible().sum()),
+                total_tiles=int(step.ws.layout.total_tiles), depth_sort_passes=4,
+                tile_sort_passes=tile_sort_passes(step.ws.layout))
     # end-to-end through the public API (eager gs_step): targets uploaded from pinned host
     # memory every step and the loss read back
     h_rgb = trgb.cpu().pin_memory()
@@ -304,23 +310,70 @@ def run_gpu(args, rank, world):
     adam_steps = int(step.ws.counters().adam_step)
     step.release()
     return dict(total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=loss_end,
-                tune=tune, adam_steps=adam_steps, eager_ms=eager_ms, h2d_ms=h2d_ms,
+                tune=tune, adam_steps=adam_steps, eager_ms=eager_ms, h2d_ms=h2d_ms, work=work,
                 clocks=clk.summary(), e2e_s=e_dt, px=px, h2d=int(h_rgb.numel() * 4 + h_dep.numel() * 4),
                 d2h=int(h_loss.numel() * 4), sc=sc, cams=cams, trgb=trgb, tdep=tdep, n=n,
                 kernels=kernels_per_step(step.ws.layout))
 
 
+def tile_sort_passes(L):
+    tb = 0
+    while (1 << tb) < L.total_tiles:
+        tb += 1
+    return (tb + 7) // 8
+
+
 def kernels_per_step(L):
     """Kernels one gs_step launches (the graph replays exactly these)."""
-    tiles = L.total_tiles
-    tb = 0
-    while (1 << tb) < tiles:
-        tb += 1
-    passes = 4 + (tb + 7) // 8
-    # view table, project, 3 scan + emit, 3 per radix pass, ranges, 3 tile-order kernels,
-    # loss count + composite + loss finalize, composite backward + projection backward,
-    # Adam counter + Adam
-    return 1 + 1 + 4 + 3 * passes + 1 + 3 + 3 + 2 + 2
+    # view table, project, entry count / scan / compaction, 4 depth-sort passes of 3
+    # kernels, pair count / scan / emission, 3 per tile-sort pass, ranges, 3 tile-order
+    # kernels, loss count + composite + loss finalize, gradient-record clear + composite
+    # backward + projection backward, Adam counter + Adam
+    return 1 + 1 + 3 + 3 * 4 + 3 + 3 * tile_sort_passes(L) + 1 + 3 + 3 + 3 + 2
+
+
+# Algorithmic work per unit (see DESIGN.md, kernel table):
+#   FP32 operations per evaluated fragment (FMA = 2): dx, dy 2; h_x, h_y, e 9; ex2 1; o*G 1;
+#   clamp 1 -> 14.  Added in the forward: 1 - alpha, T (1 - alpha), w, 4 FMA -> +11.  Added in
+#   the backward: 1 - alpha, rcp, T update, w (4), g.c (7), dL/dalpha (3), S (2), 4 colour /
+#   depth FMA (8), h, h dx (2), 5 geometry terms (11), dL/do (2) and the 10 additions that sum
+#   the fragment into its Gaussian's totals -> +49.
+FLOP_EVAL, FLOP_FWD_ADD, FLOP_BWD_ADD = 14, 11, 49
+
+
+def roofline_table(stage, w, pk, pk_kind):
+    """Bound, algorithmic work and achieved fraction of every stage."""
+    hbm = pk["hbm_gbs"]
+    fp32 = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    n, V, P, E = w["n"], w["views"], w["pairs"], w["visible_entries"]
+    VN = V * n
+    B = {
+        "project": 236 * n + 4 * VN + 48 * E,
+        # entry count + compaction (touched twice, z, entry write), depth sort (20 B per
+        # entry per pass), pair count + emission (entry id, touched, record u v rx ry, pair
+        # write), tile sort (20 B per pair per pass), ranges (tile ids)
+        "bin_sort": 8 * VN + 12 * E + w["depth_sort_passes"] * 20 * E + 8 * E + 24 * E + 8 * P
+                    + w["tile_sort_passes"] * 20 * P + 4 * P,
+        # fused projection backward + Adam, rows visible in some view: parameters, m and v
+        # read, parameters, m and v written (6 x 236 B); visibility and touched flags of every
+        # row; screen-space sums of the visible entries
+        "project_bwd_adam": 6 * 236 * w["visible_gaussians"] + n + 4 * VN + 48 * E,
+    }
+    F = {
+        "render_fwd": FLOP_EVAL * w["frag_fwd_eval"] + FLOP_FWD_ADD * w["frag_fwd_add"],
+        "composite_bwd": FLOP_EVAL * w["frag_bwd_eval"] + FLOP_BWD_ADD * w["frag_bwd_add"],
+    }
+    out = {}
+    for k, ms in stage.items():
+        if k in B:
+            ach = B[k] / (ms * 1e-3) / 1e9
+            out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                      "frac": round(ach / hbm, 4), "bytes": int(B[k]), "ms": round(ms, 4)}
+        else:
+            ach = F[k] / (ms * 1e-3) / 1e12
+            out[k] = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32, 1), "unit": "TFLOP/s",
+                      "frac": round(ach / fp32, 4), "flops": int(F[k]), "ms": round(ms, 4)}
+    return out
 
 
 def run_learned(args):
@@ -396,7 +449,14 @@ def main():
     pk, pk_kind = peaks()
     stage = r["stage_ms"]
     dom = max(stage, key=stage.get)
-    roof = roofline(dom, stage, r, pk, pk_kind)
+    table = roofline_table(stage, r["work"], pk, pk_kind)
+    roof = dict(table[dom])
+    roof.update({"kernel": {"composite_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel",
+                            "project_bwd_adam": "project_bwd_kernel (fused Adam)", "project": "project_kernel",
+                            "bin_sort": "scan/emit/radix/ranges kernels"}[dom],
+                 "traffic": None,
+                 "peak_kind": (pk_kind + " HBM copy") if roof["bound"] == "hbm" else
+                 "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock " + str(pk.get("sm_max_mhz", 2070.0)) + " MHz"})
     line = {
         "metric": METRIC, "value": round(mpix, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "iters_per_s": round(1e3 / ms_step, 2),
@@ -404,11 +464,12 @@ def main():
         "config": workload_config(args),
         "stage_ms": {k: round(v, 4) for k, v in stage.items()}, "n_pairs": r["n_pairs"],
         "loss": [round(r["loss0"], 6), round(r["loss_end"], 6)],
-        "roofline": roof, "clocks": r["clocks"],
+        "roofline": roof, "roofline_stages": table, "work": r["work"], "clocks": r["clocks"],
         "e2e": {"value": round(r["px"] / r["e2e_s"] / 1e6, 2), "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"], "ms_per_step": round(1e3 * r["e2e_s"], 3),
                 "eager_device_ms_per_step": round(r["eager_ms"], 3), "h2d_ms_per_step": round(r["h2d_ms"], 3)},
         "gpu_launches": r["kernels"] * args.steps, "timed": "CUDA-graph replay of gs_step",
+        "kernel_shape": {"tile": args.tile, "chunk": args.chunk},
         "autotune": r["tune"],
     }
     if not args.no_cpu_baseline and world == 1:
@@ -417,27 +478,6 @@ def main():
                   __import__("paper_2604_12942_gb300").unpack_plane(r["tdep"], r["cams"]))]
         line["cpu_baseline"] = cpu_baseline_line(r["sc"], r["cams"], tg)
     print(json.dumps(line), flush=True)
-
-
-def roofline(dom, stage, r, pk, pk_kind):
-    """Bound and achieved fraction of the dominant stage (see the design doc for the per-unit
-    algorithmic work)."""
-    n, V, P = r["n"], len(SIZES), r["n_pairs"]
-    hbm = pk["hbm_gbs"]
-    if dom in ("project", "adam", "bin_sort"):
-        if dom == "project":
-            byts = 236 * n + V * n * 4 + 0.3 * V * n * 48    # params once, touched, records of visible
-        elif dom == "adam":
-            byts = 32 * 59 * n
-        else:
-            byts = P * (12 + 6 * 32) + V * n * 12
-        ach = byts / (stage[dom] * 1e-3) / 1e9
-        return {"bound": "hbm", "stage": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": None, "peak_kind": pk_kind}
-    # compositing: FP32 ALU bound
-    fp32 = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    return {"bound": "alu", "stage": dom, "achieved": None, "peak": round(fp32, 1), "unit": "TFLOP/s",
-            "frac": None, "traffic": None, "peak_kind": pk_kind + " clock x 152 SM x 128 FP32 lanes x 2"}
 
 
 def run_reference(args):

@@ -108,15 +108,24 @@ typedef struct {
                             2-D covariance times -log2(e)/2, so alpha = o * 2^(a dx^2 +
                             2 b dx dy + c dy^2); rx, ry are the box half-extents (int32) */
     size_t touched;      /* uint32 [n_views*n] tiles covered */
-    size_t offsets;      /* uint32 [n_views*n] exclusive scan of touched */
-    size_t scan_tmp;     /* uint32 scratch of the scan */
-    size_t keys0, keys1; /* uint64 [max_pairs] ping-pong: (global tile << 32) | bits(z) */
-    size_t vals0, vals1; /* uint32 [max_pairs] ping-pong: view * n + Gaussian index */
-    size_t sort_tmp;     /* uint32 scratch of the radix sort */
+    size_t scan_tmp;     /* uint32 scratch of the scans */
+    size_t ekeys0, ekeys1; /* uint32 [n_views*n] ping-pong: bits(z) of the visible entries */
+    size_t evals0, evals1; /* uint32 [n_views*n] ping-pong: their view * n + Gaussian index;
+                              after gs_bin_sort evals0 lists the entries by depth */
+    size_t keys0, keys1; /* uint32 [max_pairs] ping-pong: global tile id of each pair */
+    size_t vals0, vals1; /* uint32 [max_pairs] ping-pong: view * n + Gaussian index; after
+                            gs_bin_sort buffer sorted_buf holds the pairs ordered by (tile,
+                            depth, view, index) */
+    size_t pair_mask;    /* uint8 [max_pairs] per sorted pair: the 8x4-pixel warp regions of
+                            its tile that hold pixels with alpha >= alpha_min (written by
+                            gs_render_fwd, read by the backward) */
+    size_t emit_tmp;     /* uint32 scratch of the pair emission */
+    size_t sort_tmp;     /* uint32 scratch of the radix sorts */
     size_t ranges;       /* uint32 [total_tiles][2] [first, last+1) in the sorted pairs */
     size_t T_final;      /* float [total_pixels] */
     size_t n_contrib;    /* uint32 [total_pixels] tile-list position after the last added */
-    size_t grad2d;       /* [n_views*n] records of 12 floats (screen-space gradient sums) */
+    size_t grad2d;       /* [n_views*n] records of 12 floats (screen-space gradient sums);
+                            only the records of visible entries are defined after a backward */
     size_t visible;      /* uint8 [n]: 1 if the Gaussian covers a tile of any view */
     size_t tile_order;   /* uint32 [total_tiles]: compositing work order, largest pair count
                             first (power-of-two buckets), then scratch */
@@ -133,9 +142,12 @@ typedef struct {
 /* Device-side counters copied back by gs_read_counters. */
 typedef struct {
     uint32_t status;     /* gs_status of the device work since the last reset */
-    uint32_t reserved;
+    uint32_t n_entries;  /* visible (view, Gaussian) entries of the last gs_bin_sort */
     uint64_t n_pairs;    /* (tile, Gaussian) pairs of the last gs_bin_sort */
     uint64_t adam_step;  /* Adam steps taken by gs_step / a captured graph */
+    uint64_t frag_fwd_eval, frag_fwd_add;  /* (pixel, Gaussian) fragments tested / added by the */
+    uint64_t frag_bwd_eval, frag_bwd_add;  /* forward and the backward compositing of the step  */
+    uint32_t visits_fwd, visits_bwd;       /* (record, warp) pairs the compositing loops walked */
 } gs_counters;
 
 /* Inputs and outputs of one batched step (gs_step / gs_graph_create).  Device pointers,
@@ -191,9 +203,11 @@ gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, const gs_rend
 /* a2-a4 -- Tile binning, (tile, depth) radix sort and tile ranges (§II-A tile-based
  * rasterizer).  A record with box half-extents rx, ry covers tiles x in
  * [floor((u-rx)/T), floor((u+rx)/T)] and y in [floor((v-ry)/T), floor((v+ry)/T)], clamped to
- * the view's grid, computed in FP32 exactly as written.  Pair key
- * = ((tile_offset(v) + ty*tiles_x + tx) << 32) | float_bits(z), value = v*n + i, emitted in
- * ascending (v, i) then row-major tile order and sorted stably by key.  If the pairs exceed
+ * the view's grid, computed in FP32 exactly as written.  The pairs (global tile id
+ * tile_offset(v) + ty*tiles_x + tx, value v*n + i) come out in the order of the key
+ * (tile id << 32) | float_bits(z) sorted stably from emission in ascending (v, i) then
+ * row-major tile order -- computed as a stable sort of the visible (v, i) entries by
+ * float_bits(z) followed by a stable sort of their pairs by tile id.  If the pairs exceed
  * max_pairs the status word becomes GS_ERR_CAPACITY, n_pairs holds the required count and
  * the later stages of the step do nothing. */
 gs_status gs_bin_sort(const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L,
@@ -219,29 +233,55 @@ gs_status gs_render_fwd(const gs_camera *cams, const gs_render_opts *opts, const
  * recomputed back to front from the stored final T (T_i = T_{i+1} / (1 - alpha_i)); no
  * per-fragment state is stored.  Gradients are ADDED to `grads` (same layout as g) and, if
  * grad_twist is non-NULL, to grad_twist [n_views][6]: the derivative w.r.t. the twist
- * xi = (rho, phi) of a left perturbation T_cw <- Exp(xi) T_cw of each view's pose. */
+ * xi = (rho, phi) of a left perturbation T_cw <- Exp(xi) T_cw of each view's pose.
+ * Only rows with a nonzero `visible` flag of the workspace (the Gaussian covers a tile of
+ * some view) are read and written; the other gradient rows are left as they are. */
 gs_status gs_render_bwd(const gs_gaussians *g, const gs_camera *cams, const gs_render_opts *opts,
                         const gs_ws_layout *L, void *ws, const float *dl_drgb,
                         const float *dl_ddepth, gs_gaussians *grads, float *grad_twist,
                         void *stream);
+
+/* a6 and a7 separately (gs_render_bwd = gs_composite_bwd then gs_project_bwd): the backward
+ * compositing into the workspace's per-(view, Gaussian) screen-space sums (cleared first), and
+ * the chain rule from those sums to the parameter gradients (added to grads) and the twists
+ * (added to grad_twist, may be NULL). */
+gs_status gs_composite_bwd(const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L,
+                           void *ws, const float *dl_drgb, const float *dl_ddepth, void *stream);
+gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *cams, const gs_render_opts *opts,
+                         const gs_ws_layout *L, void *ws, gs_gaussians *grads, float *grad_twist,
+                         void *stream);
 
 /* a8 -- Fused masked Adam (§III-C: visible and unfrozen Gaussians are refined by a sparse
  * gradient-based optimiser; only the most recent segments are updated).  Row i is updated
  * iff (update_mask == NULL or update_mask[i]) and (visible == NULL or visible[i]);
  * other rows keep p, m and v unchanged.  m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr_group * m_hat / (sqrt(v_hat) + eps) with bias correction by `step` (>= 1).
- * lr[6]: means, log-scales, quats, opacity, SH DC, SH rest.  Zeroes every gradient row
- * afterwards. */
+ * lr[6]: means, log-scales, quats, opacity, SH DC, SH rest.  Zeroes the gradient rows
+ * with visible[i] != 0 (all rows when visible == NULL) afterwards; rows with visible[i] ==
+ * 0 are neither read nor written -- gs_project_bwd leaves exactly those rows untouched,
+ * so after a step of gs_project_bwd + gs_adam_step every gradient row is zero again. */
 gs_status gs_adam_step(gs_gaussians *params, gs_gaussians *grads, gs_gaussians *m, gs_gaussians *v,
                        const uint8_t *update_mask, const uint8_t *visible, const float lr[6],
                        float b1, float b2, float eps, int64_t step, void *stream);
 
+/* a7 + a8 fused -- gs_project_bwd followed by gs_adam_step (with the workspace's visible
+ * flags) in one kernel: every visible row's gradient is formed in registers and applied by
+ * the masked Adam update directly, so the gradient planes are never written or read.
+ * Gives the same parameters, moments and twists as the two calls in sequence on zeroed
+ * gradients.  `params` is read and updated in place; step as for gs_adam_step. */
+gs_status gs_project_bwd_adam(gs_gaussians *params, const gs_camera *cams, const gs_render_opts *opts,
+                              const gs_ws_layout *L, void *ws, gs_gaussians *m, gs_gaussians *v,
+                              const uint8_t *update_mask, const float lr[6], float b1, float b2,
+                              float eps, int64_t step, float *grad_twist, void *stream);
+
 /* a9 -- The batched mapping step (§III-C: each iteration samples keyframes from the recent and
  * history windows and updates the visible, unfrozen Gaussians): gs_project, gs_bin_sort,
  * gs_render_fwd with the fused L1 loss, gs_render_bwd and, if io->optimize, the masked Adam
- * step, for every view of the batch, on one stream without host synchronisation.  Gradients
- * are accumulated into `grads` and zeroed again by the Adam step.  The Adam step counter is a
- * device counter in the workspace (gs_workspace_init sets it to 0), so the sequence can be
+ * step, for every view of the batch, on one stream without host synchronisation.  With
+ * io->optimize the projection backward and Adam run fused (gs_project_bwd_adam): each row's
+ * gradient goes straight into its Adam update and `grads` is neither read nor written;
+ * without it the gradients are added to `grads`.  The Adam step counter is a device
+ * counter in the workspace (gs_workspace_init sets it to 0), so the sequence can be
  * captured once and replayed. */
 gs_status gs_step(gs_gaussians *params, gs_gaussians *grads, gs_gaussians *m, gs_gaussians *v,
                   const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L, void *ws,

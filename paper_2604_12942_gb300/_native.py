@@ -34,15 +34,17 @@ class RenderOpts(C.Structure):
 
 
 class WsLayout(C.Structure):
-    _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "touched", "offsets", "scan_tmp",
-                                          "keys0", "keys1", "vals0", "vals1", "sort_tmp", "ranges", "T_final",
+    _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "touched", "scan_tmp",
+                                          "ekeys0", "ekeys1", "evals0", "evals1", "keys0", "keys1", "vals0", "vals1", "pair_mask", "emit_tmp", "sort_tmp", "ranges", "T_final",
                                           "n_contrib", "grad2d", "visible", "tile_order", "total")] + \
                [("sorted_buf", C.c_int32), ("total_tiles", C.c_int32), ("total_pixels", C.c_int64),
                 ("max_pairs", C.c_int64), ("n", C.c_int64), ("n_views", C.c_int32), ("tile", C.c_int32)]
 
 
 class Counters(C.Structure):
-    _fields_ = [("status", C.c_uint32), ("reserved", C.c_uint32), ("n_pairs", C.c_uint64), ("adam_step", C.c_uint64)]
+    _fields_ = [("status", C.c_uint32), ("n_entries", C.c_uint32), ("n_pairs", C.c_uint64), ("adam_step", C.c_uint64),
+                ("frag_fwd_eval", C.c_uint64), ("frag_fwd_add", C.c_uint64), ("frag_bwd_eval", C.c_uint64),
+                ("frag_bwd_add", C.c_uint64), ("visits_fwd", C.c_uint32), ("visits_bwd", C.c_uint32)]
 
 
 class StepIO(C.Structure):
@@ -90,6 +92,14 @@ _SIGS = {
                       [C.c_void_p] * 3 + [C.c_void_p] * 3 + [C.c_void_p], C.c_int),
     "gs_render_bwd": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p,
                        C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p], C.c_int),
+    "gs_composite_bwd": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.c_void_p,
+                          C.c_void_p, C.c_void_p], C.c_int),
+    "gs_project_bwd": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout),
+                        C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p], C.c_int),
+    "gs_project_bwd_adam": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout),
+                             C.c_void_p, C.POINTER(Gaussians), C.POINTER(Gaussians), C.c_void_p,
+                             C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float, C.c_int64, C.c_void_p,
+                             C.c_void_p], C.c_int),
     "gs_sort_pairs_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],
                               C.c_int),
     "gs_pca_workspace_size": ([C.c_int64], C.c_size_t),

@@ -139,6 +139,25 @@ class Workspace:
                                       _ptr(self.buf), _ptr(dl_drgb), _ptr(dl_ddepth), C.byref(gg),
                                       _ptr(grad_twist), _stream()), "gs_render_bwd")
 
+    def composite_bwd(self, dl_drgb, dl_ddepth=None):
+        N.check(N.lib().gs_composite_bwd(self.cams_c, C.byref(self.opts), C.byref(self.layout), _ptr(self.buf),
+                                         _ptr(dl_drgb), _ptr(dl_ddepth), _stream()), "gs_composite_bwd")
+
+    def project_bwd(self, planes, sh_degree, grad_planes, grad_twist=None):
+        g = gaussians_struct(planes, sh_degree)
+        gg = gaussians_struct(grad_planes, sh_degree)
+        N.check(N.lib().gs_project_bwd(C.byref(g), self.cams_c, C.byref(self.opts), C.byref(self.layout),
+                                       _ptr(self.buf), C.byref(gg), _ptr(grad_twist), _stream()), "gs_project_bwd")
+
+    def project_bwd_adam(self, planes, sh_degree, m, v, step, lr, update_mask=None, b1=0.9, b2=0.999, eps=1e-15,
+                         grad_twist=None):
+        """Fused projection backward + masked Adam (parameters, m, v updated in place)."""
+        gp, gm, gv = (gaussians_struct(t, sh_degree) for t in (planes, m, v))
+        lrs = (C.c_float * 6)(*lr)
+        N.check(N.lib().gs_project_bwd_adam(C.byref(gp), self.cams_c, C.byref(self.opts), C.byref(self.layout),
+                                            _ptr(self.buf), C.byref(gm), C.byref(gv), _ptr(update_mask), lrs, b1, b2,
+                                            eps, int(step), _ptr(grad_twist), _stream()), "gs_project_bwd_adam")
+
     def counters(self) -> N.Counters:
         c = N.Counters()
         N.check(N.lib().gs_read_counters(C.byref(self.layout), _ptr(self.buf), C.byref(c), _stream()),
@@ -147,9 +166,19 @@ class Workspace:
 
     # -- views of intermediate state (for tests) ------------------------------------------
     def sorted_pairs(self, n_pairs):
+        """The sorted pairs as (key, value) with key = (tile id << 32) | bits(z) -- the tile
+        ids from the sort's output, z from each value's projected record."""
         L = self.layout
         kname, vname = ("keys1", "vals1") if L.sorted_buf else ("keys0", "vals0")
-        return self.region(kname, torch.int64, n_pairs), self.region(vname, torch.int32, n_pairs)
+        tiles = self.region(kname, torch.int32, n_pairs).to(torch.int64) & 0xFFFFFFFF
+        vals = self.region(vname, torch.int32, n_pairs)
+        rec = self.region("proj", torch.int32, 12 * self.layout.n_views * self.n)
+        zbits = rec[vals.to(torch.int64) * 12 + 2].to(torch.int64) & 0xFFFFFFFF
+        return (tiles << 32) | zbits, vals
+
+    def sorted_entries(self, n_entries):
+        """The visible (view, Gaussian) entries in depth order (values view * n + index)."""
+        return self.region("evals0", torch.int32, n_entries)
 
     def visible(self):
         return self.region("visible", torch.uint8, self.n)

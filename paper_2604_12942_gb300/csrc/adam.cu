@@ -5,15 +5,11 @@
 
 namespace gs {
 
-__device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v, bool upd, float lr, const AdamArgs& a,
-                                         float bc1, float bc2) {
-    if (upd) {
-        m = a.b1 * m + (1.f - a.b1) * g;
-        v = a.b2 * v + (1.f - a.b2) * g * g;
-        const float mh = m / bc1, vh = v / bc2;
-        p -= lr * mh / (sqrtf(vh) + a.eps);
-    }
-    g = 0.f;
+// One row of one plane: update p, m, v if `upd`, consume (zero) the gradient if `vis`.
+__device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v, bool upd, bool vis, float lr,
+                                         const AdamArgs& a, float bc1, float bc2) {
+    if (upd) adam_update(p, g, m, v, lr, a.b1, a.b2, a.eps, bc1, bc2);
+    if (vis) g = 0.f;
 }
 
 // Advances the device-side Adam step counter and stores the bias corrections of that step
@@ -49,34 +45,52 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
     if (i0 >= n) return;
     const float bc1 = a.step_dev ? a.step_dev->adam_bc1 : a.bc1;
     const float bc2 = a.step_dev ? a.step_dev->adam_bc2 : a.bc2;
-    bool upd[4];
+    bool upd[4], vis[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         const int64_t i = i0 + q;
-        upd[q] = i < n && (!a.update_mask || a.update_mask[i]) && (!a.visible || a.visible[i]);
+        vis[q] = i < n && (!a.visible || a.visible[i]);
+        upd[q] = vis[q] && (!a.update_mask || a.update_mask[i]);
     }
+    // Rows outside `visible` received no gradient this step: nothing to read or write.
+    if (!(vis[0] | vis[1] | vis[2] | vis[3])) return;
+    const bool any_upd = upd[0] | upd[1] | upd[2] | upd[3];
     const bool vec = ((n & 3) == 0) && (((uintptr_t)P | (uintptr_t)G | (uintptr_t)M | (uintptr_t)V) & 15) == 0;
     if (vec) {
+        if (!any_upd) {   // visible but frozen: only consume the gradient
+            if (vis[0] & vis[1] & vis[2] & vis[3]) {
+                *reinterpret_cast<float4*>(G + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (vis[q]) G[i0 + q] = 0.f;
+            }
+            return;
+        }
         float4 p = *reinterpret_cast<float4*>(P + i0), g = *reinterpret_cast<float4*>(G + i0);
         float4 m = *reinterpret_cast<float4*>(M + i0), v = *reinterpret_cast<float4*>(V + i0);
-        adam_one(p.x, g.x, m.x, v.x, upd[0], lr, a, bc1, bc2);
-        adam_one(p.y, g.y, m.y, v.y, upd[1], lr, a, bc1, bc2);
-        adam_one(p.z, g.z, m.z, v.z, upd[2], lr, a, bc1, bc2);
-        adam_one(p.w, g.w, m.w, v.w, upd[3], lr, a, bc1, bc2);
+        adam_one(p.x, g.x, m.x, v.x, upd[0], vis[0], lr, a, bc1, bc2);
+        adam_one(p.y, g.y, m.y, v.y, upd[1], vis[1], lr, a, bc1, bc2);
+        adam_one(p.z, g.z, m.z, v.z, upd[2], vis[2], lr, a, bc1, bc2);
+        adam_one(p.w, g.w, m.w, v.w, upd[3], vis[3], lr, a, bc1, bc2);
         *reinterpret_cast<float4*>(P + i0) = p;
         *reinterpret_cast<float4*>(G + i0) = g;
-        if (upd[0] | upd[1] | upd[2] | upd[3]) {
-            *reinterpret_cast<float4*>(M + i0) = m;
-            *reinterpret_cast<float4*>(V + i0) = v;
-        }
+        *reinterpret_cast<float4*>(M + i0) = m;
+        *reinterpret_cast<float4*>(V + i0) = v;
     } else {
         for (int q = 0; q < 4 && i0 + q < n; q++) {
+            if (!vis[q]) continue;
             const int64_t i = i0 + q;
+            if (!upd[q]) {
+                G[i] = 0.f;
+                continue;
+            }
             float p = P[i], g = G[i], m = M[i], v = V[i];
-            adam_one(p, g, m, v, upd[q], lr, a, bc1, bc2);
+            adam_one(p, g, m, v, true, true, lr, a, bc1, bc2);
             P[i] = p;
             G[i] = g;
-            if (upd[q]) { M[i] = m; V[i] = v; }
+            M[i] = m;
+            V[i] = v;
         }
     }
 }

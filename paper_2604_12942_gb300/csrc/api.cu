@@ -94,11 +94,11 @@ static int tile_bits(int total_tiles) {
     return b;
 }
 
-static int sort_passes(int total_tiles, int* shifts) {
+// Passes of the pair sort: 8-bit digits over the global tile id bits (0 when one tile).
+static int pair_sort_passes(int total_tiles, int* shifts) {
     int np = 0;
-    for (int s = 0; s < 32; s += 8) shifts[np++] = s;
     const int tb = tile_bits(total_tiles);
-    for (int s = 0; s < tb; s += 8) shifts[np++] = 32 + s;
+    for (int s = 0; s < tb; s += 8) shifts[np++] = s;
     return np;
 }
 
@@ -118,13 +118,18 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.loss_acc = take(sizeof(double) * 2 * GS_MAX_VIEWS + sizeof(uint32_t) * 2 * GS_MAX_VIEWS);
     L.proj = take(sizeof(float) * 12 * (size_t)VN);
     L.touched = take(sizeof(uint32_t) * (size_t)VN);
-    L.offsets = take(sizeof(uint32_t) * (size_t)VN);
     L.scan_tmp = take(sizeof(uint32_t) * ((size_t)VN / kScanBlock + 2));
-    L.keys0 = take(sizeof(unsigned long long) * (size_t)max_pairs);
-    L.keys1 = take(sizeof(unsigned long long) * (size_t)max_pairs);
+    L.ekeys0 = take(sizeof(uint32_t) * (size_t)VN);
+    L.ekeys1 = take(sizeof(uint32_t) * (size_t)VN);
+    L.evals0 = take(sizeof(uint32_t) * (size_t)VN);
+    L.evals1 = take(sizeof(uint32_t) * (size_t)VN);
+    L.keys0 = take(sizeof(uint32_t) * (size_t)max_pairs);
+    L.keys1 = take(sizeof(uint32_t) * (size_t)max_pairs);
     L.vals0 = take(sizeof(uint32_t) * (size_t)max_pairs);
     L.vals1 = take(sizeof(uint32_t) * (size_t)max_pairs);
-    L.sort_tmp = take(sizeof(uint32_t) * ((size_t)kSortBins * 4096 + kSortBins));
+    L.pair_mask = take((size_t)max_pairs);
+    L.emit_tmp = take(sizeof(uint32_t) * ((size_t)max_pairs / kEmitChunk + 2));
+    L.sort_tmp = take(sizeof(uint32_t) * ((size_t)kSortBins * kSortMaxGrid + kSortBins));
     L.ranges = take(sizeof(uint32_t) * 2 * (size_t)G.total_tiles);
     L.T_final = take(sizeof(float) * (size_t)G.total_pixels);
     L.n_contrib = take(sizeof(uint32_t) * (size_t)G.total_pixels);
@@ -133,7 +138,7 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.tile_order = take(sizeof(uint32_t) * ((size_t)G.total_tiles + 2 * 34));
     L.total = off;
     int shifts[16];
-    L.sorted_buf = sort_passes(G.total_tiles, shifts) & 1;
+    L.sorted_buf = pair_sort_passes(G.total_tiles, shifts) & 1;
     L.total_tiles = G.total_tiles;
     L.total_pixels = G.total_pixels;
     L.max_pairs = max_pairs;
@@ -231,31 +236,45 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     b.max_pairs = L->max_pairs;
     b.proj = at<float4>(ws, L->proj);
     b.touched = at<uint32_t>(ws, L->touched);
-    b.offsets = at<uint32_t>(ws, L->offsets);
     b.scan_tmp = at<uint32_t>(ws, L->scan_tmp);
-    b.keys = at<unsigned long long>(ws, L->keys0);
-    b.vals = at<uint32_t>(ws, L->vals0);
+    b.ekeys = at<uint32_t>(ws, L->ekeys0);
+    b.evals = at<uint32_t>(ws, L->evals0);
+    b.sorted_evals = at<uint32_t>(ws, L->evals0);   // 4 passes: the entry sort ends in buffer 0
+    b.pkeys = at<uint32_t>(ws, L->keys0);
+    b.pvals = at<uint32_t>(ws, L->vals0);
+    b.poff = at<uint32_t>(ws, L->ekeys1);           // free once the entries are sorted
+    b.chunk_first = at<uint32_t>(ws, L->emit_tmp);
     b.counters = cnt;
-    cudaError_t e = launch_bin(b, st);
+    cudaError_t e = launch_entries(b, st);
     if (e != cudaSuccess) return e;
     SortArgs sa;
-    sa.keys[0] = at<unsigned long long>(ws, L->keys0);
-    sa.keys[1] = at<unsigned long long>(ws, L->keys1);
+    sa.hist = at<uint32_t>(ws, L->sort_tmp);
+    sa.digit_tot = sa.hist + (size_t)kSortBins * kSortMaxGrid;
+    sa.counters = cnt;
+    sa.grid = sort_grid();
+    // 1. entries by depth
+    sa.keys[0] = at<uint32_t>(ws, L->ekeys0);
+    sa.keys[1] = at<uint32_t>(ws, L->ekeys1);
+    sa.vals[0] = at<uint32_t>(ws, L->evals0);
+    sa.vals[1] = at<uint32_t>(ws, L->evals1);
+    sa.count = &cnt->n_entries;
+    const int depth_shifts[4] = {0, 8, 16, 24};
+    if ((e = launch_sort32(sa, 4, depth_shifts, st)) != cudaSuccess) return e;
+    // 2. pairs emitted in depth order, then by tile
+    if ((e = launch_emit(b, st)) != cudaSuccess) return e;
+    sa.keys[0] = at<uint32_t>(ws, L->keys0);
+    sa.keys[1] = at<uint32_t>(ws, L->keys1);
     sa.vals[0] = at<uint32_t>(ws, L->vals0);
     sa.vals[1] = at<uint32_t>(ws, L->vals1);
-    sa.grid = sort_grid();
-    if (sa.grid > 4096) sa.grid = 4096;
-    sa.hist = at<uint32_t>(ws, L->sort_tmp);
-    sa.digit_tot = sa.hist + (size_t)kSortBins * 4096;
-    sa.counters = cnt;
+    sa.count = &cnt->n_pairs;
     int shifts[16];
-    const int np = sort_passes(L->total_tiles, shifts);
-    if ((e = launch_sort(sa, np, shifts, st)) != cudaSuccess) return e;
+    const int np = pair_sort_passes(L->total_tiles, shifts);
+    if ((e = launch_sort32(sa, np, shifts, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(at<uint32_t>(ws, L->ranges), 0, sizeof(uint32_t) * 2 * (size_t)L->total_tiles, st)) !=
         cudaSuccess)
         return e;
     RangeArgs r;
-    r.keys = sa.keys[np & 1];
+    r.keys = static_cast<const uint32_t*>(sa.keys[np & 1]);
     r.ranges = at<uint2>(ws, L->ranges);
     r.counters = cnt;
     if ((e = launch_ranges(r, L->total_tiles, st)) != cudaSuccess) return e;
@@ -287,6 +306,7 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
     a.ranges = at<uint2>(ws, L->ranges);
     a.order = at<uint32_t>(ws, L->tile_order);
     a.counters = at<Counters>(ws, L->counters);
+    a.pair_mask = at<uint8_t>(ws, L->pair_mask);
     a.T_final = at<float>(ws, L->T_final);
     a.n_contrib = at<uint32_t>(ws, L->n_contrib);
     a.out_rgb = out_rgb;
@@ -306,12 +326,8 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
     return cudaSuccess;
 }
 
-static cudaError_t run_bwd(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
-                           const float* dl_drgb, const float* dl_ddepth, gs_gaussians* grads, float* grad_twist,
-                           cudaStream_t st) {
-    const int64_t VN = (int64_t)L->n_views * L->n;
-    cudaError_t e = cudaMemsetAsync(at<float>(ws, L->grad2d), 0, sizeof(float) * 12 * (size_t)VN, st);
-    if (e != cudaSuccess) return e;
+static cudaError_t run_composite_bwd(const gs_render_opts* opts, const gs_ws_layout* L, void* ws, const float* dl_drgb,
+                                     const float* dl_ddepth, cudaStream_t st) {
     BwdArgs b;
     b.n_views = L->n_views;
     b.views = at<View>(ws, L->views);
@@ -321,24 +337,70 @@ static cudaError_t run_bwd(const gs_gaussians* g, const gs_render_opts* opts, co
     b.ranges = at<uint2>(ws, L->ranges);
     b.order = at<uint32_t>(ws, L->tile_order);
     b.counters = at<Counters>(ws, L->counters);
+    b.pair_mask = at<uint8_t>(ws, L->pair_mask);
+    b.entries = at<uint32_t>(ws, L->evals0);
     b.T_final = at<float>(ws, L->T_final);
     b.n_contrib = at<uint32_t>(ws, L->n_contrib);
     b.dl_drgb = dl_drgb;
     b.dl_ddepth = dl_ddepth;
     b.grad2d = at<float4>(ws, L->grad2d);
-    if ((e = launch_render_bwd(b, L->total_tiles, st)) != cudaSuccess) return e;
+    return launch_render_bwd(b, L->total_tiles, st);
+}
+
+// Adam settings of the fused projection backward (a7 + a8).
+struct FusedAdam {
+    gs_gaussians *params, *m, *v;
+    const uint8_t* update_mask;
+    const float* lr;
+    float b1, b2, eps;
+    int64_t step;                // host step (used when step_dev is null)
+    const Counters* step_dev;
+};
+
+static cudaError_t run_project_bwd(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                                   gs_gaussians* grads, float* grad_twist, cudaStream_t st,
+                                   const FusedAdam* fa = nullptr) {
     ProjectBwdArgs p;
+    memset(&p, 0, sizeof(p));
     p.n = L->n;
     p.n_views = L->n_views;
     p.views = at<View>(ws, L->views);
     p.op = to_opts(opts);
     p.means = g->means; p.log_scales = g->log_scales; p.quats = g->quats; p.logits = g->opacity_logits; p.sh = g->sh;
     p.touched = at<uint32_t>(ws, L->touched);
+    p.visible = at<uint8_t>(ws, L->visible);
     p.grad2d = at<float4>(ws, L->grad2d);
-    p.g_means = grads->means; p.g_log_scales = grads->log_scales; p.g_quats = grads->quats;
-    p.g_logits = grads->opacity_logits; p.g_sh = grads->sh;
+    if (grads) {
+        p.g_means = grads->means; p.g_log_scales = grads->log_scales; p.g_quats = grads->quats;
+        p.g_logits = grads->opacity_logits; p.g_sh = grads->sh;
+    }
     p.grad_twist = grad_twist;
+    if (fa) {
+        p.fused_adam = 1;
+        p.p_means = fa->params->means; p.p_log_scales = fa->params->log_scales; p.p_quats = fa->params->quats;
+        p.p_logits = fa->params->opacity_logits; p.p_sh = fa->params->sh;
+        const gs_gaussians* mv[2] = {fa->m, fa->v};
+        float** dst[2] = {p.m, p.v};
+        for (int k = 0; k < 2; k++) {
+            dst[k][0] = mv[k]->means; dst[k][1] = mv[k]->log_scales; dst[k][2] = mv[k]->quats;
+            dst[k][3] = mv[k]->opacity_logits; dst[k][4] = mv[k]->sh;
+        }
+        p.update_mask = fa->update_mask;
+        for (int k = 0; k < 6; k++) p.lr[k] = fa->lr[k];
+        p.b1 = fa->b1; p.b2 = fa->b2; p.eps = fa->eps;
+        p.bc1 = fa->step > 0 ? (float)(1.0 - pow((double)fa->b1, (double)fa->step)) : 1.f;
+        p.bc2 = fa->step > 0 ? (float)(1.0 - pow((double)fa->b2, (double)fa->step)) : 1.f;
+        p.step_dev = fa->step_dev;
+    }
     return launch_project_bwd(p, g->sh_degree, st);
+}
+
+static cudaError_t run_bwd(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                           const float* dl_drgb, const float* dl_ddepth, gs_gaussians* grads, float* grad_twist,
+                           cudaStream_t st) {
+    cudaError_t e = run_composite_bwd(opts, L, ws, dl_drgb, dl_ddepth, st);
+    if (e != cudaSuccess) return e;
+    return run_project_bwd(g, opts, L, ws, grads, grad_twist, st);
 }
 
 static gs_status check_adam(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
@@ -402,13 +464,15 @@ static gs_status run_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussian
     GS_CUDA(run_fwd(opts, L, G, ws, io->out_rgb, io->out_depth, nullptr, io->target_rgb, io->target_depth, io->mask,
                     io->dl_drgb, io->target_depth ? io->dl_ddepth : nullptr, io->loss_out, st));
     if (io->grad_twist) GS_CUDA(cudaMemsetAsync(io->grad_twist, 0, sizeof(float) * 6 * L->n_views, st));
-    GS_CUDA(run_bwd(params, opts, L, ws, io->dl_drgb, io->target_depth ? io->dl_ddepth : nullptr, grads,
-                    io->grad_twist, st));
+    const float* dl_dd = io->target_depth ? io->dl_ddepth : nullptr;
     if (io->optimize) {
         Counters* c = at<Counters>(ws, L->counters);
+        GS_CUDA(run_composite_bwd(opts, L, ws, io->dl_drgb, dl_dd, st));
         GS_CUDA(launch_adam_step_counter(c, io->b1, io->b2, st));
-        GS_CUDA(run_adam(params, grads, m, v, io->update_mask, at<uint8_t>(ws, L->visible), io->lr, io->b1, io->b2,
-                         io->eps, 0, c, st));
+        FusedAdam fa{params, m, v, io->update_mask, io->lr, io->b1, io->b2, io->eps, 0, c};
+        GS_CUDA(run_project_bwd(params, opts, L, ws, nullptr, io->grad_twist, st, &fa));
+    } else {
+        GS_CUDA(run_bwd(params, opts, L, ws, io->dl_drgb, dl_dd, grads, io->grad_twist, st));
     }
     return GS_OK;
 }
@@ -485,9 +549,15 @@ gs_status gs_read_counters(const gs_ws_layout* L, const void* ws, gs_counters* o
     GS_CUDA(cudaMemcpyAsync(&c, at<Counters>(const_cast<void*>(ws), L->counters), sizeof(c), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
     out->status = c.status;
-    out->reserved = 0;
+    out->n_entries = c.n_entries32;
     out->n_pairs = c.n_pairs;
     out->adam_step = c.adam_step;
+    out->frag_fwd_eval = c.frag_fwd_eval;
+    out->frag_fwd_add = c.frag_fwd_add;
+    out->frag_bwd_eval = c.frag_bwd_eval;
+    out->frag_bwd_add = c.frag_bwd_add;
+    out->visits_fwd = c.visits_fwd;
+    out->visits_bwd = c.visits_bwd;
     return GS_OK;
 }
 
@@ -557,6 +627,54 @@ gs_status gs_render_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_r
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
     GS_CUDA(run_bwd(g, opts, L, ws, dl_drgb, dl_ddepth, grads, grad_twist, st));
+    return GS_OK;
+}
+
+gs_status gs_composite_bwd(const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                           const float* dl_drgb, const float* dl_ddepth, void* stream) {
+    gs_status s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    if (!dl_drgb) return fail(GS_ERR_INVALID_ARG, "dl_drgb is required");
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    GS_CUDA(run_composite_bwd(opts, L, ws, dl_drgb, dl_ddepth, st));
+    return GS_OK;
+}
+
+gs_status gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_render_opts* opts,
+                         const gs_ws_layout* L, void* ws, gs_gaussians* grads, float* grad_twist, void* stream) {
+    gs_status s = check_gaussians(g, true);
+    if (s != GS_OK) return s;
+    if ((s = check_gaussians(grads, true)) != GS_OK) return s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    if (g->n != L->n || grads->n != L->n || grads->sh_degree != g->sh_degree)
+        return fail(GS_ERR_INVALID_ARG, "gaussians / grads do not match the layout");
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    GS_CUDA(run_project_bwd(g, opts, L, ws, grads, grad_twist, st));
+    return GS_OK;
+}
+
+gs_status gs_project_bwd_adam(gs_gaussians* params, const gs_camera* cams, const gs_render_opts* opts,
+                              const gs_ws_layout* L, void* ws, gs_gaussians* m, gs_gaussians* v,
+                              const uint8_t* update_mask, const float lr[6], float b1, float b2, float eps,
+                              int64_t step, float* grad_twist, void* stream) {
+    gs_status s;
+    // the parameter planes stand in for the (unused) gradient planes in the shape checks
+    if ((s = check_adam(params, params, m, v, lr, b1, b2, eps)) != GS_OK) return s;
+    if (step < 1) return fail(GS_ERR_INVALID_ARG, "step must be >= 1");
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    if (params->n != L->n) return fail(GS_ERR_INVALID_ARG, "gaussians do not match the layout");
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    FusedAdam fa{params, m, v, update_mask, lr, b1, b2, eps, step, nullptr};
+    GS_CUDA(run_project_bwd(params, opts, L, ws, nullptr, grad_twist, st, &fa));
     return GS_OK;
 }
 

@@ -1,18 +1,28 @@
-// a2-a4: tile binning (scan of tiles-touched, pair emission), the stable LSD radix sort of
-// the (tile, depth) keys and the per-tile ranges.  Tile-based rasterizer of §II-A / §III-C.
+// a2-a4: tile binning, the stable LSD radix sorts and the per-tile ranges.  Tile-based
+// rasterizer of §II-A / §III-C: every Gaussian is listed, in depth order, in each tile its
+// alpha >= alpha_min box covers.
 //
-// The sort runs on a fixed grid (a multiple of the SM count) whose blocks each own a
-// contiguous run of chunks; the pair count is read on the device, so no host round trip
-// or re-launch is needed between binning and sorting and the whole sequence can be
-// captured in a CUDA graph.  Every pass: per-block digit histograms (upsweep), a scan of
-// the histograms (one block, one warp per digit), then a stable scatter (downsweep) that
-// ranks each chunk with warp match/ballot counting and writes digit runs contiguously.
+// The required order is (global tile, depth, view, Gaussian index).  Instead of one sort on
+// a (tile << 32 | bits(z)) key over all pairs, the binning sorts twice:
+//   1. the visible (view, Gaussian) entries -- compacted in (view, index) order -- by the
+//      32-bit depth key (4 passes over the entries, about a fifth of the pairs);
+//   2. the pairs, emitted from the depth-sorted entries, by the global tile id alone
+//      (ceil(tile bits / 8) passes with 32-bit keys).
+// Both sorts are stable, so pass 2 keeps the depth order within a tile and pass 1 keeps
+// (view, index) order between equal depths: the result is the order above.
+//
+// The sorts run on a fixed grid (a multiple of the SM count) whose blocks each own a
+// contiguous run of chunks; element counts are read on the device, so no host round trip
+// is needed between the stages and the whole sequence can be captured in a CUDA graph.
+// Every pass: per-block digit histograms (upsweep), a per-digit scan over the blocks (one
+// warp per digit), then a stable scatter (downsweep) that ranks each chunk with warp
+// ballot counting and writes digit runs contiguously.
 #include "gs_kernels.cuh"
 
 namespace gs {
 
 // ----------------------------------------------------------------------------------------
-// Exclusive scan of tiles-touched -> pair offsets and the pair count.
+// Block-wide scans.
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t block_exclusive_scan_1024(uint32_t x, uint32_t* s_warp, uint32_t& total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -42,7 +52,36 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_1024(uint32_t x, uint32
     return r;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n,
+// One block: exclusive scan of nb block sums in place; the total goes to *total_out and
+// sets GS_ERR_CAPACITY when it exceeds max_total (max_total < 0: no limit).
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t* __restrict__ bsum, int nb,
+                                                                  unsigned long long* total_out,
+                                                                  uint32_t* total32_out, Counters* c,
+                                                                  int64_t max_total) {
+    __shared__ uint32_t s[33];
+    if (c->status != 0) return;
+    unsigned long long carry = 0;
+    for (int base = 0; base < nb; base += kScanThreads) {
+        const int j = base + threadIdx.x;
+        const uint32_t x = j < nb ? bsum[j] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan_1024(x, s, tot);
+        if (j < nb) bsum[j] = (uint32_t)(carry + ex);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        *total_out = carry;
+        if (total32_out) *total32_out = (uint32_t)carry;
+        if (max_total >= 0 && carry > (unsigned long long)max_total) set_status(c, GS_ERR_CAPACITY);
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// Entry compaction: block b of kScanBlock (view, Gaussian) slots counts its visible
+// entries, the block counts are scanned, then each block writes its entries' depth keys
+// and ids at their offsets (so entries stay in (view, index) order).
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) entry_count_kernel(const uint32_t* __restrict__ touched, int64_t n,
                                                                   uint32_t* __restrict__ bsum) {
     __shared__ uint32_t s[33];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
@@ -50,7 +89,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
         const int64_t j = base + (int64_t)k * kScanThreads + threadIdx.x;
-        if (j < n) sum += in[j];
+        if (j < n) sum += touched[j] != 0u;
     }
     sum = warp_sum(sum);
     if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = sum;
@@ -62,156 +101,169 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_
     }
 }
 
-// One block: exclusive scan of the block sums, the pair count and the capacity check.
-__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t* __restrict__ bsum, int nb,
-                                                                  Counters* c, int64_t max_pairs) {
+__global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, int64_t n) {
     __shared__ uint32_t s[33];
-    unsigned long long carry = 0;
-    for (int base = 0; base < nb; base += kScanThreads) {
-        const int j = base + threadIdx.x;
-        const uint32_t x = j < nb ? bsum[j] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan_1024(x, s, tot);
-        if (j < nb) bsum[j] = (uint32_t)(carry + ex);
-        carry += tot;
-    }
-    if (threadIdx.x == 0) {
-        c->n_pairs = carry;
-        if (carry > (unsigned long long)max_pairs) set_status(c, GS_ERR_CAPACITY);
-    }
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t* __restrict__ in, int64_t n,
-                                                                const uint32_t* __restrict__ bsum,
-                                                                uint32_t* __restrict__ out) {
-    __shared__ uint32_t s[33];
+    if (a.counters->status != 0) return;
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
-    uint32_t x[kScanItems], sum = 0;
+    uint32_t f[kScanItems], sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
-        x[k] = (base + k < n) ? in[base + k] : 0u;
-        sum += x[k];
+        f[k] = (base + k < n) ? (a.touched[base + k] != 0u) : 0u;
+        sum += f[k];
     }
     uint32_t tot;
-    uint32_t run = block_exclusive_scan_1024(sum, s, tot) + bsum[blockIdx.x];
+    uint32_t off = block_exclusive_scan_1024(sum, s, tot) + a.scan_tmp[blockIdx.x];
+    const float* pf = reinterpret_cast<const float*>(a.proj);
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
-        if (base + k < n) out[base + k] = run;
-        run += x[k];
-    }
-}
-
-// One thread per (view, Gaussian): write its pairs at its scanned offset.
-__global__ void __launch_bounds__(256) emit_kernel(BinArgs a) {
-    if (a.counters->status != 0) return;
-    const int64_t total = (int64_t)a.n_views * a.n;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = a.touched[idx];
-        if (t == 0) continue;
-        const int v = (int)(idx / a.n);
-        const View& V = a.views[v];
-        const float4 r0 = a.proj[3 * idx];
-        const int rx = __float_as_int(a.proj[3 * idx + 1].w);
-        const int ry = __float_as_int(a.proj[3 * idx + 2].w);
-        int x0, x1, y0, y1;
-        if (!tile_span(r0.x, rx, a.tile, V.tiles_x, x0, x1) || !tile_span(r0.y, ry, a.tile, V.tiles_y, y0, y1))
-            continue;
-        const unsigned long long zb = (unsigned long long)__float_as_uint(r0.z);
-        uint32_t off = a.offsets[idx];
-        for (int ty = y0; ty <= y1; ty++) {
-            for (int tx = x0; tx <= x1; tx++) {
-                const unsigned long long tileid = (unsigned long long)(V.tile_off + ty * V.tiles_x + tx);
-                a.keys[off] = (tileid << 32) | zb;
-                a.vals[off] = (uint32_t)idx;
-                off++;
-            }
+        if (f[k]) {
+            const int64_t idx = base + k;
+            a.ekeys[off] = __float_as_uint(__ldg(pf + 12 * idx + 2));   // z > 0: bits are monotone
+            a.evals[off] = (uint32_t)idx;
+            off++;
         }
     }
 }
 
-cudaError_t launch_exclusive_scan(const uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp, Counters* c,
-                                  int64_t max_total, cudaStream_t st) {
-    const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
-    if (nb > 0) scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, tmp);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(tmp, nb, c, max_total);
-    if (nb > 0) scan_down_kernel<<<nb, kScanThreads, 0, st>>>(in, n, tmp, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bin(const BinArgs& a, cudaStream_t st) {
+cudaError_t launch_entries(const BinArgs& a, cudaStream_t st) {
     const int64_t total = (int64_t)a.n_views * a.n;
-    cudaError_t e = launch_exclusive_scan(a.touched, total, a.offsets, a.scan_tmp, a.counters, a.max_pairs, st);
-    if (e != cudaSuccess) return e;
-    const int64_t eb64 = (total + 255) / 256;
-    const int eb = (int)(eb64 < 152 * 32 ? eb64 : 152 * 32);
-    if (eb > 0) emit_kernel<<<eb, 256, 0, st>>>(a);
+    const int nb = (int)((total + kScanBlock - 1) / kScanBlock);
+    if (nb > 0) entry_count_kernel<<<nb, kScanThreads, 0, st>>>(a.touched, total, a.scan_tmp);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(a.scan_tmp, nb, &a.counters->n_entries, &a.counters->n_entries32,
+                                                   a.counters, -1);
+    if (nb > 0) entry_compact_kernel<<<nb, kScanThreads, 0, st>>>(a, total);
     return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------------------
-// Radix sort.
+// Pair emission from the depth-sorted entries: the tiles-touched counts gathered in that
+// order are scanned into pair offsets (total = pair count), then each entry writes one
+// (global tile id, entry id) pair per covered tile, tiles in row-major order.
 // ----------------------------------------------------------------------------------------
-__device__ __forceinline__ void chunk_span(const Counters* c, int grid, int b, int64_t& lo, int64_t& hi) {
-    const int64_t P = (int64_t)c->n_pairs;
+__global__ void __launch_bounds__(kScanThreads) pair_count_kernel(BinArgs a) {
+    __shared__ uint32_t s[33];
+    const int64_t E = (int64_t)a.counters->n_entries;
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    uint32_t sum = 0;
+    if (base < E) {
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            const int64_t j = base + (int64_t)k * kScanThreads + threadIdx.x;
+            if (j < E) sum += __ldg(a.touched + a.sorted_evals[j]);
+        }
+    }
+    sum = warp_sum(sum);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = threadIdx.x < (kScanThreads >> 5) ? s[threadIdx.x] : 0u;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) a.scan_tmp[blockIdx.x] = t;
+    }
+}
+
+// Pair offsets of the depth-sorted entries (poff[e] = pairs of the entries before e), and
+// for every output chunk of kEmitChunk pairs the entry holding its first pair.
+__global__ void __launch_bounds__(kScanThreads) pair_offsets_kernel(BinArgs a) {
+    __shared__ uint32_t s[33];
+    if (a.counters->status != 0) return;
+    const int64_t E = (int64_t)a.counters->n_entries;
+    if ((int64_t)blockIdx.x * kScanBlock >= E) return;
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    uint32_t t[kScanItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        t[k] = base + k < E ? __ldg(a.touched + a.sorted_evals[base + k]) : 0u;
+        sum += t[k];
+    }
+    uint32_t tot;
+    uint32_t off = block_exclusive_scan_1024(sum, s, tot) + a.scan_tmp[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        if (base + k < E) {
+            a.poff[base + k] = off;
+            // chunk starts c * kEmitChunk inside [off, off + t)
+            for (uint32_t c = (off + kEmitChunk - 1) / kEmitChunk; c * (uint64_t)kEmitChunk < (uint64_t)off + t[k]; c++)
+                a.chunk_first[c] = (uint32_t)(base + k);
+        }
+        off += t[k];
+    }
+}
+
+// Emission balanced over the output: a block takes chunks of kEmitChunk consecutive pairs,
+// stages the entries they come from (at most kEmitChunk + 1) with their tile rectangles in
+// shared memory, and each thread writes pairs p0 + tid, p0 + tid + 256, ... after a binary
+// search for its entry.  Stores are contiguous across the block; a few entries with very
+// many tiles no longer serialise on one warp.
+__global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
+    __shared__ uint32_t s_off[kEmitChunk + 1], s_row0[kEmitChunk + 1], s_id[kEmitChunk + 1];
+    __shared__ uint16_t s_x0[kEmitChunk + 1], s_wx[kEmitChunk + 1], s_tx[kEmitChunk + 1];
+    if (a.counters->status != 0) return;
+    const uint64_t P = a.counters->n_pairs;
+    const int64_t E = (int64_t)a.counters->n_entries;
+    const uint64_t n_chunks = (P + kEmitChunk - 1) / kEmitChunk;
+    for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const uint64_t p0 = c * kEmitChunk, p1 = p0 + kEmitChunk < P ? p0 + kEmitChunk : P;
+        const int64_t e0 = a.chunk_first[c];
+        const int64_t e1 = c + 1 < n_chunks ? (int64_t)a.chunk_first[c + 1] : E - 1;
+        const int ne = (int)(e1 - e0 + 1);   // <= kEmitChunk + 1: every entry has >= 1 pair
+        for (int j = threadIdx.x; j < ne; j += blockDim.x) {
+            const int64_t e = e0 + j;
+            const uint32_t idx = a.sorted_evals[e];
+            const View& V = a.views[(int)(idx / a.n)];
+            const float4 r0 = __ldg(a.proj + 3 * (size_t)idx);
+            const int rx = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 1).w);
+            const int ry = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 2).w);
+            int xa, xb, ya, yb;
+            tile_span(r0.x, rx, a.tile, V.tiles_x, xa, xb);
+            tile_span(r0.y, ry, a.tile, V.tiles_y, ya, yb);
+            s_off[j] = a.poff[e];
+            s_row0[j] = (uint32_t)(V.tile_off + ya * V.tiles_x);
+            s_id[j] = idx;
+            s_x0[j] = (uint16_t)xa;
+            s_wx[j] = (uint16_t)(xb - xa + 1);
+            s_tx[j] = (uint16_t)V.tiles_x;
+        }
+        __syncthreads();
+        for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const uint32_t pp = (uint32_t)p;
+            int lo = 0, hi = ne - 1;   // last j with s_off[j] <= p
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= pp) lo = mid; else hi = mid - 1;
+            }
+            const uint32_t kk = pp - s_off[lo], wx = s_wx[lo];
+            const uint32_t ty = kk / wx, tx = kk - ty * wx;
+            a.pkeys[p] = s_row0[lo] + ty * (uint32_t)s_tx[lo] + (uint32_t)s_x0[lo] + tx;
+            a.pvals[p] = s_id[lo];
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_emit(const BinArgs& a, cudaStream_t st) {
+    const int64_t total = (int64_t)a.n_views * a.n;   // upper bound of the entry count
+    const int nb = (int)((total + kScanBlock - 1) / kScanBlock);
+    if (nb > 0) pair_count_kernel<<<nb, kScanThreads, 0, st>>>(a);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(a.scan_tmp, nb, &a.counters->n_pairs, nullptr, a.counters,
+                                                   a.max_pairs);
+    if (nb > 0) pair_offsets_kernel<<<nb, kScanThreads, 0, st>>>(a);
+    pair_emit_kernel<<<sort_grid() * 2, kEmitThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------
+// Radix sort (8-bit digits), keys K = uint32_t or unsigned long long.
+// ----------------------------------------------------------------------------------------
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kItemsPerWarp = kSortChunk / kSortWarps;   // 512
+
+__device__ __forceinline__ void chunk_span(unsigned long long count, int grid, int b, int64_t& lo, int64_t& hi) {
+    const int64_t P = (int64_t)count;
     const int64_t nch = (P + kSortChunk - 1) / kSortChunk;
     const int64_t c0 = nch * b / grid, c1 = nch * (b + 1) / grid;
     lo = c0 * kSortChunk;
     hi = min(c1 * kSortChunk, P);
-}
-
-__global__ void __launch_bounds__(kSortThreads) sort_upsweep_kernel(SortArgs a, int in_buf, int shift) {
-    // one private histogram per warp keeps shared-memory atomics on a digit to one warp
-    __shared__ uint32_t h[kSortThreads / 32][kSortBins];
-    if (a.counters->status != 0) return;
-    for (int t = threadIdx.x; t < (kSortThreads / 32) * kSortBins; t += blockDim.x) (&h[0][0])[t] = 0;
-    __syncthreads();
-    int64_t lo, hi;
-    chunk_span(a.counters, a.grid, blockIdx.x, lo, hi);
-    const unsigned long long* keys = a.keys[in_buf];
-    uint32_t* hw = h[threadIdx.x >> 5];
-    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-        const uint32_t d = (uint32_t)(keys[j] >> shift) & (kSortBins - 1);
-        atomicAdd(&hw[d], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) {
-        uint32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < kSortThreads / 32; w++) s += h[w][d];
-        a.hist[(int64_t)d * a.grid + blockIdx.x] = s;
-    }
-}
-
-// One block of 1024 threads: per digit (one warp per 8 digits) exclusive prefix over the
-// blocks; digit totals scanned into digit_tot as the start of each digit's output run.
-__global__ void __launch_bounds__(1024) sort_scan_kernel(SortArgs a) {
-    __shared__ uint32_t s_tot[kSortBins];
-    __shared__ uint32_t s_w[33];
-    if (a.counters->status != 0) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int d = w; d < kSortBins; d += 32) {
-        uint32_t* row = a.hist + (int64_t)d * a.grid;
-        uint32_t carry = 0;
-        for (int b0 = 0; b0 < a.grid; b0 += 32) {
-            const int b = b0 + lane;
-            const uint32_t x = b < a.grid ? row[b] : 0u;
-            uint32_t inc = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (b < a.grid) row[b] = carry + inc - x;
-            carry += __shfl_sync(0xffffffffu, inc, 31);
-        }
-        if (lane == 0) s_tot[d] = carry;
-    }
-    __syncthreads();
-    uint32_t tot;
-    const uint32_t x = threadIdx.x < kSortBins ? s_tot[threadIdx.x] : 0u;
-    const uint32_t ex = block_exclusive_scan_1024(x, s_w, tot);
-    if (threadIdx.x < kSortBins) a.digit_tot[threadIdx.x] = ex;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -220,11 +272,95 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kItemsPerWarp = kSortChunk / kSortWarps;   // 512
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K k, int shift) {
+    return (uint32_t)(k >> shift) & (kSortBins - 1);
+}
 
+// Lanes of the warp whose digit equals this lane's (d < 256, or 256 for "no key"): one
+// ballot per bit of the 9-bit value, each narrowing the set to the lanes that agree on it.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; b++) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t v = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? v : ~v;
+    }
+    return m;
+}
+
+// Per-block digit histograms.  Each warp keeps a private histogram; lanes holding the
+// same digit are merged (digit_peers) before the shared-memory add.
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) sort_upsweep_kernel(SortArgs a, int in_buf, int shift) {
+    __shared__ uint32_t h[kSortWarps][kSortBins];
+    if (a.counters->status != 0) return;
+    for (int t = threadIdx.x; t < kSortWarps * kSortBins; t += blockDim.x) (&h[0][0])[t] = 0;
+    __syncthreads();
+    int64_t lo, hi;
+    chunk_span(*a.count, a.grid, blockIdx.x, lo, hi);
+    const K* keys = static_cast<const K*>(in_buf ? a.keys[1] : a.keys[0]);
+    uint32_t* hw = h[threadIdx.x >> 5];
+    const uint32_t ltm = lanemask_lt();
+    for (int64_t base = lo; base < hi; base += kSortChunk) {
+        K k[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            const int64_t idx = base + (int64_t)j * kSortThreads + threadIdx.x;
+            k[j] = idx < hi ? keys[idx] : (K)0;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            const int64_t idx = base + (int64_t)j * kSortThreads + threadIdx.x;
+            const uint32_t d = idx < hi ? digit_of(k[j], shift) : (uint32_t)kSortBins;
+            const uint32_t peers = digit_peers(d);
+            if (d < (uint32_t)kSortBins && (peers & ltm) == 0) hw[d] += __popc(peers);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) s += h[w][d];
+        a.hist[(int64_t)d * a.grid + blockIdx.x] = s;
+    }
+}
+
+// One warp per digit: exclusive prefix of the digit's block counts (in place) and the
+// digit total.  8 warps per block, kSortBins / 8 blocks.
+__global__ void __launch_bounds__(256) sort_scan_kernel(SortArgs a) {
+    if (a.counters->status != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
+    uint32_t* row = a.hist + (int64_t)d * a.grid;
+    constexpr int C = kSortMaxGrid / 32;
+    uint32_t x[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        const int b = c * 32 + lane;
+        x[c] = b < a.grid ? row[b] : 0u;
+    }
+    uint32_t carry = 0;
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        if (c * 32 >= a.grid) break;
+        uint32_t inc = x[c];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int b = c * 32 + lane;
+        if (b < a.grid) row[b] = carry + inc - x[c];
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) a.digit_tot[d] = carry;
+}
+
+template <typename K>
 struct SortSmem {
-    unsigned long long keys[kSortChunk];
+    K keys[kSortChunk];
     uint32_t vals[kSortChunk];
     uint32_t wcnt[kSortWarps][kSortBins];
     uint32_t run[kSortBins];
@@ -233,35 +369,72 @@ struct SortSmem {
     uint32_t scan_w[33];
 };
 
-__global__ void __launch_bounds__(kSortThreads) sort_downsweep_kernel(SortArgs a, int in_buf, int shift) {
+// Exclusive scan over the block's 256 threads (one value each, kSortThreads == kSortBins).
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_t* scan_w) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) scan_w[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t t0 = lane < kSortWarps ? scan_w[lane] : 0u;
+        uint32_t ti = t0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < kSortWarps) scan_w[lane] = ti - t0;
+    }
+    __syncthreads();
+    const uint32_t r = scan_w[w] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArgs a, int in_buf, int shift) {
+    static_assert(kSortThreads == kSortBins, "one thread per digit");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+    SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
     if (a.counters->status != 0) return;
     int64_t lo, hi;
-    chunk_span(a.counters, a.grid, blockIdx.x, lo, hi);
-    const unsigned long long* kin = a.keys[in_buf];
-    const uint32_t* vin = a.vals[in_buf];
-    unsigned long long* kout = a.keys[in_buf ^ 1];
-    uint32_t* vout = a.vals[in_buf ^ 1];
+    chunk_span(*a.count, a.grid, blockIdx.x, lo, hi);
+    // (selects, not a runtime index into the parameter arrays, which would go to local memory)
+    const K* kin = static_cast<const K*>(in_buf ? a.keys[1] : a.keys[0]);
+    const uint32_t* vin = in_buf ? a.vals[1] : a.vals[0];
+    K* kout = static_cast<K*>(in_buf ? a.keys[0] : a.keys[1]);
+    uint32_t* vout = in_buf ? a.vals[0] : a.vals[1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x)
-        S.run[d] = a.digit_tot[d] + a.hist[(int64_t)d * a.grid + blockIdx.x];
+    // start of this block's run of each digit: digit offset + count in earlier blocks
+    S.run[threadIdx.x] = block_exclusive_scan_256(a.digit_tot[threadIdx.x], S.scan_w) +
+                         a.hist[(int64_t)threadIdx.x * a.grid + blockIdx.x];
     const uint32_t ltm = lanemask_lt();
     for (int64_t base = lo; base < hi; base += kSortChunk) {
         const int m = (int)(hi - base < kSortChunk ? hi - base : kSortChunk);
         for (int t = threadIdx.x; t < kSortWarps * kSortBins; t += blockDim.x) (&S.wcnt[0][0])[t] = 0;
-        __syncthreads();
-        unsigned long long key[kSortItems];
+        K key[kSortItems];
         uint32_t val[kSortItems];
         uint32_t rank[kSortItems];
+        // all loads first: the chunk's reads are in flight together
 #pragma unroll
         for (int j = 0; j < kSortItems; j++) {
             const int item = w * kItemsPerWarp + j * 32 + lane;
             const bool valid = item < m;
-            key[j] = valid ? kin[base + item] : 0ull;
+            key[j] = valid ? kin[base + item] : (K)0;
             val[j] = valid ? vin[base + item] : 0u;
-            const uint32_t d = valid ? ((uint32_t)(key[j] >> shift) & (kSortBins - 1)) : (uint32_t)kSortBins;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            const int item = w * kItemsPerWarp + j * 32 + lane;
+            const bool valid = item < m;
+            const uint32_t d = valid ? digit_of(key[j], shift) : (uint32_t)kSortBins;
+            const uint32_t peers = digit_peers(d);
             uint32_t r = __popc(peers & ltm);
             if (valid) r += S.wcnt[w][d];
             __syncwarp();
@@ -270,8 +443,9 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_kernel(SortArgs a
             rank[j] = r;
         }
         __syncthreads();
-        // per digit: prefix over warps, chunk totals
-        for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) {
+        {
+            // per digit: prefix over warps and the chunk total
+            const int d = threadIdx.x;
             uint32_t run = 0;
 #pragma unroll
             for (int ww = 0; ww < kSortWarps; ww++) {
@@ -280,38 +454,14 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_kernel(SortArgs a
                 run += c;
             }
             S.tot[d] = run;
-        }
-        __syncthreads();
-        {
-            // exclusive scan of the chunk totals over digits (kSortThreads == kSortBins)
-            const uint32_t x = S.tot[threadIdx.x];
-            uint32_t inc = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (lane == 31) S.scan_w[w] = inc;
-            __syncthreads();
-            if (w == 0) {
-                const uint32_t t0 = lane < kSortWarps ? S.scan_w[lane] : 0u;
-                uint32_t ti = t0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
-                    if (lane >= o) ti += y;
-                }
-                if (lane < kSortWarps) S.scan_w[lane] = ti - t0;
-            }
-            __syncthreads();
-            S.cstart[threadIdx.x] = S.scan_w[w] + inc - x;
+            S.cstart[d] = block_exclusive_scan_256(run, S.scan_w);
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kSortItems; j++) {
             const int item = w * kItemsPerWarp + j * 32 + lane;
             if (item < m) {
-                const uint32_t d = (uint32_t)(key[j] >> shift) & (kSortBins - 1);
+                const uint32_t d = digit_of(key[j], shift);
                 const uint32_t pos = S.cstart[d] + S.wcnt[w][d] + rank[j];
                 S.keys[pos] = key[j];
                 S.vals[pos] = val[j];
@@ -319,15 +469,14 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_kernel(SortArgs a
         }
         __syncthreads();
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
-            const unsigned long long kk = S.keys[k];
-            const uint32_t d = (uint32_t)(kk >> shift) & (kSortBins - 1);
+            const K kk = S.keys[k];
+            const uint32_t d = digit_of(kk, shift);
             const int64_t g = (int64_t)S.run[d] + (k - (int)S.cstart[d]);
             kout[g] = kk;
             vout[g] = S.vals[k];
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) S.run[d] += S.tot[d];
-        __syncthreads();
+        S.run[threadIdx.x] += S.tot[threadIdx.x];
     }
 }
 
@@ -337,26 +486,38 @@ int sort_grid() {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g_sort_grid = (sms > 0 ? sms : 148) * 2;
+        int g = (sms > 0 ? sms : 148) * 2;
+        g_sort_grid = g < kSortMaxGrid ? g : kSortMaxGrid;
     }
     return g_sort_grid;
 }
 
-cudaError_t launch_sort(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
+template <typename K>
+static cudaError_t launch_sort_t(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
     static bool attr_set = false;
-    const size_t smem = sizeof(SortSmem);
+    const size_t smem = sizeof(SortSmem<K>);
+    if (a.grid < 1 || a.grid > kSortMaxGrid) return cudaErrorInvalidValue;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sort_downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(sort_downsweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     for (int p = 0; p < n_passes; p++) {
         const int in_buf = p & 1;
-        sort_upsweep_kernel<<<a.grid, kSortThreads, 0, st>>>(a, in_buf, shifts[p]);
-        sort_scan_kernel<<<1, 1024, 0, st>>>(a);
-        sort_downsweep_kernel<<<a.grid, kSortThreads, smem, st>>>(a, in_buf, shifts[p]);
+        sort_upsweep_kernel<K><<<a.grid, kSortThreads, 0, st>>>(a, in_buf, shifts[p]);
+        sort_scan_kernel<<<kSortBins / 8, 256, 0, st>>>(a);
+        sort_downsweep_kernel<K><<<a.grid, kSortThreads, smem, st>>>(a, in_buf, shifts[p]);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
+    return launch_sort_t<uint32_t>(a, n_passes, shifts, st);
+}
+
+cudaError_t launch_sort64(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
+    return launch_sort_t<unsigned long long>(a, n_passes, shifts, st);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -366,9 +527,9 @@ __global__ void __launch_bounds__(256) ranges_kernel(RangeArgs a) {
     if (a.counters->status != 0) return;
     const int64_t P = (int64_t)a.counters->n_pairs;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = (uint32_t)(a.keys[i] >> 32);
-        if (i == 0 || (uint32_t)(a.keys[i - 1] >> 32) != t) a.ranges[t].x = (uint32_t)i;
-        if (i == P - 1 || (uint32_t)(a.keys[i + 1] >> 32) != t) a.ranges[t].y = (uint32_t)(i + 1);
+        const uint32_t t = a.keys[i];
+        if (i == 0 || a.keys[i - 1] != t) a.ranges[t].x = (uint32_t)i;
+        if (i == P - 1 || a.keys[i + 1] != t) a.ranges[t].y = (uint32_t)(i + 1);
     }
 }
 

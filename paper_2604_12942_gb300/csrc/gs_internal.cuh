@@ -16,9 +16,12 @@ constexpr int kSortBins = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;                     // per thread per chunk
 constexpr int kSortChunk = kSortThreads * kSortItems;
+constexpr int kSortMaxGrid = 512;                 // blocks of a sort pass (at most)
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kScanThreads * kScanItems;
+constexpr int kEmitThreads = 256;
+constexpr int kEmitChunk = 2048;                  // pairs per chunk of the balanced emission
 
 // Per-view table held in the workspace.
 struct View {
@@ -34,14 +37,36 @@ struct View {
 
 struct Counters {
     uint32_t status;
-    uint32_t reserved;
+    uint32_t n_entries32;  // copy of n_entries for the host-side counter block
     unsigned long long n_pairs;
-    uint32_t n_chunks;    // radix-sort chunk count (device-computed)
-    uint32_t pad0;
+    // fragments (pixel, Gaussian) evaluated / added by the forward and backward compositing
+    unsigned long long frag_fwd_eval, frag_fwd_add, frag_bwd_eval, frag_bwd_add;
+    uint32_t visits_fwd, visits_bwd;   // (record, warp) visits of the compositing loops
     unsigned long long adam_step;   // Adam step counter of gs_step (device-side, graph-safe)
     float adam_bc1, adam_bc2;       // 1 - b1^t, 1 - b2^t for that step
+    unsigned long long n_entries;   // visible (view, Gaussian) entries of the last binning
 };
-constexpr size_t kCountersResetBytes = 16;   // status, reserved, n_pairs: cleared per step
+constexpr size_t kCountersResetBytes = 56;   // status .. visit counters: cleared per step
+
+// One Adam update of a parameter p with gradient g (bias corrections bc1 = 1 - b1^t,
+// bc2 = 1 - b2^t); shared by the Adam kernel and the fused projection backward.  Every
+// operation is an explicitly rounded intrinsic, so the compiler cannot contract it
+// differently in the two kernels and both give bit-identical results.
+__device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, float b1, float b2,
+                                            float eps, float bc1, float bc2) {
+    m = __fmaf_rn(b1, m, __fmul_rn(__fsub_rn(1.f, b1), g));
+    v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(__fsub_rn(1.f, b2), g), g));
+    const float mh = __fdiv_rn(m, bc1), vh = __fdiv_rn(v, bc2);
+    p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, mh), __fadd_rn(__fsqrt_rn(vh), eps)));
+}
+
+// Adds a warp's per-lane counts to a device counter (one atomic per warp).
+__device__ __forceinline__ void warp_count_add(unsigned long long* dst, uint32_t v) {
+    unsigned long long s = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, s);
+}
 
 struct Opts {
     float near_z, dilation, alpha_min, alpha_max, T_min, clamp_fov;

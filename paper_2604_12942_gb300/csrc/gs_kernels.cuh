@@ -23,11 +23,22 @@ struct ProjectBwdArgs {
     Opts op;
     const float *means, *log_scales, *quats, *logits, *sh;
     const uint32_t* touched;
+    const uint8_t* visible;   // [n] covers a tile of some view (rows without it are skipped)
     const float4* grad2d;  // [V*n][3]
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
     float* grad_twist;     // [V][6] or null
+    // fused Adam (fused_adam != 0): parameters updated in place, gradients not stored
+    int fused_adam;
+    float *p_means, *p_log_scales, *p_quats, *p_logits, *p_sh;
+    float* m[5];
+    float* v[5];
+    const uint8_t* update_mask;
+    float lr[6];
+    float b1, b2, eps, bc1, bc2;
+    const Counters* step_dev;   // if set, bias corrections come from this device counter block
 };
 
+// Binning in two sorts: the visible (view, Gaussian) entries by depth, then their pairs by tile.
 struct BinArgs {
     int64_t n;
     int n_views;
@@ -36,24 +47,31 @@ struct BinArgs {
     int64_t max_pairs;
     const float4* proj;
     const uint32_t* touched;
-    uint32_t* offsets;
-    uint32_t* scan_tmp;
-    unsigned long long* keys;   // emission output (keys0)
-    uint32_t* vals;
+    uint32_t* scan_tmp;           // block sums of the scans
+    uint32_t* ekeys;              // compaction output: bits(z) of each entry
+    uint32_t* evals;              //   and its view * n + Gaussian index
+    const uint32_t* sorted_evals; // entries in depth order (input of the pair emission)
+    uint32_t* pkeys;              // emission output: global tile id of each pair
+    uint32_t* pvals;              //   and the entry's view * n + Gaussian index
+    uint32_t* poff;               // [n_views * n] pair offset of each depth-sorted entry
+    uint32_t* chunk_first;        // [max_pairs / kEmitChunk + 2] entry of each chunk's first pair
     Counters* counters;
 };
 
+// Stable LSD radix sort of (key, value) pairs with 8-bit digits; pass p reads buffer
+// (p & 1) of keys / vals and writes the other.  Keys are uint32 or uint64 per the launcher.
 struct SortArgs {
-    unsigned long long* keys[2];
+    void* keys[2];
     uint32_t* vals[2];
-    uint32_t* hist;            // [grid][256] block histograms, then offsets
-    uint32_t* digit_tot;       // [256]
-    Counters* counters;
+    uint32_t* hist;            // [256][grid] block histograms, then block offsets
+    uint32_t* digit_tot;       // [256] digit totals
+    const Counters* counters;  // status word (a set status skips the sort)
+    const unsigned long long* count;   // element count, read on the device
     int grid;
 };
 
 struct RangeArgs {
-    const unsigned long long* keys;
+    const uint32_t* keys;      // sorted global tile ids
     uint2* ranges;
     Counters* counters;
 };
@@ -66,7 +84,8 @@ struct FwdArgs {
     const uint32_t* vals;
     const uint2* ranges;
     const uint32_t* order;     // work order of the (view, tile) items, or null (identity)
-    const Counters* counters;
+    Counters* counters;
+    uint8_t* pair_mask;        // [max_pairs] out: warp regions of its tile each pair can reach
     float* T_final;
     uint32_t* n_contrib;
     float *out_rgb, *out_depth, *out_T;
@@ -85,7 +104,9 @@ struct BwdArgs {
     const uint32_t* vals;
     const uint2* ranges;
     const uint32_t* order;
-    const Counters* counters;
+    Counters* counters;
+    const uint8_t* pair_mask;  // [max_pairs] from the forward
+    const uint32_t* entries;   // visible (view, Gaussian) entries (counters->n_entries of them)
     const float* T_final;
     const uint32_t* n_contrib;
     const float *dl_drgb, *dl_ddepth;
@@ -109,12 +130,14 @@ struct AdamArgs {
 
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st);
-cudaError_t launch_bin(const BinArgs& a, cudaStream_t st);
-// Exclusive scan of n uint32 values; the total goes to c->n_pairs (status GS_ERR_CAPACITY if it
-// exceeds max_total).  tmp holds n / 4096 + 2 values.
-cudaError_t launch_exclusive_scan(const uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp, Counters* c,
-                                  int64_t max_total, cudaStream_t st);
-cudaError_t launch_sort(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st);
+// Compaction of the visible entries (touched > 0) in (view, Gaussian) order with their
+// depth keys; the count goes to c->n_entries.
+cudaError_t launch_entries(const BinArgs& a, cudaStream_t st);
+// Pair offsets over the depth-sorted entries (total to c->n_pairs, GS_ERR_CAPACITY above
+// max_pairs) and emission of one (tile id, entry) pair per covered tile.
+cudaError_t launch_emit(const BinArgs& a, cudaStream_t st);
+cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st);
+cudaError_t launch_sort64(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st);
 cudaError_t launch_ranges(const RangeArgs& a, int n_tiles, cudaStream_t st);
 cudaError_t launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, uint32_t* tmp, const Counters* c,
                               cudaStream_t st);

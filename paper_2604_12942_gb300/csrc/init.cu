@@ -282,7 +282,7 @@ static PcaWs pca_layout(int64_t n) {
     L.keys1 = take(8 * (size_t)n);
     L.vals0 = take(4 * (size_t)n);
     L.vals1 = take(4 * (size_t)n);
-    L.hist = take(sizeof(uint32_t) * ((size_t)kSortBins * 4096 + kSortBins));
+    L.hist = take(sizeof(uint32_t) * ((size_t)kSortBins * kSortMaxGrid + kSortBins));
     L.total = off;
     return L;
 }
@@ -297,19 +297,21 @@ cudaError_t launch_voxel_pca(const float* pts, const float* rgb, int64_t n, cons
     char* b = static_cast<char*>(ws);
     Counters* cnt = reinterpret_cast<Counters*>(b + L.counters);
     SortArgs sa;
-    sa.keys[0] = reinterpret_cast<unsigned long long*>(b + L.keys0);
-    sa.keys[1] = reinterpret_cast<unsigned long long*>(b + L.keys1);
+    unsigned long long* vkeys = reinterpret_cast<unsigned long long*>(b + L.keys0);
+    sa.keys[0] = vkeys;
+    sa.keys[1] = b + L.keys1;
     sa.vals[0] = reinterpret_cast<uint32_t*>(b + L.vals0);
     sa.vals[1] = reinterpret_cast<uint32_t*>(b + L.vals1);
     sa.hist = reinterpret_cast<uint32_t*>(b + L.hist);
-    sa.digit_tot = sa.hist + (size_t)kSortBins * 4096;
+    sa.digit_tot = sa.hist + (size_t)kSortBins * kSortMaxGrid;
     sa.counters = cnt;
-    sa.grid = sort_grid() < 4096 ? sort_grid() : 4096;
+    sa.count = &cnt->n_pairs;
+    sa.grid = sort_grid();
     const int blocks = (int)((n + 255) / 256);
     point_depth_kernel<<<blocks, 256, 0, st>>>(pts, n, fs, depth, inside);
-    voxel_key_kernel<<<blocks, 256, 0, st>>>(pts, n, voxel, sa.keys[0], sa.vals[0], cnt);
+    voxel_key_kernel<<<blocks, 256, 0, st>>>(pts, n, voxel, vkeys, sa.vals[0], cnt);
     int shifts[8] = {0, 8, 16, 24, 32, 40, 48, 56};
-    cudaError_t e = launch_sort(sa, 8, shifts, st);   // 63-bit keys, result back in buffer 0
+    cudaError_t e = launch_sort64(sa, 8, shifts, st);   // 63-bit keys, result back in buffer 0
     if (e != cudaSuccess) return e;
     PcaArgs a;
     a.n = n;
@@ -321,7 +323,7 @@ cudaError_t launch_voxel_pca(const float* pts, const float* rgb, int64_t n, cons
     a.sigma2 = sigma * sigma;
     a.tau_trace = tau_trace;
     a.min_pts = min_pts;
-    a.keys = sa.keys[0];
+    a.keys = vkeys;
     a.idx = sa.vals[0];
     a.x = x;
     a.has_feature = has_feature;

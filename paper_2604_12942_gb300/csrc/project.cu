@@ -72,38 +72,62 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 // (k = -log2(e)/2, ln2 log2(e) = 1): dL/du = -2 ln2 r0.x, dL/dv = -2 ln2 r0.y,
 // dL/dA = -r0.z / 2, dL/dB = -r0.w, dL/dC = -r1.x / 2.  Pose: xi = (rho, phi), T_cw <- Exp(xi) T_cw, so
 // dp_c = rho + phi x p_c, dW = [phi]x W and the camera centre moves by -W^T rho.
-template <int DEG>
-__global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdArgs a) {
+// One thread per Gaussian, kProjBwdThreads per block.  The 3K SH coefficients and their
+// gradient sums live in shared memory (one column per thread) rather than registers, which
+// keeps the kernel within 128 registers at SH degree 3.
+constexpr int kProjBwdThreads = 128;
+
+// FUSED_ADAM: apply the masked Adam step of a8 to the row with its finished gradient instead
+// of adding the gradient to the gradient planes (same arithmetic as adam_kernel).
+template <int DEG, bool FUSED_ADAM>
+__global__ void __launch_bounds__(kProjBwdThreads, 4) project_bwd_kernel(ProjectBwdArgs a) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ float s_tw[GS_MAX_VIEWS * 6];
+    // dynamic shared memory: SH gradient sums [3K][threads], then SH coefficients [3K][threads]
+    extern __shared__ float s_dyn[];
     for (int t = threadIdx.x; t < a.n_views * 6; t += blockDim.x) s_tw[t] = 0.f;
+    float* g_sh = s_dyn + threadIdx.x;                           // g_sh[k * kProjBwdThreads]
+    float* sh = s_dyn + 3 * K * kProjBwdThreads + threadIdx.x;   // sh[k * kProjBwdThreads]
+#pragma unroll
+    for (int k = 0; k < 3 * K; k++) g_sh[k * kProjBwdThreads] = 0.f;
     __syncthreads();
     const int64_t n = a.n;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < n;
+    // Rows that cover no tile of any view have no gradient: they read and write nothing.
+    const bool live = i < n && a.visible[i] != 0;
     const int64_t ii = live ? i : 0;
-    float mu[3], ls[3], q[4], sh[3 * K];
+    // views whose tiles the row covers, loaded together
+    uint64_t vmask = 0;
+    if (live) {
+#pragma unroll 8
+        for (int v = 0; v < a.n_views; v++)
+            if (__ldg(a.touched + (int64_t)v * n + ii) != 0u) vmask |= 1ull << v;
+    }
+    if (__all_sync(0xffffffffu, !live)) {
+        if (a.grad_twist == nullptr) return;
+    }
+    float mu[3], ls[3], q[4];
 #pragma unroll
-    for (int k = 0; k < 3; k++) { mu[k] = __ldg(a.means + k * n + ii); ls[k] = __ldg(a.log_scales + k * n + ii); }
+    for (int k = 0; k < 3; k++) {
+        mu[k] = live ? __ldg(a.means + k * n + ii) : 0.f;
+        ls[k] = live ? __ldg(a.log_scales + k * n + ii) : 0.f;
+    }
 #pragma unroll
-    for (int k = 0; k < 4; k++) q[k] = __ldg(a.quats + k * n + ii);
-    const float logit = __ldg(a.logits + ii);
+    for (int k = 0; k < 4; k++) q[k] = live ? __ldg(a.quats + k * n + ii) : (k == 0 ? 1.f : 0.f);
+    const float logit = live ? __ldg(a.logits + ii) : 0.f;
 #pragma unroll
-    for (int k = 0; k < 3 * K; k++) sh[k] = __ldg(a.sh + k * n + ii);
+    for (int k = 0; k < 3 * K; k++) sh[k * kProjBwdThreads] = live ? __ldg(a.sh + k * n + ii) : 0.f;
     Cov3 cv;
     cov3_forward(q, ls, cv);
     const Opts op = a.op;
     float g_mu[3] = {0, 0, 0};
     float gS[6] = {0, 0, 0, 0, 0, 0};   // dL/dSigma as a symmetric matrix: xx xy xz yy yz zz
     float g_o = 0.f;
-    float g_sh[3 * K];
-#pragma unroll
-    for (int k = 0; k < 3 * K; k++) g_sh[k] = 0.f;
     const int lane = threadIdx.x & 31;
     for (int v = 0; v < a.n_views; v++) {
         const View& V = a.views[v];
         const int64_t idx = (int64_t)v * n + ii;
-        const bool act = live && a.touched[idx] != 0;
+        const bool act = (vmask >> v) & 1ull;
         float tw[6] = {0, 0, 0, 0, 0, 0};
         if (act) {
             ProjV P;
@@ -208,12 +232,12 @@ __global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdArgs a) {
             for (int c = 0; c < 3; c++) {
                 float s = 0.5f;
 #pragma unroll
-                for (int k = 0; k < K; k++) s += sh[k * 3 + c] * Y[k];
+                for (int k = 0; k < K; k++) s += sh[(k * 3 + c) * kProjBwdThreads] * Y[k];
                 if (s < 0.f) continue;   // clamped channel: no gradient
 #pragma unroll
                 for (int k = 0; k < K; k++) {
-                    g_sh[k * 3 + c] += grgb[c] * Y[k];
-                    wk[k] += grgb[c] * sh[k * 3 + c];
+                    g_sh[(k * 3 + c) * kProjBwdThreads] += grgb[c] * Y[k];
+                    wk[k] += grgb[c] * sh[(k * 3 + c) * kProjBwdThreads];
                 }
             }
             if (DEG > 0) {
@@ -263,15 +287,72 @@ __global__ void __launch_bounds__(256, 2) project_bwd_kernel(ProjectBwdArgs a) {
         const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
         const float qn[4] = {w, x, y, z};
         const float o = 1.0f / (1.0f + expf(-logit));
+        if constexpr (FUSED_ADAM) {
+            // a8 on this row: the gradient goes straight into Adam (never stored)
+            if (!a.update_mask || a.update_mask[i]) {
+                const float bc1 = a.step_dev ? a.step_dev->adam_bc1 : a.bc1;
+                const float bc2 = a.step_dev ? a.step_dev->adam_bc2 : a.bc2;
+                // Moments are loaded a group of planes at a time, all loads of a group before
+                // its stores, so that a row waits for a few memory round trips, not 11 + 3K.
+                {
+                    float p[11], g[11], mm[11], vv[11];
+                    // element i of geometry plane k (means 0-2, log-scales 3-5, quats 6-9, logit 10)
+                    auto at = [&](float* const* grp, int k) -> float& {
+                        return k < 3 ? grp[0][k * n + i] : k < 6 ? grp[1][(k - 3) * n + i]
+                             : k < 10 ? grp[2][(k - 6) * n + i] : grp[3][i];
+                    };
+                    float* const pg[4] = {a.p_means, a.p_log_scales, a.p_quats, a.p_logits};
 #pragma unroll
-        for (int k = 0; k < 3; k++) a.g_means[k * n + i] += g_mu[k];
+                    for (int k = 0; k < 11; k++) { mm[k] = at(a.m, k); vv[k] = at(a.v, k); }
 #pragma unroll
-        for (int k = 0; k < 3; k++) a.g_log_scales[k * n + i] += gls[k];
+                    for (int k = 0; k < 3; k++) { p[k] = mu[k]; g[k] = g_mu[k]; p[3 + k] = ls[k]; g[3 + k] = gls[k]; }
 #pragma unroll
-        for (int k = 0; k < 4; k++) a.g_quats[k * n + i] += (gq[k] - qn[k] * dq) * cv.qinv;
-        a.g_logits[i] += g_o * o * (1.f - o);
+                    for (int k = 0; k < 4; k++) { p[6 + k] = q[k]; g[6 + k] = (gq[k] - qn[k] * dq) * cv.qinv; }
+                    p[10] = logit;
+                    g[10] = g_o * o * (1.f - o);
 #pragma unroll
-        for (int k = 0; k < 3 * K; k++) a.g_sh[k * n + i] += g_sh[k];
+                    for (int k = 0; k < 11; k++) {
+                        const float lr = k < 3 ? a.lr[0] : k < 6 ? a.lr[1] : k < 10 ? a.lr[2] : a.lr[3];
+                        adam_update(p[k], g[k], mm[k], vv[k], lr, a.b1, a.b2, a.eps, bc1, bc2);
+                        at(pg, k) = p[k];
+                        at(a.m, k) = mm[k];
+                        at(a.v, k) = vv[k];
+                    }
+                }
+                constexpr int GS = 3 * K < 16 ? 3 * K : 16;
+#pragma unroll
+                for (int k0 = 0; k0 < 3 * K; k0 += GS) {
+                    float mm[GS], vv[GS];
+#pragma unroll
+                    for (int k = 0; k < GS; k++) {
+                        mm[k] = a.m[4][(k0 + k) * n + i];
+                        vv[k] = a.v[4][(k0 + k) * n + i];
+                    }
+#pragma unroll
+                    for (int k = 0; k < GS; k++) {
+                        float p = sh[(k0 + k) * kProjBwdThreads];
+                        adam_update(p, g_sh[(k0 + k) * kProjBwdThreads], mm[k], vv[k], k0 + k < 3 ? a.lr[4] : a.lr[5],
+                                    a.b1, a.b2, a.eps, bc1, bc2);
+                        a.p_sh[(k0 + k) * n + i] = p;
+                        a.m[4][(k0 + k) * n + i] = mm[k];
+                        a.v[4][(k0 + k) * n + i] = vv[k];
+                    }
+                }
+            }
+        } else {
+            // (explicit adds: the accumulation is never contracted into the last product of
+            // the gradient, which keeps it equal to the value the fused variant feeds to Adam)
+#pragma unroll
+            for (int k = 0; k < 3; k++) a.g_means[k * n + i] = __fadd_rn(a.g_means[k * n + i], g_mu[k]);
+#pragma unroll
+            for (int k = 0; k < 3; k++) a.g_log_scales[k * n + i] = __fadd_rn(a.g_log_scales[k * n + i], gls[k]);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                a.g_quats[k * n + i] = __fadd_rn(a.g_quats[k * n + i], (gq[k] - qn[k] * dq) * cv.qinv);
+            a.g_logits[i] = __fadd_rn(a.g_logits[i], g_o * o * (1.f - o));
+#pragma unroll
+            for (int k = 0; k < 3 * K; k++) a.g_sh[k * n + i] = __fadd_rn(a.g_sh[k * n + i], g_sh[k * kProjBwdThreads]);
+        }
     }
     if (a.grad_twist) {
         __syncthreads();
@@ -293,17 +374,34 @@ cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st) {
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((a.n + threads - 1) / threads);
+template <int DEG, bool FUSED_ADAM>
+static cudaError_t launch_project_bwd_d(const ProjectBwdArgs& a, unsigned blocks, cudaStream_t st) {
+    constexpr size_t smem = sizeof(float) * 2 * 3 * (DEG + 1) * (DEG + 1) * kProjBwdThreads;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(project_bwd_kernel<DEG, FUSED_ADAM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    project_bwd_kernel<DEG, FUSED_ADAM><<<blocks, kProjBwdThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool FUSED_ADAM>
+static cudaError_t launch_project_bwd_t(const ProjectBwdArgs& a, int deg, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((a.n + kProjBwdThreads - 1) / kProjBwdThreads);
     if (blocks == 0) return cudaSuccess;
     switch (deg) {
-        case 0: project_bwd_kernel<0><<<blocks, threads, 0, st>>>(a); break;
-        case 1: project_bwd_kernel<1><<<blocks, threads, 0, st>>>(a); break;
-        case 2: project_bwd_kernel<2><<<blocks, threads, 0, st>>>(a); break;
-        default: project_bwd_kernel<3><<<blocks, threads, 0, st>>>(a); break;
+        case 0: return launch_project_bwd_d<0, FUSED_ADAM>(a, blocks, st);
+        case 1: return launch_project_bwd_d<1, FUSED_ADAM>(a, blocks, st);
+        case 2: return launch_project_bwd_d<2, FUSED_ADAM>(a, blocks, st);
+        default: return launch_project_bwd_d<3, FUSED_ADAM>(a, blocks, st);
     }
-    return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st) {
+    return a.fused_adam ? launch_project_bwd_t<true>(a, deg, st) : launch_project_bwd_t<false>(a, deg, st);
 }
 
 }  // namespace gs

@@ -83,6 +83,7 @@ cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int
 // ----------------------------------------------------------------------------------------
 constexpr int kFwdPPT = 1;
 constexpr int kBwdPPT = 2;
+static_assert(kFwdPPT == 1 && kBwdPPT == 2, "bwd_mask_from_fwd maps 8 x 4 forward regions to 8 x 8 ones");
 
 template <int TILE, int PPT>
 struct TileMap {
@@ -91,28 +92,79 @@ struct TileMap {
     static constexpr int RH = 4 * PPT;              // warp region height
 };
 
-// Bit r of the result is set when the record's alpha >= alpha_min box overlaps warp region
-// r of the tile whose top-left pixel is (X0, Y0).  Computed once per staged record by the
-// thread that stages it; warps then test one bit per fragment.
+// Least value over the rectangle [x0, x1] x [y0, y1] of Q(d) = A dx^2 + 2 B dx dy + C dy^2
+// (positive definite): 0 if the rectangle holds the origin, else the least of its four edge
+// minima, each a 1-D quadratic minimised at its stationary point clamped to the edge.
+__device__ __forceinline__ float rect_min_quadratic(float A, float B, float C, float iA, float iC, float x0, float x1,
+                                                    float y0, float y1) {
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return 0.f;
+    float m = INFINITY;
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        const float X = s ? x1 : x0;
+        const float dy = fminf(fmaxf(-B * X * iC, y0), y1);
+        m = fminf(m, (A * X + 2.f * B * dy) * X + C * dy * dy);
+        const float Y = s ? y1 : y0;
+        const float dx = fminf(fmaxf(-B * Y * iA, x0), x1);
+        m = fminf(m, (C * Y + 2.f * B * dx) * Y + A * dx * dx);
+    }
+    return m;
+}
+
+// Bit r of the result is set when warp region r of the tile whose top-left pixel is (X0, Y0)
+// may hold a fragment of the record with alpha >= alpha_min.  Regions are first tested
+// against the record's alpha box, then exactly: alpha = o 2^e >= alpha_min needs
+// Q = -e <= thr = log2(o / alpha_min), so a region is dropped when the least Q over the
+// rectangle spanned by its pixel centres exceeds thr by more than a margin that covers the
+// FP32 rounding of e in the compositing loops (well above 10 ulp of the largest term).
+// Computed once per staged record; warps then test one bit per fragment.
 template <int TILE, int PPT>
-__device__ __forceinline__ uint32_t region_mask(float u, float v, float rx, float ry, float X0, float Y0) {
+__device__ __forceinline__ uint32_t region_mask(float u, float v, float rx, float ry, float a, float b, float c,
+                                                float o, float alpha_min, float X0, float Y0) {
     using TM = TileMap<TILE, PPT>;
     uint32_t cols = 0, rows = 0;
 #pragma unroll
-    for (int c = 0; c < TM::WX; c++) {
-        const float x0 = X0 + 8.f * c;
-        if (u - rx <= x0 + 7.5f && u + rx >= x0 + 0.5f) cols |= 1u << c;
+    for (int cc = 0; cc < TM::WX; cc++) {
+        const float x0 = X0 + 8.f * cc;
+        if (u - rx <= x0 + 7.5f && u + rx >= x0 + 0.5f) cols |= 1u << cc;
     }
 #pragma unroll
     for (int r = 0; r < TILE / TM::RH; r++) {
         const float y0 = Y0 + (float)(TM::RH * r);
         if (v - ry <= y0 + ((float)TM::RH - 0.5f) && v + ry >= y0 + 0.5f) rows |= 1u << r;
     }
+    if (!(cols && rows)) return 0u;
+    const float A = -a, B = -b, C = -c;   // e = -(A dx^2 + 2 B dx dy + C dy^2)
+    const float iA = 1.f / A, iC = 1.f / C;
+    const float thr = __log2f(o / alpha_min);
     uint32_t m = 0;
 #pragma unroll
-    for (int r = 0; r < TILE / TM::RH; r++)
-        if (rows & (1u << r)) m |= cols << (r * TM::WX);
+    for (int r = 0; r < TILE / TM::RH; r++) {
+        if (!(rows & (1u << r))) continue;
+        const float y0 = Y0 + (float)(TM::RH * r) + 0.5f - v, y1 = y0 + (float)(TM::RH - 1);
+#pragma unroll
+        for (int cc = 0; cc < TM::WX; cc++) {
+            if (!(cols & (1u << cc))) continue;
+            const float x0 = X0 + 8.f * cc + 0.5f - u, x1 = x0 + 7.f;
+            const float q = rect_min_quadratic(A, B, C, iA, iC, x0, x1, y0, y1);
+            const float X = fmaxf(fabsf(x0), fabsf(x1)), Y = fmaxf(fabsf(y0), fabsf(y1));
+            const float margin = 1e-5f * (A * X * X + 2.f * fabsf(B) * X * Y + C * Y * Y) + 1e-3f;
+            if (!(q > thr + margin)) m |= 1u << (r * TM::WX + cc);
+        }
+    }
     return m;
+}
+
+// Backward warp regions (8 x 8) from the forward ones (8 x 4): region (c, r) is the union of
+// forward regions (c, 2r) and (c, 2r + 1).
+template <int TILE>
+__device__ __forceinline__ uint32_t bwd_mask_from_fwd(uint32_t m) {
+    constexpr int WX = TILE / 8;
+    uint32_t out = 0;
+#pragma unroll
+    for (int r = 0; r < TILE / 8; r++)
+        out |= (((m >> (2 * r * WX)) | (m >> ((2 * r + 1) * WX))) & ((1u << WX) - 1u)) << (r * WX);
+    return out;
 }
 
 __device__ __forceinline__ void load_record(const float4* proj, uint32_t gid, float2& uv, float4& co, float4& cz,
@@ -129,8 +181,13 @@ __device__ __forceinline__ void load_record(const float4* proj, uint32_t gid, fl
 // ----------------------------------------------------------------------------------------
 // Forward compositing.
 // ----------------------------------------------------------------------------------------
+// 40 resident warps per SM (at most 51 registers a thread): the compositing loop is latency
+// bound and gains more from occupancy than from the few registers the staging code wants.
+constexpr int kFwdThreadsPerSM = 1280;
+
 template <int TILE, int CHUNK>
-__global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM / TileMap<TILE, kFwdPPT>::NT)
+    render_fwd_kernel(FwdArgs a) {
     constexpr int kPPT = kFwdPPT;
     using TM = TileMap<TILE, kPPT>;
     constexpr int NT = TM::NT;
@@ -163,6 +220,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
     const uint2 rg = a.ranges[gt];
     const int n = (int)(rg.y - rg.x);
     const float amin = a.op.alpha_min, amax = a.op.alpha_max, tmin = a.op.T_min;
+    uint32_t n_eval = 0, n_add = 0, n_visit = 0;
     for (int base = 0; base < n; base += CHUNK) {
         bool alive = false;
 #pragma unroll
@@ -172,10 +230,15 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
             const int j = base + k;
             if (j < n) {
                 float2 uv;
+                float4 co;
                 float rxf, ryf;
-                load_record(a.proj, a.vals[rg.x + j], uv, s_co[k], s_cz[k], rxf, ryf);
+                load_record(a.proj, a.vals[rg.x + j], uv, co, s_cz[k], rxf, ryf);
                 s_uv[k] = uv;
-                s_mask[k] = region_mask<TILE, kPPT>(uv.x, uv.y, rxf, ryf, (float)(tx * TILE), (float)(ty * TILE));
+                s_co[k] = co;
+                const uint32_t msk = region_mask<TILE, kPPT>(uv.x, uv.y, rxf, ryf, co.x, co.y, co.z, co.w, amin,
+                                                             (float)(tx * TILE), (float)(ty * TILE));
+                s_mask[k] = msk;
+                a.pair_mask[rg.x + j] = (uint8_t)msk;
             }
         }
         __syncthreads();
@@ -183,6 +246,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
             const int m = min(CHUNK, n - base);
             for (int k = 0; k < m; k++) {
                 if (!((s_mask[k] >> w) & 1u)) continue;
+                n_visit++;
                 const float2 uv = s_uv[k];
                 const float4 co = s_co[k];
 #pragma unroll
@@ -191,6 +255,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
                     const float dx = ((float)x[q] + 0.5f) - uv.x, dy = ((float)y[q] + 0.5f) - uv.y;
                     const float G = ex2_approx(frag_exponent(dx, dy, co.x, co.y, co.z).e);
                     const float alpha = fminf(amax, co.w * G);
+                    n_eval++;
                     if (alpha < amin) continue;
                     const float test_T = T[q] * (1.f - alpha);
                     if (test_T < tmin) {
@@ -205,11 +270,17 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
                     dep[q] = fmaf(wgt, cz.w, dep[q]);
                     T[q] = test_T;
                     last[q] = (uint32_t)(base + k + 1);
+                    n_add++;
                 }
             }
         }
     }
-    double lr = 0.0, ld = 0.0;
+    warp_count_add(&a.counters->frag_fwd_eval, n_eval);
+    warp_count_add(&a.counters->frag_fwd_add, n_add);
+    if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_fwd, n_visit);
+    // L1 sums: FP32 within a warp (at most 32 * kPPT pixels), FP64 across warps and CTAs
+    // (the FP64 pipe is narrow: it only sees the per-warp totals)
+    float lr = 0.f, ld = 0.f;
 #pragma unroll
     for (int q = 0; q < kPPT; q++) {
         if (!inside[q]) continue;
@@ -236,14 +307,14 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
             dl[p] = krgb * (float)((r0 > 0.f) - (r0 < 0.f));
             dl[P + p] = krgb * (float)((r1 > 0.f) - (r1 < 0.f));
             dl[2 * P + p] = krgb * (float)((r2 > 0.f) - (r2 < 0.f));
-            if (in) lr += (double)fabsf(r0) + (double)fabsf(r1) + (double)fabsf(r2);
+            if (in) lr += fabsf(r0) + fabsf(r1) + fabsf(r2);
             if (a.dl_ddepth) {
                 const float td = a.tgt_depth ? a.tgt_depth[g] : 0.f;
                 const bool ind = in && td > 0.f;
                 const float kd = (ind && cd > 0.f) ? a.op.lambda_depth * inv_v / cd : 0.f;
                 const float rd = dep[q] - td;
                 a.dl_ddepth[g] = kd * (float)((rd > 0.f) - (rd < 0.f));
-                if (ind) ld += (double)fabsf(rd);
+                if (ind) ld += fabsf(rd);
             }
         }
     }
@@ -254,7 +325,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT) render_fwd_kernel(
             lr += __shfl_xor_sync(0xffffffffu, lr, o);
             ld += __shfl_xor_sync(0xffffffffu, ld, o);
         }
-        if (lane == 0) { s_red[0][w] = lr; s_red[1][w] = ld; }
+        if (lane == 0) { s_red[0][w] = (double)lr; s_red[1][w] = (double)ld; }
         __syncthreads();
         if (threadIdx.x == 0) {
             double sr = 0, sd = 0;
@@ -348,6 +419,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
     const int rx0 = tx * TILE + (w % TM::WX) * 8, ry0 = ty * TILE + (w / TM::WX) * TM::RH;
     const uint2 rg = a.ranges[gt];
     const float amin = a.op.alpha_min, amax = a.op.alpha_max;
+    uint32_t n_eval = 0, n_add = 0, n_visit = 0;
     float px[kPPT], py[kPPT], T[kPPT], S[kPPT], gc0[kPPT], gc1[kPPT], gc2[kPPT], gd[kPPT];
     uint32_t last[kPPT];
     uint32_t mylast = 0;
@@ -389,7 +461,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
             float rxf, ryf;
             load_record(a.proj, gid, uv, s_co[k], s_cz[k], rxf, ryf);
             s_uv[k] = uv;
-            s_mask[k] = region_mask<TILE, kPPT>(uv.x, uv.y, rxf, ryf, (float)(tx * TILE), (float)(ty * TILE));
+            s_mask[k] = bwd_mask_from_fwd<TILE>(a.pair_mask[rg.x + lo + k]);
             s_id[k] = gid;
         }
         __syncthreads();
@@ -397,6 +469,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
         for (int j = jstart; j >= lo; j--) {
             const int k = j - lo;
             if (!((s_mask[k] >> w) & 1u)) continue;
+            n_visit++;
             const float2 bx = s_uv[k];
             const float4 co = s_co[k];
             float val[10];
@@ -411,8 +484,10 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
                 const float G = ex2_approx(fe.e);
                 const float a0 = co.w * G;
                 const float alpha = fminf(amax, a0);
+                n_eval++;
                 if (alpha < amin) continue;
                 contrib = true;
+                n_add++;
                 const float rom = rcp_approx(1.f - alpha);
                 T[q] = T[q] * rom;
                 const float wgt = alpha * T[q];
@@ -448,6 +523,9 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
             }
         }
     }
+    warp_count_add(&a.counters->frag_bwd_eval, n_eval);
+    warp_count_add(&a.counters->frag_bwd_add, n_add);
+    if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_bwd, n_visit);
 }
 
 template <int TILE>
@@ -478,8 +556,19 @@ cudaError_t launch_render_fwd(const FwdArgs& a, int total_tiles, cudaStream_t st
                           : launch_fwd_t<16>(a, total_tiles, a.op.chunk, st);
 }
 
+// Zeroes the screen-space gradient records of the visible entries -- the only records the
+// backward compositing adds to and the projection backward reads.
+__global__ void __launch_bounds__(256) clear_grad2d_kernel(BwdArgs a) {
+    if (a.counters->status != 0) return;
+    const int64_t E = (int64_t)a.counters->n_entries;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * E; e += (int64_t)gridDim.x * blockDim.x)
+        a.grad2d[3 * (size_t)a.entries[e / 3] + (size_t)(e % 3)] = z;
+}
+
 cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st) {
-    if (total_tiles <= 0) return cudaSuccess;
+    clear_grad2d_kernel<<<sort_grid() * 4, 256, 0, st>>>(a);
+    if (total_tiles <= 0) return cudaGetLastError();
     return a.op.tile == 8 ? launch_bwd_t<8>(a, total_tiles, a.op.chunk, st)
                           : launch_bwd_t<16>(a, total_tiles, a.op.chunk, st);
 }

@@ -56,9 +56,8 @@ static cudaError_t noalloc_scratch(void** out) {
 __global__ void noalloc_init_kernel(Counters* c, unsigned long long n) {
     if (threadIdx.x == 0) {
         c->status = 0;
-        c->reserved = 0;
+        c->n_entries32 = 0;
         c->n_pairs = n;
-        c->n_chunks = 0;
     }
 }
 
@@ -101,6 +100,7 @@ extern "C" gs_status gs_sort_pairs_noalloc(const uint64_t* keys_in, const uint32
     a.hist = hist;
     a.digit_tot = hist + (size_t)kSortBins * kNoAllocMaxGrid;
     a.counters = cnt;
+    a.count = &cnt->n_pairs;
     a.grid = sort_grid() < kNoAllocMaxGrid ? sort_grid() : kNoAllocMaxGrid;
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
@@ -113,7 +113,7 @@ extern "C" gs_status gs_sort_pairs_noalloc(const uint64_t* keys_in, const uint32
         }
         a.keys[1] = kdst[p & 1];
         a.vals[1] = vdst[p & 1];
-        e = launch_sort(a, 1, &shift, st);
+        e = launch_sort64(a, 1, &shift, st);
         if (e != cudaSuccess) return record_error(GS_ERR_CUDA, cudaGetErrorString(e));
     }
     return GS_OK;

@@ -107,6 +107,12 @@ def _bin_case(cams, n, tile, seed, radius_max=48):
     c = ws.counters()
     assert c.status == 0
     assert c.n_pairs == P
+    # the visible entries in depth order: a stable sort of (view, index) order by bits(z)
+    vis_ids = np.nonzero(ref["touched"].reshape(-1) > 0)[0]
+    assert c.n_entries == len(vis_ids)
+    zb = rec.reshape(-1, 12)[vis_ids, 2].view(np.uint32)
+    np.testing.assert_array_equal(ws.sorted_entries(len(vis_ids)).cpu().numpy().view(np.uint32),
+                                  vis_ids[np.argsort(zb, kind="stable")].astype(np.uint32))
     k, vals = ws.sorted_pairs(P)
     np.testing.assert_array_equal(k.cpu().numpy().view(np.uint64), ref["sorted_keys"])
     np.testing.assert_array_equal(vals.cpu().numpy().view(np.uint32), ref["sorted_vals"])
@@ -125,6 +131,11 @@ def test_bin_sort_bit_exact_multichunk():
     cams = [synth.camera(1280, 720, 900.0), synth.camera(640, 480, 500.0)]
     P = _bin_case(cams, 300_000, 8, seed=4, radius_max=64)
     assert P > 2_500_000
+
+
+def test_bin_sort_single_tile():
+    """One tile per view set: no tile-sort pass, the pairs stay in depth order."""
+    _bin_case([synth.camera(16, 16, 20.0)], 2000, 16, seed=5, radius_max=12)
 
 
 def test_bin_sort_empty():
@@ -310,7 +321,10 @@ def test_adam_matches_oracle(n):
     off = (upd & vis) == 0
     np.testing.assert_array_equal(T[0].cpu().numpy()[:, off], p[:, off])
     np.testing.assert_array_equal(T[2].cpu().numpy()[:, off], m[:, off])
-    assert float(T[1].abs().sum()) == 0.0
+    # gradients consumed on visible rows; rows outside `visible` are neither read nor written
+    G = T[1].cpu().numpy()
+    assert float(np.abs(G[:, vis == 1]).sum()) == 0.0
+    np.testing.assert_array_equal(G[:, vis == 0], g[:, vis == 0])
 
 
 # ----------------------------------------------------------------------------------------

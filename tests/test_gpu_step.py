@@ -78,3 +78,68 @@ def test_graph_set_cameras_matches_eager_with_new_poses():
     torch.cuda.synchronize()
     assert torch.equal(step.rgb, ref.rgb) and torch.equal(step.depth, ref.depth)
     step.release()
+
+
+def test_fused_project_bwd_adam_equals_project_bwd_then_adam():
+    """On the same screen-space sums the fused kernel is bit-identical to the two calls."""
+    sc, cams, trgb, td = _setup(47)
+    lr = (1e-3, 1e-2, 1e-2, 5e-2, 1e-2, 1e-3)
+    ws = gs.Workspace(sc.n, cams, gs.default_opts(), 1 << 20)
+    P = ws.layout.total_pixels
+    planes = planes_of(sc)
+    rgb = torch.zeros(3 * P, device="cuda"); dep = torch.zeros(P, device="cuda")
+    dl = torch.zeros(3 * P, device="cuda"); dld = torch.zeros(P, device="cuda")
+    loss = torch.zeros(len(cams) + 1, device="cuda")
+    ws.project(planes, 3)
+    ws.bin_sort()
+    ws.render_fwd(rgb, dep, None, trgb, td, None, dl, dld, loss)
+    ws.composite_bwd(dl, dld)
+    rng = np.random.default_rng(5)
+    m0 = torch.as_tensor(rng.normal(0, 1e-3, tuple(planes.shape)).astype(np.float32), device="cuda")
+    v0 = torch.as_tensor(rng.uniform(0, 1e-6, tuple(planes.shape)).astype(np.float32), device="cuda")
+    upd = torch.as_tensor((rng.uniform(size=sc.n) < 0.8).astype(np.uint8), device="cuda")
+    # two calls
+    pa, ma, va = planes.clone(), m0.clone(), v0.clone()
+    grads = torch.zeros_like(planes)
+    twa = torch.zeros(len(cams), 6, device="cuda")
+    ws.project_bwd(pa, 3, grads, twa)
+    gs.adam_step(pa, grads, ma, va, 3, 3, lr, upd, ws.visible())
+    # fused
+    pb, mb, vb = planes.clone(), m0.clone(), v0.clone()
+    twb = torch.zeros(len(cams), 6, device="cuda")
+    ws.project_bwd_adam(pb, 3, mb, vb, 3, lr, upd, grad_twist=twb)
+    torch.cuda.synchronize()
+    assert torch.equal(pa, pb) and torch.equal(ma, mb) and torch.equal(va, vb)
+    assert not torch.equal(pa, planes)
+    assert torch.allclose(twa, twb, rtol=1e-5, atol=1e-7 * float(twa.abs().max()))
+    assert float(grads.abs().sum()) == 0.0   # consumed by the Adam step
+
+
+def test_optimizing_step_equals_staged_step():
+    """gs_step with the optimiser (fused path) against project / bin / fwd / bwd / Adam calls;
+    the screen-space sums are float atomics, so results agree up to summation order."""
+    sc, cams, trgb, td = _setup(49)
+    lr = (1e-3, 1e-2, 1e-2, 5e-2, 1e-2, 1e-3)
+    step = gs.MappingStep(planes_of(sc), 3, cams, lr=lr)
+    step(trgb, td)
+    ws = gs.Workspace(sc.n, cams, gs.default_opts(), step.ws.layout.max_pairs)
+    P = ws.layout.total_pixels
+    planes = planes_of(sc)
+    m = torch.zeros_like(planes); v = torch.zeros_like(planes); grads = torch.zeros_like(planes)
+    rgb = torch.zeros(3 * P, device="cuda"); dep = torch.zeros(P, device="cuda")
+    dl = torch.zeros(3 * P, device="cuda"); dld = torch.zeros(P, device="cuda")
+    loss = torch.zeros(len(cams) + 1, device="cuda")
+    ws.project(planes, 3)
+    ws.bin_sort()
+    ws.render_fwd(rgb, dep, None, trgb, td, None, dl, dld, loss)
+    ws.render_bwd(planes, 3, grads, dl, dld)
+    gs.adam_step(planes, grads, m, v, 3, 1, lr, None, ws.visible())
+    torch.cuda.synchronize()
+    assert torch.allclose(m, step.m, rtol=1e-4, atol=1e-6 * float(m.abs().max()))
+    assert torch.allclose(v, step.v, rtol=1e-4, atol=1e-6 * float(v.abs().max()))
+    # first Adam step moves each parameter by about lr * sign(g): a sign decided by rounding
+    # (|g| at the level of the summation error) may differ
+    d = (planes - step.planes).abs()
+    assert float(d.max()) <= 2.05 * max(lr)
+    assert float((d > 1e-6 * float(planes.abs().max())).float().mean()) < 1e-3
+    assert float(step.grads.abs().sum()) == 0.0   # the fused step does not touch the gradients
