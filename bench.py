@@ -317,10 +317,11 @@ def run_gpu(args, rank, world):
 
 
 def tile_sort_passes(L):
+    """Radix passes of the pair sort: 8-bit digits, or 9-bit ones where that saves a pass."""
     tb = 0
     while (1 << tb) < L.total_tiles:
         tb += 1
-    return (tb + 7) // 8
+    return min((tb + 7) // 8, (tb + 8) // 9)
 
 
 def kernels_per_step(L):

@@ -94,11 +94,14 @@ static int tile_bits(int total_tiles) {
     return b;
 }
 
-// Passes of the pair sort: 8-bit digits over the global tile id bits (0 when one tile).
-static int pair_sort_passes(int total_tiles, int* shifts) {
-    int np = 0;
+// Passes of the pair sort over the global tile id bits (0 passes when there is one tile):
+// 8-bit digits, or 9-bit ones where that saves a pass (17 or 18 tile bits: 2 passes, not 3).
+static int pair_sort_passes(int total_tiles, int* shifts, int* bits) {
     const int tb = tile_bits(total_tiles);
-    for (int s = 0; s < tb; s += 8) shifts[np++] = s;
+    const int p8 = (tb + 7) / 8, p9 = (tb + 8) / 9;
+    *bits = p9 < p8 ? 9 : 8;
+    int np = 0;
+    for (int s = 0; s < tb; s += *bits) shifts[np++] = s;
     return np;
 }
 
@@ -129,7 +132,7 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.vals1 = take(sizeof(uint32_t) * (size_t)max_pairs);
     L.pair_mask = take((size_t)max_pairs);
     L.emit_tmp = take(sizeof(uint32_t) * ((size_t)max_pairs / kEmitChunk + 2));
-    L.sort_tmp = take(sizeof(uint32_t) * ((size_t)kSortBins * kSortMaxGrid + kSortBins));
+    L.sort_tmp = take(sizeof(uint32_t) * ((size_t)kSortMaxBins * kSortMaxGrid + kSortMaxBins));
     L.ranges = take(sizeof(uint32_t) * 2 * (size_t)G.total_tiles);
     L.T_final = take(sizeof(float) * (size_t)G.total_pixels);
     L.n_contrib = take(sizeof(uint32_t) * (size_t)G.total_pixels);
@@ -137,8 +140,8 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.visible = take((size_t)n);
     L.tile_order = take(sizeof(uint32_t) * ((size_t)G.total_tiles + 2 * 34));
     L.total = off;
-    int shifts[16];
-    L.sorted_buf = pair_sort_passes(G.total_tiles, shifts) & 1;
+    int shifts[16], bits;
+    L.sorted_buf = pair_sort_passes(G.total_tiles, shifts, &bits) & 1;
     L.total_tiles = G.total_tiles;
     L.total_pixels = G.total_pixels;
     L.max_pairs = max_pairs;
@@ -249,7 +252,7 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     if (e != cudaSuccess) return e;
     SortArgs sa;
     sa.hist = at<uint32_t>(ws, L->sort_tmp);
-    sa.digit_tot = sa.hist + (size_t)kSortBins * kSortMaxGrid;
+    sa.digit_tot = sa.hist + (size_t)kSortMaxBins * kSortMaxGrid;
     sa.counters = cnt;
     sa.grid = sort_grid();
     // 1. entries by depth
@@ -259,7 +262,7 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     sa.vals[1] = at<uint32_t>(ws, L->evals1);
     sa.count = &cnt->n_entries;
     const int depth_shifts[4] = {0, 8, 16, 24};
-    if ((e = launch_sort32(sa, 4, depth_shifts, st)) != cudaSuccess) return e;
+    if ((e = launch_sort32(sa, 4, depth_shifts, 8, st)) != cudaSuccess) return e;
     // 2. pairs emitted in depth order, then by tile
     if ((e = launch_emit(b, st)) != cudaSuccess) return e;
     sa.keys[0] = at<uint32_t>(ws, L->keys0);
@@ -267,9 +270,9 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     sa.vals[0] = at<uint32_t>(ws, L->vals0);
     sa.vals[1] = at<uint32_t>(ws, L->vals1);
     sa.count = &cnt->n_pairs;
-    int shifts[16];
-    const int np = pair_sort_passes(L->total_tiles, shifts);
-    if ((e = launch_sort32(sa, np, shifts, st)) != cudaSuccess) return e;
+    int shifts[16], bits;
+    const int np = pair_sort_passes(L->total_tiles, shifts, &bits);
+    if ((e = launch_sort32(sa, np, shifts, bits, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(at<uint32_t>(ws, L->ranges), 0, sizeof(uint32_t) * 2 * (size_t)L->total_tiles, st)) !=
         cudaSuccess)
         return e;

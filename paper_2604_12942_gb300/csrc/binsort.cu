@@ -253,10 +253,13 @@ cudaError_t launch_emit(const BinArgs& a, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------------------------------------
-// Radix sort (8-bit digits), keys K = uint32_t or unsigned long long.
+// Radix sort with BITS-bit digits (8 or 9), keys K = uint32_t or unsigned long long.
 // ----------------------------------------------------------------------------------------
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItemsPerWarp = kSortChunk / kSortWarps;   // 512
+constexpr int kUpThreads = 512;                          // upsweep block (same chunk range, more warps)
+constexpr int kUpWarps = kUpThreads / 32;
+constexpr int kUpItems = kSortChunk / kUpThreads;        // 8
 
 __device__ __forceinline__ void chunk_span(unsigned long long count, int grid, int b, int64_t& lo, int64_t& hi) {
     const int64_t P = (int64_t)count;
@@ -272,63 +275,48 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-template <typename K>
+template <int BITS, typename K>
 __device__ __forceinline__ uint32_t digit_of(K k, int shift) {
-    return (uint32_t)(k >> shift) & (kSortBins - 1);
+    return (uint32_t)(k >> shift) & ((1u << BITS) - 1u);
 }
 
-// Lanes of the warp whose digit equals this lane's (d < 256, or 256 for "no key"): one
-// ballot per bit of the 9-bit value, each narrowing the set to the lanes that agree on it.
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
-    uint32_t m = 0xffffffffu;
-#pragma unroll
-    for (int b = 0; b < 9; b++) {
-        const bool bit = (d >> b) & 1u;
-        const uint32_t v = __ballot_sync(0xffffffffu, bit);
-        m &= bit ? v : ~v;
-    }
-    return m;
-}
-
-// Per-block digit histograms.  Each warp keeps a private histogram; lanes holding the
-// same digit are merged (digit_peers) before the shared-memory add.
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads) sort_upsweep_kernel(SortArgs a, int in_buf, int shift) {
-    __shared__ uint32_t h[kSortWarps][kSortBins];
+// Per-block digit histograms over the block's chunks: every thread loads its kUpItems keys of
+// a chunk first, then adds them to its warp's private histogram with shared-memory atomics.
+template <typename K, int BITS>
+__global__ void __launch_bounds__(kUpThreads) sort_upsweep_kernel(SortArgs a, int in_buf, int shift) {
+    constexpr int BINS = 1 << BITS;
+    __shared__ uint32_t h[kUpWarps][BINS];
     if (a.counters->status != 0) return;
-    for (int t = threadIdx.x; t < kSortWarps * kSortBins; t += blockDim.x) (&h[0][0])[t] = 0;
+    for (int t = threadIdx.x; t < kUpWarps * BINS; t += blockDim.x) (&h[0][0])[t] = 0;
     __syncthreads();
     int64_t lo, hi;
     chunk_span(*a.count, a.grid, blockIdx.x, lo, hi);
     const K* keys = static_cast<const K*>(in_buf ? a.keys[1] : a.keys[0]);
     uint32_t* hw = h[threadIdx.x >> 5];
-    const uint32_t ltm = lanemask_lt();
     for (int64_t base = lo; base < hi; base += kSortChunk) {
-        K k[kSortItems];
+        K k[kUpItems];
 #pragma unroll
-        for (int j = 0; j < kSortItems; j++) {
-            const int64_t idx = base + (int64_t)j * kSortThreads + threadIdx.x;
+        for (int j = 0; j < kUpItems; j++) {
+            const int64_t idx = base + (int64_t)j * kUpThreads + threadIdx.x;
             k[j] = idx < hi ? keys[idx] : (K)0;
         }
 #pragma unroll
-        for (int j = 0; j < kSortItems; j++) {
-            const int64_t idx = base + (int64_t)j * kSortThreads + threadIdx.x;
-            const uint32_t d = idx < hi ? digit_of(k[j], shift) : (uint32_t)kSortBins;
-            const uint32_t peers = digit_peers(d);
-            if (d < (uint32_t)kSortBins && (peers & ltm) == 0) hw[d] += __popc(peers);
+        for (int j = 0; j < kUpItems; j++) {
+            const int64_t idx = base + (int64_t)j * kUpThreads + threadIdx.x;
+            if (idx < hi) atomicAdd(&hw[digit_of<BITS>(k[j], shift)], 1u);
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kSortBins; d += blockDim.x) {
+    for (int d = threadIdx.x; d < BINS; d += blockDim.x) {
         uint32_t s = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; w++) s += h[w][d];
+        for (int w = 0; w < kUpWarps; w++) s += h[w][d];
         a.hist[(int64_t)d * a.grid + blockIdx.x] = s;
     }
 }
 
 // One warp per digit: exclusive prefix of the digit's block counts (in place) and the
-// digit total.  8 warps per block, kSortBins / 8 blocks.
+// digit total.  8 warps per block.
 __global__ void __launch_bounds__(256) sort_scan_kernel(SortArgs a) {
     if (a.counters->status != 0) return;
     const int lane = threadIdx.x & 31;
@@ -358,21 +346,28 @@ __global__ void __launch_bounds__(256) sort_scan_kernel(SortArgs a) {
     if (lane == 0) a.digit_tot[d] = carry;
 }
 
-template <typename K>
+template <typename K, int BITS>
 struct SortSmem {
+    static constexpr int BINS = 1 << BITS;
     K keys[kSortChunk];
     uint32_t vals[kSortChunk];
-    uint32_t wcnt[kSortWarps][kSortBins];
-    uint32_t run[kSortBins];
-    uint32_t tot[kSortBins];
-    uint32_t cstart[kSortBins];
+    uint32_t wcnt[kSortWarps][BINS];
+    uint32_t run[BINS];
+    uint32_t tot[BINS];
+    uint32_t cstart[BINS];
     uint32_t scan_w[33];
 };
 
-// Exclusive scan over the block's 256 threads (one value each, kSortThreads == kSortBins).
-__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_t* scan_w) {
+// Exclusive scan of DPT consecutive values per thread over the block (kSortThreads threads);
+// out[q] receives the prefix of value q.
+template <int DPT>
+__device__ __forceinline__ void block_exclusive_scan_dpt(const uint32_t (&x)[DPT], uint32_t (&out)[DPT],
+                                                         uint32_t* scan_w) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t inc = x;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; q++) sum += x[q];
+    uint32_t inc = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -391,16 +386,22 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
         if (lane < kSortWarps) scan_w[lane] = ti - t0;
     }
     __syncthreads();
-    const uint32_t r = scan_w[w] + inc - x;
+    uint32_t r = scan_w[w] + inc - sum;
+#pragma unroll
+    for (int q = 0; q < DPT; q++) {
+        out[q] = r;
+        r += x[q];
+    }
     __syncthreads();
-    return r;
 }
 
-template <typename K>
+template <typename K, int BITS>
 __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArgs a, int in_buf, int shift) {
-    static_assert(kSortThreads == kSortBins, "one thread per digit");
+    constexpr int BINS = 1 << BITS;
+    constexpr int DPT = BINS / kSortThreads;   // digits per thread: 1 or 2
+    static_assert(DPT * kSortThreads == BINS, "whole digits per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
+    SortSmem<K, BITS>& S = *reinterpret_cast<SortSmem<K, BITS>*>(smem_raw);
     if (a.counters->status != 0) return;
     int64_t lo, hi;
     chunk_span(*a.count, a.grid, blockIdx.x, lo, hi);
@@ -410,13 +411,20 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
     K* kout = static_cast<K*>(in_buf ? a.keys[0] : a.keys[1]);
     uint32_t* vout = in_buf ? a.vals[0] : a.vals[1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // start of this block's run of each digit: digit offset + count in earlier blocks
-    S.run[threadIdx.x] = block_exclusive_scan_256(a.digit_tot[threadIdx.x], S.scan_w) +
-                         a.hist[(int64_t)threadIdx.x * a.grid + blockIdx.x];
+    const int d0 = threadIdx.x * DPT;   // this thread's digits d0 .. d0 + DPT - 1
+    {
+        // start of this block's run of each digit: digit offset + count in earlier blocks
+        uint32_t x[DPT], ex[DPT];
+#pragma unroll
+        for (int q = 0; q < DPT; q++) x[q] = a.digit_tot[d0 + q];
+        block_exclusive_scan_dpt<DPT>(x, ex, S.scan_w);
+#pragma unroll
+        for (int q = 0; q < DPT; q++) S.run[d0 + q] = ex[q] + a.hist[(int64_t)(d0 + q) * a.grid + blockIdx.x];
+    }
     const uint32_t ltm = lanemask_lt();
     for (int64_t base = lo; base < hi; base += kSortChunk) {
         const int m = (int)(hi - base < kSortChunk ? hi - base : kSortChunk);
-        for (int t = threadIdx.x; t < kSortWarps * kSortBins; t += blockDim.x) (&S.wcnt[0][0])[t] = 0;
+        for (int t = threadIdx.x; t < kSortWarps * BINS; t += blockDim.x) (&S.wcnt[0][0])[t] = 0;
         K key[kSortItems];
         uint32_t val[kSortItems];
         uint32_t rank[kSortItems];
@@ -433,8 +441,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
         for (int j = 0; j < kSortItems; j++) {
             const int item = w * kItemsPerWarp + j * 32 + lane;
             const bool valid = item < m;
-            const uint32_t d = valid ? digit_of(key[j], shift) : (uint32_t)kSortBins;
-            const uint32_t peers = digit_peers(d);
+            const uint32_t d = valid ? digit_of<BITS>(key[j], shift) : (uint32_t)BINS;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
             uint32_t r = __popc(peers & ltm);
             if (valid) r += S.wcnt[w][d];
             __syncwarp();
@@ -444,24 +452,30 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
         }
         __syncthreads();
         {
-            // per digit: prefix over warps and the chunk total
-            const int d = threadIdx.x;
-            uint32_t run = 0;
+            // per digit: prefix over warps and the chunk total, then the chunk's digit starts
+            uint32_t tot[DPT], cs[DPT];
 #pragma unroll
-            for (int ww = 0; ww < kSortWarps; ww++) {
-                const uint32_t c = S.wcnt[ww][d];
-                S.wcnt[ww][d] = run;
-                run += c;
+            for (int q = 0; q < DPT; q++) {
+                uint32_t run = 0;
+#pragma unroll
+                for (int ww = 0; ww < kSortWarps; ww++) {
+                    const uint32_t c = S.wcnt[ww][d0 + q];
+                    S.wcnt[ww][d0 + q] = run;
+                    run += c;
+                }
+                tot[q] = run;
+                S.tot[d0 + q] = run;
             }
-            S.tot[d] = run;
-            S.cstart[d] = block_exclusive_scan_256(run, S.scan_w);
+            block_exclusive_scan_dpt<DPT>(tot, cs, S.scan_w);
+#pragma unroll
+            for (int q = 0; q < DPT; q++) S.cstart[d0 + q] = cs[q];
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kSortItems; j++) {
             const int item = w * kItemsPerWarp + j * 32 + lane;
             if (item < m) {
-                const uint32_t d = digit_of(key[j], shift);
+                const uint32_t d = digit_of<BITS>(key[j], shift);
                 const uint32_t pos = S.cstart[d] + S.wcnt[w][d] + rank[j];
                 S.keys[pos] = key[j];
                 S.vals[pos] = val[j];
@@ -470,13 +484,14 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
         __syncthreads();
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
             const K kk = S.keys[k];
-            const uint32_t d = digit_of(kk, shift);
+            const uint32_t d = digit_of<BITS>(kk, shift);
             const int64_t g = (int64_t)S.run[d] + (k - (int)S.cstart[d]);
             kout[g] = kk;
             vout[g] = S.vals[k];
         }
         __syncthreads();
-        S.run[threadIdx.x] += S.tot[threadIdx.x];
+#pragma unroll
+        for (int q = 0; q < DPT; q++) S.run[d0 + q] += S.tot[d0 + q];
     }
 }
 
@@ -492,32 +507,33 @@ int sort_grid() {
     return g_sort_grid;
 }
 
-template <typename K>
+template <typename K, int BITS>
 static cudaError_t launch_sort_t(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
     static bool attr_set = false;
-    const size_t smem = sizeof(SortSmem<K>);
+    const size_t smem = sizeof(SortSmem<K, BITS>);
     if (a.grid < 1 || a.grid > kSortMaxGrid) return cudaErrorInvalidValue;
     if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(sort_downsweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(sort_downsweep_kernel<K, BITS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     for (int p = 0; p < n_passes; p++) {
         const int in_buf = p & 1;
-        sort_upsweep_kernel<K><<<a.grid, kSortThreads, 0, st>>>(a, in_buf, shifts[p]);
-        sort_scan_kernel<<<kSortBins / 8, 256, 0, st>>>(a);
-        sort_downsweep_kernel<K><<<a.grid, kSortThreads, smem, st>>>(a, in_buf, shifts[p]);
+        sort_upsweep_kernel<K, BITS><<<a.grid, kUpThreads, 0, st>>>(a, in_buf, shifts[p]);
+        sort_scan_kernel<<<(1 << BITS) / 8, 256, 0, st>>>(a);
+        sort_downsweep_kernel<K, BITS><<<a.grid, kSortThreads, smem, st>>>(a, in_buf, shifts[p]);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
-    return launch_sort_t<uint32_t>(a, n_passes, shifts, st);
+cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, int bits, cudaStream_t st) {
+    return bits == 9 ? launch_sort_t<uint32_t, 9>(a, n_passes, shifts, st)
+                     : launch_sort_t<uint32_t, 8>(a, n_passes, shifts, st);
 }
 
 cudaError_t launch_sort64(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
-    return launch_sort_t<unsigned long long>(a, n_passes, shifts, st);
+    return launch_sort_t<unsigned long long, 8>(a, n_passes, shifts, st);
 }
 
 // ----------------------------------------------------------------------------------------

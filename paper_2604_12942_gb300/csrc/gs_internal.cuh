@@ -12,7 +12,8 @@ namespace gs {
 
 constexpr float kLn2 = 0.69314718055994530942f;
 constexpr float kLog2e = 1.44269504088896340736f;
-constexpr int kSortBins = 256;
+constexpr int kSortBins = 256;                    // 8-bit digits (64-bit keys)
+constexpr int kSortMaxBins = 512;                 // up to 9-bit digits (32-bit keys)
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;                     // per thread per chunk
 constexpr int kSortChunk = kSortThreads * kSortItems;
@@ -59,6 +60,16 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
     const float mh = __fdiv_rn(m, bc1), vh = __fdiv_rn(v, bc2);
     p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, mh), __fadd_rn(__fsqrt_rn(vh), eps)));
 }
+
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only), in commit groups.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all but the most recently committed group have completed
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Adds a warp's per-lane counts to a device counter (one atomic per warp).
 __device__ __forceinline__ void warp_count_add(unsigned long long* dst, uint32_t v) {

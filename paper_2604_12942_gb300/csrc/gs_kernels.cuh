@@ -136,7 +136,8 @@ cudaError_t launch_entries(const BinArgs& a, cudaStream_t st);
 // Pair offsets over the depth-sorted entries (total to c->n_pairs, GS_ERR_CAPACITY above
 // max_pairs) and emission of one (tile id, entry) pair per covered tile.
 cudaError_t launch_emit(const BinArgs& a, cudaStream_t st);
-cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st);
+// 32-bit keys with `bits`-bit digits (8 or 9) at the given shifts; 64-bit keys with 8-bit digits.
+cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, int bits, cudaStream_t st);
 cudaError_t launch_sort64(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st);
 cudaError_t launch_ranges(const RangeArgs& a, int n_tiles, cudaStream_t st);
 cudaError_t launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, uint32_t* tmp, const Counters* c,

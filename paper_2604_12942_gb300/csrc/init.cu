@@ -282,7 +282,7 @@ static PcaWs pca_layout(int64_t n) {
     L.keys1 = take(8 * (size_t)n);
     L.vals0 = take(4 * (size_t)n);
     L.vals1 = take(4 * (size_t)n);
-    L.hist = take(sizeof(uint32_t) * ((size_t)kSortBins * kSortMaxGrid + kSortBins));
+    L.hist = take(sizeof(uint32_t) * ((size_t)kSortMaxBins * kSortMaxGrid + kSortMaxBins));
     L.total = off;
     return L;
 }
@@ -303,7 +303,7 @@ cudaError_t launch_voxel_pca(const float* pts, const float* rgb, int64_t n, cons
     sa.vals[0] = reinterpret_cast<uint32_t*>(b + L.vals0);
     sa.vals[1] = reinterpret_cast<uint32_t*>(b + L.vals1);
     sa.hist = reinterpret_cast<uint32_t*>(b + L.hist);
-    sa.digit_tot = sa.hist + (size_t)kSortBins * kSortMaxGrid;
+    sa.digit_tot = sa.hist + (size_t)kSortMaxBins * kSortMaxGrid;
     sa.counters = cnt;
     sa.count = &cnt->n_pairs;
     sa.grid = sort_grid();

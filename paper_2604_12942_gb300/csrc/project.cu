@@ -320,7 +320,9 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) project_bwd_kernel(Project
                     }
                 }
                 constexpr int GS = 3 * K < 16 ? 3 * K : 16;
-#pragma unroll
+                // (the group loop stays rolled: an unrolled tail of 3K planes would crowd the
+                // instruction cache of this already long kernel)
+#pragma unroll 1
                 for (int k0 = 0; k0 < 3 * K; k0 += GS) {
                     float mm[GS], vv[GS];
 #pragma unroll

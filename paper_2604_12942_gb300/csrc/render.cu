@@ -83,6 +83,9 @@ cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int
 // ----------------------------------------------------------------------------------------
 constexpr int kFwdPPT = 1;
 constexpr int kBwdPPT = 2;
+// Backward visits with at most this many contributing lanes skip the warp reduction: those
+// lanes add their sums to the record directly.
+constexpr int kBwdDirectLanes = 2;
 static_assert(kFwdPPT == 1 && kBwdPPT == 2, "bwd_mask_from_fwd maps 8 x 4 forward regions to 8 x 8 ones");
 
 template <int TILE, int PPT>
@@ -188,14 +191,15 @@ constexpr int kFwdThreadsPerSM = 1280;
 template <int TILE, int CHUNK>
 __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM / TileMap<TILE, kFwdPPT>::NT)
     render_fwd_kernel(FwdArgs a) {
-    constexpr int kPPT = kFwdPPT;
-    using TM = TileMap<TILE, kPPT>;
+    using TM = TileMap<TILE, kFwdPPT>;
     constexpr int NT = TM::NT;
-    __shared__ float2 s_uv[CHUNK];
-    __shared__ float4 s_co[CHUNK];   // a, b, c, opacity
-    __shared__ float4 s_cz[CHUNK];   // r, g, b, z
+    constexpr int NW = NT / 32;
+    // two chunk buffers of raw records (u, v, z, o), (a, b, c, rx), (r, g, b, ry): while the
+    // warps composite one, cp.async fills the other
+    __shared__ float4 s_rec[2][CHUNK][3];
     __shared__ uint32_t s_mask[CHUNK];
-    __shared__ double s_red[2][NT / 32];
+    __shared__ uint16_t s_list[NW][CHUNK];   // per warp: the chunk's records that reach its region
+    __shared__ double s_red[2][NW];
     if (a.counters->status != 0) return;
     const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     const int v = view_of_tile(a.views, a.n_views, gt);
@@ -203,99 +207,139 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
     const int lt = gt - V.tile_off;
     const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int rx0 = tx * TILE + (w % TM::WX) * 8, ry0 = ty * TILE + (w / TM::WX) * TM::RH;
-    int x[kPPT], y[kPPT];
-    bool inside[kPPT], done[kPPT];
-    float T[kPPT], c0[kPPT], c1[kPPT], c2[kPPT], dep[kPPT];
-    uint32_t last[kPPT];
-#pragma unroll
-    for (int q = 0; q < kPPT; q++) {
-        x[q] = rx0 + (lane & 7);
-        y[q] = ry0 + (lane >> 3) + 4 * q;
-        inside[q] = x[q] < V.W && y[q] < V.H;
-        done[q] = !inside[q];
-        T[q] = 1.f; c0[q] = c1[q] = c2[q] = dep[q] = 0.f;
-        last[q] = 0;
-    }
+    uint32_t ltm;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(ltm));
+    // one pixel per thread
+    const int x = tx * TILE + (w % TM::WX) * 8 + (lane & 7), y = ty * TILE + (w / TM::WX) * TM::RH + (lane >> 3);
+    const float pxc = (float)x + 0.5f, pyc = (float)y + 0.5f;
+    const bool inside = x < V.W && y < V.H;
+    bool done = !inside;
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
+    uint32_t last = 0;
     const uint2 rg = a.ranges[gt];
     const int n = (int)(rg.y - rg.x);
     const float amin = a.op.alpha_min, amax = a.op.alpha_max, tmin = a.op.T_min;
     uint32_t n_eval = 0, n_add = 0, n_visit = 0;
-    for (int base = 0; base < n; base += CHUNK) {
-        bool alive = false;
+    int b = 0;   // buffer holding the chunk being composited
+    // composite one fragment with opacity alpha of chunk record k (front to back)
+    auto add = [&](float alpha, int k, int base) {
+        n_eval++;
+        if (alpha < amin) return;
+        const float test_T = T * (1.f - alpha);
+        if (test_T < tmin) {
+            done = true;
+            return;
+        }
+        const float wgt = alpha * T;
+        const float4 r2 = s_rec[b][k][2];
+        c0 = fmaf(wgt, r2.x, c0);
+        c1 = fmaf(wgt, r2.y, c1);
+        c2 = fmaf(wgt, r2.z, c2);
+        dep = fmaf(wgt, s_rec[b][k][0].z, dep);
+        T = test_T;
+        last = (uint32_t)(base + k + 1);
+        n_add++;
+    };
+    auto alpha_of = [&](int k) {
+        const float4 r0 = s_rec[b][k][0], r1 = s_rec[b][k][1];
+        const float G = ex2_approx(frag_exponent(pxc - r0.x, pyc - r0.y, r1.x, r1.y, r1.z).e);
+        return fminf(amax, r0.w * G);
+    };
+    // Pipeline over chunks c = [c CHUNK, (c + 1) CHUNK): the pair ids of chunk c + 2 are loaded
+    // into registers and the records of chunk c + 1 copied asynchronously while chunk c is
+    // composited.
+    const int nchunks = (n + CHUNK - 1) / CHUNK;
+    constexpr int R = (CHUNK + NT - 1) / NT;   // staged records per thread
+    uint32_t pid[R];
+    auto fetch_ids = [&](int c) {
 #pragma unroll
-        for (int q = 0; q < kPPT; q++) alive |= !done[q];
-        if (__syncthreads_count(alive) == 0) break;
-        for (int k = threadIdx.x; k < CHUNK; k += NT) {
-            const int j = base + k;
-            if (j < n) {
-                float2 uv;
-                float4 co;
-                float rxf, ryf;
-                load_record(a.proj, a.vals[rg.x + j], uv, co, s_cz[k], rxf, ryf);
-                s_uv[k] = uv;
-                s_co[k] = co;
-                const uint32_t msk = region_mask<TILE, kPPT>(uv.x, uv.y, rxf, ryf, co.x, co.y, co.z, co.w, amin,
-                                                             (float)(tx * TILE), (float)(ty * TILE));
-                s_mask[k] = msk;
-                a.pair_mask[rg.x + j] = (uint8_t)msk;
+        for (int r = 0; r < R; r++) {
+            const int j = c * CHUNK + (int)threadIdx.x + r * NT;
+            if (c < nchunks && (int)threadIdx.x + r * NT < CHUNK && j < n) pid[r] = a.vals[rg.x + j];
+        }
+    };
+    auto stage = [&](int c, int bb) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int k = (int)threadIdx.x + r * NT;
+            const int j = c * CHUNK + k;
+            if (c < nchunks && k < CHUNK && j < n) {
+                const float4* src = a.proj + 3 * (size_t)pid[r];
+#pragma unroll
+                for (int h = 0; h < 3; h++) cp_async16(&s_rec[bb][k][h], src + h);
             }
         }
+        cp_async_commit();
+    };
+    fetch_ids(0);
+    stage(0, 0);
+    fetch_ids(1);
+    for (int c = 0; c < nchunks; c++) {
+        b = c & 1;
+        const int base = c * CHUNK;
+        if (__syncthreads_count(!done) == 0) break;   // (also: every warp is done with buffer b ^ 1)
+        stage(c + 1, b ^ 1);
+        fetch_ids(c + 2);
+        cp_async_wait_prior();   // chunk c has landed (chunk c + 1 may still be in flight)
         __syncthreads();
-        if (__any_sync(0xffffffffu, alive)) {
-            const int m = min(CHUNK, n - base);
-            for (int k = 0; k < m; k++) {
-                if (!((s_mask[k] >> w) & 1u)) continue;
-                n_visit++;
-                const float2 uv = s_uv[k];
-                const float4 co = s_co[k];
-#pragma unroll
-                for (int q = 0; q < kPPT; q++) {
-                    if (done[q]) continue;
-                    const float dx = ((float)x[q] + 0.5f) - uv.x, dy = ((float)y[q] + 0.5f) - uv.y;
-                    const float G = ex2_approx(frag_exponent(dx, dy, co.x, co.y, co.z).e);
-                    const float alpha = fminf(amax, co.w * G);
-                    n_eval++;
-                    if (alpha < amin) continue;
-                    const float test_T = T[q] * (1.f - alpha);
-                    if (test_T < tmin) {
-                        done[q] = true;
-                        continue;
-                    }
-                    const float wgt = alpha * T[q];
-                    const float4 cz = s_cz[k];
-                    c0[q] = fmaf(wgt, cz.x, c0[q]);
-                    c1[q] = fmaf(wgt, cz.y, c1[q]);
-                    c2[q] = fmaf(wgt, cz.z, c2[q]);
-                    dep[q] = fmaf(wgt, cz.w, dep[q]);
-                    T[q] = test_T;
-                    last[q] = (uint32_t)(base + k + 1);
-                    n_add++;
-                }
+        const int m = min(CHUNK, n - base);
+        // warp-region masks of the chunk's records, kept per pair for the backward
+        for (int k = threadIdx.x; k < m; k += NT) {
+            const float4 r0 = s_rec[b][k][0], r1 = s_rec[b][k][1];
+            const float rxf = (float)__float_as_int(r1.w), ryf = (float)__float_as_int(s_rec[b][k][2].w);
+            const uint32_t msk = region_mask<TILE, kFwdPPT>(r0.x, r0.y, rxf, ryf, r1.x, r1.y, r1.z, r0.w, amin,
+                                                           (float)(tx * TILE), (float)(ty * TILE));
+            s_mask[k] = msk;
+            a.pair_mask[rg.x + base + k] = (uint8_t)msk;
+        }
+        __syncthreads();
+        if (__any_sync(0xffffffffu, !done)) {
+            // compact the records whose alpha >= alpha_min region reaches this warp's pixels
+            int cnt = 0;
+            for (int k0 = 0; k0 < m; k0 += 32) {
+                const int k = k0 + lane;
+                const bool hit = k < m && ((s_mask[k] >> w) & 1u);
+                const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) s_list[w][cnt + __popc(bal & ltm)] = (uint16_t)k;
+                cnt += __popc(bal);
+            }
+            __syncwarp();
+            n_visit += cnt;
+            // two records per iteration: their alphas are independent, the compositing is not
+            int t = 0;
+            for (; t + 1 < cnt; t += 2) {
+                const int ka = s_list[w][t], kb = s_list[w][t + 1];
+                if (done) continue;
+                const float alpha_a = alpha_of(ka), alpha_b = alpha_of(kb);
+                add(alpha_a, ka, base);
+                if (!done) add(alpha_b, kb, base);
+            }
+            if (t < cnt && !done) {
+                const int k = s_list[w][t];
+                add(alpha_of(k), k, base);
             }
         }
     }
+    cp_async_wait_all();
     warp_count_add(&a.counters->frag_fwd_eval, n_eval);
     warp_count_add(&a.counters->frag_fwd_add, n_add);
     if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_fwd, n_visit);
-    // L1 sums: FP32 within a warp (at most 32 * kPPT pixels), FP64 across warps and CTAs
-    // (the FP64 pipe is narrow: it only sees the per-warp totals)
+    // L1 sums: FP32 within a warp (32 pixels), FP64 across warps and CTAs (the FP64 pipe is
+    // narrow: it only sees the per-warp totals)
     float lr = 0.f, ld = 0.f;
-#pragma unroll
-    for (int q = 0; q < kPPT; q++) {
-        if (!inside[q]) continue;
+    if (inside) {
         const int64_t P = (int64_t)V.W * V.H;
-        const int64_t p = (int64_t)y[q] * V.W + x[q];
+        const int64_t p = (int64_t)y * V.W + x;
         const int64_t g = V.pix_off + p;
-        const float o0 = c0[q] + T[q] * a.op.bg0, o1 = c1[q] + T[q] * a.op.bg1, o2 = c2[q] + T[q] * a.op.bg2;
+        const float o0 = c0 + T * a.op.bg0, o1 = c1 + T * a.op.bg1, o2 = c2 + T * a.op.bg2;
         float* rgb = a.out_rgb + 3 * V.pix_off;
         rgb[p] = o0;
         rgb[P + p] = o1;
         rgb[2 * P + p] = o2;
-        a.out_depth[g] = dep[q];
-        if (a.out_T) a.out_T[g] = T[q];
-        a.T_final[g] = T[q];
-        a.n_contrib[g] = last[q];
+        a.out_depth[g] = dep;
+        if (a.out_T) a.out_T[g] = T;
+        a.T_final[g] = T;
+        a.n_contrib[g] = last;
         if (a.tgt_rgb) {
             const bool in = a.mask ? a.mask[g] != 0 : true;
             const float cm = (float)a.loss_counts[2 * v], cd = (float)a.loss_counts[2 * v + 1];
@@ -312,7 +356,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
                 const float td = a.tgt_depth ? a.tgt_depth[g] : 0.f;
                 const bool ind = in && td > 0.f;
                 const float kd = (ind && cd > 0.f) ? a.op.lambda_depth * inv_v / cd : 0.f;
-                const float rd = dep[q] - td;
+                const float rd = dep - td;
                 a.dl_ddepth[g] = kd * (float)((rd > 0.f) - (rd < 0.f));
                 if (ind) ld += fabsf(rd);
             }
@@ -329,7 +373,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
         __syncthreads();
         if (threadIdx.x == 0) {
             double sr = 0, sd = 0;
-            for (int k = 0; k < NT / 32; k++) { sr += s_red[0][k]; sd += s_red[1][k]; }
+            for (int k = 0; k < NW; k++) { sr += s_red[0][k]; sd += s_red[1][k]; }
             if (sr != 0.0) atomicAdd(&a.loss_sums[2 * v], sr);
             if (sd != 0.0) atomicAdd(&a.loss_sums[2 * v + 1], sd);
         }
@@ -350,7 +394,8 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
 //   r1 = (sum h dy^2, sum dL/dalpha G, sum g_D w, 0), r2 = (sum g_C w, 0)
 // (h_x, h_y from frag_exponent) and the projection backward applies the constant factors.
 // A lane first sums its two pixels; the warp's 10 sums are then reduced (warp_reduce10) and
-// written by 10 lanes with one atomic each.
+// written by 10 lanes with one atomic each -- or, when at most kBwdDirectLanes lanes
+// contribute, added by those lanes directly with vector atomics.
 // ----------------------------------------------------------------------------------------
 // Warp sums of 10 per-lane values by transpose reductions: values 0..7 halve their count at
 // each of the lane-xor 16, 8, 4 exchanges and finish with two butterflies (lane l ends with
@@ -403,11 +448,10 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
     constexpr int kPPT = kBwdPPT;
     using TM = TileMap<TILE, kPPT>;
     constexpr int NT = TM::NT;
-    __shared__ float2 s_uv[CHUNK];
-    __shared__ float4 s_co[CHUNK];
-    __shared__ float4 s_cz[CHUNK];
-    __shared__ uint32_t s_id[CHUNK];
-    __shared__ uint32_t s_mask[CHUNK];
+    // two chunk buffers: while the warps walk one, cp.async fills the other
+    __shared__ float4 s_rec[2][CHUNK][3];   // raw projected records (u, v, z, o), (a, b, c, rx), (r, g, b, ry)
+    __shared__ uint32_t s_id[2][CHUNK];
+    __shared__ uint32_t s_mask[2][CHUNK];
     __shared__ uint32_t s_max;
     if (a.counters->status != 0) return;
     const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
@@ -452,26 +496,57 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
     if (lane == 0 && wtop) atomicMax(&s_max, wtop);
     __syncthreads();
     const int top_all = (int)s_max;
-    for (int top = top_all; top > 0; top -= CHUNK) {
-        const int lo = max(0, top - CHUNK);
-        __syncthreads();
-        for (int k = threadIdx.x; k < top - lo; k += NT) {
-            const uint32_t gid = a.vals[rg.x + lo + k];
-            float2 uv;
-            float rxf, ryf;
-            load_record(a.proj, gid, uv, s_co[k], s_cz[k], rxf, ryf);
-            s_uv[k] = uv;
-            s_mask[k] = bwd_mask_from_fwd<TILE>(a.pair_mask[rg.x + lo + k]);
-            s_id[k] = gid;
+    // Chunk c covers list positions [max(0, top_all - (c + 1) CHUNK), top_all - c CHUNK).
+    // Pipeline: the ids and masks of chunk c + 2 are loaded into registers and the records of
+    // chunk c + 1 are copied asynchronously while chunk c is composited.
+    const int nchunks = (top_all + CHUNK - 1) / CHUNK;
+    constexpr int R = (CHUNK + NT - 1) / NT;   // staged records per thread
+    uint32_t pid[R];
+    uint32_t pmsk[R];
+    auto fetch_ids = [&](int c) {
+        const int top = top_all - c * CHUNK, lo = max(0, top - CHUNK);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int k = (int)threadIdx.x + r * NT;
+            if (c < nchunks && k < top - lo) {
+                pid[r] = a.vals[rg.x + lo + k];
+                pmsk[r] = a.pair_mask[rg.x + lo + k];
+            }
         }
+    };
+    auto stage = [&](int c, int b) {
+        const int top = top_all - c * CHUNK, lo = max(0, top - CHUNK);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int k = (int)threadIdx.x + r * NT;
+            if (c < nchunks && k < top - lo) {
+                s_id[b][k] = pid[r];
+                s_mask[b][k] = bwd_mask_from_fwd<TILE>(pmsk[r]);
+                const float4* src = a.proj + 3 * (size_t)pid[r];
+#pragma unroll
+                for (int h = 0; h < 3; h++) cp_async16(&s_rec[b][k][h], src + h);
+            }
+        }
+        cp_async_commit();
+    };
+    fetch_ids(0);
+    stage(0, 0);
+    fetch_ids(1);
+    for (int c = 0; c < nchunks; c++) {
+        const int b = c & 1;
+        const int top = top_all - c * CHUNK, lo = max(0, top - CHUNK);
+        stage(c + 1, b ^ 1);
+        fetch_ids(c + 2);
+        cp_async_wait_prior();   // chunk c has landed (chunk c + 1 may still be in flight)
         __syncthreads();
         const int jstart = min(top, (int)wtop) - 1;
         for (int j = jstart; j >= lo; j--) {
             const int k = j - lo;
-            if (!((s_mask[k] >> w) & 1u)) continue;
+            if (!((s_mask[b][k] >> w) & 1u)) continue;
             n_visit++;
-            const float2 bx = s_uv[k];
-            const float4 co = s_co[k];
+            const float4 r0 = s_rec[b][k][0], r1 = s_rec[b][k][1];
+            const float2 bx = make_float2(r0.x, r0.y);
+            const float4 co = make_float4(r1.x, r1.y, r1.z, r0.w);
             float val[10];
 #pragma unroll
             for (int q = 0; q < 10; q++) val[q] = 0.f;
@@ -491,7 +566,8 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
                 const float rom = rcp_approx(1.f - alpha);
                 T[q] = T[q] * rom;
                 const float wgt = alpha * T[q];
-                const float4 cz = s_cz[k];
+                const float4 r2 = s_rec[b][k][2];
+                const float4 cz = make_float4(r2.x, r2.y, r2.z, r0.z);
                 const float gcz = gc0[q] * cz.x + gc1[q] * cz.y + gc2[q] * cz.z + gd[q] * cz.w;
                 const float dLda = T[q] * gcz - S[q] * rom;
                 S[q] = fmaf(gcz, wgt, S[q]);
@@ -510,19 +586,33 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
                     val[5] = fmaf(dLda, G, val[5]);
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                float t8, t2;
-                warp_reduce10(val, t8, t2);
-                float* rec = reinterpret_cast<float*>(a.grad2d + 3 * (size_t)s_id[k]);
-                // value index -> record slot: 0..6 -> 0..6, 7..9 -> 8..10
-                if ((lane & 3) == 0) {
-                    const int idx = lane >> 2;
-                    atomicAdd(rec + (idx < 7 ? idx : idx + 1), t8);
+            const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
+            if (cmask) {
+                float4* rec4 = a.grad2d + 3 * (size_t)s_id[b][k];
+                if (__popc(cmask) <= kBwdDirectLanes) {
+                    // few contributing lanes: each adds its own sums with three vector atomics
+                    // (slots 7 and 11 of the record are padding and receive zeros)
+                    if (contrib) {
+                        atomicAdd(rec4, make_float4(val[0], val[1], val[2], val[3]));
+                        atomicAdd(rec4 + 1, make_float4(val[4], val[5], val[6], 0.f));
+                        atomicAdd(rec4 + 2, make_float4(val[7], val[8], val[9], 0.f));
+                    }
+                } else {
+                    float t8, t2;
+                    warp_reduce10(val, t8, t2);
+                    float* rec = reinterpret_cast<float*>(rec4);
+                    // value index -> record slot: 0..6 -> 0..6, 7..9 -> 8..10
+                    if ((lane & 3) == 0) {
+                        const int idx = lane >> 2;
+                        atomicAdd(rec + (idx < 7 ? idx : idx + 1), t8);
+                    }
+                    if ((lane & 15) == 0) atomicAdd(rec + 9 + (lane >> 4), t2);
                 }
-                if ((lane & 15) == 0) atomicAdd(rec + 9 + (lane >> 4), t2);
             }
         }
+        __syncthreads();   // buffer b is refilled with chunk c + 2 in the next iteration
     }
+    cp_async_wait_all();
     warp_count_add(&a.counters->frag_bwd_eval, n_eval);
     warp_count_add(&a.counters->frag_bwd_add, n_add);
     if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_bwd, n_visit);

@@ -133,6 +133,13 @@ def test_bin_sort_bit_exact_multichunk():
     assert P > 2_500_000
 
 
+def test_bin_sort_bit_exact_nine_bit_digits():
+    """81,920 tiles (17 tile bits): the tile sort takes two 9-bit passes instead of three."""
+    cams = [synth.camera(1280, 1024, 900.0) for _ in range(4)]
+    P = _bin_case(cams, 100_000, 8, seed=6, radius_max=40)
+    assert P > 1_000_000
+
+
 def test_bin_sort_single_tile():
     """One tile per view set: no tile-sort pass, the pairs stay in depth order."""
     _bin_case([synth.camera(16, 16, 20.0)], 2000, 16, seed=5, radius_max=12)
