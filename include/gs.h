@@ -124,9 +124,12 @@ typedef struct {
     size_t ranges;       /* uint32 [total_tiles][2] [first, last+1) in the sorted pairs */
     size_t T_final;      /* float [total_pixels] */
     size_t n_contrib;    /* uint32 [total_pixels] tile-list position after the last added */
-    size_t grad2d;       /* [n_views*n] records of 12 floats (screen-space gradient sums);
-                            only the records of visible entries are defined after a backward */
+    size_t grad2d;       /* [n_views*n] records of 12 floats (screen-space gradient sums of
+                            gs_composite_bwd); only the records of visible entries are defined */
+    size_t geo2d;        /* [n_views*n] records of 12 floats: per visible entry, the gradients
+                            w.r.t. the mean and the world covariance (projection backward) */
     size_t visible;      /* uint8 [n]: 1 if the Gaussian covers a tile of any view */
+    size_t entries;      /* uint32 [n_views*n]: the visible entries in (view, Gaussian) order */
     size_t tile_order;   /* uint32 [total_tiles]: compositing work order, largest pair count
                             first (power-of-two buckets), then scratch */
     size_t total;        /* workspace bytes */

@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
     float* V = a.v[grp] + (int64_t)k * n;
     const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (i0 >= n) return;
-    const float bc1 = a.step_dev ? a.step_dev->adam_bc1 : a.bc1;
-    const float bc2 = a.step_dev ? a.step_dev->adam_bc2 : a.bc2;
+    const float bc1 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc1 : a.bc1);   // inverse bias corrections
+    const float bc2 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc2 : a.bc2);
     bool upd[4], vis[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {

@@ -94,15 +94,22 @@ static int tile_bits(int total_tiles) {
     return b;
 }
 
-// Passes of the pair sort over the global tile id bits (0 passes when there is one tile):
-// 8-bit digits, or 9-bit ones where that saves a pass (17 or 18 tile bits: 2 passes, not 3).
+// Passes of the pair sort over the global tile id bits tb (0 passes when there is one tile):
+// as few as 8- or 9-bit digits allow, P = min(ceil(tb / 8), ceil(tb / 9)).  The tb - 8 P
+// passes that need a ninth bit are the last ones: the first pass's input, in emission order,
+// spreads over all digits, and fewer digits give longer runs per digit in each chunk's
+// scatter (17 tile bits: an 8-bit then a 9-bit pass).
 static int pair_sort_passes(int total_tiles, int* shifts, int* bits) {
     const int tb = tile_bits(total_tiles);
-    const int p8 = (tb + 7) / 8, p9 = (tb + 8) / 9;
-    *bits = p9 < p8 ? 9 : 8;
-    int np = 0;
-    for (int s = 0; s < tb; s += *bits) shifts[np++] = s;
-    return np;
+    const int P = (tb + 7) / 8 < (tb + 8) / 9 ? (tb + 7) / 8 : (tb + 8) / 9;
+    const int nine = tb - 8 * P > 0 ? tb - 8 * P : 0;
+    int s = 0;
+    for (int p = 0; p < P; p++) {
+        bits[p] = p >= P - nine ? 9 : 8;
+        shifts[p] = s;
+        s += bits[p];
+    }
+    return P;
 }
 
 static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const gs_render_opts* o, int64_t max_pairs,
@@ -137,11 +144,13 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.T_final = take(sizeof(float) * (size_t)G.total_pixels);
     L.n_contrib = take(sizeof(uint32_t) * (size_t)G.total_pixels);
     L.grad2d = take(sizeof(float) * 12 * (size_t)VN);
+    L.geo2d = take(sizeof(float) * 12 * (size_t)VN);
+    L.entries = take(sizeof(uint32_t) * (size_t)VN);
     L.visible = take((size_t)n);
     L.tile_order = take(sizeof(uint32_t) * ((size_t)G.total_tiles + 2 * 34));
     L.total = off;
-    int shifts[16], bits;
-    L.sorted_buf = pair_sort_passes(G.total_tiles, shifts, &bits) & 1;
+    int shifts[16], bits[16];
+    L.sorted_buf = pair_sort_passes(G.total_tiles, shifts, bits) & 1;
     L.total_tiles = G.total_tiles;
     L.total_pixels = G.total_pixels;
     L.max_pairs = max_pairs;
@@ -242,6 +251,7 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     b.scan_tmp = at<uint32_t>(ws, L->scan_tmp);
     b.ekeys = at<uint32_t>(ws, L->ekeys0);
     b.evals = at<uint32_t>(ws, L->evals0);
+    b.entries = at<uint32_t>(ws, L->entries);
     b.sorted_evals = at<uint32_t>(ws, L->evals0);   // 4 passes: the entry sort ends in buffer 0
     b.pkeys = at<uint32_t>(ws, L->keys0);
     b.pvals = at<uint32_t>(ws, L->vals0);
@@ -261,8 +271,8 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     sa.vals[0] = at<uint32_t>(ws, L->evals0);
     sa.vals[1] = at<uint32_t>(ws, L->evals1);
     sa.count = &cnt->n_entries;
-    const int depth_shifts[4] = {0, 8, 16, 24};
-    if ((e = launch_sort32(sa, 4, depth_shifts, 8, st)) != cudaSuccess) return e;
+    const int depth_shifts[4] = {0, 8, 16, 24}, depth_bits[4] = {8, 8, 8, 8};
+    if ((e = launch_sort32(sa, 4, depth_shifts, depth_bits, st)) != cudaSuccess) return e;
     // 2. pairs emitted in depth order, then by tile
     if ((e = launch_emit(b, st)) != cudaSuccess) return e;
     sa.keys[0] = at<uint32_t>(ws, L->keys0);
@@ -270,8 +280,8 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     sa.vals[0] = at<uint32_t>(ws, L->vals0);
     sa.vals[1] = at<uint32_t>(ws, L->vals1);
     sa.count = &cnt->n_pairs;
-    int shifts[16], bits;
-    const int np = pair_sort_passes(L->total_tiles, shifts, &bits);
+    int shifts[16], bits[16];
+    const int np = pair_sort_passes(L->total_tiles, shifts, bits);
     if ((e = launch_sort32(sa, np, shifts, bits, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(at<uint32_t>(ws, L->ranges), 0, sizeof(uint32_t) * 2 * (size_t)L->total_tiles, st)) !=
         cudaSuccess)
@@ -372,7 +382,10 @@ static cudaError_t run_project_bwd(const gs_gaussians* g, const gs_render_opts* 
     p.means = g->means; p.log_scales = g->log_scales; p.quats = g->quats; p.logits = g->opacity_logits; p.sh = g->sh;
     p.touched = at<uint32_t>(ws, L->touched);
     p.visible = at<uint8_t>(ws, L->visible);
+    p.entries = at<uint32_t>(ws, L->entries);
+    p.counters = at<Counters>(ws, L->counters);
     p.grad2d = at<float4>(ws, L->grad2d);
+    p.geo2d = at<float4>(ws, L->geo2d);
     if (grads) {
         p.g_means = grads->means; p.g_log_scales = grads->log_scales; p.g_quats = grads->quats;
         p.g_logits = grads->opacity_logits; p.g_sh = grads->sh;

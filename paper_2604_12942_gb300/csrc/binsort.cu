@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
             const int64_t idx = base + k;
             a.ekeys[off] = __float_as_uint(__ldg(pf + 12 * idx + 2));   // z > 0: bits are monotone
             a.evals[off] = (uint32_t)idx;
+            a.entries[off] = (uint32_t)idx;
             off++;
         }
     }
@@ -507,8 +508,9 @@ int sort_grid() {
     return g_sort_grid;
 }
 
+// One pass (in_buf -> in_buf ^ 1) with BITS-bit digits at `shift`.
 template <typename K, int BITS>
-static cudaError_t launch_sort_t(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
+static cudaError_t launch_pass(const SortArgs& a, int in_buf, int shift, cudaStream_t st) {
     static bool attr_set = false;
     const size_t smem = sizeof(SortSmem<K, BITS>);
     if (a.grid < 1 || a.grid > kSortMaxGrid) return cudaErrorInvalidValue;
@@ -518,22 +520,27 @@ static cudaError_t launch_sort_t(const SortArgs& a, int n_passes, const int* shi
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    for (int p = 0; p < n_passes; p++) {
-        const int in_buf = p & 1;
-        sort_upsweep_kernel<K, BITS><<<a.grid, kUpThreads, 0, st>>>(a, in_buf, shifts[p]);
-        sort_scan_kernel<<<(1 << BITS) / 8, 256, 0, st>>>(a);
-        sort_downsweep_kernel<K, BITS><<<a.grid, kSortThreads, smem, st>>>(a, in_buf, shifts[p]);
-    }
+    sort_upsweep_kernel<K, BITS><<<a.grid, kUpThreads, 0, st>>>(a, in_buf, shift);
+    sort_scan_kernel<<<(1 << BITS) / 8, 256, 0, st>>>(a);
+    sort_downsweep_kernel<K, BITS><<<a.grid, kSortThreads, smem, st>>>(a, in_buf, shift);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, int bits, cudaStream_t st) {
-    return bits == 9 ? launch_sort_t<uint32_t, 9>(a, n_passes, shifts, st)
-                     : launch_sort_t<uint32_t, 8>(a, n_passes, shifts, st);
+cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, const int* bits, cudaStream_t st) {
+    for (int p = 0; p < n_passes; p++) {
+        const cudaError_t e = bits[p] == 9 ? launch_pass<uint32_t, 9>(a, p & 1, shifts[p], st)
+                                           : launch_pass<uint32_t, 8>(a, p & 1, shifts[p], st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_sort64(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st) {
-    return launch_sort_t<unsigned long long, 8>(a, n_passes, shifts, st);
+    for (int p = 0; p < n_passes; p++) {
+        const cudaError_t e = launch_pass<unsigned long long, 8>(a, p & 1, shifts[p], st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ----------------------------------------------------------------------------------------

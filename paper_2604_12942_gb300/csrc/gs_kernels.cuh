@@ -24,7 +24,10 @@ struct ProjectBwdArgs {
     const float *means, *log_scales, *quats, *logits, *sh;
     const uint32_t* touched;
     const uint8_t* visible;   // [n] covers a tile of some view (rows without it are skipped)
-    const float4* grad2d;  // [V*n][3]
+    const uint32_t* entries;  // visible (view, Gaussian) entries in (view, Gaussian) order
+    const Counters* counters; // n_entries
+    const float4* grad2d;  // [V*n][3] screen-space sums
+    float4* geo2d;         // [V*n][3] per-entry geometry gradients (entry part -> row part)
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
     float* grad_twist;     // [V][6] or null
     // fused Adam (fused_adam != 0): parameters updated in place, gradients not stored
@@ -50,6 +53,7 @@ struct BinArgs {
     uint32_t* scan_tmp;           // block sums of the scans
     uint32_t* ekeys;              // compaction output: bits(z) of each entry
     uint32_t* evals;              //   and its view * n + Gaussian index
+    uint32_t* entries;            //   a copy of evals kept in (view, Gaussian) order
     const uint32_t* sorted_evals; // entries in depth order (input of the pair emission)
     uint32_t* pkeys;              // emission output: global tile id of each pair
     uint32_t* pvals;              //   and the entry's view * n + Gaussian index
@@ -136,8 +140,8 @@ cudaError_t launch_entries(const BinArgs& a, cudaStream_t st);
 // Pair offsets over the depth-sorted entries (total to c->n_pairs, GS_ERR_CAPACITY above
 // max_pairs) and emission of one (tile id, entry) pair per covered tile.
 cudaError_t launch_emit(const BinArgs& a, cudaStream_t st);
-// 32-bit keys with `bits`-bit digits (8 or 9) at the given shifts; 64-bit keys with 8-bit digits.
-cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, int bits, cudaStream_t st);
+// 32-bit keys: pass p takes bits[p]-bit digits (8 or 9) at shifts[p]; 64-bit keys: 8-bit digits.
+cudaError_t launch_sort32(const SortArgs& a, int n_passes, const int* shifts, const int* bits, cudaStream_t st);
 cudaError_t launch_sort64(const SortArgs& a, int n_passes, const int* shifts, cudaStream_t st);
 cudaError_t launch_ranges(const RangeArgs& a, int n_tiles, cudaStream_t st);
 cudaError_t launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, uint32_t* tmp, const Counters* c,

@@ -72,6 +72,168 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
 // (k = -log2(e)/2, ln2 log2(e) = 1): dL/du = -2 ln2 r0.x, dL/dv = -2 ln2 r0.y,
 // dL/dA = -r0.z / 2, dL/dB = -r0.w, dL/dC = -r1.x / 2.  Pose: xi = (rho, phi), T_cw <- Exp(xi) T_cw, so
 // dp_c = rho + phi x p_c, dW = [phi]x W and the camera centre moves by -W^T rho.
+// Geometry part of the projection backward for one (view, Gaussian) entry: from the entry's
+// screen-space sums r0, r1 (see render.cu) to the mean through p_c, to the world covariance
+// and to the view's twist.  The opacity sum r1.y and the colour sums pass through unchanged.
+__device__ __forceinline__ void entry_geometry_bwd(const float (&mu)[3], const Cov3& cv, float logit, const View& V,
+                                                   const Opts& op, const float4 r0, const float4 r1,
+                                                   float (&g_mu)[3], float (&gS)[6], float (&tw)[6]) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) g_mu[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; k++) gS[k] = 0.f;
+    ProjV P;
+    project_view(mu, cv, logit, V, op, P);
+    const float* W = V.R;
+    // screen-space gradients
+    const float gu = -2.f * kLn2 * r0.x, gv = -2.f * kLn2 * r0.y;
+    const float gA = -0.5f * r0.z, gB = -r0.w, gC = -0.5f * r1.x;
+    float g_pc[3] = {0.f, 0.f, r1.z};
+    // conic = inverse(cov), cov = [[a, b], [b, c]]
+    const float pa = P.a, pb = P.b, pc = P.c;
+    const float id2 = 1.0f / (P.det * P.det);
+    const float ga = (-pc * pc * gA + pb * pc * gB - pb * pb * gC) * id2;
+    const float gb = (2.f * pb * pc * gA - (pa * pc + pb * pb) * gB + 2.f * pa * pb * gC) * id2;
+    const float gc = (-pb * pb * gA + pa * pb * gB - pa * pa * gC) * id2;
+    const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
+    // T Sigma
+    const float* S = cv.S;
+    float TS[6];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const float* t = &P.T[3 * r];
+        TS[3 * r + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
+        TS[3 * r + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
+        TS[3 * r + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+    }
+    // g_T = 2 G T Sigma
+    float gT[6];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        gT[k] = 2.f * (G00 * TS[k] + G01 * TS[3 + k]);
+        gT[3 + k] = 2.f * (G01 * TS[k] + G11 * TS[3 + k]);
+    }
+    // g_Sigma += T^T G T
+    {
+        float GT[6];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            GT[k] = G00 * P.T[k] + G01 * P.T[3 + k];
+            GT[3 + k] = G01 * P.T[k] + G11 * P.T[3 + k];
+        }
+        gS[0] += P.T[0] * GT[0] + P.T[3] * GT[3];
+        gS[1] += P.T[0] * GT[1] + P.T[3] * GT[4];
+        gS[2] += P.T[0] * GT[2] + P.T[3] * GT[5];
+        gS[3] += P.T[1] * GT[1] + P.T[4] * GT[4];
+        gS[4] += P.T[1] * GT[2] + P.T[4] * GT[5];
+        gS[5] += P.T[2] * GT[2] + P.T[5] * GT[5];
+    }
+    // T = J W : g_J = g_T W^T, g_W = J^T g_T
+    const float gJ00 = gT[0] * W[0] + gT[1] * W[1] + gT[2] * W[2];
+    const float gJ02 = gT[0] * W[6] + gT[1] * W[7] + gT[2] * W[8];
+    const float gJ11 = gT[3] * W[3] + gT[4] * W[4] + gT[5] * W[5];
+    const float gJ12 = gT[3] * W[6] + gT[4] * W[7] + gT[5] * W[8];
+    float gW[9];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        gW[k] = P.J00 * gT[k];
+        gW[3 + k] = P.J11 * gT[3 + k];
+        gW[6 + k] = P.J02 * gT[k] + P.J12 * gT[3 + k];
+    }
+    const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
+    const float iz = 1.0f / z, iz2 = iz * iz;
+    const float fx = V.fx, fy = V.fy;
+    const float dtx_dx = P.clx ? 0.f : iz, dtx_dz = P.clx ? 0.f : -x * iz2;
+    const float dty_dy = P.cly ? 0.f : iz, dty_dz = P.cly ? 0.f : -y * iz2;
+    g_pc[2] += -gJ00 * fx * iz2 - gJ11 * fy * iz2;
+    g_pc[2] += gJ02 * (fx * P.tx * iz2 - fx * iz * dtx_dz);
+    g_pc[0] += gJ02 * (-fx * iz * dtx_dx);
+    g_pc[2] += gJ12 * (fy * P.ty * iz2 - fy * iz * dty_dz);
+    g_pc[1] += gJ12 * (-fy * iz * dty_dy);
+    g_pc[0] += gu * fx * iz;
+    g_pc[1] += gv * fy * iz;
+    g_pc[2] += -(gu * fx * x + gv * fy * y) * iz2;
+#pragma unroll
+    for (int k = 0; k < 3; k++) g_mu[k] += W[k] * g_pc[0] + W[3 + k] * g_pc[1] + W[6 + k] * g_pc[2];
+    // pose: rho <- g_pc, phi <- p_c x g_pc + vee(g_W W^T)
+    tw[0] = g_pc[0]; tw[1] = g_pc[1]; tw[2] = g_pc[2];
+    tw[3] = y * g_pc[2] - z * g_pc[1];
+    tw[4] = z * g_pc[0] - x * g_pc[2];
+    tw[5] = x * g_pc[1] - y * g_pc[0];
+    {
+        // A = g_W W^T; need A21 - A12, A02 - A20, A10 - A01
+        auto Arc = [&](int r, int c) { return gW[3 * r] * W[3 * c] + gW[3 * r + 1] * W[3 * c + 1] + gW[3 * r + 2] * W[3 * c + 2]; };
+        tw[3] += Arc(2, 1) - Arc(1, 2);
+        tw[4] += Arc(0, 2) - Arc(2, 0);
+        tw[5] += Arc(1, 0) - Arc(0, 1);
+    }
+}
+
+// a7, entry part: one thread per visible (view, Gaussian) entry, entries in (view, Gaussian)
+// order (so a warp mostly reads consecutive rows of one view).  Writes the entry's geometry
+// gradients to its geo record -- (g_mu, gS_xx), (gS_xy, gS_xz, gS_yy, gS_yz), (gS_zz, 0, 0, 0)
+// -- and adds its geometric twist to the view's (sums over the lanes of one view, then per CTA).
+// The screen-space sums are only read, so the backward can be repeated on them.
+constexpr int kEntryThreads = 256;
+
+__global__ void __launch_bounds__(kEntryThreads) project_bwd_entry_kernel(ProjectBwdArgs a) {
+    __shared__ float s_tw[GS_MAX_VIEWS * 6];
+    for (int t = threadIdx.x; t < a.n_views * 6; t += blockDim.x) s_tw[t] = 0.f;
+    __syncthreads();
+    const int64_t E = (int64_t)a.counters->n_entries;
+    const int64_t n = a.n;
+    const int lane = threadIdx.x & 31;
+    const Opts op = a.op;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = base + threadIdx.x;
+        const bool valid = e < E;
+        int v = -1;
+        float tw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid) {
+            const uint32_t idx = a.entries[e];
+            v = (int)(idx / (uint64_t)n);
+            const int64_t i = (int64_t)idx - (int64_t)v * n;
+            float mu[3], ls[3], q[4];
+#pragma unroll
+            for (int k = 0; k < 3; k++) { mu[k] = __ldg(a.means + k * n + i); ls[k] = __ldg(a.log_scales + k * n + i); }
+#pragma unroll
+            for (int k = 0; k < 4; k++) q[k] = __ldg(a.quats + k * n + i);
+            const float logit = __ldg(a.logits + i);
+            const float4* rec = a.grad2d + 3 * (size_t)idx;
+            const float4 r0 = rec[0], r1 = rec[1];
+            Cov3 cv;
+            cov3_forward(q, ls, cv);
+            float g_mu[3], gS[6];
+            entry_geometry_bwd(mu, cv, logit, a.views[v], op, r0, r1, g_mu, gS, tw);
+            float4* geo = a.geo2d + 3 * (size_t)idx;
+            geo[0] = make_float4(g_mu[0], g_mu[1], g_mu[2], gS[0]);
+            geo[1] = make_float4(gS[1], gS[2], gS[3], gS[4]);
+            geo[2] = make_float4(gS[5], 0.f, 0.f, 0.f);
+        }
+        if (a.grad_twist) {
+            // lanes with the same view: one warp sum per view present in the warp
+            uint32_t pending = __ballot_sync(0xffffffffu, valid);
+            while (pending) {
+                const int leader = __ffs(pending) - 1;
+                const int vl = __shfl_sync(0xffffffffu, v, leader);
+                const uint32_t grp = __ballot_sync(0xffffffffu, valid && v == vl);
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    const float x = warp_sum(((grp >> lane) & 1u) ? tw[k] : 0.f);
+                    if (lane == leader) atomicAdd(&s_tw[vl * 6 + k], x);
+                }
+                pending &= ~grp;
+            }
+        }
+    }
+    if (a.grad_twist) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < a.n_views * 6; t += blockDim.x)
+            if (s_tw[t] != 0.f) atomicAdd(&a.grad_twist[t], s_tw[t]);
+    }
+}
+
+// a7, row part, and a8 when fused.
 // One thread per Gaussian, kProjBwdThreads per block.  The 3K SH coefficients and their
 // gradient sums live in shared memory (one column per thread) rather than registers, which
 // keeps the kernel within 128 registers at SH degree 3.
@@ -119,105 +281,31 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) project_bwd_kernel(Project
     for (int k = 0; k < 3 * K; k++) sh[k * kProjBwdThreads] = live ? __ldg(a.sh + k * n + ii) : 0.f;
     Cov3 cv;
     cov3_forward(q, ls, cv);
-    const Opts op = a.op;
     float g_mu[3] = {0, 0, 0};
     float gS[6] = {0, 0, 0, 0, 0, 0};   // dL/dSigma as a symmetric matrix: xx xy xz yy yz zz
     float g_o = 0.f;
     const int lane = threadIdx.x & 31;
-    for (int v = 0; v < a.n_views; v++) {
+    // Each lane walks its own views in increasing order, so the warp iterates as often as its
+    // busiest Gaussian has views, not once per view any of its Gaussians has.
+    uint64_t todo = vmask;
+    while (__any_sync(0xffffffffu, todo != 0)) {
+        const bool act = todo != 0;
+        const int v = act ? __ffsll((long long)todo) - 1 : 0;
+        todo &= todo - 1;
         const View& V = a.views[v];
         const int64_t idx = (int64_t)v * n + ii;
-        const bool act = (vmask >> v) & 1ull;
         float tw[6] = {0, 0, 0, 0, 0, 0};
         if (act) {
-            ProjV P;
-            project_view(mu, cv, logit, V, op, P);
+            // geometry gradients of the entry (entry part), opacity and colour sums
+            const float4* geo = a.geo2d + 3 * idx;
+            const float4 q0 = geo[0], q1 = geo[1], q2 = geo[2];
             const float4* gr = a.grad2d + 3 * idx;
-            const float4 r0 = gr[0], r1 = gr[1], r2 = gr[2];
+            const float o_sum = reinterpret_cast<const float*>(gr + 1)[1];
+            const float4 r2 = gr[2];
+            g_mu[0] += q0.x; g_mu[1] += q0.y; g_mu[2] += q0.z;
+            gS[0] += q0.w; gS[1] += q1.x; gS[2] += q1.y; gS[3] += q1.z; gS[4] += q1.w; gS[5] += q2.x;
+            g_o += o_sum;
             const float* W = V.R;
-            // screen-space gradients
-            const float gu = -2.f * kLn2 * r0.x, gv = -2.f * kLn2 * r0.y;
-            const float gA = -0.5f * r0.z, gB = -r0.w, gC = -0.5f * r1.x;
-            g_o += r1.y;
-            float g_pc[3] = {0.f, 0.f, r1.z};
-            // conic = inverse(cov), cov = [[a, b], [b, c]]
-            const float pa = P.a, pb = P.b, pc = P.c;
-            const float id2 = 1.0f / (P.det * P.det);
-            const float ga = (-pc * pc * gA + pb * pc * gB - pb * pb * gC) * id2;
-            const float gb = (2.f * pb * pc * gA - (pa * pc + pb * pb) * gB + 2.f * pa * pb * gC) * id2;
-            const float gc = (-pb * pb * gA + pa * pb * gB - pa * pa * gC) * id2;
-            const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
-            // T Sigma
-            const float* S = cv.S;
-            float TS[6];
-#pragma unroll
-            for (int r = 0; r < 2; r++) {
-                const float* t = &P.T[3 * r];
-                TS[3 * r + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
-                TS[3 * r + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
-                TS[3 * r + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
-            }
-            // g_T = 2 G T Sigma
-            float gT[6];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                gT[k] = 2.f * (G00 * TS[k] + G01 * TS[3 + k]);
-                gT[3 + k] = 2.f * (G01 * TS[k] + G11 * TS[3 + k]);
-            }
-            // g_Sigma += T^T G T
-            {
-                float GT[6];
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    GT[k] = G00 * P.T[k] + G01 * P.T[3 + k];
-                    GT[3 + k] = G01 * P.T[k] + G11 * P.T[3 + k];
-                }
-                gS[0] += P.T[0] * GT[0] + P.T[3] * GT[3];
-                gS[1] += P.T[0] * GT[1] + P.T[3] * GT[4];
-                gS[2] += P.T[0] * GT[2] + P.T[3] * GT[5];
-                gS[3] += P.T[1] * GT[1] + P.T[4] * GT[4];
-                gS[4] += P.T[1] * GT[2] + P.T[4] * GT[5];
-                gS[5] += P.T[2] * GT[2] + P.T[5] * GT[5];
-            }
-            // T = J W : g_J = g_T W^T, g_W = J^T g_T
-            const float gJ00 = gT[0] * W[0] + gT[1] * W[1] + gT[2] * W[2];
-            const float gJ02 = gT[0] * W[6] + gT[1] * W[7] + gT[2] * W[8];
-            const float gJ11 = gT[3] * W[3] + gT[4] * W[4] + gT[5] * W[5];
-            const float gJ12 = gT[3] * W[6] + gT[4] * W[7] + gT[5] * W[8];
-            float gW[9];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                gW[k] = P.J00 * gT[k];
-                gW[3 + k] = P.J11 * gT[3 + k];
-                gW[6 + k] = P.J02 * gT[k] + P.J12 * gT[3 + k];
-            }
-            const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
-            const float iz = 1.0f / z, iz2 = iz * iz;
-            const float fx = V.fx, fy = V.fy;
-            const float dtx_dx = P.clx ? 0.f : iz, dtx_dz = P.clx ? 0.f : -x * iz2;
-            const float dty_dy = P.cly ? 0.f : iz, dty_dz = P.cly ? 0.f : -y * iz2;
-            g_pc[2] += -gJ00 * fx * iz2 - gJ11 * fy * iz2;
-            g_pc[2] += gJ02 * (fx * P.tx * iz2 - fx * iz * dtx_dz);
-            g_pc[0] += gJ02 * (-fx * iz * dtx_dx);
-            g_pc[2] += gJ12 * (fy * P.ty * iz2 - fy * iz * dty_dz);
-            g_pc[1] += gJ12 * (-fy * iz * dty_dy);
-            g_pc[0] += gu * fx * iz;
-            g_pc[1] += gv * fy * iz;
-            g_pc[2] += -(gu * fx * x + gv * fy * y) * iz2;
-#pragma unroll
-            for (int k = 0; k < 3; k++) g_mu[k] += W[k] * g_pc[0] + W[3 + k] * g_pc[1] + W[6 + k] * g_pc[2];
-            // pose: rho <- g_pc, phi <- p_c x g_pc + vee(g_W W^T)
-            tw[0] = g_pc[0]; tw[1] = g_pc[1]; tw[2] = g_pc[2];
-            tw[3] = y * g_pc[2] - z * g_pc[1];
-            tw[4] = z * g_pc[0] - x * g_pc[2];
-            tw[5] = x * g_pc[1] - y * g_pc[0];
-            {
-                // A = g_W W^T; need A21 - A12, A02 - A20, A10 - A01
-                auto Arc = [&](int r, int c) { return gW[3 * r] * W[3 * c] + gW[3 * r + 1] * W[3 * c + 1] + gW[3 * r + 2] * W[3 * c + 2]; };
-                tw[3] += Arc(2, 1) - Arc(1, 2);
-                tw[4] += Arc(0, 2) - Arc(2, 0);
-                tw[5] += Arc(1, 0) - Arc(0, 1);
-            }
             // SH colour: rgb_c = max(0, sum_k sh_kc Y_k(dir) + 0.5), dir = (mu - cw)/|mu - cw|
             float d[3] = {mu[0] - V.cw[0], mu[1] - V.cw[1], mu[2] - V.cw[2]};
             const float rn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -252,13 +340,20 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) project_bwd_kernel(Project
                 for (int r = 0; r < 3; r++) tw[r] += W[3 * r] * gd[0] + W[3 * r + 1] * gd[1] + W[3 * r + 2] * gd[2];
             }
         }
-        if (a.grad_twist) {
-            if (__any_sync(0xffffffffu, act)) {
+        if (DEG > 0 && a.grad_twist) {
+            // the view-direction term moves only rho (the geometric twist came from the entry
+            // part): one warp sum per view present among the active lanes
+            uint32_t pending = __ballot_sync(0xffffffffu, act);
+            while (pending) {
+                const int leader = __ffs(pending) - 1;
+                const int vl = __shfl_sync(0xffffffffu, v, leader);
+                const uint32_t grp = __ballot_sync(0xffffffffu, act && v == vl);
 #pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    const float s = warp_sum(tw[k]);
-                    if (lane == 0) atomicAdd(&s_tw[v * 6 + k], s);
+                for (int k = 0; k < 3; k++) {
+                    const float x = warp_sum(((grp >> lane) & 1u) ? tw[k] : 0.f);
+                    if (lane == leader) atomicAdd(&s_tw[vl * 6 + k], x);
                 }
+                pending &= ~grp;
             }
         }
     }
@@ -290,8 +385,8 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) project_bwd_kernel(Project
         if constexpr (FUSED_ADAM) {
             // a8 on this row: the gradient goes straight into Adam (never stored)
             if (!a.update_mask || a.update_mask[i]) {
-                const float bc1 = a.step_dev ? a.step_dev->adam_bc1 : a.bc1;
-                const float bc2 = a.step_dev ? a.step_dev->adam_bc2 : a.bc2;
+                const float bc1 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc1 : a.bc1);   // inverse bias corrections
+                const float bc2 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc2 : a.bc2);
                 // Moments are loaded a group of planes at a time, all loads of a group before
                 // its stores, so that a row waits for a few memory round trips, not 11 + 3K.
                 {
@@ -403,6 +498,10 @@ static cudaError_t launch_project_bwd_t(const ProjectBwdArgs& a, int deg, cudaSt
 }
 
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st) {
+    // entry part (persistent grid over the device-side entry count), then the row part
+    project_bwd_entry_kernel<<<sort_grid() * 4, kEntryThreads, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     return a.fused_adam ? launch_project_bwd_t<true>(a, deg, st) : launch_project_bwd_t<false>(a, deg, st);
 }
 

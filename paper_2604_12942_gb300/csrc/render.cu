@@ -10,10 +10,12 @@
 
 namespace gs {
 
+// View of global tile gt: the number of views whose first tile is <= gt, minus one.  Every lane
+// of the warp tests one view (n_views <= 32), so the lookup is one parallel load.
 __device__ __forceinline__ int view_of_tile(const View* views, int n_views, int gt) {
-    int v = 0;
-    while (v + 1 < n_views && views[v + 1].tile_off <= gt) v++;
-    return v;
+    const int lane = threadIdx.x & 31;
+    const bool le = lane < n_views && views[lane].tile_off <= gt;
+    return __popc(__ballot_sync(0xffffffffu, le)) - 1;
 }
 
 // ----------------------------------------------------------------------------------------
@@ -200,9 +202,15 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
     __shared__ uint32_t s_mask[CHUNK];
     __shared__ uint16_t s_list[NW][CHUNK];   // per warp: the chunk's records that reach its region
     __shared__ double s_red[2][NW];
-    if (a.counters->status != 0) return;
+    __shared__ float s_tgt[4][NT];           // target r, g, b, depth of each thread's pixel
+    // (loads ordered so that the dependent chain order -> ranges / view -> ids -> records is
+    // as short as possible: CTAs are short and this latency is paid once per tile)
+    const uint32_t status = a.counters->status;
     const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
+    if (status != 0) return;
+    const uint2 rg = a.ranges[gt];
     const int v = view_of_tile(a.views, a.n_views, gt);
+    const int n = (int)(rg.y - rg.x);
     const View& V = a.views[v];
     const int lt = gt - V.tile_off;
     const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
@@ -216,8 +224,17 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
     bool done = !inside;
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
     uint32_t last = 0;
-    const uint2 rg = a.ranges[gt];
-    const int n = (int)(rg.y - rg.x);
+    // this pixel's targets, copied to shared memory now (cp.async, no registers held) so that
+    // the loss epilogue does not wait for them
+    if (inside && a.tgt_rgb) {
+        const int64_t P = (int64_t)V.W * V.H, p = (int64_t)y * V.W + x;
+        const float* t = a.tgt_rgb + 3 * V.pix_off;
+        cp_async4(&s_tgt[0][threadIdx.x], t + p);
+        cp_async4(&s_tgt[1][threadIdx.x], t + P + p);
+        cp_async4(&s_tgt[2][threadIdx.x], t + 2 * P + p);
+        if (a.tgt_depth) cp_async4(&s_tgt[3][threadIdx.x], a.tgt_depth + V.pix_off + p);
+    }
+    cp_async_commit();
     const float amin = a.op.alpha_min, amax = a.op.alpha_max, tmin = a.op.T_min;
     uint32_t n_eval = 0, n_add = 0, n_visit = 0;
     int b = 0;   // buffer holding the chunk being composited
@@ -342,18 +359,18 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
         a.n_contrib[g] = last;
         if (a.tgt_rgb) {
             const bool in = a.mask ? a.mask[g] != 0 : true;
+            const float tr = s_tgt[0][threadIdx.x], tgr = s_tgt[1][threadIdx.x], tbl = s_tgt[2][threadIdx.x];
             const float cm = (float)a.loss_counts[2 * v], cd = (float)a.loss_counts[2 * v + 1];
             const float inv_v = 1.0f / (float)a.n_views;
             const float krgb = (in && cm > 0.f) ? a.op.lambda_rgb * inv_v / cm : 0.f;
-            const float* t = a.tgt_rgb + 3 * V.pix_off;
-            const float r0 = o0 - t[p], r1 = o1 - t[P + p], r2 = o2 - t[2 * P + p];
+            const float r0 = o0 - tr, r1 = o1 - tgr, r2 = o2 - tbl;
             float* dl = a.dl_drgb + 3 * V.pix_off;
             dl[p] = krgb * (float)((r0 > 0.f) - (r0 < 0.f));
             dl[P + p] = krgb * (float)((r1 > 0.f) - (r1 < 0.f));
             dl[2 * P + p] = krgb * (float)((r2 > 0.f) - (r2 < 0.f));
             if (in) lr += fabsf(r0) + fabsf(r1) + fabsf(r2);
             if (a.dl_ddepth) {
-                const float td = a.tgt_depth ? a.tgt_depth[g] : 0.f;
+                const float td = a.tgt_depth ? s_tgt[3][threadIdx.x] : 0.f;
                 const bool ind = in && td > 0.f;
                 const float kd = (ind && cd > 0.f) ? a.op.lambda_depth * inv_v / cd : 0.f;
                 const float rd = dep - td;
@@ -453,15 +470,16 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
     __shared__ uint32_t s_id[2][CHUNK];
     __shared__ uint32_t s_mask[2][CHUNK];
     __shared__ uint32_t s_max;
-    if (a.counters->status != 0) return;
+    const uint32_t status = a.counters->status;
     const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
+    if (status != 0) return;
+    const uint2 rg = a.ranges[gt];
     const int v = view_of_tile(a.views, a.n_views, gt);
     const View& V = a.views[v];
     const int lt = gt - V.tile_off;
     const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int rx0 = tx * TILE + (w % TM::WX) * 8, ry0 = ty * TILE + (w / TM::WX) * TM::RH;
-    const uint2 rg = a.ranges[gt];
     const float amin = a.op.alpha_min, amax = a.op.alpha_max;
     uint32_t n_eval = 0, n_add = 0, n_visit = 0;
     float px[kPPT], py[kPPT], T[kPPT], S[kPPT], gc0[kPPT], gc1[kPPT], gc2[kPPT], gd[kPPT];
@@ -490,12 +508,17 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
         S[q] = (gc0[q] * a.op.bg0 + gc1[q] * a.op.bg1 + gc2[q] * a.op.bg2) * T[q];
         mylast = max(mylast, last[q]);
     }
-    if (threadIdx.x == 0) s_max = 0;
-    __syncthreads();
     const uint32_t wtop = __reduce_max_sync(0xffffffffu, mylast);
-    if (lane == 0 && wtop) atomicMax(&s_max, wtop);
-    __syncthreads();
-    const int top_all = (int)s_max;
+    int top_all;
+    if constexpr (NT == 32) {
+        top_all = (int)wtop;   // one warp: no block reduction
+    } else {
+        if (threadIdx.x == 0) s_max = 0;
+        __syncthreads();
+        if (lane == 0 && wtop) atomicMax(&s_max, wtop);
+        __syncthreads();
+        top_all = (int)s_max;
+    }
     // Chunk c covers list positions [max(0, top_all - (c + 1) CHUNK), top_all - c CHUNK).
     // Pipeline: the ids and masks of chunk c + 2 are loaded into registers and the records of
     // chunk c + 1 are copied asynchronously while chunk c is composited.
