@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kScanThreads) pair_offsets_kernel(BinArgs a) {
     }
 }
 
-// Emission balanced over the output: a block takes chunks of kEmitChunk consecutive pairs,
+// Emission balanced over the output: a block takes a chunk of kEmitChunk consecutive pairs,
 // stages the entries they come from (at most kEmitChunk + 1) with their tile rectangles in
 // shared memory, and each thread writes pairs p0 + tid, p0 + tid + 256, ... after a binary
 // search for its entry.  Stores are contiguous across the block; a few entries with very
@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
     const uint64_t P = a.counters->n_pairs;
     const int64_t E = (int64_t)a.counters->n_entries;
     const uint64_t n_chunks = (P + kEmitChunk - 1) / kEmitChunk;
+    // one chunk per block (the grid covers the pair capacity; blocks past the last chunk exit)
     for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
         const uint64_t p0 = c * kEmitChunk, p1 = p0 + kEmitChunk < P ? p0 + kEmitChunk : P;
         const int64_t e0 = a.chunk_first[c];
@@ -249,7 +250,9 @@ cudaError_t launch_emit(const BinArgs& a, cudaStream_t st) {
     scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(a.scan_tmp, nb, &a.counters->n_pairs, nullptr, a.counters,
                                                    a.max_pairs);
     if (nb > 0) pair_offsets_kernel<<<nb, kScanThreads, 0, st>>>(a);
-    pair_emit_kernel<<<sort_grid() * 2, kEmitThreads, 0, st>>>(a);
+    const int64_t emit_blocks = (a.max_pairs + kEmitChunk - 1) / kEmitChunk;
+    pair_emit_kernel<<<(unsigned)(emit_blocks > 0 ? (emit_blocks < (1 << 30) ? emit_blocks : (1 << 30)) : 1), kEmitThreads,
+                       0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -347,11 +350,16 @@ __global__ void __launch_bounds__(256) sort_scan_kernel(SortArgs a) {
     if (lane == 0) a.digit_tot[d] = carry;
 }
 
+// Chunk position k is stored at k + k / 32: ranked keys of one warp step often land at a
+// fixed stride (consecutive digits with similar counts), which without the skew would hit the
+// same few shared-memory banks.
+__device__ __forceinline__ int skew(int k) { return k + (k >> 5); }
+
 template <typename K, int BITS>
 struct SortSmem {
     static constexpr int BINS = 1 << BITS;
-    K keys[kSortChunk];
-    uint32_t vals[kSortChunk];
+    K keys[kSortChunk + kSortChunk / 32];
+    uint32_t vals[kSortChunk + kSortChunk / 32];
     uint32_t wcnt[kSortWarps][BINS];
     uint32_t run[BINS];
     uint32_t tot[BINS];
@@ -477,18 +485,18 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
             const int item = w * kItemsPerWarp + j * 32 + lane;
             if (item < m) {
                 const uint32_t d = digit_of<BITS>(key[j], shift);
-                const uint32_t pos = S.cstart[d] + S.wcnt[w][d] + rank[j];
+                const int pos = skew((int)(S.cstart[d] + S.wcnt[w][d] + rank[j]));
                 S.keys[pos] = key[j];
                 S.vals[pos] = val[j];
             }
         }
         __syncthreads();
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
-            const K kk = S.keys[k];
+            const K kk = S.keys[skew(k)];
             const uint32_t d = digit_of<BITS>(kk, shift);
             const int64_t g = (int64_t)S.run[d] + (k - (int)S.cstart[d]);
             kout[g] = kk;
-            vout[g] = S.vals[k];
+            vout[g] = S.vals[skew(k)];
         }
         __syncthreads();
 #pragma unroll
@@ -546,13 +554,38 @@ cudaError_t launch_sort64(const SortArgs& a, int n_passes, const int* shifts, cu
 // ----------------------------------------------------------------------------------------
 // Tile ranges.
 // ----------------------------------------------------------------------------------------
+// Each thread takes 4 consecutive sorted tile ids (one 16-byte load) and the id before them
+// (from the previous lane, or loaded by lane 0); a start boundary j (key[j] != key[j - 1])
+// opens key[j]'s range and closes key[j - 1]'s.
 __global__ void __launch_bounds__(256) ranges_kernel(RangeArgs a) {
     if (a.counters->status != 0) return;
     const int64_t P = (int64_t)a.counters->n_pairs;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = a.keys[i];
-        if (i == 0 || a.keys[i - 1] != t) a.ranges[t].x = (uint32_t)i;
-        if (i == P - 1 || a.keys[i + 1] != t) a.ranges[t].y = (uint32_t)(i + 1);
+    const int64_t groups = (P + 3) / 4;
+    const int lane = threadIdx.x & 31;
+    for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < groups; g0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = g0 + threadIdx.x;
+        const int64_t i0 = 4 * g;
+        uint32_t k[4] = {0u, 0u, 0u, 0u};
+        if (i0 + 3 < P) {
+            const uint4 q = *reinterpret_cast<const uint4*>(a.keys + i0);
+            k[0] = q.x; k[1] = q.y; k[2] = q.z; k[3] = q.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) k[j] = i0 + j < P ? a.keys[i0 + j] : 0u;
+        }
+        uint32_t prev = __shfl_up_sync(0xffffffffu, k[3], 1);
+        if (lane == 0 && i0 > 0 && i0 < P) prev = a.keys[i0 - 1];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t i = i0 + j;
+            if (i >= P) break;
+            const uint32_t before = j == 0 ? prev : k[j - 1];
+            if (i == 0 || before != k[j]) {
+                a.ranges[k[j]].x = (uint32_t)i;
+                if (i > 0) a.ranges[before].y = (uint32_t)i;
+            }
+            if (i == P - 1) a.ranges[k[j]].y = (uint32_t)P;
+        }
     }
 }
 
