@@ -350,6 +350,11 @@ __global__ void __launch_bounds__(256) sort_scan_kernel(SortArgs a) {
     if (lane == 0) a.digit_tot[d] = carry;
 }
 
+// Digit-indexed shared arrays are stored at dix(d) = d with its low 5 bits XORed with the next
+// ones: digits 32 m apart (tile ids one or more tile rows apart, which a warp step often holds)
+// then fall in different banks.  A bijection on [0, 2^BITS).
+__device__ __forceinline__ int dix(uint32_t d) { return (int)(d ^ ((d >> 5) & 31u)); }
+
 // Chunk position k is stored at k + k / 32: ranked keys of one warp step often land at a
 // fixed stride (consecutive digits with similar counts), which without the skew would hit the
 // same few shared-memory banks.
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
         for (int q = 0; q < DPT; q++) x[q] = a.digit_tot[d0 + q];
         block_exclusive_scan_dpt<DPT>(x, ex, S.scan_w);
 #pragma unroll
-        for (int q = 0; q < DPT; q++) S.run[d0 + q] = ex[q] + a.hist[(int64_t)(d0 + q) * a.grid + blockIdx.x];
+        for (int q = 0; q < DPT; q++) S.run[dix(d0 + q)] = ex[q] + a.hist[(int64_t)(d0 + q) * a.grid + blockIdx.x];
     }
     const uint32_t ltm = lanemask_lt();
     for (int64_t base = lo; base < hi; base += kSortChunk) {
@@ -453,9 +458,9 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
             const uint32_t d = valid ? digit_of<BITS>(key[j], shift) : (uint32_t)BINS;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             uint32_t r = __popc(peers & ltm);
-            if (valid) r += S.wcnt[w][d];
+            if (valid) r += S.wcnt[w][dix(d)];
             __syncwarp();
-            if (valid && lane == 31 - __clz(peers)) S.wcnt[w][d] += __popc(peers);
+            if (valid && lane == 31 - __clz(peers)) S.wcnt[w][dix(d)] += __popc(peers);
             __syncwarp();
             rank[j] = r;
         }
@@ -468,16 +473,16 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
                 uint32_t run = 0;
 #pragma unroll
                 for (int ww = 0; ww < kSortWarps; ww++) {
-                    const uint32_t c = S.wcnt[ww][d0 + q];
-                    S.wcnt[ww][d0 + q] = run;
+                    const uint32_t c = S.wcnt[ww][dix(d0 + q)];
+                    S.wcnt[ww][dix(d0 + q)] = run;
                     run += c;
                 }
                 tot[q] = run;
-                S.tot[d0 + q] = run;
+                S.tot[dix(d0 + q)] = run;
             }
             block_exclusive_scan_dpt<DPT>(tot, cs, S.scan_w);
 #pragma unroll
-            for (int q = 0; q < DPT; q++) S.cstart[d0 + q] = cs[q];
+            for (int q = 0; q < DPT; q++) S.cstart[dix(d0 + q)] = cs[q];
         }
         __syncthreads();
 #pragma unroll
@@ -485,7 +490,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
             const int item = w * kItemsPerWarp + j * 32 + lane;
             if (item < m) {
                 const uint32_t d = digit_of<BITS>(key[j], shift);
-                const int pos = skew((int)(S.cstart[d] + S.wcnt[w][d] + rank[j]));
+                const int pos = skew((int)(S.cstart[dix(d)] + S.wcnt[w][dix(d)] + rank[j]));
                 S.keys[pos] = key[j];
                 S.vals[pos] = val[j];
             }
@@ -494,13 +499,13 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
             const K kk = S.keys[skew(k)];
             const uint32_t d = digit_of<BITS>(kk, shift);
-            const int64_t g = (int64_t)S.run[d] + (k - (int)S.cstart[d]);
+            const int64_t g = (int64_t)S.run[dix(d)] + (k - (int)S.cstart[dix(d)]);
             kout[g] = kk;
             vout[g] = S.vals[skew(k)];
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < DPT; q++) S.run[d0 + q] += S.tot[d0 + q];
+        for (int q = 0; q < DPT; q++) S.run[dix(d0 + q)] += S.tot[dix(d0 + q)];
     }
 }
 

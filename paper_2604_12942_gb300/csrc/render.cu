@@ -238,24 +238,26 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
     const float amin = a.op.alpha_min, amax = a.op.alpha_max, tmin = a.op.T_min;
     uint32_t n_eval = 0, n_add = 0, n_visit = 0;
     int b = 0;   // buffer holding the chunk being composited
-    // composite one fragment with opacity alpha of chunk record k (front to back)
+    // composite one fragment with opacity alpha of chunk record k (front to back), branch-free:
+    // a fragment that is skipped (alpha < alpha_min), stops the pixel (T (1 - alpha) < T_min)
+    // or comes after the stop adds exact zeros
     auto add = [&](float alpha, int k, int base) {
-        n_eval++;
-        if (alpha < amin) return;
+        const bool act = !done;
+        const bool pass = act && !(alpha < amin);
         const float test_T = T * (1.f - alpha);
-        if (test_T < tmin) {
-            done = true;
-            return;
-        }
-        const float wgt = alpha * T;
+        const bool stop = pass && test_T < tmin;
+        const bool c = pass && !stop;
+        n_eval += act;
+        n_add += c;
+        done = done || stop;
+        const float wgt = c ? alpha * T : 0.f;
         const float4 r2 = s_rec[b][k][2];
         c0 = fmaf(wgt, r2.x, c0);
         c1 = fmaf(wgt, r2.y, c1);
         c2 = fmaf(wgt, r2.z, c2);
         dep = fmaf(wgt, s_rec[b][k][0].z, dep);
-        T = test_T;
-        last = (uint32_t)(base + k + 1);
-        n_add++;
+        T = c ? test_T : T;
+        last = c ? (uint32_t)(base + k + 1) : last;
     };
     auto alpha_of = [&](int k) {
         const float4 r0 = s_rec[b][k][0], r1 = s_rec[b][k][1];
@@ -325,13 +327,13 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
             // two records per iteration: their alphas are independent, the compositing is not
             int t = 0;
             for (; t + 1 < cnt; t += 2) {
+                if (__all_sync(0xffffffffu, done)) break;
                 const int ka = s_list[w][t], kb = s_list[w][t + 1];
-                if (done) continue;
                 const float alpha_a = alpha_of(ka), alpha_b = alpha_of(kb);
                 add(alpha_a, ka, base);
-                if (!done) add(alpha_b, kb, base);
+                add(alpha_b, kb, base);
             }
-            if (t < cnt && !done) {
+            if (t < cnt) {
                 const int k = s_list[w][t];
                 add(alpha_of(k), k, base);
             }
@@ -469,6 +471,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
     __shared__ float4 s_rec[2][CHUNK][3];   // raw projected records (u, v, z, o), (a, b, c, rx), (r, g, b, ry)
     __shared__ uint32_t s_id[2][CHUNK];
     __shared__ uint32_t s_mask[2][CHUNK];
+    __shared__ uint16_t s_list[NT / 32][CHUNK];   // per warp: the chunk's records that reach its region
     __shared__ uint32_t s_max;
     const uint32_t status = a.counters->status;
     const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
@@ -562,11 +565,24 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
         fetch_ids(c + 2);
         cp_async_wait_prior();   // chunk c has landed (chunk c + 1 may still be in flight)
         __syncthreads();
-        const int jstart = min(top, (int)wtop) - 1;
-        for (int j = jstart; j >= lo; j--) {
-            const int k = j - lo;
-            if (!((s_mask[b][k] >> w) & 1u)) continue;
-            n_visit++;
+        uint32_t ltm;
+        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(ltm));
+        // this warp's records of the chunk, back to front: positions below its pixels' last
+        // added fragment whose alpha >= alpha_min region reaches the warp's pixels
+        const int kstart = min(top, (int)wtop) - 1 - lo;
+        int cnt = 0;
+        for (int k0 = kstart; k0 >= 0; k0 -= 32) {
+            const int kk = k0 - lane;
+            const bool hit = kk >= 0 && ((s_mask[b][kk] >> w) & 1u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) s_list[w][cnt + __popc(bal & ltm)] = (uint16_t)kk;
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        n_visit += cnt;
+        for (int t = 0; t < cnt; t++) {
+            const int k = s_list[w][t];
+            const int j = lo + k;
             const float4 r0 = s_rec[b][k][0], r1 = s_rec[b][k][1];
             const float2 bx = make_float2(r0.x, r0.y);
             const float4 co = make_float4(r1.x, r1.y, r1.z, r0.w);
@@ -574,40 +590,44 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
 #pragma unroll
             for (int q = 0; q < 10; q++) val[q] = 0.f;
             bool contrib = false;
+            const float4 r2 = s_rec[b][k][2];
+            const float4 cz = make_float4(r2.x, r2.y, r2.z, r0.z);
+            // Branch-free per pixel: every lane computes the fragment and commits it with
+            // selects (adding exact zeros where it does not contribute), so the warp runs one
+            // straight path instead of re-converging around per-pixel branches.
 #pragma unroll
             for (int q = 0; q < kPPT; q++) {
-                if ((uint32_t)j >= last[q]) continue;
+                const bool live = (uint32_t)j < last[q];
                 const float dx = px[q] - bx.x, dy = py[q] - bx.y;
                 const FragE fe = frag_exponent(dx, dy, co.x, co.y, co.z);
                 const float G = ex2_approx(fe.e);
                 const float a0 = co.w * G;
                 const float alpha = fminf(amax, a0);
-                n_eval++;
-                if (alpha < amin) continue;
-                contrib = true;
-                n_add++;
+                const bool c = live && !(alpha < amin);
+                n_eval += live;
+                n_add += c;
+                contrib |= c;
                 const float rom = rcp_approx(1.f - alpha);
-                T[q] = T[q] * rom;
-                const float wgt = alpha * T[q];
-                const float4 r2 = s_rec[b][k][2];
-                const float4 cz = make_float4(r2.x, r2.y, r2.z, r0.z);
+                const float Tn = T[q] * rom;
+                const float wgt = alpha * Tn;
                 const float gcz = gc0[q] * cz.x + gc1[q] * cz.y + gc2[q] * cz.z + gd[q] * cz.w;
-                const float dLda = T[q] * gcz - S[q] * rom;
-                S[q] = fmaf(gcz, wgt, S[q]);
-                val[7] = fmaf(gc0[q], wgt, val[7]);
-                val[8] = fmaf(gc1[q], wgt, val[8]);
-                val[9] = fmaf(gc2[q], wgt, val[9]);
-                val[6] = fmaf(gd[q], wgt, val[6]);
-                if (a0 < amax) {
-                    const float h = dLda * a0;
-                    const float hdx = h * dx;
-                    val[0] = fmaf(h, fe.hx, val[0]);
-                    val[1] = fmaf(h, fe.hy, val[1]);
-                    val[2] = fmaf(hdx, dx, val[2]);
-                    val[3] = fmaf(hdx, dy, val[3]);
-                    val[4] = fmaf(h * dy, dy, val[4]);
-                    val[5] = fmaf(dLda, G, val[5]);
-                }
+                const float dLda = Tn * gcz - S[q] * rom;
+                S[q] = c ? fmaf(gcz, wgt, S[q]) : S[q];
+                T[q] = c ? Tn : T[q];
+                const float wc = c ? wgt : 0.f;
+                val[7] = fmaf(gc0[q], wc, val[7]);
+                val[8] = fmaf(gc1[q], wc, val[8]);
+                val[9] = fmaf(gc2[q], wc, val[9]);
+                val[6] = fmaf(gd[q], wc, val[6]);
+                const float gl = (c && a0 < amax) ? dLda : 0.f;   // the 0.99 clamp stops the gradient
+                const float h = gl * a0;
+                const float hdx = h * dx;
+                val[0] = fmaf(h, fe.hx, val[0]);
+                val[1] = fmaf(h, fe.hy, val[1]);
+                val[2] = fmaf(hdx, dx, val[2]);
+                val[3] = fmaf(hdx, dy, val[3]);
+                val[4] = fmaf(h * dy, dy, val[4]);
+                val[5] = fmaf(gl, G, val[5]);
             }
             const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
             if (cmask) {
