@@ -14,6 +14,7 @@ on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -28,12 +29,34 @@ sys.path.insert(0, ROOT)
 
 SIZES = [(640, 480), (640, 480), (960, 540), (960, 540), (1280, 720), (1280, 720), (1280, 1024), (1280, 1024)]
 METRIC = "fwd+bwd render Mpix/s and iters/s at 2M Gaussians; secs-to-PSNR learned vs plain"
+# DRAM bytes (read + write) per launch of the compositing kernels on this workload, from one
+# ncu capture of dram__bytes_read.sum / dram__bytes_write.sum (a one-pass metric set) of the
+# full 2M-Gaussian step; the command and figures are in profiles/launches_c3_2M_8views.md.
+# Keyed by (kernel, tile, chunk); the projection backward does not depend on the tile shape
+# (key tile = chunk = 0).  Once a kernel changes these must be captured again; a shape without an
+# entry reports null.
+NCU_TRAFFIC = {
+    ("render_bwd_kernel", 16, 256): 323_786_240 + 62_372_096,
+    ("render_fwd_kernel", 16, 256): 224_189_440 + 202_370_816,
+    ("project_bwd_entry_kernel", 0, 0): 157_859_584 + 51_326_720,
+    ("project_bwd_kernel", 0, 0): 1_195_727_872 + 861_909_248,
+}
+
+
+def stage_traffic(stage, tile, chunk):
+    """Captured DRAM bytes of one stage's kernels, or None when a kernel has no entry."""
+    ks = {"composite_bwd": [("render_bwd_kernel", tile, chunk)],
+          "render_fwd": [("render_fwd_kernel", tile, chunk)],
+          "project_bwd_adam": [("project_bwd_entry_kernel", 0, 0), ("project_bwd_kernel", 0, 0)]}.get(stage)
+    if not ks or any(k not in NCU_TRAFFIC for k in ks):
+        return None
+    return sum(NCU_TRAFFIC[k] for k in ks)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--n", type=int, default=2_000_000)
@@ -82,16 +105,25 @@ class Clocks:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}",
-                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "--query-gpu=timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            # the timed region starts only once the sampler is producing rows
+            t_end = time.time() + 5.0
+            while time.time() < t_end and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
+    def mark(self, which):
+        """Wall-clock bounds of the timed region (host time, same clock as nvidia-smi's)."""
+        setattr(self, which, datetime.datetime.now())
+
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.15)   # one more sample after the region
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -105,17 +137,22 @@ class Clocks:
         rows = []
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
-            if len(p) >= 9:
+            if len(p) >= 10:
                 try:
-                    rows.append((float(p[1]), float(p[2]), p[5:9]))
+                    ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f")
+                    rows.append((ts, float(p[2]), float(p[3]), p[6:10]))
                 except ValueError:
                     pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        t0, t1 = getattr(self, "start", None), getattr(self, "stop", None)
+        inside = [r for r in rows if t0 is not None and t1 is not None and t0 <= r[0] <= t1]
+        # a region shorter than the sampling period may hold no row: take the row nearest to it
+        use = inside or [min(rows, key=lambda r: abs((r[0] - (t0 or r[0])).total_seconds()))]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r) if x.lower() == "active"})
-        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[i] for _, _, _, r in use for i, x in enumerate(r) if x.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(inside), "samples_total": len(rows)}
 
 
 def peaks():
@@ -160,11 +197,15 @@ def oracle_sample(sc, cams, targets, crop=(64, 48)):
 
 
 def cpu_baseline_line(sc, cams, targets, budget_s=20.0):
-    dt, px, thr = oracle_sample(sc, cams, targets, (32, 24))
-    # scale the crop so the sample takes about budget_s
-    per_px = dt / px
-    side = int(max(32, min(256, math.sqrt(max(1.0, budget_s / per_px) * 4 / 3))))
-    w, h = side, max(24, side * 3 // 4)
+    # two small samples give the fixed cost (projecting every Gaussian, Adam over every
+    # parameter) and the cost per pixel; the crop is then sized for about budget_s
+    dt1, px1, thr = oracle_sample(sc, cams, targets, (32, 24))
+    dt2, px2, thr = oracle_sample(sc, cams, targets, (64, 48))
+    per_px = max((dt2 - dt1) / (px2 - px1), 1e-9)
+    fixed = max(dt1 - per_px * px1, 0.0)
+    want_px = max(px2, (budget_s - fixed) / per_px)
+    side = int(max(64, min(cams[0]["width"], math.sqrt(want_px * 4 / 3))))
+    w, h = side, min(cams[0]["height"], max(48, side * 3 // 4))
     dt, px, thr = oracle_sample(sc, cams, targets, (w, h))
     return {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": thr, "kind": "oracle",
             "sample": f"{w}x{h} crop of view 0 (1280-wide class) with all {sc.n} Gaussians projected, "
@@ -250,11 +291,13 @@ def run_gpu(args, rank, world):
     with Clocks(dev.index) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        clk.mark("start")
         t0.record(st)
         for _ in range(args.steps):
             step.replay()
         t1.record(st)
         torch.cuda.synchronize()
+        clk.mark("stop")
     if world > 1:
         dist.barrier()
     total_ms = t0.elapsed_time(t1)
@@ -451,11 +494,13 @@ def main():
     stage = r["stage_ms"]
     dom = max(stage, key=stage.get)
     table = roofline_table(stage, r["work"], pk, pk_kind)
+    for k in table:
+        table[k]["traffic"] = stage_traffic(k, args.tile, args.chunk)
     roof = dict(table[dom])
     roof.update({"kernel": {"composite_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel",
                             "project_bwd_adam": "project_bwd_kernel (fused Adam)", "project": "project_kernel",
                             "bin_sort": "scan/emit/radix/ranges kernels"}[dom],
-                 "traffic": None,
+                 "traffic": stage_traffic(dom, args.tile, args.chunk),
                  "peak_kind": (pk_kind + " HBM copy") if roof["bound"] == "hbm" else
                  "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock " + str(pk.get("sm_max_mhz", 2070.0)) + " MHz"})
     line = {

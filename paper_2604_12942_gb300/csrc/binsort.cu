@@ -193,22 +193,28 @@ __global__ void __launch_bounds__(kScanThreads) pair_offsets_kernel(BinArgs a) {
 
 // Emission balanced over the output: a block takes a chunk of kEmitChunk consecutive pairs,
 // stages the entries they come from (at most kEmitChunk + 1) with their tile rectangles in
-// shared memory, and each thread writes pairs p0 + tid, p0 + tid + 256, ... after a binary
-// search for its entry.  Stores are contiguous across the block; a few entries with very
-// many tiles no longer serialise on one warp.
+// shared memory, marks the slot where each entry starts, and finds every slot's entry with a
+// running maximum over the chunk.  A few entries
+// with very many tiles no longer serialise on one warp.
 __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
+    static_assert(kEmitChunk == 8 * kEmitThreads, "each thread owns 8 consecutive slots of the chunk");
     __shared__ uint32_t s_off[kEmitChunk + 1], s_row0[kEmitChunk + 1], s_id[kEmitChunk + 1];
     __shared__ uint16_t s_x0[kEmitChunk + 1], s_wx[kEmitChunk + 1], s_tx[kEmitChunk + 1];
+    __shared__ __align__(16) uint16_t s_own[kEmitChunk];   // slot -> local entry index
+    __shared__ uint32_t s_wmax[kEmitThreads / 32];
     if (a.counters->status != 0) return;
     const uint64_t P = a.counters->n_pairs;
     const int64_t E = (int64_t)a.counters->n_entries;
     const uint64_t n_chunks = (P + kEmitChunk - 1) / kEmitChunk;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // one chunk per block (the grid covers the pair capacity; blocks past the last chunk exit)
     for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
         const uint64_t p0 = c * kEmitChunk, p1 = p0 + kEmitChunk < P ? p0 + kEmitChunk : P;
         const int64_t e0 = a.chunk_first[c];
         const int64_t e1 = c + 1 < n_chunks ? (int64_t)a.chunk_first[c + 1] : E - 1;
         const int ne = (int)(e1 - e0 + 1);   // <= kEmitChunk + 1: every entry has >= 1 pair
+        for (int i = threadIdx.x; i < kEmitChunk; i += blockDim.x) s_own[i] = 0;
+        __syncthreads();
         for (int j = threadIdx.x; j < ne; j += blockDim.x) {
             const int64_t e = e0 + j;
             const uint32_t idx = a.sorted_evals[e];
@@ -219,25 +225,53 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
             int xa, xb, ya, yb;
             tile_span(r0.x, rx, a.tile, V.tiles_x, xa, xb);
             tile_span(r0.y, ry, a.tile, V.tiles_y, ya, yb);
-            s_off[j] = a.poff[e];
+            const uint32_t off = a.poff[e];
+            s_off[j] = off;
             s_row0[j] = (uint32_t)(V.tile_off + ya * V.tiles_x);
             s_id[j] = idx;
             s_x0[j] = (uint16_t)xa;
             s_wx[j] = (uint16_t)(xb - xa + 1);
             s_tx[j] = (uint16_t)V.tiles_x;
+            // the entry's first pair slot in this chunk (entry 0 starts at or before p0)
+            if (j > 0 && off < p1) s_own[off - p0] = (uint16_t)j;
         }
         __syncthreads();
-        for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-            const uint32_t pp = (uint32_t)p;
-            int lo = 0, hi = ne - 1;   // last j with s_off[j] <= p
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= pp) lo = mid; else hi = mid - 1;
+        // slot owner = the last entry starting at or before the slot: a running maximum over
+        // the chunk (8 slots per thread, then warp and block maxima of the thread maxima)
+        uint32_t own[8], mx = 0;
+        {
+            const uint4 q = *reinterpret_cast<const uint4*>(s_own + 8 * threadIdx.x);
+            const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                mx = max(mx, wd[h] & 0xFFFFu);
+                own[2 * h] = mx;
+                mx = max(mx, wd[h] >> 16);
+                own[2 * h + 1] = mx;
             }
-            const uint32_t kk = pp - s_off[lo], wx = s_wx[lo];
+        }
+        uint32_t inc = mx;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc = max(inc, y);
+        }
+        if (lane == 31) s_wmax[w] = inc;
+        uint32_t before = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) before = 0;
+        __syncthreads();
+        for (int ww = 0; ww < w; ww++) before = max(before, s_wmax[ww]);
+        __syncthreads();   // every thread has read its slots
+#pragma unroll
+        for (int h = 0; h < 8; h++) s_own[8 * threadIdx.x + h] = (uint16_t)max(before, own[h]);
+        __syncthreads();
+        // coalesced writes: thread t writes slots t, t + 256, ...
+        for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const uint32_t j = s_own[p - p0];
+            const uint32_t kk = (uint32_t)p - s_off[j], wx = s_wx[j];
             const uint32_t ty = kk / wx, tx = kk - ty * wx;
-            a.pkeys[p] = s_row0[lo] + ty * (uint32_t)s_tx[lo] + (uint32_t)s_x0[lo] + tx;
-            a.pvals[p] = s_id[lo];
+            a.pkeys[p] = s_row0[j] + ty * (uint32_t)s_tx[j] + (uint32_t)s_x0[j] + tx;
+            a.pvals[p] = s_id[j];
         }
         __syncthreads();
     }
