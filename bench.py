@@ -36,10 +36,10 @@ METRIC = "fwd+bwd render Mpix/s and iters/s at 2M Gaussians; secs-to-PSNR learne
 # (key tile = chunk = 0).  Once a kernel changes these must be captured again; a shape without an
 # entry reports null.
 NCU_TRAFFIC = {
-    ("render_bwd_kernel", 16, 256): 323_786_240 + 62_372_096,
-    ("render_fwd_kernel", 16, 256): 224_189_440 + 202_370_816,
-    ("project_bwd_entry_kernel", 0, 0): 157_859_584 + 51_326_720,
-    ("project_bwd_kernel", 0, 0): 1_195_727_872 + 861_909_248,
+    ("render_bwd_kernel", 16, 256): 323_915_008 + 62_461_696,
+    ("render_fwd_kernel", 16, 256): 223_638_528 + 199_961_088,
+    ("project_bwd_entry_kernel", 0, 0): 159_465_984 + 52_321_024,
+    ("project_bwd_kernel", 0, 0): 1_195_707_648 + 861_927_680,
 }
 
 
@@ -307,6 +307,12 @@ def run_gpu(args, rank, world):
         staged(e)
     torch.cuda.synchronize()
     stage_ms = {s: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, s in enumerate(stages)}
+    # the work counts come from one more step with the compositing kernels' counters enabled
+    # (an option of the library, off in every timed step)
+    opts.count_fragments = 1
+    staged(evs[0])
+    torch.cuda.synchronize()
+    opts.count_fragments = 0
     cnt = step.ws.counters()
     work = dict(n=n, views=len(cams), pairs=int(cnt.n_pairs), frag_fwd_eval=int(cnt.frag_fwd_eval),
                 frag_fwd_add=int(cnt.frag_fwd_add), frag_bwd_eval=int(cnt.frag_bwd_eval),

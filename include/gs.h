@@ -95,6 +95,9 @@ typedef struct {
     float lambda_depth; /* default 0.1 */
     int32_t tile;       /* default 16 */
     int32_t chunk;      /* default 64 */
+    int32_t count_fragments; /* 1: the compositing kernels fill the frag_* and visits_* counters
+                                of gs_counters (a few percent slower); 0 (default): those
+                                counters stay 0 */
 } gs_render_opts;
 
 /* Byte offsets of the workspace regions (all 256-byte aligned) -- exposed so callers and
@@ -150,7 +153,8 @@ typedef struct {
     uint64_t adam_step;  /* Adam steps taken by gs_step / a captured graph */
     uint64_t frag_fwd_eval, frag_fwd_add;  /* (pixel, Gaussian) fragments tested / added by the */
     uint64_t frag_bwd_eval, frag_bwd_add;  /* forward and the backward compositing of the step  */
-    uint32_t visits_fwd, visits_bwd;       /* (record, warp) pairs the compositing loops walked */
+    uint32_t visits_fwd, visits_bwd;       /* (record, warp) pairs the compositing loops walked;
+                                              these six only with opts.count_fragments = 1 */
 } gs_counters;
 
 /* Inputs and outputs of one batched step (gs_step / gs_graph_create).  Device pointers,

@@ -30,7 +30,8 @@ class Gaussians(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("near_z", C.c_float), ("dilation", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("T_min", C.c_float), ("clamp_fov", C.c_float), ("bg", C.c_float * 3), ("lambda_rgb", C.c_float),
-                ("lambda_depth", C.c_float), ("tile", C.c_int32), ("chunk", C.c_int32)]
+                ("lambda_depth", C.c_float), ("tile", C.c_int32), ("chunk", C.c_int32),
+                ("count_fragments", C.c_int32)]
 
 
 class WsLayout(C.Structure):

@@ -170,6 +170,7 @@ static Opts to_opts(const gs_render_opts* o) {
     r.bg0 = o->bg[0]; r.bg1 = o->bg[1]; r.bg2 = o->bg[2];
     r.lambda_rgb = o->lambda_rgb; r.lambda_depth = o->lambda_depth;
     r.tile = o->tile; r.chunk = o->chunk;
+    r.count = o->count_fragments != 0;
     return r;
 }
 
@@ -541,6 +542,7 @@ void gs_default_opts(gs_render_opts* o) {
     o->lambda_depth = 0.1f;
     o->tile = 16;
     o->chunk = 64;
+    o->count_fragments = 0;
 }
 
 size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams, const gs_render_opts* opts,

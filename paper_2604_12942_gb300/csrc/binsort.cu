@@ -443,8 +443,11 @@ __device__ __forceinline__ void block_exclusive_scan_dpt(const uint32_t (&x)[DPT
     __syncthreads();
 }
 
+// resident downsweep blocks per SM (and the grid of every sort pass: this many per SM)
+constexpr int kSortBlocksPerSM = 3;
+
 template <typename K, int BITS>
-__global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArgs a, int in_buf, int shift) {
+__global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) sort_downsweep_kernel(SortArgs a, int in_buf, int shift) {
     constexpr int BINS = 1 << BITS;
     constexpr int DPT = BINS / kSortThreads;   // digits per thread: 1 or 2
     static_assert(DPT * kSortThreads == BINS, "whole digits per thread");
@@ -490,7 +493,16 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_downsweep_kernel(SortArg
             const int item = w * kItemsPerWarp + j * 32 + lane;
             const bool valid = item < m;
             const uint32_t d = valid ? digit_of<BITS>(key[j], shift) : (uint32_t)BINS;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            // lanes holding the same digit: one ballot per digit bit, and one for validity (a
+            // fixed cost; __match_any_sync is slower when a warp holds many distinct digits)
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+            if (!valid) peers = ~peers;
+#pragma unroll
+            for (int bit = 0; bit < BITS; bit++) {
+                const bool set = (d >> bit) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, set);
+                peers &= set ? bb : ~bb;
+            }
             uint32_t r = __popc(peers & ltm);
             if (valid) r += S.wcnt[w][dix(d)];
             __syncwarp();
@@ -549,7 +561,7 @@ int sort_grid() {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int g = (sms > 0 ? sms : 148) * 2;
+        int g = (sms > 0 ? sms : 148) * kSortBlocksPerSM;
         g_sort_grid = g < kSortMaxGrid ? g : kSortMaxGrid;
     }
     return g_sort_grid;

@@ -90,6 +90,7 @@ struct Opts {
     float bg0, bg1, bg2;
     float lambda_rgb, lambda_depth;
     int tile, chunk;
+    int count;   // fill the fragment / visit counters
 };
 
 __device__ __forceinline__ void set_status(Counters* c, uint32_t s) { atomicCAS(&c->status, 0u, s); }

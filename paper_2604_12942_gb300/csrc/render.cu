@@ -87,7 +87,7 @@ constexpr int kFwdPPT = 1;
 constexpr int kBwdPPT = 2;
 // Backward visits with at most this many contributing lanes skip the warp reduction: those
 // lanes add their sums to the record directly.
-constexpr int kBwdDirectLanes = 2;
+constexpr int kBwdDirectLanes = 20;
 static_assert(kFwdPPT == 1 && kBwdPPT == 2, "bwd_mask_from_fwd maps 8 x 4 forward regions to 8 x 8 ones");
 
 template <int TILE, int PPT>
@@ -190,7 +190,8 @@ __device__ __forceinline__ void load_record(const float4* proj, uint32_t gid, fl
 // bound and gains more from occupancy than from the few registers the staging code wants.
 constexpr int kFwdThreadsPerSM = 1280;
 
-template <int TILE, int CHUNK>
+// COUNT: fill the fragment and visit counters (a diagnostic option; off in the step).
+template <int TILE, int CHUNK, bool COUNT>
 __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM / TileMap<TILE, kFwdPPT>::NT)
     render_fwd_kernel(FwdArgs a) {
     using TM = TileMap<TILE, kFwdPPT>;
@@ -247,8 +248,10 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
         const float test_T = T * (1.f - alpha);
         const bool stop = pass && test_T < tmin;
         const bool c = pass && !stop;
-        n_eval += act;
-        n_add += c;
+        if constexpr (COUNT) {
+            n_eval += act;
+            n_add += c;
+        }
         done = done || stop;
         const float wgt = c ? alpha * T : 0.f;
         const float4 r2 = s_rec[b][k][2];
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
                 cnt += __popc(bal);
             }
             __syncwarp();
-            n_visit += cnt;
+            if constexpr (COUNT) n_visit += cnt;
             // two records per iteration: their alphas are independent, the compositing is not
             int t = 0;
             for (; t + 1 < cnt; t += 2) {
@@ -340,9 +343,11 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
         }
     }
     cp_async_wait_all();
-    warp_count_add(&a.counters->frag_fwd_eval, n_eval);
-    warp_count_add(&a.counters->frag_fwd_add, n_add);
-    if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_fwd, n_visit);
+    if constexpr (COUNT) {
+        warp_count_add(&a.counters->frag_fwd_eval, n_eval);
+        warp_count_add(&a.counters->frag_fwd_add, n_add);
+        if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_fwd, n_visit);
+    }
     // L1 sums: FP32 within a warp (32 pixels), FP64 across warps and CTAs (the FP64 pipe is
     // narrow: it only sees the per-warp totals)
     float lr = 0.f, ld = 0.f;
@@ -462,7 +467,7 @@ __device__ __forceinline__ void warp_reduce10(float (&v)[10], float& out8, float
     out2 = b;
 }
 
-template <int TILE, int CHUNK>
+template <int TILE, int CHUNK, bool COUNT>
 __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(BwdArgs a) {
     constexpr int kPPT = kBwdPPT;
     using TM = TileMap<TILE, kPPT>;
@@ -579,7 +584,7 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
             cnt += __popc(bal);
         }
         __syncwarp();
-        n_visit += cnt;
+        if constexpr (COUNT) n_visit += cnt;
         for (int t = 0; t < cnt; t++) {
             const int k = s_list[w][t];
             const int j = lo + k;
@@ -604,8 +609,10 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
                 const float a0 = co.w * G;
                 const float alpha = fminf(amax, a0);
                 const bool c = live && !(alpha < amin);
-                n_eval += live;
-                n_add += c;
+                if constexpr (COUNT) {
+                    n_eval += live;
+                    n_add += c;
+                }
                 contrib |= c;
                 const float rom = rcp_approx(1.f - alpha);
                 const float Tn = T[q] * rom;
@@ -656,29 +663,45 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
         __syncthreads();   // buffer b is refilled with chunk c + 2 in the next iteration
     }
     cp_async_wait_all();
-    warp_count_add(&a.counters->frag_bwd_eval, n_eval);
-    warp_count_add(&a.counters->frag_bwd_add, n_add);
-    if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_bwd, n_visit);
+    if constexpr (COUNT) {
+        warp_count_add(&a.counters->frag_bwd_eval, n_eval);
+        warp_count_add(&a.counters->frag_bwd_add, n_add);
+        if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_bwd, n_visit);
+    }
+}
+
+template <int TILE, int CHUNK>
+static void launch_fwd_c(const FwdArgs& a, int total_tiles, cudaStream_t st) {
+    constexpr int NT = TileMap<TILE, kFwdPPT>::NT;
+    if (a.op.count) render_fwd_kernel<TILE, CHUNK, true><<<total_tiles, NT, 0, st>>>(a);
+    else render_fwd_kernel<TILE, CHUNK, false><<<total_tiles, NT, 0, st>>>(a);
 }
 
 template <int TILE>
 static cudaError_t launch_fwd_t(const FwdArgs& a, int total_tiles, int chunk, cudaStream_t st) {
     switch (chunk) {
-        case 32: render_fwd_kernel<TILE, 32><<<total_tiles, TileMap<TILE, kFwdPPT>::NT, 0, st>>>(a); break;
-        case 64: render_fwd_kernel<TILE, 64><<<total_tiles, TileMap<TILE, kFwdPPT>::NT, 0, st>>>(a); break;
-        case 128: render_fwd_kernel<TILE, 128><<<total_tiles, TileMap<TILE, kFwdPPT>::NT, 0, st>>>(a); break;
-        default: render_fwd_kernel<TILE, 256><<<total_tiles, TileMap<TILE, kFwdPPT>::NT, 0, st>>>(a); break;
+        case 32: launch_fwd_c<TILE, 32>(a, total_tiles, st); break;
+        case 64: launch_fwd_c<TILE, 64>(a, total_tiles, st); break;
+        case 128: launch_fwd_c<TILE, 128>(a, total_tiles, st); break;
+        default: launch_fwd_c<TILE, 256>(a, total_tiles, st); break;
     }
     return cudaGetLastError();
+}
+
+template <int TILE, int CHUNK>
+static void launch_bwd_c(const BwdArgs& a, int total_tiles, cudaStream_t st) {
+    constexpr int NT = TileMap<TILE, kBwdPPT>::NT;
+    if (a.op.count) render_bwd_kernel<TILE, CHUNK, true><<<total_tiles, NT, 0, st>>>(a);
+    else render_bwd_kernel<TILE, CHUNK, false><<<total_tiles, NT, 0, st>>>(a);
 }
 
 template <int TILE>
 static cudaError_t launch_bwd_t(const BwdArgs& a, int total_tiles, int chunk, cudaStream_t st) {
     switch (chunk) {
-        case 32: render_bwd_kernel<TILE, 32><<<total_tiles, TileMap<TILE, kBwdPPT>::NT, 0, st>>>(a); break;
-        case 64: render_bwd_kernel<TILE, 64><<<total_tiles, TileMap<TILE, kBwdPPT>::NT, 0, st>>>(a); break;
-        case 128: render_bwd_kernel<TILE, 128><<<total_tiles, TileMap<TILE, kBwdPPT>::NT, 0, st>>>(a); break;
-        default: render_bwd_kernel<TILE, 256><<<total_tiles, TileMap<TILE, kBwdPPT>::NT, 0, st>>>(a); break;
+        case 32: launch_bwd_c<TILE, 32>(a, total_tiles, st); break;
+        case 64: launch_bwd_c<TILE, 64>(a, total_tiles, st); break;
+        case 128: launch_bwd_c<TILE, 128>(a, total_tiles, st); break;
+        default: launch_bwd_c<TILE, 256>(a, total_tiles, st); break;
     }
     return cudaGetLastError();
 }

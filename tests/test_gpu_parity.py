@@ -224,6 +224,34 @@ def test_render_forward_background_and_transmittance():
         np.testing.assert_allclose(C[ch] + Tt * (1 - bg[ch]), 1.0, atol=2e-5)
 
 
+def test_fragment_counters_optional_and_consistent():
+    """The fragment counters are filled only with count_fragments = 1, which changes no output;
+    the forward's added fragments equal the oracle's count (each pixel the oracle flags as
+    fragile may differ by one or two) and the backward re-adds exactly the same fragments."""
+    sc = _scene_c1(10_000, 0, seed=3)
+    cams = [synth.camera(320, 240, 300.0)]
+    ws0, planes, rgb0, depth0, T0 = gpu_forward(sc, cams, gs.default_opts())
+    ws1, _, rgb1, depth1, T1 = gpu_forward(sc, cams, gs.default_opts(count_fragments=1))
+    c0, c1 = ws0.counters(), ws1.counters()
+    assert (c0.frag_fwd_eval, c0.frag_fwd_add, c0.visits_fwd) == (0, 0, 0)
+    assert torch.equal(rgb0, rgb1) and torch.equal(depth0, depth1) and torch.equal(T0, T1)
+    im = oracle.render(oracle.project(sc, cams[0]), cams[0])
+    n_ref, n_fragile = int(im["n_frag"].sum()), int(im["fragile"].sum())
+    assert n_ref > 100_000
+    assert abs(int(c1.frag_fwd_add) - n_ref) <= 2 * n_fragile, (c1.frag_fwd_add, n_ref, n_fragile)
+    assert c1.frag_fwd_eval >= c1.frag_fwd_add and c1.visits_fwd > 0
+    P = ws0.layout.total_pixels
+    up = torch.linspace(-1.0, 1.0, 3 * P, device="cuda")
+    upd = torch.linspace(0.5, -0.5, P, device="cuda")
+    for ws in (ws0, ws1):
+        grads = torch.zeros_like(planes)
+        ws.render_bwd(planes, 0, grads, up, upd, None)
+    torch.cuda.synchronize()
+    c0, c1 = ws0.counters(), ws1.counters()
+    assert (c0.frag_bwd_eval, c0.frag_bwd_add, c0.visits_bwd) == (0, 0, 0)
+    assert c1.frag_bwd_add == c1.frag_fwd_add and c1.frag_bwd_eval >= c1.frag_bwd_add and c1.visits_bwd > 0
+
+
 # ----------------------------------------------------------------------------------------
 # a6-a7 backward
 # ----------------------------------------------------------------------------------------
