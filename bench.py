@@ -398,7 +398,8 @@ def roofline_table(stage, w, pk, pk_kind):
     n, V, P, E = w["n"], w["views"], w["pairs"], w["visible_entries"]
     VN = V * n
     B = {
-        "project": 236 * n + 4 * VN + 48 * E,
+        # geometry of every row, SH of the rows some view sees
+        "project": 44 * n + 192 * w["visible_gaussians"] + 4 * VN + 48 * E,
         # entry count + compaction (touched twice, z, entry write), depth sort (20 B per
         # entry per pass), pair count + emission (entry id, touched, record u v rx ry, pair
         # write), tile sort (20 B per pair per pass), ranges (tile ids)

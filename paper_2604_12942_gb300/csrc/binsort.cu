@@ -444,7 +444,7 @@ __device__ __forceinline__ void block_exclusive_scan_dpt(const uint32_t (&x)[DPT
 }
 
 // resident downsweep blocks per SM (and the grid of every sort pass: this many per SM)
-constexpr int kSortBlocksPerSM = 3;
+constexpr int kSortBlocksPerSM = 3;   // (2 and 4 measured slower on GB300)
 
 template <typename K, int BITS>
 __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) sort_downsweep_kernel(SortArgs a, int in_buf, int shift) {

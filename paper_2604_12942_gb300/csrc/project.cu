@@ -6,24 +6,26 @@
 
 namespace gs {
 
+// 4 blocks of 256 threads per SM (at most 64 registers a thread): the kernel waits on memory
+// and gains more from resident warps than it loses to the few spilled values.
 template <int DEG>
-__global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
+__global__ void __launch_bounds__(256, 4) project_kernel(ProjectArgs a) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = a.n;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float mu[3], ls[3], q[4], sh[3 * K];
+    float mu[3], ls[3], q[4];
 #pragma unroll
     for (int k = 0; k < 3; k++) { mu[k] = __ldg(a.means + k * n + i); ls[k] = __ldg(a.log_scales + k * n + i); }
 #pragma unroll
     for (int k = 0; k < 4; k++) q[k] = __ldg(a.quats + k * n + i);
     const float logit = __ldg(a.logits + i);
-#pragma unroll
-    for (int k = 0; k < 3 * K; k++) sh[k] = __ldg(a.sh + k * n + i);
     Cov3 cv;
     cov3_forward(q, ls, cv);
     const Opts op = a.op;
-    bool vis = false;
+    // geometry of every view first; the SH coefficients are then loaded only by rows that
+    // some view sees (a row no view sees reads 11 of its 11 + 3K floats)
+    uint32_t vis = 0;
     for (int v = 0; v < a.n_views; v++) {
         const View& V = a.views[v];
         const int64_t idx = (int64_t)v * n + i;
@@ -39,28 +41,40 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a) {
         if (touched) {
             const float idet = 1.0f / P.det;
             const float A = P.c * idet, B = -P.b * idet, C = P.a * idet;
-            // colour along the viewing direction
-            float d[3] = {mu[0] - V.cw[0], mu[1] - V.cw[1], mu[2] - V.cw[2]};
-            const float rn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            float Y[16];
-            sh_basis<DEG>(d[0] * rn, d[1] * rn, d[2] * rn, Y);
-            float rgb[3];
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                float s = 0.5f;
-#pragma unroll
-                for (int k = 0; k < K; k++) s += sh[k * 3 + c] * Y[k];
-                rgb[c] = fmaxf(s, 0.0f);
-            }
             float4* rec = a.proj + 3 * idx;
             rec[0] = make_float4(P.u, P.v, P.pc[2], P.o);
             rec[1] = make_float4(kConicScale * A, kConicScale * B, kConicScale * C, __int_as_float(P.rx));
-            rec[2] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(P.ry));
-            vis = true;
+            rec[2].w = __int_as_float(P.ry);
+            vis |= 1u << v;
         }
         a.touched[idx] = touched;
     }
     a.visible[i] = vis ? 1 : 0;
+    if (!vis) return;
+    float sh[3 * K];
+#pragma unroll
+    for (int k = 0; k < 3 * K; k++) sh[k] = __ldg(a.sh + k * n + i);
+    // colour along each seeing view's direction
+    for (uint32_t m = vis; m; m &= m - 1) {
+        const int v = __ffs(m) - 1;
+        const View& V = a.views[v];
+        float d[3] = {mu[0] - V.cw[0], mu[1] - V.cw[1], mu[2] - V.cw[2]};
+        const float rn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        float Y[16];
+        sh_basis<DEG>(d[0] * rn, d[1] * rn, d[2] * rn, Y);
+        float rgb[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float s = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; k++) s += sh[k * 3 + c] * Y[k];
+            rgb[c] = fmaxf(s, 0.0f);
+        }
+        float* r2 = reinterpret_cast<float*>(a.proj + 3 * ((int64_t)v * n + i) + 2);
+        r2[0] = rgb[0];
+        r2[1] = rgb[1];
+        r2[2] = rgb[2];
+    }
 }
 
 // Backward of the projection.  Screen-space sums per (view, Gaussian) come from the
