@@ -256,6 +256,7 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     b.sorted_evals = at<uint32_t>(ws, L->evals0);   // 4 passes: the entry sort ends in buffer 0
     b.pkeys = at<uint32_t>(ws, L->keys0);
     b.pvals = at<uint32_t>(ws, L->vals0);
+    b.vis_bits = at<uint32_t>(ws, L->ekeys1);       // free until the entry sort
     b.poff = at<uint32_t>(ws, L->ekeys1);           // free once the entries are sorted
     b.chunk_first = at<uint32_t>(ws, L->emit_tmp);
     b.counters = cnt;

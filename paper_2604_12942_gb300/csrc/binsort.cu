@@ -77,22 +77,41 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t* __r
 }
 
 // ----------------------------------------------------------------------------------------
-// Entry compaction: block b of kScanBlock (view, Gaussian) slots counts its visible
-// entries, the block counts are scanned, then each block writes its entries' depth keys
-// and ids at their offsets (so entries stay in (view, index) order).
+// Entry compaction.  The (view, Gaussian) slots are taken 32 at a time as one bit word (bit
+// set: touched > 0).  A block of 1024 threads covers 1024 words (32768 slots): the count
+// kernel reads the touched counts once, writes the words and the block's entry total; the
+// totals are scanned; the compaction kernel then reads only the words, gives each its offset
+// by a block scan of the word counts, and each warp writes the entries of 32 words, one word
+// at a time with a lane per slot, so entries stay in (view, index) order.
 // ----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) entry_count_kernel(const uint32_t* __restrict__ touched, int64_t n,
+constexpr int64_t kEntrySlotsPerBlock = (int64_t)kScanThreads * 32;
+
+__global__ void __launch_bounds__(kScanThreads) entry_count_kernel(const uint32_t* __restrict__ touched, int64_t total,
+                                                                  uint32_t* __restrict__ bits,
                                                                   uint32_t* __restrict__ bsum) {
     __shared__ uint32_t s[33];
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
-    uint32_t sum = 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // the warp's 32 words are slots s0 .. s0 + 1023; word k of the warp ends up in lane k
+    const int64_t s0 = (int64_t)blockIdx.x * kEntrySlotsPerBlock + (int64_t)w * 1024;
+    uint32_t mine = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-        const int64_t j = base + (int64_t)k * kScanThreads + threadIdx.x;
-        if (j < n) sum += touched[j] != 0u;
+    for (int k0 = 0; k0 < 32; k0 += 8) {
+        uint32_t t[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int64_t j = s0 + (int64_t)(k0 + k) * 32 + lane;
+            t[k] = j < total ? touched[j] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t b = __ballot_sync(0xffffffffu, t[k] != 0u);
+            if (lane == k0 + k) mine = b;
+        }
     }
-    sum = warp_sum(sum);
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = sum;
+    const int64_t word = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+    if (word * 32 < total) bits[word] = mine;
+    uint32_t sum = warp_sum((uint32_t)__popc(mine));
+    if (lane == 0) s[w] = sum;
     __syncthreads();
     if (threadIdx.x < 32) {
         uint32_t t = threadIdx.x < (kScanThreads >> 5) ? s[threadIdx.x] : 0u;
@@ -101,35 +120,38 @@ __global__ void __launch_bounds__(kScanThreads) entry_count_kernel(const uint32_
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, int64_t n) {
+__global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, int64_t total) {
     __shared__ uint32_t s[33];
+    __shared__ uint32_t s_off[kScanThreads], s_word[kScanThreads];
     if (a.counters->status != 0) return;
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
-    uint32_t f[kScanItems], sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-        f[k] = (base + k < n) ? (a.touched[base + k] != 0u) : 0u;
-        sum += f[k];
-    }
+    const int64_t word = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+    const uint32_t b = word * 32 < total ? a.vis_bits[word] : 0u;
     uint32_t tot;
-    uint32_t off = block_exclusive_scan_1024(sum, s, tot) + a.scan_tmp[blockIdx.x];
+    const uint32_t off = block_exclusive_scan_1024((uint32_t)__popc(b), s, tot) + a.scan_tmp[blockIdx.x];
+    s_off[threadIdx.x] = off;
+    s_word[threadIdx.x] = b;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t ltm;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(ltm));
     const float* pf = reinterpret_cast<const float*>(a.proj);
-#pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-        if (f[k]) {
-            const int64_t idx = base + k;
-            a.ekeys[off] = __float_as_uint(__ldg(pf + 12 * idx + 2));   // z > 0: bits are monotone
-            a.evals[off] = (uint32_t)idx;
-            a.entries[off] = (uint32_t)idx;
-            off++;
+    for (int k = 0; k < 32; k++) {
+        const int lw = w * 32 + k;
+        const uint32_t bw = s_word[lw];
+        if ((bw >> lane) & 1u) {
+            const uint32_t pos = s_off[lw] + (uint32_t)__popc(bw & ltm);
+            const int64_t idx = ((int64_t)blockIdx.x * kScanThreads + lw) * 32 + lane;
+            a.ekeys[pos] = __float_as_uint(__ldg(pf + 12 * idx + 2));   // z > 0: bits are monotone
+            a.evals[pos] = (uint32_t)idx;
+            a.entries[pos] = (uint32_t)idx;
         }
     }
 }
 
 cudaError_t launch_entries(const BinArgs& a, cudaStream_t st) {
     const int64_t total = (int64_t)a.n_views * a.n;
-    const int nb = (int)((total + kScanBlock - 1) / kScanBlock);
-    if (nb > 0) entry_count_kernel<<<nb, kScanThreads, 0, st>>>(a.touched, total, a.scan_tmp);
+    const int nb = (int)((total + kEntrySlotsPerBlock - 1) / kEntrySlotsPerBlock);
+    if (nb > 0) entry_count_kernel<<<nb, kScanThreads, 0, st>>>(a.touched, total, a.vis_bits, a.scan_tmp);
     scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(a.scan_tmp, nb, &a.counters->n_entries, &a.counters->n_entries32,
                                                    a.counters, -1);
     if (nb > 0) entry_compact_kernel<<<nb, kScanThreads, 0, st>>>(a, total);

@@ -51,6 +51,7 @@ struct BinArgs {
     const float4* proj;
     const uint32_t* touched;
     uint32_t* scan_tmp;           // block sums of the scans
+    uint32_t* vis_bits;           // [ceil(n_views * n / 32)] scratch: one bit per (view, Gaussian) slot
     uint32_t* ekeys;              // compaction output: bits(z) of each entry
     uint32_t* evals;              //   and its view * n + Gaussian index
     uint32_t* entries;            //   a copy of evals kept in (view, Gaussian) order
