@@ -140,6 +140,12 @@ def test_bin_sort_bit_exact_nine_bit_digits():
     assert P > 1_000_000
 
 
+def test_bin_sort_tiny_ragged():
+    # 2 x 37 (view, Gaussian) slots: the visibility bit words straddle the views and the last
+    # one is partial
+    _bin_case(_cams_small()[:2], 37, 16, seed=7, radius_max=60)
+
+
 def test_bin_sort_single_tile():
     """One tile per view set: no tile-sort pass, the pairs stay in depth order."""
     _bin_case([synth.camera(16, 16, 20.0)], 2000, 16, seed=5, radius_max=12)
