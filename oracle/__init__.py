@@ -339,3 +339,8 @@ def descriptor_cov(P, k, sigma=0.02):
     lib().or_descriptor_cov(N, _p(np.ascontiguousarray(P)), _p(np.ascontiguousarray(mu)), _p(lam),
                             _p(np.ascontiguousarray(V)), k, sigma, _p(Sg), _p(J))
     return Sg.reshape(6, 6), J.reshape(N, 6, 3), lam, V
+
+
+# The render-derived masks and the SSIM term of the objective (plain NumPy, FP64).
+from .objective import (erode, gaussian_window, masked_objective, render_mask,  # noqa: E402,F401
+                        ssim_loss)
