@@ -98,6 +98,13 @@ typedef struct {
     int32_t count_fragments; /* 1: the compositing kernels fill the frag_* and visits_* counters
                                 of gs_counters (a few percent slower); 0 (default): those
                                 counters stay 0 */
+    /* The rest of the §III-C objective (total-loss equation, SSIM term, interior mask):   */
+    float lambda_ssim;       /* weight of 1 - SSIM over the mask (default 0: no SSIM term); a
+                                workspace laid out with lambda_ssim > 0 holds its scratch */
+    float mask_opacity;      /* M_geo = [1 - T_final >= mask_opacity] (default 0.5) */
+    int32_t mask_erode;      /* >= 0: the step supervises inside M_int = Erode(M_geo, disk of this
+                                radius, 0..16) of its own rendering, intersected with the caller's
+                                mask; -1 (default): the caller's mask alone */
 } gs_render_opts;
 
 /* Byte offsets of the workspace regions (all 256-byte aligned) -- exposed so callers and
@@ -105,7 +112,8 @@ typedef struct {
 typedef struct {
     size_t views;        /* internal per-view table */
     size_t counters;     /* gs_counters-compatible block: status, n_pairs, ... */
-    size_t loss_acc;     /* double [n_views][2] masked L1 sums, uint32 [n_views][2] counts */
+    size_t loss_acc;     /* double [GS_MAX_VIEWS][3] masked L1 colour / L1 depth / SSIM sums,
+                            uint32 [GS_MAX_VIEWS][2] counts |M|, |M and D~ > 0| */
     size_t proj;         /* [n_views*n] records of 12 floats: (u, v, z, opacity),
                             (a, b, c, rx bits), (r, g, b, ry bits); (a, b, c) is the inverse
                             2-D covariance times -log2(e)/2, so alpha = o * 2^(a dx^2 +
@@ -135,7 +143,10 @@ typedef struct {
     size_t entries;      /* uint32 [n_views*n]: the visible entries in (view, Gaussian) order */
     size_t tile_order;   /* uint32 [total_tiles]: compositing work order, largest pair count
                             first (power-of-two buckets), then scratch */
+    size_t render_mask;  /* uint8 [total_pixels]: the step's interior mask (mask_erode >= 0) */
+    size_t ssim_tmp;     /* float [9 * total_pixels] SSIM partials (only if has_ssim) */
     size_t total;        /* workspace bytes */
+    int32_t has_ssim;    /* laid out with lambda_ssim > 0 */
     int32_t sorted_buf;  /* 0 or 1: which ping-pong buffer holds the sorted pairs */
     int32_t total_tiles;
     int64_t total_pixels;
@@ -221,7 +232,9 @@ gs_status gs_bin_sort(const gs_camera *cams, const gs_render_opts *opts, const g
                       void *ws, void *stream);
 
 /* a5 -- Front-to-back compositing of colour and depth (§III-C, depth equation) with the
- * fused L1 loss (§III-C loss equations, SSIM weight 0).  Outputs (packed per view, see
+ * fused L1 loss (§III-C loss equations, SSIM weight 0).  With opts.lambda_ssim > 0 or
+ * opts.mask_erode >= 0 the compositing only renders and the loss is that of gs_objective, on
+ * gs_render_mask's mask when mask_erode >= 0 (else on `mask`).  Outputs (packed per view, see
  * above): out_rgb [3*P], out_depth [P]; out_T [P] (final transmittance) may be NULL.
  * When target_rgb is non-NULL the loss is evaluated:
  *   L = 1/V sum_v [ lambda_rgb/|M_v| sum_{x in M_v} ||C - C~||_1
@@ -234,6 +247,32 @@ gs_status gs_render_fwd(const gs_camera *cams, const gs_render_opts *opts, const
                         void *ws, float *out_rgb, float *out_depth, float *out_T,
                         const float *target_rgb, const float *target_depth, const uint8_t *mask,
                         float *dl_drgb, float *dl_ddepth, float *loss_out, void *stream);
+
+/* f1 -- Interior mask (§III-C, optimization: a geometric support mask from the accumulated
+ * opacity of the current rendering, eroded morphologically; supervision is evaluated inside
+ * it).  mask_out[p] = [1 - T_final(q) >= opts.mask_opacity for every pixel q of the view with
+ * |q - p| <= r] and caller_mask[p] != 0 (caller_mask may be NULL), r = max(0, opts.mask_erode);
+ * pixels outside the image count as outside the support.  T_final is the workspace's, from
+ * the last gs_render_fwd.  The threshold is decided on the FP32 value, 1 - T computed in
+ * FP32.  mask_out: device uint8 [P], packed per view; the caller owns it. */
+gs_status gs_render_mask(const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L,
+                         void *ws, const uint8_t *caller_mask, uint8_t *mask_out, void *stream);
+
+/* f1 -- The full §III-C objective over a mask M (total-loss, L_rgb, L_ssim and L_depth
+ * equations): per view lambda_rgb L_rgb + lambda_ssim (1 - SSIM) + lambda_depth L_depth,
+ * averaged over the views.  L_rgb and L_depth are as in gs_render_fwd; SSIM is taken on
+ * x = C M and y = C~ M per channel with an 11 x 11 Gaussian window (sigma 1.5, normalised,
+ * zeros outside the image), C1 = 0.01^2, C2 = 0.03^2, and averaged over the pixels of M and
+ * the three channels (an empty M contributes 0).  rgb [3*P], depth [P]: rendered images (from
+ * gs_render_fwd); target_depth may be NULL (then depth and dl_ddepth may be too); mask may be
+ * NULL (all pixels).  dl_drgb / dl_ddepth are overwritten with dL/dC, dL/dD (the mask is a
+ * constant: no gradient flows through it); loss_out (device, n_views + 1 floats) receives the
+ * per-view terms and their mean.  lambda_ssim > 0 needs a workspace laid out with
+ * lambda_ssim > 0 (it holds 9 floats of scratch per pixel). */
+gs_status gs_objective(const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L,
+                       void *ws, const float *rgb, const float *depth, const float *target_rgb,
+                       const float *target_depth, const uint8_t *mask, float *dl_drgb,
+                       float *dl_ddepth, float *loss_out, void *stream);
 
 /* a6-a7 -- Analytic backward of gs_render_fwd and gs_project for upstream per-pixel
  * gradients dl_drgb [3*P], dl_ddepth [P] (dl_ddepth may be NULL).  Transmittance is

@@ -31,14 +31,16 @@ class RenderOpts(C.Structure):
     _fields_ = [("near_z", C.c_float), ("dilation", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("T_min", C.c_float), ("clamp_fov", C.c_float), ("bg", C.c_float * 3), ("lambda_rgb", C.c_float),
                 ("lambda_depth", C.c_float), ("tile", C.c_int32), ("chunk", C.c_int32),
-                ("count_fragments", C.c_int32)]
+                ("count_fragments", C.c_int32), ("lambda_ssim", C.c_float), ("mask_opacity", C.c_float),
+                ("mask_erode", C.c_int32)]
 
 
 class WsLayout(C.Structure):
     _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "touched", "scan_tmp",
                                           "ekeys0", "ekeys1", "evals0", "evals1", "keys0", "keys1", "vals0", "vals1", "pair_mask", "emit_tmp", "sort_tmp", "ranges", "T_final",
-                                          "n_contrib", "grad2d", "geo2d", "visible", "entries", "tile_order", "total")] + \
-               [("sorted_buf", C.c_int32), ("total_tiles", C.c_int32), ("total_pixels", C.c_int64),
+                                          "n_contrib", "grad2d", "geo2d", "visible", "entries", "tile_order", "render_mask",
+                                          "ssim_tmp", "total")] + \
+               [("has_ssim", C.c_int32), ("sorted_buf", C.c_int32), ("total_tiles", C.c_int32), ("total_pixels", C.c_int64),
                 ("max_pairs", C.c_int64), ("n", C.c_int64), ("n_views", C.c_int32), ("tile", C.c_int32)]
 
 
@@ -91,6 +93,10 @@ _SIGS = {
     "gs_bin_sort": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.c_void_p], C.c_int),
     "gs_render_fwd": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p] + [C.c_void_p] * 3 +
                       [C.c_void_p] * 3 + [C.c_void_p] * 3 + [C.c_void_p], C.c_int),
+    "gs_render_mask": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.c_void_p,
+                        C.c_void_p, C.c_void_p], C.c_int),
+    "gs_objective": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p] + [C.c_void_p] * 9,
+                     C.c_int),
     "gs_render_bwd": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p,
                        C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p], C.c_int),
     "gs_composite_bwd": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.c_void_p,

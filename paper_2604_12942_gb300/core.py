@@ -132,6 +132,18 @@ class Workspace:
                                       _ptr(target_depth), _ptr(mask), _ptr(dl_drgb), _ptr(dl_ddepth),
                                       _ptr(loss_out), _stream()), "gs_render_fwd")
 
+    def render_mask(self, mask_out, caller_mask=None):
+        """Interior mask of the last forward's transmittance (opts.mask_opacity, mask_erode)."""
+        N.check(N.lib().gs_render_mask(self.cams_c, C.byref(self.opts), C.byref(self.layout), _ptr(self.buf),
+                                       _ptr(caller_mask), _ptr(mask_out), _stream()), "gs_render_mask")
+
+    def objective(self, rgb, depth, target_rgb, target_depth, mask, dl_drgb, dl_ddepth, loss_out):
+        """lambda_rgb L_rgb + lambda_ssim (1 - SSIM) + lambda_depth L_depth over `mask`, with
+        dL/dC and dL/dD."""
+        N.check(N.lib().gs_objective(self.cams_c, C.byref(self.opts), C.byref(self.layout), _ptr(self.buf),
+                                     _ptr(rgb), _ptr(depth), _ptr(target_rgb), _ptr(target_depth), _ptr(mask),
+                                     _ptr(dl_drgb), _ptr(dl_ddepth), _ptr(loss_out), _stream()), "gs_objective")
+
     def render_bwd(self, planes, sh_degree, grad_planes, dl_drgb, dl_ddepth=None, grad_twist=None):
         g = gaussians_struct(planes, sh_degree)
         gg = gaussians_struct(grad_planes, sh_degree)

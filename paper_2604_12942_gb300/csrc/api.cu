@@ -31,6 +31,9 @@ static gs_status fail(gs_status s, const char* fmt, ...) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// loss accumulators: double [GS_MAX_VIEWS][3] sums, then uint32 [GS_MAX_VIEWS][2] counts
+constexpr size_t kLossAccBytes = sizeof(double) * 3 * GS_MAX_VIEWS + sizeof(uint32_t) * 2 * GS_MAX_VIEWS;
+
 struct Geometry {
     int total_tiles = 0;
     int64_t total_pixels = 0;
@@ -47,6 +50,9 @@ static gs_status check_opts(const gs_render_opts* o) {
         return fail(GS_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max <= 1");
     if (!(o->T_min >= 0.f) || !(o->near_z >= 0.f) || !(o->dilation >= 0.f) || !(o->clamp_fov > 0.f))
         return fail(GS_ERR_INVALID_ARG, "invalid compositing constants");
+    if (!(o->lambda_ssim >= 0.f) || !(o->mask_opacity >= 0.f && o->mask_opacity <= 1.f) || o->mask_erode < -1 ||
+        o->mask_erode > 16)
+        return fail(GS_ERR_INVALID_ARG, "need lambda_ssim >= 0, mask_opacity in [0, 1], mask_erode in [-1, 16]");
     return GS_OK;
 }
 
@@ -125,7 +131,7 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     auto take = [&](size_t bytes) { const size_t r = off; off = align256(off + bytes); return r; };
     L.views = take(sizeof(View) * GS_MAX_VIEWS);
     L.counters = take(sizeof(Counters));
-    L.loss_acc = take(sizeof(double) * 2 * GS_MAX_VIEWS + sizeof(uint32_t) * 2 * GS_MAX_VIEWS);
+    L.loss_acc = take(kLossAccBytes);
     L.proj = take(sizeof(float) * 12 * (size_t)VN);
     L.touched = take(sizeof(uint32_t) * (size_t)VN);
     L.scan_tmp = take(sizeof(uint32_t) * ((size_t)VN / kScanBlock + 2));
@@ -148,6 +154,9 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.entries = take(sizeof(uint32_t) * (size_t)VN);
     L.visible = take((size_t)n);
     L.tile_order = take(sizeof(uint32_t) * ((size_t)G.total_tiles + 2 * 34));
+    L.render_mask = take((size_t)G.total_pixels);
+    L.has_ssim = o->lambda_ssim > 0.f ? 1 : 0;
+    L.ssim_tmp = take(L.has_ssim ? sizeof(float) * 9 * (size_t)G.total_pixels : 0);
     L.total = off;
     int shifts[16], bits[16];
     L.sorted_buf = pair_sort_passes(G.total_tiles, shifts, bits) & 1;
@@ -215,6 +224,8 @@ static gs_status geometry_for(const gs_ws_layout* L, const gs_camera* cams, cons
     if (s != GS_OK) return s;
     if (G.total_tiles != L->total_tiles || G.total_pixels != L->total_pixels || opts->tile != L->tile)
         return fail(GS_ERR_INVALID_ARG, "cameras / tile size do not match the workspace layout");
+    if (opts->lambda_ssim > 0.f && !L->has_ssim)
+        return fail(GS_ERR_INVALID_ARG, "lambda_ssim > 0 needs a workspace laid out with lambda_ssim > 0");
     return GS_OK;
 }
 
@@ -297,17 +308,72 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     return launch_tile_order(r.ranges, L->total_tiles, order, order + L->total_tiles, cnt, st);
 }
 
+static ObjArgs obj_args(const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws) {
+    ObjArgs o;
+    memset(&o, 0, sizeof(o));
+    o.n_views = L->n_views;
+    o.views = at<View>(ws, L->views);
+    for (int v = 0; v < L->n_views; v++) {
+        o.max_w = G.views[v].W > o.max_w ? G.views[v].W : o.max_w;
+        o.max_h = G.views[v].H > o.max_h ? G.views[v].H : o.max_h;
+    }
+    o.T_final = at<float>(ws, L->T_final);
+    o.tau = opts->mask_opacity;
+    o.r_erode = opts->mask_erode > 0 ? opts->mask_erode : 0;
+    double* sums = at<double>(ws, L->loss_acc);
+    o.sums = sums;
+    o.counts = reinterpret_cast<uint32_t*>(sums + 3 * GS_MAX_VIEWS);
+    o.ssim_part = L->has_ssim ? at<float>(ws, L->ssim_tmp) : nullptr;
+    o.lambda_rgb = opts->lambda_rgb;
+    o.lambda_depth = opts->lambda_depth;
+    o.lambda_ssim = opts->lambda_ssim;
+    ssim_window(o.win);
+    return o;
+}
+
+// M_int of the last forward's transmittance (and the caller's mask) into mask_out.
+static cudaError_t run_render_mask(const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
+                                   const uint8_t* caller_mask, uint8_t* mask_out, cudaStream_t st) {
+    ObjArgs o = obj_args(opts, L, G, ws);
+    o.caller_mask = caller_mask;
+    o.mask_out = mask_out;
+    return launch_render_mask(o, st);
+}
+
+// The objective over `mask`: counts, masked L1 terms, SSIM (if lambda_ssim > 0), per-view
+// losses and their mean.
+static cudaError_t run_objective(const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
+                                 const float* rgb, const float* depth, const float* target_rgb,
+                                 const float* target_depth, const uint8_t* mask, float* dl_drgb, float* dl_ddepth,
+                                 float* loss_out, cudaStream_t st) {
+    ObjArgs o = obj_args(opts, L, G, ws);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(o.sums, 0, kLossAccBytes, st)) != cudaSuccess) return e;
+    if ((e = launch_loss_count(o.views, L->n_views, G.pix, target_depth, mask, const_cast<uint32_t*>(o.counts), st)) !=
+        cudaSuccess)
+        return e;
+    o.rgb = rgb; o.depth = depth; o.tgt_rgb = target_rgb; o.tgt_depth = target_depth; o.mask = mask;
+    o.dl_drgb = dl_drgb;
+    o.dl_ddepth = target_depth ? dl_ddepth : nullptr;
+    if ((e = launch_objective(o, st)) != cudaSuccess) return e;
+    return launch_loss_finalize(o.sums, o.counts, L->n_views, opts->lambda_rgb, opts->lambda_depth, opts->lambda_ssim,
+                                target_depth != nullptr, loss_out, st);
+}
+
+// Forward compositing.  With a target and neither the SSIM term nor the render-derived mask,
+// the L1 loss is fused into the compositing epilogue; otherwise the forward only renders and
+// the mask and the objective follow as separate kernels.
 static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
                            float* out_rgb, float* out_depth, float* out_T, const float* target_rgb,
                            const float* target_depth, const uint8_t* mask, float* dl_drgb, float* dl_ddepth,
                            float* loss_out, cudaStream_t st) {
     double* sums = at<double>(ws, L->loss_acc);
-    uint32_t* counts = reinterpret_cast<uint32_t*>(sums + 2 * GS_MAX_VIEWS);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(sums + 3 * GS_MAX_VIEWS);
+    const bool separate = target_rgb && (opts->lambda_ssim > 0.f || opts->mask_erode >= 0);
+    const bool fused = target_rgb && !separate;
     cudaError_t e;
-    if (target_rgb) {
-        if ((e = cudaMemsetAsync(sums, 0, sizeof(double) * 2 * GS_MAX_VIEWS + sizeof(uint32_t) * 2 * GS_MAX_VIEWS, st)) !=
-            cudaSuccess)
-            return e;
+    if (fused) {
+        if ((e = cudaMemsetAsync(sums, 0, kLossAccBytes, st)) != cudaSuccess) return e;
         if ((e = launch_loss_count(at<View>(ws, L->views), L->n_views, G.pix, target_depth, mask, counts, st)) !=
             cudaSuccess)
             return e;
@@ -327,17 +393,27 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
     a.out_rgb = out_rgb;
     a.out_depth = out_depth;
     a.out_T = out_T;
-    a.tgt_rgb = target_rgb;
-    a.tgt_depth = target_depth;
-    a.mask = mask;
-    a.dl_drgb = target_rgb ? dl_drgb : nullptr;
-    a.dl_ddepth = target_rgb ? dl_ddepth : nullptr;
+    a.tgt_rgb = fused ? target_rgb : nullptr;
+    a.tgt_depth = fused ? target_depth : nullptr;
+    a.mask = fused ? mask : nullptr;
+    a.dl_drgb = fused ? dl_drgb : nullptr;
+    a.dl_ddepth = fused ? dl_ddepth : nullptr;
     a.loss_sums = sums;
     a.loss_counts = counts;
     if ((e = launch_render_fwd(a, L->total_tiles, st)) != cudaSuccess) return e;
-    if (target_rgb)
-        return launch_loss_finalize(sums, counts, L->n_views, opts->lambda_rgb, opts->lambda_depth,
+    if (fused)
+        return launch_loss_finalize(sums, counts, L->n_views, opts->lambda_rgb, opts->lambda_depth, 0.f,
                                     target_depth != nullptr, loss_out, st);
+    if (separate) {
+        const uint8_t* m = mask;
+        if (opts->mask_erode >= 0) {
+            uint8_t* rm = at<uint8_t>(ws, L->render_mask);
+            if ((e = run_render_mask(opts, L, G, ws, mask, rm, st)) != cudaSuccess) return e;
+            m = rm;
+        }
+        return run_objective(opts, L, G, ws, out_rgb, out_depth, target_rgb, target_depth, m, dl_drgb, dl_ddepth,
+                             loss_out, st);
+    }
     return cudaSuccess;
 }
 
@@ -544,6 +620,9 @@ void gs_default_opts(gs_render_opts* o) {
     o->tile = 16;
     o->chunk = 64;
     o->count_fragments = 0;
+    o->lambda_ssim = 0.0f;
+    o->mask_opacity = 0.5f;
+    o->mask_erode = -1;
 }
 
 size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams, const gs_render_opts* opts,
@@ -628,6 +707,34 @@ gs_status gs_render_fwd(const gs_camera* cams, const gs_render_opts* opts, const
     if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
     GS_CUDA(run_fwd(opts, L, G, ws, out_rgb, out_depth, out_T, target_rgb, target_depth, mask, dl_drgb, dl_ddepth,
                     loss_out, st));
+    return GS_OK;
+}
+
+gs_status gs_render_mask(const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                         const uint8_t* caller_mask, uint8_t* mask_out, void* stream) {
+    gs_status s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    if (!mask_out) return fail(GS_ERR_INVALID_ARG, "mask_out is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    GS_CUDA(run_render_mask(opts, L, G, ws, caller_mask, mask_out, st));
+    return GS_OK;
+}
+
+gs_status gs_objective(const gs_camera* cams, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                       const float* rgb, const float* depth, const float* target_rgb, const float* target_depth,
+                       const uint8_t* mask, float* dl_drgb, float* dl_ddepth, float* loss_out, void* stream) {
+    gs_status s;
+    if ((s = check_ws(ws, L)) != GS_OK) return s;
+    Geometry G;
+    if ((s = geometry_for(L, cams, opts, G)) != GS_OK) return s;
+    if (!rgb || !target_rgb || !dl_drgb || !loss_out) return fail(GS_ERR_INVALID_ARG, "rgb, target_rgb, dl_drgb and loss_out are required");
+    if (target_depth && (!depth || !dl_ddepth)) return fail(GS_ERR_INVALID_ARG, "the depth term needs depth and dl_ddepth");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
+    GS_CUDA(run_objective(opts, L, G, ws, rgb, depth, target_rgb, target_depth, mask, dl_drgb, dl_ddepth, loss_out, st));
     return GS_OK;
 }
 

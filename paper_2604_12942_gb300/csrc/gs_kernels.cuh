@@ -97,7 +97,7 @@ struct FwdArgs {
     const float *tgt_rgb, *tgt_depth;
     const uint8_t* mask;
     float *dl_drgb, *dl_ddepth;
-    double* loss_sums;         // [V][2]
+    double* loss_sums;         // [V][3] (L1 rgb, L1 depth, SSIM)
     const uint32_t* loss_counts;  // [V][2]
 };
 
@@ -133,6 +133,32 @@ struct AdamArgs {
     const Counters* step_dev;   // if set, bias corrections come from this device counter block
 };
 
+// The render-derived mask and the masked objective (objective.cu).
+struct ObjArgs {
+    int n_views;
+    const View* views;
+    int max_w, max_h;            // largest view size (grid extent)
+    // interior mask
+    const float* T_final;        // [P] from the forward
+    const uint8_t* caller_mask;  // [P] or null
+    uint8_t* mask_out;           // [P]
+    float tau;                   // accumulated-opacity threshold
+    int r_erode;                 // erosion disk radius (pixels)
+    // objective over `mask`
+    const float *rgb, *depth;    // rendered [3P] planar per view, [P]
+    const float *tgt_rgb, *tgt_depth;
+    const uint8_t* mask;         // [P] or null (all pixels)
+    const uint32_t* counts;      // [V][2] |M|, |M and D~ > 0|
+    double* sums;                // [V][3] L1 rgb, L1 depth, SSIM sums
+    float *dl_drgb, *dl_ddepth;  // outputs (overwritten by the L1 terms, SSIM added)
+    float* ssim_part;            // [9P] scratch, planar per view
+    float lambda_rgb, lambda_depth, lambda_ssim;
+    float win[11];               // 1-D Gaussian window
+};
+cudaError_t launch_render_mask(const ObjArgs& a, cudaStream_t st);
+cudaError_t launch_objective(const ObjArgs& a, cudaStream_t st);
+void ssim_window(float (&w)[11]);
+
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st);
 // Compaction of the visible entries (touched > 0) in (view, Gaussian) order with their
@@ -151,7 +177,8 @@ cudaError_t launch_loss_count(const View* views, int n_views, const int64_t* pix
                               const float* tgt_depth, const uint8_t* mask, uint32_t* counts, cudaStream_t st);
 cudaError_t launch_render_fwd(const FwdArgs& a, int total_tiles, cudaStream_t st);
 cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
-                                 float lambda_depth, int has_depth, float* loss_out, cudaStream_t st);
+                                 float lambda_depth, float lambda_ssim, int has_depth, float* loss_out,
+                                 cudaStream_t st);
 cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st);
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t st);
 cudaError_t launch_adam_step_counter(Counters* c, float b1, float b2, cudaStream_t st);

@@ -1,0 +1,272 @@
+// The rest of the mapping objective (RMGS-SLAM §III-C, "Optimization"): the interior mask
+// M_int = Erode(M_geo, r_erode) with M_geo the accumulated-opacity support of the current
+// rendering, and lambda_rgb L_rgb + lambda_ssim (1 - SSIM) + lambda_depth L_depth evaluated
+// inside it, with dL/dC and dL/dD for the backward.  Used by the step instead of the forward's
+// fused L1 epilogue when the SSIM term or the render-derived mask is switched on (the mask
+// needs every neighbour's transmittance, so it cannot be taken inside the forward).
+//
+// SSIM (per channel): x = C * M, y = C~ * M, 11 x 11 Gaussian window (sigma 1.5) with zeros
+// outside the image, C1 = 0.01^2, C2 = 0.03^2; the SSIM map is averaged over M and the three
+// channels.  The window is separable: each kernel makes a horizontal pass over a tile with a
+// 5-pixel halo in shared memory, then a vertical one.  The forward writes, per pixel and
+// channel, the three partial derivatives of the weighted SSIM map with respect to the local
+// mean, second moment and cross moment; the backward convolves them back onto the pixels.
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+constexpr int kObjTX = 32, kObjTY = 8;          // threads of a block
+constexpr int kObjRows = 2;                      // output rows per thread
+constexpr int kObjH = kObjTY * kObjRows;         // output tile: 32 x 16 pixels
+constexpr int kHalo = 5;                         // window radius
+constexpr int kInW = kObjTX + 2 * kHalo, kInH = kObjH + 2 * kHalo;
+constexpr float kSsimC1 = 0.01f * 0.01f, kSsimC2 = 0.03f * 0.03f;
+
+// Interior mask: [1 - T >= tau] eroded by the radius-r disk (outside the image counts as
+// outside the support), and the caller's mask.
+__global__ void __launch_bounds__(kObjTX * kObjTY) render_mask_kernel(ObjArgs a) {
+    const View& V = a.views[blockIdx.z];
+    const int x = blockIdx.x * kObjTX + threadIdx.x, y = blockIdx.y * kObjTY + threadIdx.y;
+    if (x >= V.W || y >= V.H) return;
+    const float* T = a.T_final + V.pix_off;
+    const int r = a.r_erode;
+    bool in = true;
+    for (int dy = -r; dy <= r; dy++) {
+        for (int dx = -r; dx <= r; dx++) {
+            if (dx * dx + dy * dy > r * r) continue;
+            const int xx = x + dx, yy = y + dy;
+            const bool inside = xx >= 0 && xx < V.W && yy >= 0 && yy < V.H;
+            in = in && inside && __fsub_rn(1.f, __ldg(T + (int64_t)yy * V.W + xx)) >= a.tau;
+        }
+    }
+    const int64_t g = V.pix_off + (int64_t)y * V.W + x;
+    if (a.caller_mask) in = in && a.caller_mask[g] != 0;
+    a.mask_out[g] = in ? 1 : 0;
+}
+
+__device__ __forceinline__ void block_add2(float s0, float s1, double* dst0, double* dst1) {
+    __shared__ double s_r[2][kObjTX * kObjTY / 32];
+    const int t = threadIdx.y * kObjTX + threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) { s_r[0][w] = (double)s0; s_r[1][w] = (double)s1; }
+    __syncthreads();
+    if (t == 0) {
+        double a0 = 0, a1 = 0;
+        for (int k = 0; k < kObjTX * kObjTY / 32; k++) { a0 += s_r[0][k]; a1 += s_r[1][k]; }
+        if (a0 != 0.0) atomicAdd(dst0, a0);
+        if (dst1 && a1 != 0.0) atomicAdd(dst1, a1);
+    }
+}
+
+// Masked L1 terms: the same arithmetic as the forward's fused epilogue, on a given mask.
+__global__ void __launch_bounds__(kObjTX * kObjTY) masked_l1_kernel(ObjArgs a) {
+    const int v = blockIdx.z;
+    const View& V = a.views[v];
+    const int x = blockIdx.x * kObjTX + threadIdx.x, y = blockIdx.y * kObjTY + threadIdx.y;
+    float lr = 0.f, ld = 0.f;
+    if (x < V.W && y < V.H) {
+        const int64_t P = (int64_t)V.W * V.H, p = (int64_t)y * V.W + x, g = V.pix_off + p;
+        const float* c = a.rgb + 3 * V.pix_off;
+        const float* t = a.tgt_rgb + 3 * V.pix_off;
+        const bool in = a.mask ? a.mask[g] != 0 : true;
+        const float cm = (float)a.counts[2 * v], cd = (float)a.counts[2 * v + 1];
+        const float inv_v = 1.0f / (float)a.n_views;
+        const float krgb = (in && cm > 0.f) ? a.lambda_rgb * inv_v / cm : 0.f;
+        float* dl = a.dl_drgb + 3 * V.pix_off;
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            const float r = c[ch * P + p] - t[ch * P + p];
+            dl[ch * P + p] = krgb * (float)((r > 0.f) - (r < 0.f));
+            if (in) lr += fabsf(r);
+        }
+        if (a.dl_ddepth) {
+            const float td = a.tgt_depth ? a.tgt_depth[g] : 0.f;
+            const bool ind = in && td > 0.f;
+            const float kd = (ind && cd > 0.f) ? a.lambda_depth * inv_v / cd : 0.f;
+            const float rd = a.depth[g] - td;
+            a.dl_ddepth[g] = kd * (float)((rd > 0.f) - (rd < 0.f));
+            if (ind) ld += fabsf(rd);
+        }
+    }
+    block_add2(lr, ld, &a.sums[3 * v], &a.sums[3 * v + 1]);
+}
+
+// SSIM forward: local statistics of channel c over the tile, the weighted SSIM sum of the
+// view, and the partials k(q) dS/dmu_x, k(q) dS/dE[x^2], k(q) dS/dE[xy] with
+// k(q) = -lambda_ssim M(q) / (3 |M| views) (the gradient of lambda_ssim (1 - SSIM) / views).
+__global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
+    __shared__ float s_x[kInH][kInW], s_y[kInH][kInW];
+    __shared__ float s_h[5][kInH][kObjTX];
+    const int v = blockIdx.z;
+    const View& V = a.views[v];
+    const int x0 = blockIdx.x * kObjTX, y0 = blockIdx.y * kObjH;
+    if (x0 >= V.W || y0 >= V.H) return;   // (the whole block: no barrier is skipped by part of it)
+    const int t = threadIdx.y * kObjTX + threadIdx.x;
+    const int64_t P = (int64_t)V.W * V.H;
+    const uint32_t cm = a.counts[2 * v];
+    const float k = cm > 0 ? -a.lambda_ssim / (3.f * (float)cm * (float)a.n_views) : 0.f;
+    float ssum = 0.f;
+    for (int ch = 0; ch < 3; ch++) {
+        const float* c = a.rgb + 3 * V.pix_off + ch * P;
+        const float* tc = a.tgt_rgb + 3 * V.pix_off + ch * P;
+        for (int i = t; i < kInH * kInW; i += kObjTX * kObjTY) {
+            const int iy = i / kInW, ix = i - iy * kInW;
+            const int gx = x0 - kHalo + ix, gy = y0 - kHalo + iy;
+            float xv = 0.f, yv = 0.f;
+            if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
+                const int64_t p = (int64_t)gy * V.W + gx;
+                const bool in = a.mask ? a.mask[V.pix_off + p] != 0 : true;
+                xv = in ? c[p] : 0.f;
+                yv = in ? tc[p] : 0.f;
+            }
+            s_x[iy][ix] = xv;
+            s_y[iy][ix] = yv;
+        }
+        __syncthreads();
+        for (int i = t; i < kInH * kObjTX; i += kObjTX * kObjTY) {
+            const int iy = i / kObjTX, ix = i - iy * kObjTX;
+            float hx = 0.f, hy = 0.f, hxx = 0.f, hyy = 0.f, hxy = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2 * kHalo + 1; q++) {
+                const float w = a.win[q], xv = s_x[iy][ix + q], yv = s_y[iy][ix + q];
+                hx = fmaf(w, xv, hx);
+                hy = fmaf(w, yv, hy);
+                hxx = fmaf(w, xv * xv, hxx);
+                hyy = fmaf(w, yv * yv, hyy);
+                hxy = fmaf(w, xv * yv, hxy);
+            }
+            s_h[0][iy][ix] = hx; s_h[1][iy][ix] = hy; s_h[2][iy][ix] = hxx; s_h[3][iy][ix] = hyy; s_h[4][iy][ix] = hxy;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < kObjRows; rr++) {
+            const int oy = threadIdx.y * kObjRows + rr, ox = threadIdx.x;
+            const int gx = x0 + ox, gy = y0 + oy;
+            if (gx >= V.W || gy >= V.H) continue;
+            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2 * kHalo + 1; q++) {
+                const float w = a.win[q];
+                mx = fmaf(w, s_h[0][oy + q][ox], mx);
+                my = fmaf(w, s_h[1][oy + q][ox], my);
+                exx = fmaf(w, s_h[2][oy + q][ox], exx);
+                eyy = fmaf(w, s_h[3][oy + q][ox], eyy);
+                exy = fmaf(w, s_h[4][oy + q][ox], exy);
+            }
+            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+            const float A1 = 2.f * mx * my + kSsimC1, A2 = 2.f * sxy + kSsimC2;
+            const float B1 = mx * mx + my * my + kSsimC1, B2 = sxx + syy + kSsimC2;
+            const float inv = 1.f / (B1 * B2);
+            const float S = A1 * A2 * inv;
+            const int64_t p = (int64_t)gy * V.W + gx;
+            const bool in = a.mask ? a.mask[V.pix_off + p] != 0 : true;
+            const float kq = in ? k : 0.f;
+            if (in) ssum += S;
+            const float d_mu = 2.f * my * (A2 - A1) * inv - 2.f * mx * S * (1.f / B1 - 1.f / B2);
+            float* part = a.ssim_part + 9 * V.pix_off + (3 * ch) * P + p;
+            part[0] = kq * d_mu;
+            part[P] = kq * (-S / B2);
+            part[2 * P] = kq * (2.f * A1 * inv);
+        }
+        __syncthreads();   // the tile buffers are refilled for the next channel
+    }
+    block_add2(ssum, 0.f, &a.sums[3 * v + 2], nullptr);
+}
+
+// SSIM backward: dL/dx(p) = sum_q w(q - p) [P_mu(q) + 2 x(p) P_xx(q) + y(p) P_xy(q)], and
+// dL/dC = M dL/dx, added to the L1 gradient already in dl_drgb.
+__global__ void __launch_bounds__(kObjTX * kObjTY) ssim_bwd_kernel(ObjArgs a) {
+    __shared__ float s_p[3][kInH][kInW];
+    __shared__ float s_h[3][kInH][kObjTX];
+    const View& V = a.views[blockIdx.z];
+    const int x0 = blockIdx.x * kObjTX, y0 = blockIdx.y * kObjH;
+    if (x0 >= V.W || y0 >= V.H) return;
+    const int t = threadIdx.y * kObjTX + threadIdx.x;
+    const int64_t P = (int64_t)V.W * V.H;
+    for (int ch = 0; ch < 3; ch++) {
+        const float* part = a.ssim_part + 9 * V.pix_off + (3 * ch) * P;
+        for (int i = t; i < kInH * kInW; i += kObjTX * kObjTY) {
+            const int iy = i / kInW, ix = i - iy * kInW;
+            const int gx = x0 - kHalo + ix, gy = y0 - kHalo + iy;
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f;
+            if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
+                const int64_t p = (int64_t)gy * V.W + gx;
+                p0 = part[p]; p1 = part[P + p]; p2 = part[2 * P + p];
+            }
+            s_p[0][iy][ix] = p0; s_p[1][iy][ix] = p1; s_p[2][iy][ix] = p2;
+        }
+        __syncthreads();
+        for (int i = t; i < kInH * kObjTX; i += kObjTX * kObjTY) {
+            const int iy = i / kObjTX, ix = i - iy * kObjTX;
+            float h0 = 0.f, h1 = 0.f, h2 = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2 * kHalo + 1; q++) {
+                const float w = a.win[q];
+                h0 = fmaf(w, s_p[0][iy][ix + q], h0);
+                h1 = fmaf(w, s_p[1][iy][ix + q], h1);
+                h2 = fmaf(w, s_p[2][iy][ix + q], h2);
+            }
+            s_h[0][iy][ix] = h0; s_h[1][iy][ix] = h1; s_h[2][iy][ix] = h2;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < kObjRows; rr++) {
+            const int oy = threadIdx.y * kObjRows + rr, ox = threadIdx.x;
+            const int gx = x0 + ox, gy = y0 + oy;
+            if (gx >= V.W || gy >= V.H) continue;
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2 * kHalo + 1; q++) {
+                const float w = a.win[q];
+                c0 = fmaf(w, s_h[0][oy + q][ox], c0);
+                c1 = fmaf(w, s_h[1][oy + q][ox], c1);
+                c2 = fmaf(w, s_h[2][oy + q][ox], c2);
+            }
+            const int64_t p = (int64_t)gy * V.W + gx;
+            const bool in = a.mask ? a.mask[V.pix_off + p] != 0 : true;
+            if (!in) continue;
+            const float xv = a.rgb[3 * V.pix_off + ch * P + p], yv = a.tgt_rgb[3 * V.pix_off + ch * P + p];
+            float* dl = a.dl_drgb + 3 * V.pix_off + ch * P + p;
+            *dl += c0 + 2.f * xv * c1 + yv * c2;
+        }
+        __syncthreads();
+    }
+}
+
+static dim3 obj_grid(const ObjArgs& a, int tile_h) {
+    return dim3((unsigned)((a.max_w + kObjTX - 1) / kObjTX), (unsigned)((a.max_h + tile_h - 1) / tile_h),
+                (unsigned)a.n_views);
+}
+
+cudaError_t launch_render_mask(const ObjArgs& a, cudaStream_t st) {
+    if (a.n_views <= 0) return cudaSuccess;
+    render_mask_kernel<<<obj_grid(a, kObjTY), dim3(kObjTX, kObjTY), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const ObjArgs& a, cudaStream_t st) {
+    if (a.n_views <= 0) return cudaSuccess;
+    masked_l1_kernel<<<obj_grid(a, kObjTY), dim3(kObjTX, kObjTY), 0, st>>>(a);
+    if (a.lambda_ssim > 0.f) {
+        ssim_fwd_kernel<<<obj_grid(a, kObjH), dim3(kObjTX, kObjTY), 0, st>>>(a);
+        ssim_bwd_kernel<<<obj_grid(a, kObjH), dim3(kObjTX, kObjTY), 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// 1-D weights of the normalised 11-tap Gaussian (sigma 1.5), rounded once to FP32.
+void ssim_window(float (&w)[11]) {
+    double g[11], s = 0;
+    for (int i = 0; i < 11; i++) {
+        const double d = i - 5;
+        g[i] = exp(-d * d / (2.0 * 1.5 * 1.5));
+        s += g[i];
+    }
+    for (int i = 0; i < 11; i++) w[i] = (float)(g[i] / s);
+}
+
+}  // namespace gs

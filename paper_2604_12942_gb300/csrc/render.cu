@@ -53,13 +53,14 @@ cudaError_t launch_loss_count(const View* views, int n_views, const int64_t* pix
 }
 
 __global__ void loss_finalize_kernel(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
-                                     float lambda_depth, int has_depth, float* loss_out) {
+                                     float lambda_depth, float lambda_ssim, int has_depth, float* loss_out) {
     if (threadIdx.x != 0) return;
     double tot = 0;
     for (int v = 0; v < n_views; v++) {
         const double cm = counts[2 * v], cd = counts[2 * v + 1];
-        double l = cm > 0 ? lambda_rgb * sums[2 * v] / cm : 0.0;
-        if (has_depth && cd > 0) l += lambda_depth * sums[2 * v + 1] / cd;
+        double l = cm > 0 ? lambda_rgb * sums[3 * v] / cm : 0.0;
+        if (has_depth && cd > 0) l += lambda_depth * sums[3 * v + 1] / cd;
+        if (lambda_ssim > 0.f && cm > 0) l += lambda_ssim * (1.0 - sums[3 * v + 2] / (3.0 * cm));
         loss_out[v] = (float)l;
         tot += l;
     }
@@ -67,8 +68,9 @@ __global__ void loss_finalize_kernel(const double* sums, const uint32_t* counts,
 }
 
 cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
-                                 float lambda_depth, int has_depth, float* loss_out, cudaStream_t st) {
-    loss_finalize_kernel<<<1, 32, 0, st>>>(sums, counts, n_views, lambda_rgb, lambda_depth, has_depth, loss_out);
+                                 float lambda_depth, float lambda_ssim, int has_depth, float* loss_out, cudaStream_t st) {
+    loss_finalize_kernel<<<1, 32, 0, st>>>(sums, counts, n_views, lambda_rgb, lambda_depth, lambda_ssim, has_depth,
+                                           loss_out);
     return cudaGetLastError();
 }
 
@@ -398,8 +400,8 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
         if (threadIdx.x == 0) {
             double sr = 0, sd = 0;
             for (int k = 0; k < NW; k++) { sr += s_red[0][k]; sd += s_red[1][k]; }
-            if (sr != 0.0) atomicAdd(&a.loss_sums[2 * v], sr);
-            if (sd != 0.0) atomicAdd(&a.loss_sums[2 * v + 1], sd);
+            if (sr != 0.0) atomicAdd(&a.loss_sums[3 * v], sr);
+            if (sd != 0.0) atomicAdd(&a.loss_sums[3 * v + 1], sd);
         }
     }
 }
