@@ -344,3 +344,5 @@ def descriptor_cov(P, k, sigma=0.02):
 # The render-derived masks and the SSIM term of the objective (plain NumPy, FP64).
 from .objective import (erode, gaussian_window, masked_objective, render_mask,  # noqa: E402,F401
                         ssim_loss)
+# Map-size updates between mapping iterations: pruning plan, proximity dedup, compaction.
+from .mapupdate import apply_update, dedup_plan, logit_threshold, prune_plan  # noqa: E402,F401
