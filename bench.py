@@ -397,7 +397,10 @@ def run_gpu(args, rank, world):
 
 
 F1_LAMBDA_SSIM, F1_ERODE = 0.2, 2
-F1_BYTES_PER_PIXEL = 6 + 5 + 49 + 61 + 85   # mask, counts, L1 terms, SSIM forward, SSIM backward
+# mask (T, caller mask, mask out), counts (mask, target depth), SSIM forward with the L1 terms
+# (C, C~, M, D, D~ in; 9 partials, dL/dC, dL/dD out), SSIM backward (partials, C, C~, M in;
+# dL/dC read and written)
+F1_BYTES_PER_PIXEL = 6 + 5 + (12 + 12 + 1 + 8 + 36 + 16) + (36 + 24 + 1 + 24)
 
 
 def f1_measure(args, step, cams, trgb, tdep, planes0, cap, st, dev):

@@ -274,6 +274,40 @@ gs_status gs_objective(const gs_camera *cams, const gs_render_opts *opts, const 
                        const float *target_depth, const uint8_t *mask, float *dl_drgb,
                        float *dl_ddepth, float *loss_out, void *stream);
 
+/* f2 -- Map-size updates between mapping iterations (§III-C, optimization: new Gaussians pass
+ * a 3-D Euclidean proximity test before insertion; low-opacity Gaussians are pruned under a
+ * bounded removal ratio).  The three calls below read counts back and so synchronize `stream`.
+ * They share one caller-owned device scratch buffer of gs_map_update_scratch_bytes(n_map,
+ * n_new) bytes (256-byte multiple); calls that overlap on the GPU must not share it. */
+size_t gs_map_update_scratch_bytes(int64_t n_map, int64_t n_new);
+
+/* Prune plan: rows with sigmoid(logit) < opacity_min (decided on the FP32 logit against the
+ * FP32 logit of opacity_min) are candidates; at most floor(max_ratio * n) of them (in double
+ * precision) are removed,
+ * those with the smallest (logit, row index).  keep: device uint8 [n] (1 = stays); *n_keep
+ * (host) receives the rows kept.  Only g->opacity_logits is read. */
+gs_status gs_prune_plan(const gs_gaussians *g, float opacity_min, double max_ratio, uint8_t *keep,
+                        void *scratch, size_t scratch_bytes, int64_t *n_keep, void *stream);
+
+/* Proximity plan: accept[j] = 1 unless a mean of `map` lies strictly within `radius` of
+ * new_means[:, j] (squared distance summed in FP32 in x, y, z order; new means are not tested
+ * against each other).  new_means: device [3][n_new] planes; accept: device uint8 [n_new];
+ * *n_accept (host) receives the count accepted.  Only map->means is read. */
+gs_status gs_dedup_plan(const gs_gaussians *map, const float *new_means, int64_t n_new, float radius,
+                        uint8_t *accept, void *scratch, size_t scratch_bytes, int64_t *n_accept,
+                        void *stream);
+
+/* Update: out = the rows of `in` with keep != 0, in order, then the rows of new_rows (may be
+ * NULL) with accept != 0 (accept may be NULL = all), in order; m_out / v_out carry the kept
+ * rows' Adam moments and zeros for the new rows; tags_out (may be NULL) the kept rows' tags_in
+ * and the new rows' new_tags (either may be NULL = 0).  out->n (= m_out->n = v_out->n) must
+ * equal the rows kept plus accepted; all maps share sh_degree; outputs must not alias inputs. */
+gs_status gs_map_update(const gs_gaussians *in, const gs_gaussians *m_in, const gs_gaussians *v_in,
+                        const uint8_t *keep, const gs_gaussians *new_rows, const uint8_t *accept,
+                        const uint32_t *tags_in, const uint32_t *new_tags, gs_gaussians *out,
+                        gs_gaussians *m_out, gs_gaussians *v_out, uint32_t *tags_out, void *scratch,
+                        size_t scratch_bytes, void *stream);
+
 /* a6-a7 -- Analytic backward of gs_render_fwd and gs_project for upstream per-pixel
  * gradients dl_drgb [3*P], dl_ddepth [P] (dl_ddepth may be NULL).  Transmittance is
  * recomputed back to front from the stored final T (T_i = T_{i+1} / (1 - alpha_i)); no

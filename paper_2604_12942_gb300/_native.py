@@ -97,6 +97,13 @@ _SIGS = {
                         C.c_void_p, C.c_void_p], C.c_int),
     "gs_objective": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p] + [C.c_void_p] * 9,
                      C.c_int),
+    "gs_map_update_scratch_bytes": ([C.c_int64, C.c_int64], C.c_size_t),
+    "gs_prune_plan": ([C.POINTER(Gaussians), C.c_float, C.c_double, C.c_void_p, C.c_void_p, C.c_size_t,
+                       C.POINTER(C.c_int64), C.c_void_p], C.c_int),
+    "gs_dedup_plan": ([C.POINTER(Gaussians), C.c_void_p, C.c_int64, C.c_float, C.c_void_p, C.c_void_p, C.c_size_t,
+                       C.POINTER(C.c_int64), C.c_void_p], C.c_int),
+    "gs_map_update": ([C.POINTER(Gaussians)] * 3 + [C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p, C.c_void_p] +
+                      [C.POINTER(Gaussians)] * 3 + [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "gs_render_bwd": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p,
                        C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p], C.c_int),
     "gs_composite_bwd": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.c_void_p,

@@ -302,3 +302,57 @@ class MappingStep:
             self.release()
         except Exception:
             pass
+
+
+# -- map-size updates between mapping iterations (f2) -----------------------------------------
+def map_update_scratch(n_map, n_new=0, device="cuda") -> torch.Tensor:
+    return torch.empty(int(N.lib().gs_map_update_scratch_bytes(int(n_map), int(n_new))), dtype=torch.uint8,
+                       device=device)
+
+
+def prune_plan(planes, sh_degree, opacity_min=0.005, max_ratio=0.01, scratch=None):
+    """(keep uint8 [n], rows kept): low-opacity rows to remove, at most max_ratio of the map."""
+    n = planes.shape[1]
+    keep = torch.empty(n, dtype=torch.uint8, device=planes.device)
+    scratch = map_update_scratch(n, 0, planes.device) if scratch is None else scratch
+    nk = C.c_int64()
+    g = gaussians_struct(planes, sh_degree)
+    N.check(N.lib().gs_prune_plan(C.byref(g), float(opacity_min), float(max_ratio), _ptr(keep), _ptr(scratch),
+                                  scratch.numel(), C.byref(nk), _stream()), "gs_prune_plan")
+    return keep, nk.value
+
+
+def dedup_plan(planes, sh_degree, new_means, radius=0.05, scratch=None):
+    """(accept uint8 [n_new], accepted): new means [3, n_new] with no map mean within radius."""
+    new_means = new_means.contiguous()
+    n_new = new_means.shape[1]
+    accept = torch.empty(max(n_new, 1), dtype=torch.uint8, device=planes.device)[:n_new]
+    scratch = map_update_scratch(planes.shape[1], n_new, planes.device) if scratch is None else scratch
+    na = C.c_int64()
+    g = gaussians_struct(planes, sh_degree)
+    N.check(N.lib().gs_dedup_plan(C.byref(g), _ptr(new_means), n_new, float(radius), _ptr(accept), _ptr(scratch),
+                                  scratch.numel(), C.byref(na), _stream()), "gs_dedup_plan")
+    return accept, na.value
+
+
+def map_update(planes, m, v, sh_degree, keep, new_planes=None, accept=None, tags=None, new_tags=None,
+               scratch=None):
+    """New (planes, m, v[, tags]) tensors: kept rows in order, then accepted new rows (zero
+    moments)."""
+    n = planes.shape[1]
+    n_new = 0 if new_planes is None else new_planes.shape[1]
+    n_out = int(keep.sum()) + (0 if new_planes is None else (n_new if accept is None else int(accept.sum())))
+    P = planes.shape[0]
+    dev = planes.device
+    out, m_out, v_out = (torch.empty(P, n_out, device=dev) for _ in range(3))
+    tags_out = torch.empty(n_out, dtype=torch.int32, device=dev) if tags is not None else None
+    scratch = map_update_scratch(n, n_new, dev) if scratch is None else scratch
+    gs_ = [gaussians_struct(t, sh_degree) for t in (planes, m, v)]
+    go = [gaussians_struct(t, sh_degree) for t in (out, m_out, v_out)]
+    gn = gaussians_struct(new_planes.contiguous(), sh_degree) if new_planes is not None else None
+    N.check(N.lib().gs_map_update(C.byref(gs_[0]), C.byref(gs_[1]), C.byref(gs_[2]), _ptr(keep),
+                                  C.byref(gn) if gn is not None else None, _ptr(accept), _ptr(tags), _ptr(new_tags),
+                                  C.byref(go[0]), C.byref(go[1]), C.byref(go[2]), _ptr(tags_out), _ptr(scratch),
+                                  scratch.numel(), _stream()), "gs_map_update")
+    return (out, m_out, v_out) if tags is None else (out, m_out, v_out, tags_out)
+

@@ -906,4 +906,111 @@ gs_status gs_graph_destroy(gs_graph g) {
     return GS_OK;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// f2: map-size updates between mapping iterations (mapupdate.cu).
+// ---------------------------------------------------------------------------------------
+static int map_planes(const gs_gaussians* g, int64_t stride, const float** out) {
+    const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
+    int p = 0;
+    for (int k = 0; k < 3; k++) out[p++] = g->means + k * stride;
+    for (int k = 0; k < 3; k++) out[p++] = g->log_scales + k * stride;
+    for (int k = 0; k < 4; k++) out[p++] = g->quats + k * stride;
+    out[p++] = g->opacity_logits;
+    for (int k = 0; k < 3 * K; k++) out[p++] = g->sh + k * stride;
+    return p;
+}
+
+// The plans and the update read their counts back: they synchronize the caller's stream.
+static gs_status sync_counts(cudaStream_t st) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, "%s", cudaGetErrorString(e));
+    return GS_OK;
+}
+
+size_t gs_map_update_scratch_bytes(int64_t n_map, int64_t n_new) {
+    if (n_map < 0 || n_new < 0) return 0;
+    return map_update_scratch_bytes(n_map, n_new);
+}
+
+gs_status gs_prune_plan(const gs_gaussians* g, float opacity_min, double max_ratio, uint8_t* keep, void* scratch,
+                        size_t scratch_bytes, int64_t* n_keep, void* stream) {
+    gs_status s = check_gaussians(g, true);
+    if (s != GS_OK) return s;
+    if (!keep || !scratch || !n_keep) return fail(GS_ERR_INVALID_ARG, "keep, scratch and n_keep are required");
+    if (!(opacity_min > 0.f && opacity_min < 1.f) || !(max_ratio >= 0.0 && max_ratio <= 1.0))
+        return fail(GS_ERR_INVALID_ARG, "need 0 < opacity_min < 1 and 0 <= max_ratio <= 1");
+    if (g->n >= (int64_t)0xFFFFFFFFll) return fail(GS_ERR_INVALID_ARG, "n must be < 2^32");
+    if (scratch_bytes < map_update_scratch_bytes(g->n, 0)) return fail(GS_ERR_INVALID_ARG, "scratch too small");
+    // the FP32 logit of opacity_min: sigmoid(logit) < opacity_min iff logit < it
+    const float thr = (float)log((double)opacity_min / (1.0 - (double)opacity_min));
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long kept = 0;
+    GS_CUDA(launch_prune_plan(g->opacity_logits, g->n, thr, max_ratio, keep, scratch, &kept, st));
+    if ((s = sync_counts(st)) != GS_OK) return s;
+    *n_keep = (int64_t)kept;
+    return GS_OK;
+}
+
+gs_status gs_dedup_plan(const gs_gaussians* map, const float* new_means, int64_t n_new, float radius,
+                        uint8_t* accept, void* scratch, size_t scratch_bytes, int64_t* n_accept, void* stream) {
+    gs_status s = check_gaussians(map, false);
+    if (s != GS_OK) return s;
+    if (map->n > 0 && !map->means) return fail(GS_ERR_INVALID_ARG, "map means are NULL");
+    if (n_new < 0 || (n_new > 0 && (!new_means || !accept)) || !scratch || !n_accept)
+        return fail(GS_ERR_INVALID_ARG, "new_means, accept, scratch and n_accept are required");
+    if (!(radius > 0.f)) return fail(GS_ERR_INVALID_ARG, "radius must be > 0");
+    if (map->n >= (int64_t)0x7FFFFFFFll || n_new >= (int64_t)0x7FFFFFFFll) return fail(GS_ERR_INVALID_ARG, "sizes must be < 2^31");
+    if (scratch_bytes < map_update_scratch_bytes(map->n, n_new)) return fail(GS_ERR_INVALID_ARG, "scratch too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long acc = 0;
+    GS_CUDA(launch_dedup_plan(map->means, map->n, new_means, n_new, radius, accept, scratch, &acc, st));
+    if ((s = sync_counts(st)) != GS_OK) return s;
+    *n_accept = (int64_t)acc;
+    return GS_OK;
+}
+
+gs_status gs_map_update(const gs_gaussians* in, const gs_gaussians* m_in, const gs_gaussians* v_in, const uint8_t* keep,
+                        const gs_gaussians* new_rows, const uint8_t* accept, const uint32_t* tags_in,
+                        const uint32_t* new_tags, gs_gaussians* out, gs_gaussians* m_out, gs_gaussians* v_out,
+                        uint32_t* tags_out, void* scratch, size_t scratch_bytes, void* stream) {
+    gs_status s;
+    const gs_gaussians* need[6] = {in, m_in, v_in, out, m_out, v_out};
+    for (const gs_gaussians* g : need)
+        if ((s = check_gaussians(g, true)) != GS_OK) return s;
+    if (new_rows && (s = check_gaussians(new_rows, true)) != GS_OK) return s;
+    const int deg = in->sh_degree;
+    if (m_in->n != in->n || v_in->n != in->n || m_out->n != out->n || v_out->n != out->n ||
+        m_in->sh_degree != deg || v_in->sh_degree != deg || out->sh_degree != deg || m_out->sh_degree != deg ||
+        v_out->sh_degree != deg || (new_rows && new_rows->sh_degree != deg))
+        return fail(GS_ERR_INVALID_ARG, "the maps, moments and new rows must agree in n and sh_degree");
+    if (!keep || !scratch) return fail(GS_ERR_INVALID_ARG, "keep and scratch are required");
+    const int64_t n_new = new_rows ? new_rows->n : 0;
+    if (in->n >= (int64_t)0x7FFFFFFFll || n_new >= (int64_t)0x7FFFFFFFll) return fail(GS_ERR_INVALID_ARG, "sizes must be < 2^31");
+    if (scratch_bytes < map_update_scratch_bytes(in->n, n_new)) return fail(GS_ERR_INVALID_ARG, "scratch too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    MapUpdateArgs a;
+    memset(&a, 0, sizeof(a));
+    uint32_t totals[2] = {0, 0};
+    uint32_t *pk = nullptr, *pn = nullptr;
+    GS_CUDA(launch_map_scan(keep, in->n, new_rows ? accept : nullptr, n_new, scratch, &pk, &pn, totals, st));
+    if ((s = sync_counts(st)) != GS_OK) return s;
+    const int64_t n_acc = new_rows ? (accept ? (int64_t)totals[1] : n_new) : 0;
+    if (out->n != (int64_t)totals[0] + n_acc)
+        return fail(GS_ERR_INVALID_ARG, "out->n must be %lld (kept %u + accepted %lld), got %lld",
+                    (long long)((int64_t)totals[0] + n_acc), totals[0], (long long)n_acc, (long long)out->n);
+    a.n = in->n; a.n_new = n_new; a.n_out = out->n; a.n_keep = totals[0];
+    a.keep = keep; a.accept = new_rows ? accept : nullptr; a.pos_keep = pk; a.pos_new = pn;
+    a.n_planes = map_planes(in, in->n, a.in);
+    map_planes(m_in, in->n, a.m_in);
+    map_planes(v_in, in->n, a.v_in);
+    if (new_rows) map_planes(new_rows, n_new, a.nw);
+    map_planes(out, out->n, const_cast<const float**>(a.out));
+    map_planes(m_out, out->n, const_cast<const float**>(a.m_out));
+    map_planes(v_out, out->n, const_cast<const float**>(a.v_out));
+    a.tags_in = tags_in; a.new_tags = new_tags; a.tags_out = tags_out;
+    GS_CUDA(launch_compact(a, st));
+    return GS_OK;
+}
+
 }  // extern "C"

@@ -159,6 +159,34 @@ cudaError_t launch_render_mask(const ObjArgs& a, cudaStream_t st);
 cudaError_t launch_objective(const ObjArgs& a, cudaStream_t st);
 void ssim_window(float (&w)[11]);
 
+// Map-size updates (mapupdate.cu).
+constexpr int kMapMaxPlanes = 11 + 3 * 16;
+struct MapUpdateArgs {
+    int64_t n, n_new, n_out, n_keep;
+    int n_planes;
+    const uint8_t* keep;         // [n]
+    const uint8_t* accept;       // [n_new] or null (all accepted)
+    const uint32_t* pos_keep;    // exclusive scan of keep
+    const uint32_t* pos_new;     // exclusive scan of accept (null: identity)
+    const float* in[kMapMaxPlanes];
+    const float* m_in[kMapMaxPlanes];
+    const float* v_in[kMapMaxPlanes];
+    const float* nw[kMapMaxPlanes];
+    float* out[kMapMaxPlanes];
+    float* m_out[kMapMaxPlanes];
+    float* v_out[kMapMaxPlanes];
+    const uint32_t *tags_in, *new_tags;
+    uint32_t* tags_out;
+};
+size_t map_update_scratch_bytes(int64_t n_map, int64_t n_new);
+cudaError_t launch_prune_plan(const float* logits, int64_t n, float thr, double max_ratio, uint8_t* keep,
+                              void* scratch, unsigned long long* kept_host, cudaStream_t st);
+cudaError_t launch_dedup_plan(const float* map_means, int64_t n, const float* new_means, int64_t nq, float radius,
+                              uint8_t* accept, void* scratch, unsigned long long* accepted_host, cudaStream_t st);
+cudaError_t launch_map_scan(const uint8_t* keep, int64_t n, const uint8_t* accept, int64_t n_new, void* scratch,
+                            uint32_t** pos_keep, uint32_t** pos_new, uint32_t* totals_host, cudaStream_t st);
+cudaError_t launch_compact(const MapUpdateArgs& a, cudaStream_t st);
+
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st);
 // Compaction of the visible entries (touched > 0) in (view, Gaussian) order with their

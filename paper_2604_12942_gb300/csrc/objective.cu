@@ -23,30 +23,46 @@ constexpr int kInW = kObjTX + 2 * kHalo, kInH = kObjH + 2 * kHalo;
 constexpr float kSsimC1 = 0.01f * 0.01f, kSsimC2 = 0.03f * 0.03f;
 
 // Interior mask: [1 - T >= tau] eroded by the radius-r disk (outside the image counts as
-// outside the support), and the caller's mask.
+// outside the support), and the caller's mask.  The block thresholds its 32 x 8 pixels and a
+// halo of r once into shared memory, then every pixel tests the disk there.
+constexpr int kMaskMaxR = 16;
 __global__ void __launch_bounds__(kObjTX * kObjTY) render_mask_kernel(ObjArgs a) {
+    __shared__ uint8_t s_geo[kObjTY + 2 * kMaskMaxR][kObjTX + 2 * kMaskMaxR];
     const View& V = a.views[blockIdx.z];
-    const int x = blockIdx.x * kObjTX + threadIdx.x, y = blockIdx.y * kObjTY + threadIdx.y;
-    if (x >= V.W || y >= V.H) return;
-    const float* T = a.T_final + V.pix_off;
+    const int x0 = blockIdx.x * kObjTX, y0 = blockIdx.y * kObjTY;
+    if (x0 >= V.W || y0 >= V.H) return;   // (the whole block)
     const int r = a.r_erode;
+    const int tw = kObjTX + 2 * r, th = kObjTY + 2 * r;
+    const float* T = a.T_final + V.pix_off;
+    const int t = threadIdx.y * kObjTX + threadIdx.x;
+    for (int i = t; i < tw * th; i += kObjTX * kObjTY) {
+        const int iy = i / tw, ix = i - iy * tw;
+        const int gx = x0 - r + ix, gy = y0 - r + iy;
+        const bool inside = gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
+        s_geo[iy][ix] = inside && __fsub_rn(1.f, __ldg(T + (int64_t)gy * V.W + gx)) >= a.tau;
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= V.W || y >= V.H) return;
     bool in = true;
     for (int dy = -r; dy <= r; dy++) {
-        for (int dx = -r; dx <= r; dx++) {
-            if (dx * dx + dy * dy > r * r) continue;
-            const int xx = x + dx, yy = y + dy;
-            const bool inside = xx >= 0 && xx < V.W && yy >= 0 && yy < V.H;
-            in = in && inside && __fsub_rn(1.f, __ldg(T + (int64_t)yy * V.W + xx)) >= a.tau;
-        }
+        // half-width of the disk in row dy: the largest w with w^2 + dy^2 <= r^2
+        int w = 0;
+        while ((w + 1) * (w + 1) + dy * dy <= r * r) w++;
+        const uint8_t* row = &s_geo[threadIdx.y + r + dy][threadIdx.x + r];
+        for (int dx = -w; dx <= w; dx++) in = in && row[dx];
     }
     const int64_t g = V.pix_off + (int64_t)y * V.W + x;
     if (a.caller_mask) in = in && a.caller_mask[g] != 0;
     a.mask_out[g] = in ? 1 : 0;
 }
 
+// Block sums of two per-thread values, one FP64 atomic each (every thread of the block calls
+// it; the leading barrier lets it be called again right after).
 __device__ __forceinline__ void block_add2(float s0, float s1, double* dst0, double* dst1) {
     __shared__ double s_r[2][kObjTX * kObjTY / 32];
     const int t = threadIdx.y * kObjTX + threadIdx.x, lane = t & 31, w = t >> 5;
+    __syncthreads();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -95,9 +111,31 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) masked_l1_kernel(ObjArgs a) {
     block_add2(lr, ld, &a.sums[3 * v], &a.sums[3 * v + 1]);
 }
 
-// SSIM forward: local statistics of channel c over the tile, the weighted SSIM sum of the
-// view, and the partials k(q) dS/dmu_x, k(q) dS/dE[x^2], k(q) dS/dE[xy] with
-// k(q) = -lambda_ssim M(q) / (3 |M| views) (the gradient of lambda_ssim (1 - SSIM) / views).
+// Register-blocked separable passes over a tile (kInH x kInW inputs -> kObjH x kObjTX outputs):
+// a horizontal task makes 4 consecutive outputs of one row from 14 inputs held in registers, a
+// vertical task 2 consecutive rows of one column from 12.
+constexpr int kSeg = 4;                       // horizontal outputs per task
+constexpr int kSegs = kObjTX / kSeg;          // tasks per row
+constexpr int kHIn = kSeg + 2 * kHalo;        // inputs per horizontal task
+
+__device__ __forceinline__ void hpass(const float (&win)[11], const float* in, float* out) {
+    float v[kHIn];
+#pragma unroll
+    for (int k = 0; k < kHIn; k++) v[k] = in[k];
+#pragma unroll
+    for (int o = 0; o < kSeg; o++) {
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 2 * kHalo + 1; q++) acc = fmaf(win[q], v[o + q], acc);
+        out[o] = acc;
+    }
+}
+
+// SSIM forward, fused with the masked L1 terms.  Per channel: the five local moments of
+// x = C M and y = C~ M, the SSIM map (summed over M), and the partials
+// k(q) dS/dmu_x, k(q) dS/dE[x^2], k(q) dS/dE[xy], k(q) = -lambda_ssim M(q) / (3 |M| views)
+// (the gradient of lambda_ssim (1 - SSIM) / views); and at the same output pixels the L1
+// colour terms (and, with the first channel, the depth term) with the epilogue's arithmetic.
 __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
     __shared__ float s_x[kInH][kInW], s_y[kInH][kInW];
     __shared__ float s_h[5][kInH][kObjTX];
@@ -108,8 +146,12 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
     const int t = threadIdx.y * kObjTX + threadIdx.x;
     const int64_t P = (int64_t)V.W * V.H;
     const uint32_t cm = a.counts[2 * v];
+    const float cd = (float)a.counts[2 * v + 1];
+    const float inv_v = 1.0f / (float)a.n_views;
     const float k = cm > 0 ? -a.lambda_ssim / (3.f * (float)cm * (float)a.n_views) : 0.f;
-    float ssum = 0.f;
+    const float kr = cm > 0 ? a.lambda_rgb * inv_v / (float)cm : 0.f;
+    const int ox = t & 31, oy0 = (t >> 5) * kObjRows;   // vertical task: column, first row
+    float ssum = 0.f, lr = 0.f, ld = 0.f;
     for (int ch = 0; ch < 3; ch++) {
         const float* c = a.rgb + 3 * V.pix_off + ch * P;
         const float* tc = a.tgt_rgb + 3 * V.pix_off + ch * P;
@@ -127,36 +169,43 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
             s_y[iy][ix] = yv;
         }
         __syncthreads();
-        for (int i = t; i < kInH * kObjTX; i += kObjTX * kObjTY) {
-            const int iy = i / kObjTX, ix = i - iy * kObjTX;
-            float hx = 0.f, hy = 0.f, hxx = 0.f, hyy = 0.f, hxy = 0.f;
+        for (int task = t; task < kInH * kSegs; task += kObjTX * kObjTY) {
+            const int iy = task / kSegs, cx = (task - iy * kSegs) * kSeg;
+            float xs[kHIn], ys[kHIn], tmp[kHIn];
 #pragma unroll
-            for (int q = 0; q < 2 * kHalo + 1; q++) {
-                const float w = a.win[q], xv = s_x[iy][ix + q], yv = s_y[iy][ix + q];
-                hx = fmaf(w, xv, hx);
-                hy = fmaf(w, yv, hy);
-                hxx = fmaf(w, xv * xv, hxx);
-                hyy = fmaf(w, yv * yv, hyy);
-                hxy = fmaf(w, xv * yv, hxy);
-            }
-            s_h[0][iy][ix] = hx; s_h[1][iy][ix] = hy; s_h[2][iy][ix] = hxx; s_h[3][iy][ix] = hyy; s_h[4][iy][ix] = hxy;
+            for (int q = 0; q < kHIn; q++) { xs[q] = s_x[iy][cx + q]; ys[q] = s_y[iy][cx + q]; }
+            hpass(a.win, xs, &s_h[0][iy][cx]);
+            hpass(a.win, ys, &s_h[1][iy][cx]);
+#pragma unroll
+            for (int q = 0; q < kHIn; q++) tmp[q] = xs[q] * xs[q];
+            hpass(a.win, tmp, &s_h[2][iy][cx]);
+#pragma unroll
+            for (int q = 0; q < kHIn; q++) tmp[q] = ys[q] * ys[q];
+            hpass(a.win, tmp, &s_h[3][iy][cx]);
+#pragma unroll
+            for (int q = 0; q < kHIn; q++) tmp[q] = xs[q] * ys[q];
+            hpass(a.win, tmp, &s_h[4][iy][cx]);
         }
         __syncthreads();
+        float mo[5][kObjRows];
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            float col[kObjRows + 2 * kHalo];
+#pragma unroll
+            for (int q = 0; q < kObjRows + 2 * kHalo; q++) col[q] = s_h[m][oy0 + q][ox];
+#pragma unroll
+            for (int rr = 0; rr < kObjRows; rr++) {
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < 2 * kHalo + 1; q++) acc = fmaf(a.win[q], col[rr + q], acc);
+                mo[m][rr] = acc;
+            }
+        }
 #pragma unroll
         for (int rr = 0; rr < kObjRows; rr++) {
-            const int oy = threadIdx.y * kObjRows + rr, ox = threadIdx.x;
-            const int gx = x0 + ox, gy = y0 + oy;
+            const int gx = x0 + ox, gy = y0 + oy0 + rr;
             if (gx >= V.W || gy >= V.H) continue;
-            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
-#pragma unroll
-            for (int q = 0; q < 2 * kHalo + 1; q++) {
-                const float w = a.win[q];
-                mx = fmaf(w, s_h[0][oy + q][ox], mx);
-                my = fmaf(w, s_h[1][oy + q][ox], my);
-                exx = fmaf(w, s_h[2][oy + q][ox], exx);
-                eyy = fmaf(w, s_h[3][oy + q][ox], eyy);
-                exy = fmaf(w, s_h[4][oy + q][ox], exy);
-            }
+            const float mx = mo[0][rr], my = mo[1][rr], exx = mo[2][rr], eyy = mo[3][rr], exy = mo[4][rr];
             const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
             const float A1 = 2.f * mx * my + kSsimC1, A2 = 2.f * sxy + kSsimC2;
             const float B1 = mx * mx + my * my + kSsimC1, B2 = sxx + syy + kSsimC2;
@@ -171,9 +220,24 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
             part[0] = kq * d_mu;
             part[P] = kq * (-S / B2);
             part[2 * P] = kq * (2.f * A1 * inv);
+            // L1 colour term of this channel (x, y are C, C~ inside the mask)
+            const float r = s_x[oy0 + rr + kHalo][ox + kHalo] - s_y[oy0 + rr + kHalo][ox + kHalo];
+            const float krgb = in ? kr : 0.f;
+            a.dl_drgb[3 * V.pix_off + ch * P + p] = krgb * (float)((r > 0.f) - (r < 0.f));
+            if (in) lr += fabsf(r);
+            if (ch == 0 && a.dl_ddepth) {
+                const int64_t g = V.pix_off + p;
+                const float td = a.tgt_depth ? a.tgt_depth[g] : 0.f;
+                const bool ind = in && td > 0.f;
+                const float kd = (ind && cd > 0.f) ? a.lambda_depth * inv_v / cd : 0.f;
+                const float rd = a.depth[g] - td;
+                a.dl_ddepth[g] = kd * (float)((rd > 0.f) - (rd < 0.f));
+                if (ind) ld += fabsf(rd);
+            }
         }
         __syncthreads();   // the tile buffers are refilled for the next channel
     }
+    block_add2(lr, ld, &a.sums[3 * v], &a.sums[3 * v + 1]);
     block_add2(ssum, 0.f, &a.sums[3 * v + 2], nullptr);
 }
 
@@ -187,6 +251,7 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_bwd_kernel(ObjArgs a) {
     if (x0 >= V.W || y0 >= V.H) return;
     const int t = threadIdx.y * kObjTX + threadIdx.x;
     const int64_t P = (int64_t)V.W * V.H;
+    const int ox = t & 31, oy0 = (t >> 5) * kObjRows;
     for (int ch = 0; ch < 3; ch++) {
         const float* part = a.ssim_part + 9 * V.pix_off + (3 * ch) * P;
         for (int i = t; i < kInH * kInW; i += kObjTX * kObjTY) {
@@ -200,38 +265,36 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_bwd_kernel(ObjArgs a) {
             s_p[0][iy][ix] = p0; s_p[1][iy][ix] = p1; s_p[2][iy][ix] = p2;
         }
         __syncthreads();
-        for (int i = t; i < kInH * kObjTX; i += kObjTX * kObjTY) {
-            const int iy = i / kObjTX, ix = i - iy * kObjTX;
-            float h0 = 0.f, h1 = 0.f, h2 = 0.f;
-#pragma unroll
-            for (int q = 0; q < 2 * kHalo + 1; q++) {
-                const float w = a.win[q];
-                h0 = fmaf(w, s_p[0][iy][ix + q], h0);
-                h1 = fmaf(w, s_p[1][iy][ix + q], h1);
-                h2 = fmaf(w, s_p[2][iy][ix + q], h2);
-            }
-            s_h[0][iy][ix] = h0; s_h[1][iy][ix] = h1; s_h[2][iy][ix] = h2;
+        for (int task = t; task < 3 * kInH * kSegs; task += kObjTX * kObjTY) {
+            const int m = task / (kInH * kSegs), rest = task - m * (kInH * kSegs);
+            const int iy = rest / kSegs, cx = (rest - iy * kSegs) * kSeg;
+            hpass(a.win, &s_p[m][iy][cx], &s_h[m][iy][cx]);
         }
         __syncthreads();
+        float cv[3][kObjRows];
+#pragma unroll
+        for (int m = 0; m < 3; m++) {
+            float col[kObjRows + 2 * kHalo];
+#pragma unroll
+            for (int q = 0; q < kObjRows + 2 * kHalo; q++) col[q] = s_h[m][oy0 + q][ox];
+#pragma unroll
+            for (int rr = 0; rr < kObjRows; rr++) {
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < 2 * kHalo + 1; q++) acc = fmaf(a.win[q], col[rr + q], acc);
+                cv[m][rr] = acc;
+            }
+        }
 #pragma unroll
         for (int rr = 0; rr < kObjRows; rr++) {
-            const int oy = threadIdx.y * kObjRows + rr, ox = threadIdx.x;
-            const int gx = x0 + ox, gy = y0 + oy;
+            const int gx = x0 + ox, gy = y0 + oy0 + rr;
             if (gx >= V.W || gy >= V.H) continue;
-            float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-#pragma unroll
-            for (int q = 0; q < 2 * kHalo + 1; q++) {
-                const float w = a.win[q];
-                c0 = fmaf(w, s_h[0][oy + q][ox], c0);
-                c1 = fmaf(w, s_h[1][oy + q][ox], c1);
-                c2 = fmaf(w, s_h[2][oy + q][ox], c2);
-            }
             const int64_t p = (int64_t)gy * V.W + gx;
             const bool in = a.mask ? a.mask[V.pix_off + p] != 0 : true;
             if (!in) continue;
             const float xv = a.rgb[3 * V.pix_off + ch * P + p], yv = a.tgt_rgb[3 * V.pix_off + ch * P + p];
             float* dl = a.dl_drgb + 3 * V.pix_off + ch * P + p;
-            *dl += c0 + 2.f * xv * c1 + yv * c2;
+            *dl += cv[0][rr] + 2.f * xv * cv[1][rr] + yv * cv[2][rr];
         }
         __syncthreads();
     }
@@ -250,10 +313,12 @@ cudaError_t launch_render_mask(const ObjArgs& a, cudaStream_t st) {
 
 cudaError_t launch_objective(const ObjArgs& a, cudaStream_t st) {
     if (a.n_views <= 0) return cudaSuccess;
-    masked_l1_kernel<<<obj_grid(a, kObjTY), dim3(kObjTX, kObjTY), 0, st>>>(a);
     if (a.lambda_ssim > 0.f) {
+        // (the L1 terms ride along in the SSIM forward, which holds C and C~ at every pixel)
         ssim_fwd_kernel<<<obj_grid(a, kObjH), dim3(kObjTX, kObjTY), 0, st>>>(a);
         ssim_bwd_kernel<<<obj_grid(a, kObjH), dim3(kObjTX, kObjTY), 0, st>>>(a);
+    } else {
+        masked_l1_kernel<<<obj_grid(a, kObjTY), dim3(kObjTX, kObjTY), 0, st>>>(a);
     }
     return cudaGetLastError();
 }
