@@ -346,3 +346,5 @@ from .objective import (erode, gaussian_window, masked_objective, render_mask,  
                         ssim_loss)
 # Map-size updates between mapping iterations: pruning plan, proximity dedup, compaction.
 from .mapupdate import apply_update, dedup_plan, logit_threshold, prune_plan  # noqa: E402,F401
+# Gaussian-GICP loop registration (target set, planar covariances, Gauss-Newton on SE(3)).
+from . import gicp  # noqa: E402,F401
