@@ -308,6 +308,41 @@ gs_status gs_map_update(const gs_gaussians *in, const gs_gaussians *m_in, const 
                         gs_gaussians *m_out, gs_gaussians *v_out, uint32_t *tags_out, void *scratch,
                         size_t scratch_bytes, void *stream);
 
+/* f3 -- Gaussian-GICP loop registration (§III-D: target-set, residual, covariance and loop-pose
+ * equations).  Calls synchronize `stream`; their scratch is a caller-owned device buffer of
+ * gs_gicp_scratch_bytes(n of the target map) bytes. */
+size_t gs_gicp_scratch_bytes(int64_t n_target_map);
+
+/* Target set around a historical loopframe: target_flag[i] = 1 if, for some query view k,
+ * the mean projects inside its image (z > near_z, 0 <= u < width, 0 <= v < height, u = fx x/z
+ * + cx, v = fy y/z + cy, all in FP32) and lies closer than d_max to the view's camera centre
+ * (squared distance in FP32), and source_flag[i] == 0 (source_flag may be NULL).  views: host
+ * array of 1..GS_MAX_VIEWS cameras; target_flag: device uint8 [n]; *n_target: host count. */
+gs_status gs_gicp_target_set(const gs_gaussians *map, const gs_camera *views, int32_t n_views,
+                             float near_z, float d_max, const uint8_t *source_flag,
+                             uint8_t *target_flag, void *scratch, size_t scratch_bytes,
+                             int64_t *n_target, void *stream);
+
+typedef struct {
+    double T[12];      /* row-major 3 x 4 [R | t]: maps source means onto target means */
+    double cost;       /* sum of r^T Omega r at the final correspondences */
+    int64_t n_corr;    /* correspondences at the final T */
+    int32_t iters;     /* Gauss-Newton iterations taken */
+    int32_t converged; /* 1 if the last update was below eps */
+} gs_gicp_result;
+
+/* Registration of the source rows (src_flag != 0, or all if NULL) of `src` onto the target rows
+ * of `tar`: Gauss-Newton on sum r^T (Sigma~_n + R Sigma~_m R^T)^-1 r, r = mu_n - T mu_m, with
+ * Sigma~ the planar form of each covariance (eigenvalues 1, 1, 1e-3, the smallest-scale axis
+ * getting 1e-3) and the weights held fixed within an iteration; correspondences: the nearest
+ * target mean within d_corr of T mu_m (FP32 squared distance; lower row on ties); update
+ * T <- Exp(xi) T, xi = (rho, phi); stops when |xi| < eps or after max_iters.  T_init: host
+ * row-major 3 x 4; result: host. */
+gs_status gs_gicp_register(const gs_gaussians *src, const uint8_t *src_flag, const gs_gaussians *tar,
+                           const uint8_t *tar_flag, const double T_init[12], float d_corr,
+                           int32_t max_iters, double eps, gs_gicp_result *result, void *scratch,
+                           size_t scratch_bytes, void *stream);
+
 /* a6-a7 -- Analytic backward of gs_render_fwd and gs_project for upstream per-pixel
  * gradients dl_drgb [3*P], dl_ddepth [P] (dl_ddepth may be NULL).  Transmittance is
  * recomputed back to front from the stored final T (T_i = T_{i+1} / (1 - alpha_i)); no

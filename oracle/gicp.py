@@ -51,8 +51,8 @@ def target_set(means, cams, near_z=0.2, d_max=20.0, source_flag=None):
     f32 = np.float32
     dmax2 = f32(d_max) * f32(d_max)
     for cam in cams:
-        R = np.asarray(cam["R_cw"], dtype=np.float32).reshape(3, 3)
-        t = np.asarray(cam["t_cw"], dtype=np.float32)
+        R = np.asarray(cam["R"], dtype=np.float32).reshape(3, 3)
+        t = np.asarray(cam["t"], dtype=np.float32)
         # p_c = R mu + t, each row summed left to right in FP32
         pc = [((R[r, 0] * M[0] + R[r, 1] * M[1]).astype(f32) + (R[r, 2] * M[2]).astype(f32)).astype(f32) + t[r]
               for r in range(3)]
@@ -62,8 +62,11 @@ def target_set(means, cams, near_z=0.2, d_max=20.0, source_flag=None):
             u = (f32(cam["fx"]) * pc[0] / z).astype(f32) + f32(cam["cx"])
             v = (f32(cam["fy"]) * pc[1] / z).astype(f32) + f32(cam["cy"])
         inside = (z > f32(near_z)) & (u >= 0) & (u < f32(cam["width"])) & (v >= 0) & (v < f32(cam["height"]))
-        # camera centre c = -R^T t (FP64, rounded to FP32 once)
-        c = (-(np.asarray(cam["R_cw"], dtype=np.float64).reshape(3, 3).T @ np.asarray(cam["t_cw"], np.float64))).astype(f32)
+        # camera centre c = -R^T t from the FP32 pose (as the camera record holds it), in FP64,
+        # rounded to FP32 once
+        R64 = np.asarray(cam["R"], dtype=np.float32).reshape(3, 3).astype(np.float64)
+        t64 = np.asarray(cam["t"], dtype=np.float32).astype(np.float64)
+        c = (-(R64.T @ t64)).astype(f32)
         d = [(M[k] - c[k]).astype(f32) for k in range(3)]
         d2 = ((d[0] * d[0]).astype(f32) + (d[1] * d[1]).astype(f32)).astype(f32) + (d[2] * d[2]).astype(f32)
         flag |= inside & (d2.astype(f32) < dmax2)

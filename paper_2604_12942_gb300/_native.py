@@ -35,6 +35,11 @@ class RenderOpts(C.Structure):
                 ("mask_erode", C.c_int32)]
 
 
+class GicpResult(C.Structure):
+    _fields_ = [("T", C.c_double * 12), ("cost", C.c_double), ("n_corr", C.c_int64), ("iters", C.c_int32),
+                ("converged", C.c_int32)]
+
+
 class WsLayout(C.Structure):
     _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "touched", "scan_tmp",
                                           "ekeys0", "ekeys1", "evals0", "evals1", "keys0", "keys1", "vals0", "vals1", "pair_mask", "emit_tmp", "sort_tmp", "ranges", "T_final",
@@ -104,6 +109,11 @@ _SIGS = {
                        C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "gs_map_update": ([C.POINTER(Gaussians)] * 3 + [C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p, C.c_void_p] +
                       [C.POINTER(Gaussians)] * 3 + [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "gs_gicp_scratch_bytes": ([C.c_int64], C.c_size_t),
+    "gs_gicp_target_set": ([C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32, C.c_float, C.c_float, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int64), C.c_void_p], C.c_int),
+    "gs_gicp_register": ([C.POINTER(Gaussians), C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.POINTER(C.c_double),
+                          C.c_float, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "gs_render_bwd": ([C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p,
                        C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.c_void_p], C.c_int),
     "gs_composite_bwd": ([C.POINTER(Camera), C.POINTER(RenderOpts), C.POINTER(WsLayout), C.c_void_p, C.c_void_p,

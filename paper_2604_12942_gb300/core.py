@@ -356,3 +356,41 @@ def map_update(planes, m, v, sh_degree, keep, new_planes=None, accept=None, tags
                                   scratch.numel(), _stream()), "gs_map_update")
     return (out, m_out, v_out) if tags is None else (out, m_out, v_out, tags_out)
 
+
+# -- Gaussian-GICP loop registration (f3) -------------------------------------------------------
+def gicp_target_set(planes, sh_degree, cams, near_z=0.2, d_max=20.0, source_flag=None, scratch=None):
+    """(target_flag uint8 [n], count): map rows seen by some query view, within d_max of it,
+    outside the source set."""
+    n = planes.shape[1]
+    flag = torch.empty(max(n, 1), dtype=torch.uint8, device=planes.device)[:n]
+    scratch = gicp_scratch(0, planes.device) if scratch is None else scratch
+    cnt = C.c_int64()
+    g = gaussians_struct(planes, sh_degree)
+    N.check(N.lib().gs_gicp_target_set(C.byref(g), camera_array(cams), len(cams), float(near_z), float(d_max),
+                                       _ptr(source_flag), _ptr(flag), _ptr(scratch), scratch.numel(), C.byref(cnt),
+                                       _stream()), "gs_gicp_target_set")
+    return flag, cnt.value
+
+
+def gicp_scratch(n_target_map, device="cuda") -> torch.Tensor:
+    return torch.empty(int(N.lib().gs_gicp_scratch_bytes(int(n_target_map))), dtype=torch.uint8, device=device)
+
+
+def gicp_register(src_planes, src_flag, tar_planes, tar_flag, sh_degree, T_init=None, d_corr=1.0, max_iters=30,
+                  eps=1e-7, scratch=None):
+    """Loop transform (4 x 4 numpy) mapping the source rows onto the target rows, and the
+    result record (cost, correspondences, iterations, converged)."""
+    import numpy as np
+    T0 = np.eye(4) if T_init is None else np.asarray(T_init, dtype=np.float64)
+    t12 = (C.c_double * 12)(*T0[:3, :4].reshape(-1).tolist())
+    scratch = gicp_scratch(tar_planes.shape[1], tar_planes.device) if scratch is None else scratch
+    res = N.GicpResult()
+    gs_ = gaussians_struct(src_planes, sh_degree)
+    gt = gaussians_struct(tar_planes, sh_degree)
+    N.check(N.lib().gs_gicp_register(C.byref(gs_), _ptr(src_flag), C.byref(gt), _ptr(tar_flag), t12, float(d_corr),
+                                     int(max_iters), float(eps), C.byref(res), _ptr(scratch), scratch.numel(),
+                                     _stream()), "gs_gicp_register")
+    T = np.eye(4)
+    T[:3, :4] = np.array(list(res.T)).reshape(3, 4)
+    return T, res
+

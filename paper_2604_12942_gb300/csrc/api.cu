@@ -1013,4 +1013,164 @@ gs_status gs_map_update(const gs_gaussians* in, const gs_gaussians* m_in, const 
     return GS_OK;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// f3: Gaussian-GICP loop registration (gicp.cu); host side: 6 x 6 solves and SE(3) updates.
+// ---------------------------------------------------------------------------------------
+static GicpMap gicp_map(const gs_gaussians* g) {
+    GicpMap m;
+    m.n = g->n; m.means = g->means; m.log_scales = g->log_scales; m.quats = g->quats;
+    return m;
+}
+
+size_t gs_gicp_scratch_bytes(int64_t n_target_map) {
+    if (n_target_map < 0) return 0;
+    return gicp_scratch_bytes(n_target_map);
+}
+
+gs_status gs_gicp_target_set(const gs_gaussians* map, const gs_camera* views, int32_t n_views, float near_z,
+                             float d_max, const uint8_t* source_flag, uint8_t* target_flag, void* scratch,
+                             size_t scratch_bytes, int64_t* n_target, void* stream) {
+    gs_status s = check_gaussians(map, false);
+    if (s != GS_OK) return s;
+    if (map->n > 0 && !map->means) return fail(GS_ERR_INVALID_ARG, "map means are NULL");
+    if (n_views < 1 || n_views > GS_MAX_VIEWS || !views) return fail(GS_ERR_INVALID_ARG, "need 1..%d views", GS_MAX_VIEWS);
+    if (!target_flag || !scratch || !n_target) return fail(GS_ERR_INVALID_ARG, "target_flag, scratch and n_target are required");
+    if (!(d_max > 0.f) || !(near_z >= 0.f)) return fail(GS_ERR_INVALID_ARG, "need d_max > 0 and near_z >= 0");
+    if (scratch_bytes < gicp_scratch_bytes(0)) return fail(GS_ERR_INVALID_ARG, "scratch too small");
+    GicpView gv[GS_MAX_VIEWS];
+    for (int k = 0; k < n_views; k++) {
+        const gs_camera& c = views[k];
+        for (int j = 0; j < 9; j++) gv[k].R[j] = c.R_cw[j];
+        for (int j = 0; j < 3; j++) gv[k].t[j] = c.t_cw[j];
+        // camera centre -R^T t in FP64, rounded once
+        for (int j = 0; j < 3; j++) {
+            double v = 0;
+            for (int r = 0; r < 3; r++) v -= (double)c.R_cw[3 * r + j] * (double)c.t_cw[r];
+            gv[k].c[j] = (float)v;
+        }
+        gv[k].fx = c.fx; gv[k].fy = c.fy; gv[k].cx = c.cx; gv[k].cy = c.cy;
+        gv[k].W = (float)c.width; gv[k].H = (float)c.height;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long cnt = 0;
+    GS_CUDA(launch_gicp_target_set(gicp_map(map), gv, n_views, near_z, d_max * d_max, source_flag, target_flag, scratch,
+                                   &cnt, st));
+    if ((s = sync_counts(st)) != GS_OK) return s;
+    *n_target = (int64_t)cnt;
+    return GS_OK;
+}
+
+// (rho, phi) -> 4 x 4 rigid transform
+static void se3_exp(const double xi[6], double T[16]) {
+    const double* rho = xi;
+    const double* phi = xi + 3;
+    const double th = sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+    const double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
+    double K2[9];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+    double A, B, C;
+    if (th < 1e-12) { A = 1.0; B = 0.5; C = 1.0 / 6.0; }
+    else { A = sin(th) / th; B = (1 - cos(th)) / (th * th); C = (1 - A) / (th * th); }
+    double R[9], V[9];
+    for (int k = 0; k < 9; k++) {
+        const double I = (k % 4 == 0) ? 1.0 : 0.0;
+        R[k] = I + A * K[k] + B * K2[k];
+        V[k] = I + B * K[k] + C * K2[k];
+    }
+    if (th < 1e-12) for (int k = 0; k < 9; k++) { R[k] = ((k % 4 == 0) ? 1.0 : 0.0) + K[k]; V[k] = ((k % 4 == 0) ? 1.0 : 0.0) + 0.5 * K[k]; }
+    for (int k = 0; k < 16; k++) T[k] = 0;
+    for (int r = 0; r < 3; r++) {
+        for (int c = 0; c < 3; c++) T[4 * r + c] = R[3 * r + c];
+        T[4 * r + 3] = V[3 * r] * rho[0] + V[3 * r + 1] * rho[1] + V[3 * r + 2] * rho[2];
+    }
+    T[15] = 1;
+}
+
+// Solves H x = b (6 x 6, symmetric positive definite) by Cholesky; false if not positive.
+static bool solve6(const double H[36], const double b[6], double x[6]) {
+    double L[36] = {0};
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j <= i; j++) {
+            double s = H[6 * i + j];
+            for (int k = 0; k < j; k++) s -= L[6 * i + k] * L[6 * j + k];
+            if (i == j) {
+                if (!(s > 0)) return false;
+                L[6 * i + i] = sqrt(s);
+            } else {
+                L[6 * i + j] = s / L[6 * j + j];
+            }
+        }
+    double y[6];
+    for (int i = 0; i < 6; i++) {
+        double s = b[i];
+        for (int k = 0; k < i; k++) s -= L[6 * i + k] * y[k];
+        y[i] = s / L[6 * i + i];
+    }
+    for (int i = 5; i >= 0; i--) {
+        double s = y[i];
+        for (int k = i + 1; k < 6; k++) s -= L[6 * k + i] * x[k];
+        x[i] = s / L[6 * i + i];
+    }
+    return true;
+}
+
+gs_status gs_gicp_register(const gs_gaussians* src, const uint8_t* src_flag, const gs_gaussians* tar,
+                           const uint8_t* tar_flag, const double T_init[12], float d_corr, int32_t max_iters,
+                           double eps, gs_gicp_result* result, void* scratch, size_t scratch_bytes, void* stream) {
+    gs_status s;
+    if ((s = check_gaussians(src, true)) != GS_OK) return s;
+    if ((s = check_gaussians(tar, true)) != GS_OK) return s;
+    if (!T_init || !result || !scratch) return fail(GS_ERR_INVALID_ARG, "T_init, result and scratch are required");
+    if (!(d_corr > 0.f) || max_iters < 1 || !(eps > 0.0)) return fail(GS_ERR_INVALID_ARG, "need d_corr > 0, max_iters >= 1, eps > 0");
+    if (tar->n >= (int64_t)0x7FFFFFFFll || src->n >= (int64_t)0x7FFFFFFFll) return fail(GS_ERR_INVALID_ARG, "sizes must be < 2^31");
+    if (scratch_bytes < gicp_scratch_bytes(tar->n)) return fail(GS_ERR_INVALID_ARG, "scratch too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    const GicpMap gs_src = gicp_map(src), gs_tar = gicp_map(tar);
+    GS_CUDA(launch_gicp_build(gs_tar, tar_flag, d_corr, scratch, st));
+    double T[16];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 4; c++) T[4 * r + c] = T_init[4 * r + c];
+    T[12] = T[13] = T[14] = 0; T[15] = 1;
+    double acc[29];
+    auto evaluate = [&]() -> cudaError_t {
+        const double R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+        const double t[3] = {T[3], T[7], T[11]};
+        return launch_gicp_normal_eq(gs_src, src_flag, gs_tar, d_corr, R, t, scratch, acc, st);
+    };
+    int it = 0;
+    bool converged = false;
+    for (it = 1; it <= max_iters; it++) {
+        GS_CUDA(evaluate());
+        if (acc[28] < 6) break;
+        double H[36], g[6], xi[6];
+        int k = 0;
+        for (int r = 0; r < 6; r++)
+            for (int c = r; c < 6; c++) { H[6 * r + c] = acc[k]; H[6 * c + r] = acc[k]; k++; }
+        for (int r = 0; r < 6; r++) g[r] = -acc[21 + r];
+        if (!solve6(H, g, xi)) break;
+        double E[16], Tn[16];
+        se3_exp(xi, E);
+        for (int r = 0; r < 4; r++)
+            for (int c = 0; c < 4; c++) {
+                double v = 0;
+                for (int e = 0; e < 4; e++) v += E[4 * r + e] * T[4 * e + c];
+                Tn[4 * r + c] = v;
+            }
+        for (int k2 = 0; k2 < 16; k2++) T[k2] = Tn[k2];
+        double nrm = 0;
+        for (int r = 0; r < 6; r++) nrm += xi[r] * xi[r];
+        if (sqrt(nrm) < eps) { converged = true; break; }
+    }
+    GS_CUDA(evaluate());
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 4; c++) result->T[4 * r + c] = T[4 * r + c];
+    result->cost = acc[27];
+    result->n_corr = (int64_t)acc[28];
+    result->iters = it > max_iters ? max_iters : it;
+    result->converged = converged ? 1 : 0;
+    return GS_OK;
+}
+
 }  // extern "C"

@@ -186,6 +186,29 @@ cudaError_t launch_dedup_plan(const float* map_means, int64_t n, const float* ne
 cudaError_t launch_map_scan(const uint8_t* keep, int64_t n, const uint8_t* accept, int64_t n_new, void* scratch,
                             uint32_t** pos_keep, uint32_t** pos_new, uint32_t* totals_host, cudaStream_t st);
 cudaError_t launch_compact(const MapUpdateArgs& a, cudaStream_t st);
+// exclusive scan of n uint32 (bsum: ceil(n / 1024) + 1 words of scratch; total may be null)
+cudaError_t exclusive_scan_u32(const uint32_t* x, int64_t n, uint32_t* out, uint32_t* bsum, uint32_t* total,
+                               cudaStream_t st);
+
+// Gaussian-GICP loop registration (gicp.cu).
+struct GicpView {
+    float R[9], t[3], c[3];       // world -> camera, and the camera centre (FP32)
+    float fx, fy, cx, cy, W, H;
+};
+struct GicpMap {
+    int64_t n;
+    const float *means, *log_scales, *quats;   // [3][n], [3][n], [4][n]
+};
+size_t gicp_scratch_bytes(int64_t n_tar);
+cudaError_t launch_gicp_target_set(const GicpMap& map, const GicpView* views, int n_views, float near_z, float dmax2,
+                                   const uint8_t* source_flag, uint8_t* target_flag, void* scratch,
+                                   unsigned long long* count_host, cudaStream_t st);
+// builds the target hash (once per registration)
+cudaError_t launch_gicp_build(const GicpMap& tar, const uint8_t* tar_flag, float d_corr, void* scratch, cudaStream_t st);
+// accumulates H (21, upper triangle row-major), g (6), cost, count for transform (R, t) into
+// 29 doubles copied to acc_host
+cudaError_t launch_gicp_normal_eq(const GicpMap& src, const uint8_t* src_flag, const GicpMap& tar, float d_corr,
+                                  const double* R, const double* t, void* scratch, double* acc_host, cudaStream_t st);
 
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st);

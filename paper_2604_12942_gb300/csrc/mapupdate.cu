@@ -238,6 +238,11 @@ static cudaError_t exclusive_scan(const T* x, int64_t n, uint32_t* out, uint32_t
     return cudaGetLastError();
 }
 
+cudaError_t exclusive_scan_u32(const uint32_t* x, int64_t n, uint32_t* out, uint32_t* bsum, uint32_t* total,
+                               cudaStream_t st) {
+    return exclusive_scan(x, n, out, bsum, total, st);
+}
+
 // ---------------------------------------------------------------------------------------
 // Compaction: kept rows to their scanned positions, accepted new rows after them (with zero
 // moments).  Every plane is passed by its own base pointer (input stride n, new rows n_new,

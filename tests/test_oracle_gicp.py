@@ -65,7 +65,7 @@ def test_normal_equations_match_finite_differences():
 
 def test_target_set_hand_case():
     cam = dict(width=100, height=80, fx=50.0, fy=50.0, cx=50.0, cy=40.0,
-               R_cw=np.eye(3).ravel().tolist(), t_cw=[0.0, 0.0, 0.0])
+               R=np.eye(3), t=np.zeros(3))
     pts = np.array([[0.0, 0.0, 5.0],     # centre of the image
                     [0.0, 0.0, 0.1],     # in front of the near plane
                     [0.0, 0.0, -5.0],    # behind
