@@ -28,6 +28,7 @@ constexpr float kSsimC1 = 0.01f * 0.01f, kSsimC2 = 0.03f * 0.03f;
 constexpr int kMaskMaxR = 16;
 __global__ void __launch_bounds__(kObjTX * kObjTY) render_mask_kernel(ObjArgs a) {
     __shared__ uint8_t s_geo[kObjTY + 2 * kMaskMaxR][kObjTX + 2 * kMaskMaxR];
+    __shared__ int s_w[2 * kMaskMaxR + 1];   // half-width of the disk in each row
     const View& V = a.views[blockIdx.z];
     const int x0 = blockIdx.x * kObjTX, y0 = blockIdx.y * kObjTY;
     if (x0 >= V.W || y0 >= V.H) return;   // (the whole block)
@@ -35,6 +36,12 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) render_mask_kernel(ObjArgs a)
     const int tw = kObjTX + 2 * r, th = kObjTY + 2 * r;
     const float* T = a.T_final + V.pix_off;
     const int t = threadIdx.y * kObjTX + threadIdx.x;
+    if (t <= 2 * r) {
+        const int dy = t - r;
+        int w = 0;
+        while ((w + 1) * (w + 1) + dy * dy <= r * r) w++;
+        s_w[t] = w;
+    }
     for (int i = t; i < tw * th; i += kObjTX * kObjTY) {
         const int iy = i / tw, ix = i - iy * tw;
         const int gx = x0 - r + ix, gy = y0 - r + iy;
@@ -46,9 +53,7 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) render_mask_kernel(ObjArgs a)
     if (x >= V.W || y >= V.H) return;
     bool in = true;
     for (int dy = -r; dy <= r; dy++) {
-        // half-width of the disk in row dy: the largest w with w^2 + dy^2 <= r^2
-        int w = 0;
-        while ((w + 1) * (w + 1) + dy * dy <= r * r) w++;
+        const int w = s_w[dy + r];   // the largest w with w^2 + dy^2 <= r^2
         const uint8_t* row = &s_geo[threadIdx.y + r + dy][threadIdx.x + r];
         for (int dx = -w; dx <= w; dx++) in = in && row[dx];
     }
@@ -112,33 +117,47 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) masked_l1_kernel(ObjArgs a) {
 }
 
 // Register-blocked separable passes over a tile (kInH x kInW inputs -> kObjH x kObjTX outputs):
-// a horizontal task makes 4 consecutive outputs of one row from 14 inputs held in registers, a
-// vertical task 2 consecutive rows of one column from 12.
+// a horizontal task makes 4 consecutive outputs of one row from 14 inputs (four 16-byte shared
+// loads; rows padded to kInS floats keep the quarter-warp phases conflict-free), a vertical
+// task 2 consecutive rows of one column from 12.  All three channels of a tile are loaded in
+// one phase, so the global loads of a block are in flight together.
 constexpr int kSeg = 4;                       // horizontal outputs per task
 constexpr int kSegs = kObjTX / kSeg;          // tasks per row
-constexpr int kHIn = kSeg + 2 * kHalo;        // inputs per horizontal task
+constexpr int kHIn = kSeg + 2 * kHalo;        // inputs per horizontal task (14)
+constexpr int kInS = 44;                      // padded row stride of the input tiles
+static_assert(kInS >= kInW && kInS % 4 == 0 && kInS >= 4 * ((kHIn + 3) / 4) + kObjTX - kSeg, "tile row stride");
 
-__device__ __forceinline__ void hpass(const float (&win)[11], const float* in, float* out) {
-    float v[kHIn];
+__device__ __forceinline__ void load_row16(const float* row, float (&v)[16]) {
 #pragma unroll
-    for (int k = 0; k < kHIn; k++) v[k] = in[k];
-#pragma unroll
-    for (int o = 0; o < kSeg; o++) {
-        float acc = 0.f;
-#pragma unroll
-        for (int q = 0; q < 2 * kHalo + 1; q++) acc = fmaf(win[q], v[o + q], acc);
-        out[o] = acc;
+    for (int j = 0; j < 4; j++) {
+        const float4 q = *reinterpret_cast<const float4*>(row + 4 * j);
+        v[4 * j] = q.x; v[4 * j + 1] = q.y; v[4 * j + 2] = q.z; v[4 * j + 3] = q.w;
     }
 }
 
-// SSIM forward, fused with the masked L1 terms.  Per channel: the five local moments of
-// x = C M and y = C~ M, the SSIM map (summed over M), and the partials
+__device__ __forceinline__ void hconv(const float (&win)[11], const float (&v)[16], float* out) {
+    float o[kSeg];
+#pragma unroll
+    for (int k = 0; k < kSeg; k++) {
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 2 * kHalo + 1; q++) acc = fmaf(win[q], v[k + q], acc);
+        o[k] = acc;
+    }
+    *reinterpret_cast<float4*>(out) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+// SSIM forward, fused with the masked L1 terms.  Per channel: the local means of x = C M and
+// y = C~ M, E[x^2 + y^2] and E[xy] (SSIM uses the two variances only summed), the SSIM map (summed over M), and the partials
 // k(q) dS/dmu_x, k(q) dS/dE[x^2], k(q) dS/dE[xy], k(q) = -lambda_ssim M(q) / (3 |M| views)
 // (the gradient of lambda_ssim (1 - SSIM) / views); and at the same output pixels the L1
 // colour terms (and, with the first channel, the depth term) with the epilogue's arithmetic.
 __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
-    __shared__ float s_x[kInH][kInW], s_y[kInH][kInW];
-    __shared__ float s_h[5][kInH][kObjTX];
+    __shared__ __align__(16) float s_x[3][kInH][kInS];
+    __shared__ __align__(16) float s_y[3][kInH][kInS];
+    // horizontal sums of x, y, x^2 + y^2 and xy (SSIM needs E[x^2] and E[y^2] only summed)
+    __shared__ __align__(16) float s_h[4][kInH][kObjTX];
+    __shared__ uint8_t s_m[kInH][kInW];
     const int v = blockIdx.z;
     const View& V = a.views[v];
     const int x0 = blockIdx.x * kObjTX, y0 = blockIdx.y * kObjH;
@@ -151,45 +170,47 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
     const float k = cm > 0 ? -a.lambda_ssim / (3.f * (float)cm * (float)a.n_views) : 0.f;
     const float kr = cm > 0 ? a.lambda_rgb * inv_v / (float)cm : 0.f;
     const int ox = t & 31, oy0 = (t >> 5) * kObjRows;   // vertical task: column, first row
+    const float* c = a.rgb + 3 * V.pix_off;
+    const float* tc = a.tgt_rgb + 3 * V.pix_off;
+    for (int i = t; i < kInH * kInW; i += kObjTX * kObjTY) {
+        const int iy = i / kInW, ix = i - iy * kInW;
+        const int gx = x0 - kHalo + ix, gy = y0 - kHalo + iy;
+        float xv[3] = {0.f, 0.f, 0.f}, yv[3] = {0.f, 0.f, 0.f};
+        bool in = false;
+        if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
+            const int64_t p = (int64_t)gy * V.W + gx;
+            in = a.mask ? a.mask[V.pix_off + p] != 0 : true;
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) {
+                xv[ch] = in ? c[ch * P + p] : 0.f;
+                yv[ch] = in ? tc[ch * P + p] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) { s_x[ch][iy][ix] = xv[ch]; s_y[ch][iy][ix] = yv[ch]; }
+        s_m[iy][ix] = in ? 1 : 0;
+    }
+    __syncthreads();
     float ssum = 0.f, lr = 0.f, ld = 0.f;
     for (int ch = 0; ch < 3; ch++) {
-        const float* c = a.rgb + 3 * V.pix_off + ch * P;
-        const float* tc = a.tgt_rgb + 3 * V.pix_off + ch * P;
-        for (int i = t; i < kInH * kInW; i += kObjTX * kObjTY) {
-            const int iy = i / kInW, ix = i - iy * kInW;
-            const int gx = x0 - kHalo + ix, gy = y0 - kHalo + iy;
-            float xv = 0.f, yv = 0.f;
-            if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
-                const int64_t p = (int64_t)gy * V.W + gx;
-                const bool in = a.mask ? a.mask[V.pix_off + p] != 0 : true;
-                xv = in ? c[p] : 0.f;
-                yv = in ? tc[p] : 0.f;
-            }
-            s_x[iy][ix] = xv;
-            s_y[iy][ix] = yv;
-        }
-        __syncthreads();
         for (int task = t; task < kInH * kSegs; task += kObjTX * kObjTY) {
             const int iy = task / kSegs, cx = (task - iy * kSegs) * kSeg;
-            float xs[kHIn], ys[kHIn], tmp[kHIn];
+            float xs[16], ys[16], tmp[16];
+            load_row16(&s_x[ch][iy][cx], xs);
+            load_row16(&s_y[ch][iy][cx], ys);
+            hconv(a.win, xs, &s_h[0][iy][cx]);
+            hconv(a.win, ys, &s_h[1][iy][cx]);
 #pragma unroll
-            for (int q = 0; q < kHIn; q++) { xs[q] = s_x[iy][cx + q]; ys[q] = s_y[iy][cx + q]; }
-            hpass(a.win, xs, &s_h[0][iy][cx]);
-            hpass(a.win, ys, &s_h[1][iy][cx]);
-#pragma unroll
-            for (int q = 0; q < kHIn; q++) tmp[q] = xs[q] * xs[q];
-            hpass(a.win, tmp, &s_h[2][iy][cx]);
-#pragma unroll
-            for (int q = 0; q < kHIn; q++) tmp[q] = ys[q] * ys[q];
-            hpass(a.win, tmp, &s_h[3][iy][cx]);
+            for (int q = 0; q < kHIn; q++) tmp[q] = fmaf(xs[q], xs[q], ys[q] * ys[q]);
+            hconv(a.win, tmp, &s_h[2][iy][cx]);
 #pragma unroll
             for (int q = 0; q < kHIn; q++) tmp[q] = xs[q] * ys[q];
-            hpass(a.win, tmp, &s_h[4][iy][cx]);
+            hconv(a.win, tmp, &s_h[3][iy][cx]);
         }
         __syncthreads();
-        float mo[5][kObjRows];
+        float mo[4][kObjRows];
 #pragma unroll
-        for (int m = 0; m < 5; m++) {
+        for (int m = 0; m < 4; m++) {
             float col[kObjRows + 2 * kHalo];
 #pragma unroll
             for (int q = 0; q < kObjRows + 2 * kHalo; q++) col[q] = s_h[m][oy0 + q][ox];
@@ -205,14 +226,14 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
         for (int rr = 0; rr < kObjRows; rr++) {
             const int gx = x0 + ox, gy = y0 + oy0 + rr;
             if (gx >= V.W || gy >= V.H) continue;
-            const float mx = mo[0][rr], my = mo[1][rr], exx = mo[2][rr], eyy = mo[3][rr], exy = mo[4][rr];
-            const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+            const float mx = mo[0][rr], my = mo[1][rr], e2 = mo[2][rr], exy = mo[3][rr];
+            const float sxy = exy - mx * my;
             const float A1 = 2.f * mx * my + kSsimC1, A2 = 2.f * sxy + kSsimC2;
-            const float B1 = mx * mx + my * my + kSsimC1, B2 = sxx + syy + kSsimC2;
+            const float B1 = mx * mx + my * my + kSsimC1, B2 = e2 - mx * mx - my * my + kSsimC2;
             const float inv = 1.f / (B1 * B2);
             const float S = A1 * A2 * inv;
             const int64_t p = (int64_t)gy * V.W + gx;
-            const bool in = a.mask ? a.mask[V.pix_off + p] != 0 : true;
+            const bool in = s_m[oy0 + rr + kHalo][ox + kHalo] != 0;
             const float kq = in ? k : 0.f;
             if (in) ssum += S;
             const float d_mu = 2.f * my * (A2 - A1) * inv - 2.f * mx * S * (1.f / B1 - 1.f / B2);
@@ -221,7 +242,7 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
             part[P] = kq * (-S / B2);
             part[2 * P] = kq * (2.f * A1 * inv);
             // L1 colour term of this channel (x, y are C, C~ inside the mask)
-            const float r = s_x[oy0 + rr + kHalo][ox + kHalo] - s_y[oy0 + rr + kHalo][ox + kHalo];
+            const float r = s_x[ch][oy0 + rr + kHalo][ox + kHalo] - s_y[ch][oy0 + rr + kHalo][ox + kHalo];
             const float krgb = in ? kr : 0.f;
             a.dl_drgb[3 * V.pix_off + ch * P + p] = krgb * (float)((r > 0.f) - (r < 0.f));
             if (in) lr += fabsf(r);
@@ -235,17 +256,18 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_fwd_kernel(ObjArgs a) {
                 if (ind) ld += fabsf(rd);
             }
         }
-        __syncthreads();   // the tile buffers are refilled for the next channel
+        __syncthreads();   // s_h is refilled for the next channel
     }
     block_add2(lr, ld, &a.sums[3 * v], &a.sums[3 * v + 1]);
     block_add2(ssum, 0.f, &a.sums[3 * v + 2], nullptr);
 }
 
 // SSIM backward: dL/dx(p) = sum_q w(q - p) [P_mu(q) + 2 x(p) P_xx(q) + y(p) P_xy(q)], and
-// dL/dC = M dL/dx, added to the L1 gradient already in dl_drgb.
+// dL/dC = M dL/dx, added to the L1 gradient already in dl_drgb.  The three partial maps of a
+// channel are loaded together; channels are processed one after the other.
 __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_bwd_kernel(ObjArgs a) {
-    __shared__ float s_p[3][kInH][kInW];
-    __shared__ float s_h[3][kInH][kObjTX];
+    __shared__ __align__(16) float s_p[3][kInH][kInS];
+    __shared__ __align__(16) float s_h[3][kInH][kObjTX];
     const View& V = a.views[blockIdx.z];
     const int x0 = blockIdx.x * kObjTX, y0 = blockIdx.y * kObjH;
     if (x0 >= V.W || y0 >= V.H) return;
@@ -268,7 +290,9 @@ __global__ void __launch_bounds__(kObjTX * kObjTY) ssim_bwd_kernel(ObjArgs a) {
         for (int task = t; task < 3 * kInH * kSegs; task += kObjTX * kObjTY) {
             const int m = task / (kInH * kSegs), rest = task - m * (kInH * kSegs);
             const int iy = rest / kSegs, cx = (rest - iy * kSegs) * kSeg;
-            hpass(a.win, &s_p[m][iy][cx], &s_h[m][iy][cx]);
+            float v16[16];
+            load_row16(&s_p[m][iy][cx], v16);
+            hconv(a.win, v16, &s_h[m][iy][cx]);
         }
         __syncthreads();
         float cv[3][kObjRows];
