@@ -559,6 +559,23 @@ def run_learned(args):
         "scenes": rows}), flush=True)
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's timed-region length (every rank gets it); `ms` itself at world 1."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def job_mpix(world, px_per_rank, steps, total_ms):
+    """Whole-job throughput: every rank (an independent replica) renders px_per_rank pixels per
+    step, the job takes the slowest rank's time."""
+    return world * px_per_rank * steps / (total_ms / 1e3) / 1e6
+
+
 def main():
     args = parse()
     if args.learned:
@@ -577,15 +594,9 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
         dist.init_process_group("nccl")
     r = run_gpu(args, rank, world)
-    total_ms = r["total_ms"]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t)
+    total_ms = max_over_ranks(r["total_ms"], world, "cuda")
     ms_step = total_ms / args.steps
-    mpix = world * r["px"] * args.steps / (total_ms / 1e3) / 1e6
+    mpix = job_mpix(world, r["px"], args.steps, total_ms)
     if rank != 0:
         return
     pk, pk_kind = peaks()
