@@ -328,6 +328,7 @@ def run_gpu(args, rank, world):
     # headline: its kernels alone on the rendered C3 images, and a whole graph-replayed step
     # with it switched on.
     f1 = f1_measure(args, step, cams, trgb, tdep, planes0, cap, st, dev)
+    f23 = f23_measure(step, cams, dev)
     # End to end through the public API: every step's targets are uploaded from pinned host
     # memory and its loss is read back before the next step starts.  The upload of step k + 1
     # runs on a copy stream into a staging buffer while step k computes (double buffering, as
@@ -389,7 +390,7 @@ def run_gpu(args, rank, world):
     px = sum(w * h for w, h in SIZES)
     adam_steps = int(step.ws.counters().adam_step)
     step.release()
-    return dict(f1=f1, total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=loss_end,
+    return dict(f1=f1, f23=f23, total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=loss_end,
                 tune=tune, adam_steps=adam_steps, eager_ms=eager_ms, h2d_ms=h2d_ms, work=work,
                 clocks=clk.summary(), e2e_s=e_dt, px=px, h2d=int(h_rgb.numel() * 4 + h_dep.numel() * 4),
                 d2h=int(h_loss.numel() * 4), sc=sc, cams=cams, trgb=trgb, tdep=tdep, n=n,
@@ -453,6 +454,50 @@ def f1_measure(args, step, cams, trgb, tdep, planes0, cap, st, dev):
                                    "frac": round(B / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)},
             "step_ms": round(step_ms, 4), "step_mpix_s": round(sum(w * h for w, h in SIZES) / (step_ms * 1e-3) / 1e6, 2),
             "note": "option of the step (the paper's full objective); the headline keeps the north-star loss"}
+
+
+def f23_measure(step, cams, dev):
+    """The map-size updates (f2) and the loop registration (f3) at C3 scale, each timed as its
+    public call (they synchronize: host wall clock around a synchronized call, mean of 5)."""
+    import torch
+
+    import paper_2604_12942_gb300 as gs
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3, out
+
+    planes = step.planes
+    n = planes.shape[1]
+    g = torch.Generator(device=dev).manual_seed(5)
+    n_new = 200_000
+    new = planes[:, torch.randint(0, n, (n_new,), device=dev, generator=g)].clone()
+    new[0:3] += 0.2 * torch.randn(3, n_new, device=dev, generator=g)
+    scratch = gs.map_update_scratch(n, n_new, dev)
+    prune_ms, (keep, nk) = timed(lambda: gs.prune_plan(planes, 3, 0.005, 0.01, scratch))
+    dedup_ms, (acc, na) = timed(lambda: gs.dedup_plan(planes, 3, new[0:3], 0.05, scratch))
+    upd_ms, _ = timed(lambda: gs.map_update(planes, step.m, step.v, 3, keep, new, acc, scratch=scratch))
+    gscr = gs.gicp_scratch(n, dev)
+    views = cams[:4]
+    tgt_ms, (tflag, nt) = timed(lambda: gs.gicp_target_set(planes, 3, views, 0.2, 20.0, None, gscr))
+    src_flag = torch.zeros(n, dtype=torch.uint8, device=dev)
+    src_flag[torch.randint(0, n, (20_000,), device=dev, generator=g)] = 1
+    tflag = tflag * (1 - src_flag)
+    T0 = np.eye(4)
+    T0[:3, 3] = [0.05, -0.03, 0.02]
+    reg_ms, (T, res) = timed(lambda: gs.gicp_register(planes, src_flag, planes, tflag, 3, T0, 1.0, 30, 1e-7, gscr), 3)
+    return {"prune_plan_ms": round(prune_ms, 3), "rows": n, "pruned": n - nk,
+            "dedup_plan_ms": round(dedup_ms, 3), "new_rows": n_new, "accepted": na,
+            "map_update_ms": round(upd_ms, 3), "rows_out": nk + na,
+            "gicp_target_set_ms": round(tgt_ms, 3), "target_rows": nt, "views": len(views),
+            "gicp_register_ms": round(reg_ms, 3), "source_rows": int(src_flag.sum()),
+            "gicp_iters": res.iters, "gicp_corr": res.n_corr, "gicp_converged": res.converged,
+            "note": "calls between / beside mapping steps; each synchronizes its stream"}
 
 
 def tile_sort_passes(L):
@@ -626,7 +671,7 @@ def main():
                 "path": "pinned host targets -> copy stream (next step's upload overlaps this step) -> graph "
                         "input buffers -> gs_step graph replay -> loss read back, every step"},
         "gpu_launches": r["kernels"] * args.steps, "timed": "CUDA-graph replay of gs_step",
-        "f1_ssim_and_mask": r["f1"],
+        "f1_ssim_and_mask": r["f1"], "f2_f3_calls": r["f23"],
         "kernel_shape": {"tile": args.tile, "chunk": args.chunk},
         "autotune": r["tune"],
     }

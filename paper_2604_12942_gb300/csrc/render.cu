@@ -672,6 +672,177 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
     }
 }
 
+// ----------------------------------------------------------------------------------------
+// Backward compositing, one independent warp per (16 x 16 tile, 8 x 8 region).  The warp walks
+// the tile's list back to front 32 positions at a time: each lane tests the stored region mask
+// of one position, the hits are compacted in order (a ballot) and only their records are
+// copied (cp.async) into the warp's own double buffer while the previous window's records are
+// composited.  No block barrier: every warp proceeds at its own pace.  The per-record
+// arithmetic is that of render_bwd_kernel.
+// ----------------------------------------------------------------------------------------
+constexpr int kWin = 32;   // list positions per window
+
+template <bool COUNT>
+__global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(BwdArgs a) {
+    constexpr int TILE = 16, kPPT = kBwdPPT;
+    __shared__ float4 s_rec[2][kWin][3];
+    __shared__ uint32_t s_id[2][kWin];
+    __shared__ int s_pos[2][kWin];
+    const uint32_t status = a.counters->status;
+    const int gt = a.order ? (int)a.order[blockIdx.x >> 2] : (int)(blockIdx.x >> 2);
+    const int w = blockIdx.x & 3;   // region: column w % 2, row w / 2 (the forward's mask order)
+    if (status != 0) return;
+    const uint2 rg = a.ranges[gt];
+    const int v = view_of_tile(a.views, a.n_views, gt);
+    const View& V = a.views[v];
+    const int lt = gt - V.tile_off;
+    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+    const int lane = threadIdx.x & 31;
+    const int rx0 = tx * TILE + (w & 1) * 8, ry0 = ty * TILE + (w >> 1) * 8;
+    const float amin = a.op.alpha_min, amax = a.op.alpha_max;
+    uint32_t n_eval = 0, n_add = 0, n_visit = 0;
+    float px[kPPT], py[kPPT], T[kPPT], S[kPPT], gc0[kPPT], gc1[kPPT], gc2[kPPT], gd[kPPT];
+    uint32_t last[kPPT];
+    uint32_t mylast = 0;
+#pragma unroll
+    for (int q = 0; q < kPPT; q++) {
+        const int xi = rx0 + (lane & 7), yi = ry0 + (lane >> 3) + 4 * q;
+        px[q] = (float)xi + 0.5f;
+        py[q] = (float)yi + 0.5f;
+        T[q] = 0.f; gc0[q] = gc1[q] = gc2[q] = gd[q] = 0.f;
+        last[q] = 0;
+        if (xi < V.W && yi < V.H) {
+            const int64_t P = (int64_t)V.W * V.H;
+            const int64_t p = (int64_t)yi * V.W + xi;
+            const int64_t g = V.pix_off + p;
+            T[q] = a.T_final[g];
+            last[q] = a.n_contrib[g];
+            const float* d = a.dl_drgb + 3 * V.pix_off;
+            gc0[q] = d[p];
+            gc1[q] = d[P + p];
+            gc2[q] = d[2 * P + p];
+            gd[q] = a.dl_ddepth ? a.dl_ddepth[g] : 0.f;
+            if (gc0[q] == 0.f && gc1[q] == 0.f && gc2[q] == 0.f && gd[q] == 0.f) last[q] = 0;
+        }
+        S[q] = (gc0[q] * a.op.bg0 + gc1[q] * a.op.bg1 + gc2[q] * a.op.bg2) * T[q];
+        mylast = max(mylast, last[q]);
+    }
+    const int wtop = (int)__reduce_max_sync(0xffffffffu, mylast);
+    uint32_t ltm;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(ltm));
+    // window starting (from the back) at position k0: this warp's hits, copied into buffer b
+    auto gather = [&](int k0, int b) -> int {
+        const int k = k0 - lane;
+        bool hit = false;
+        if (k >= 0) hit = (bwd_mask_from_fwd<TILE>(a.pair_mask[rg.x + k]) >> w) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int slot = __popc(bal & ltm);
+            const uint32_t id = a.vals[rg.x + k];
+            s_id[b][slot] = id;
+            s_pos[b][slot] = k;
+            const float4* src = a.proj + 3 * (size_t)id;
+#pragma unroll
+            for (int h = 0; h < 3; h++) cp_async16(&s_rec[b][slot][h], src + h);
+        }
+        cp_async_commit();
+        return __popc(bal);
+    };
+    // windows start at wtop - 1, wtop - 1 - kWin, ... (while >= 0); one commit group each
+    int next = wtop - 1;
+    bool have = next >= 0;
+    int cnt = have ? gather(next, 0) : 0;
+    next -= kWin;
+    for (int b = 0; have; b ^= 1) {
+        // the next window into the other buffer (or an empty group), then this window's records
+        const bool have_next = next >= 0;
+        int cnt_next = 0;
+        if (have_next) cnt_next = gather(next, b ^ 1);
+        else cp_async_commit();
+        next -= kWin;
+        cp_async_wait_prior();   // this window's copies (all lanes') have landed after the syncwarp
+        __syncwarp();
+        if constexpr (COUNT) n_visit += cnt;
+        for (int t = 0; t < cnt; t++) {
+            const int j = s_pos[b][t];
+            const float4 r0 = s_rec[b][t][0], r1 = s_rec[b][t][1];
+            const float2 bx = make_float2(r0.x, r0.y);
+            const float4 co = make_float4(r1.x, r1.y, r1.z, r0.w);
+            float val[10];
+#pragma unroll
+            for (int q = 0; q < 10; q++) val[q] = 0.f;
+            bool contrib = false;
+            const float4 r2 = s_rec[b][t][2];
+            const float4 cz = make_float4(r2.x, r2.y, r2.z, r0.z);
+#pragma unroll
+            for (int q = 0; q < kPPT; q++) {
+                const bool live = (uint32_t)j < last[q];
+                const float dx = px[q] - bx.x, dy = py[q] - bx.y;
+                const FragE fe = frag_exponent(dx, dy, co.x, co.y, co.z);
+                const float G = ex2_approx(fe.e);
+                const float a0 = co.w * G;
+                const float alpha = fminf(amax, a0);
+                const bool c = live && !(alpha < amin);
+                if constexpr (COUNT) {
+                    n_eval += live;
+                    n_add += c;
+                }
+                contrib |= c;
+                const float rom = rcp_approx(1.f - alpha);
+                const float Tn = T[q] * rom;
+                const float wgt = alpha * Tn;
+                const float gcz = gc0[q] * cz.x + gc1[q] * cz.y + gc2[q] * cz.z + gd[q] * cz.w;
+                const float dLda = Tn * gcz - S[q] * rom;
+                S[q] = c ? fmaf(gcz, wgt, S[q]) : S[q];
+                T[q] = c ? Tn : T[q];
+                const float wc = c ? wgt : 0.f;
+                val[7] = fmaf(gc0[q], wc, val[7]);
+                val[8] = fmaf(gc1[q], wc, val[8]);
+                val[9] = fmaf(gc2[q], wc, val[9]);
+                val[6] = fmaf(gd[q], wc, val[6]);
+                const float gl = (c && a0 < amax) ? dLda : 0.f;   // the 0.99 clamp stops the gradient
+                const float h = gl * a0;
+                const float hdx = h * dx;
+                val[0] = fmaf(h, fe.hx, val[0]);
+                val[1] = fmaf(h, fe.hy, val[1]);
+                val[2] = fmaf(hdx, dx, val[2]);
+                val[3] = fmaf(hdx, dy, val[3]);
+                val[4] = fmaf(h * dy, dy, val[4]);
+                val[5] = fmaf(gl, G, val[5]);
+            }
+            const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
+            if (cmask) {
+                float4* rec4 = a.grad2d + 3 * (size_t)s_id[b][t];
+                if (__popc(cmask) <= kBwdDirectLanes) {
+                    if (contrib) {
+                        atomicAdd(rec4, make_float4(val[0], val[1], val[2], val[3]));
+                        atomicAdd(rec4 + 1, make_float4(val[4], val[5], val[6], 0.f));
+                        atomicAdd(rec4 + 2, make_float4(val[7], val[8], val[9], 0.f));
+                    }
+                } else {
+                    float t8, t2;
+                    warp_reduce10(val, t8, t2);
+                    float* rec = reinterpret_cast<float*>(rec4);
+                    if ((lane & 3) == 0) {
+                        const int idx = lane >> 2;
+                        atomicAdd(rec + (idx < 7 ? idx : idx + 1), t8);
+                    }
+                    if ((lane & 15) == 0) atomicAdd(rec + 9 + (lane >> 4), t2);
+                }
+            }
+        }
+        __syncwarp();   // every lane is done with buffer b before it is refilled
+        cnt = cnt_next;
+        have = have_next;
+    }
+    cp_async_wait_all();
+    if constexpr (COUNT) {
+        warp_count_add(&a.counters->frag_bwd_eval, n_eval);
+        warp_count_add(&a.counters->frag_bwd_add, n_add);
+        if (lane == 0 && n_visit) atomicAdd(&a.counters->visits_bwd, n_visit);
+    }
+}
+
 template <int TILE, int CHUNK>
 static void launch_fwd_c(const FwdArgs& a, int total_tiles, cudaStream_t st) {
     constexpr int NT = TileMap<TILE, kFwdPPT>::NT;
@@ -727,6 +898,12 @@ __global__ void __launch_bounds__(256) clear_grad2d_kernel(BwdArgs a) {
 cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st) {
     clear_grad2d_kernel<<<sort_grid() * 4, 256, 0, st>>>(a);
     if (total_tiles <= 0) return cudaGetLastError();
+    // 16 x 16 tiles: one independent warp per 8 x 8 region (8 x 8 tiles are one warp already)
+    if (a.op.tile == 16) {
+        if (a.op.count) render_bwd_warp_kernel<true><<<4 * total_tiles, 32, 0, st>>>(a);
+        else render_bwd_warp_kernel<false><<<4 * total_tiles, 32, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     return a.op.tile == 8 ? launch_bwd_t<8>(a, total_tiles, a.op.chunk, st)
                           : launch_bwd_t<16>(a, total_tiles, a.op.chunk, st);
 }
