@@ -36,10 +36,10 @@ METRIC = "fwd+bwd render Mpix/s and iters/s at 2M Gaussians; secs-to-PSNR learne
 # (key tile = chunk = 0).  Once a kernel changes these must be captured again; a shape without an
 # entry reports null.
 NCU_TRAFFIC = {
-    ("render_bwd_kernel", 16, 256): 323_915_008 + 62_461_696,
-    ("render_fwd_kernel", 16, 256): 223_638_528 + 199_961_088,
-    ("project_bwd_entry_kernel", 0, 0): 159_465_984 + 52_321_024,
-    ("project_bwd_kernel", 0, 0): 1_195_707_648 + 861_927_680,
+    ("render_bwd_warp_kernel", 16, 0): 320_741_376 + 62_899_200,
+    ("render_fwd_kernel", 16, 256): 221_431_552 + 200_414_976,
+    ("project_bwd_entry_kernel", 0, 0): 159_156_736 + 52_907_264,
+    ("project_bwd_kernel", 0, 0): 1_195_792_128 + 861_713_408,
 }
 
 
@@ -48,7 +48,7 @@ def stage_traffic(stage, tile, chunk, n):
     kernel has no entry or the workload is another one."""
     if n != 2_000_000:
         return None
-    ks = {"composite_bwd": [("render_bwd_kernel", tile, chunk)],
+    ks = {"composite_bwd": [("render_bwd_warp_kernel", tile, 0) if tile == 16 else ("render_bwd_kernel", tile, chunk)],
           "render_fwd": [("render_fwd_kernel", tile, chunk)],
           "project_bwd_adam": [("project_bwd_entry_kernel", 0, 0), ("project_bwd_kernel", 0, 0)]}.get(stage)
     if not ks or any(k not in NCU_TRAFFIC for k in ks):
@@ -485,9 +485,11 @@ def f23_measure(step, cams, dev):
     gscr = gs.gicp_scratch(n, dev)
     views = cams[:4]
     tgt_ms, (tflag, nt) = timed(lambda: gs.gicp_target_set(planes, 3, views, 0.2, 20.0, None, gscr))
-    src_flag = torch.zeros(n, dtype=torch.uint8, device=dev)
-    src_flag[torch.randint(0, n, (20_000,), device=dev, generator=g)] = 1
-    tflag = tflag * (1 - src_flag)
+    # source and target: two random halves of the rows the loop views see, so that every source
+    # mean has map neighbours; the true loop transform is the identity and T0 is offset from it
+    half = (torch.rand(n, device=dev, generator=g) < 0.5).to(torch.uint8)
+    src_flag = tflag * half
+    tflag = tflag * (1 - half)
     T0 = np.eye(4)
     T0[:3, 3] = [0.05, -0.03, 0.02]
     reg_ms, (T, res) = timed(lambda: gs.gicp_register(planes, src_flag, planes, tflag, 3, T0, 1.0, 30, 1e-7, gscr), 3)
@@ -496,6 +498,7 @@ def f23_measure(step, cams, dev):
             "map_update_ms": round(upd_ms, 3), "rows_out": nk + na,
             "gicp_target_set_ms": round(tgt_ms, 3), "target_rows": nt, "views": len(views),
             "gicp_register_ms": round(reg_ms, 3), "source_rows": int(src_flag.sum()),
+            "gicp_translation_error_m": float(np.linalg.norm(np.asarray(T)[:3, 3])),
             "gicp_iters": res.iters, "gicp_corr": res.n_corr, "gicp_converged": res.converged,
             "note": "calls between / beside mapping steps; each synchronizes its stream"}
 
@@ -651,7 +654,8 @@ def main():
     for k in table:
         table[k]["traffic"] = stage_traffic(k, args.tile, args.chunk, args.n)
     roof = dict(table[dom])
-    roof.update({"kernel": {"composite_bwd": "render_bwd_kernel", "render_fwd": "render_fwd_kernel",
+    roof.update({"kernel": {"composite_bwd": "render_bwd_warp_kernel" if args.tile == 16 else "render_bwd_kernel",
+                            "render_fwd": "render_fwd_kernel",
                             "project_bwd_adam": "project_bwd_kernel (fused Adam)", "project": "project_kernel",
                             "bin_sort": "scan/emit/radix/ranges kernels"}[dom],
                  "traffic": stage_traffic(dom, args.tile, args.chunk, args.n),
