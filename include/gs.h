@@ -121,8 +121,8 @@ typedef struct {
     size_t touched;      /* uint32 [n_views*n] tiles covered */
     size_t scan_tmp;     /* uint32 scratch of the scans */
     size_t ekeys0, ekeys1; /* uint32 [n_views*n] ping-pong: bits(z) of the visible entries */
-    size_t evals0, evals1; /* uint32 [n_views*n] ping-pong: their view * n + Gaussian index;
-                              after gs_bin_sort evals0 lists the entries by depth */
+    size_t evals0, evals1; /* uint32 [n_views*n] ping-pong: their compact indices (positions
+                              in `entries`); after gs_bin_sort evals0 lists the entries by depth */
     size_t keys0, keys1; /* uint32 [max_pairs] ping-pong: global tile id of each pair */
     size_t vals0, vals1; /* uint32 [max_pairs] ping-pong: view * n + Gaussian index; after
                             gs_bin_sort buffer sorted_buf holds the pairs ordered by (tile,
@@ -141,6 +141,8 @@ typedef struct {
                             w.r.t. the mean and the world covariance (projection backward) */
     size_t visible;      /* uint8 [n]: 1 if the Gaussian covers a tile of any view */
     size_t entries;      /* uint32 [n_views*n]: the visible entries in (view, Gaussian) order */
+    size_t erect;        /* uint32 [n_views*n][2]: per visible entry, in the order of `entries`,
+                            its tile rectangle (first global tile id, wx | wy << 16) */
     size_t tile_order;   /* uint32 [total_tiles]: compositing work order, largest pair count
                             first (power-of-two buckets), then scratch */
     size_t render_mask;  /* uint8 [total_pixels]: the step's interior mask (mask_erode >= 0) */

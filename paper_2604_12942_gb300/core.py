@@ -190,7 +190,8 @@ class Workspace:
 
     def sorted_entries(self, n_entries):
         """The visible (view, Gaussian) entries in depth order (values view * n + index)."""
-        return self.region("evals0", torch.int32, n_entries)
+        order = self.region("evals0", torch.int32, n_entries).to(torch.int64)
+        return self.region("entries", torch.int32, n_entries)[order]
 
     def visible(self):
         return self.region("visible", torch.uint8, self.n)

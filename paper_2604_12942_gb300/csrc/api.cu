@@ -152,6 +152,7 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.grad2d = take(sizeof(float) * 12 * (size_t)VN);
     L.geo2d = take(sizeof(float) * 12 * (size_t)VN);
     L.entries = take(sizeof(uint32_t) * (size_t)VN);
+    L.erect = take(sizeof(uint32_t) * 2 * (size_t)VN);
     L.visible = take((size_t)n);
     L.tile_order = take(sizeof(uint32_t) * ((size_t)G.total_tiles + 2 * 34));
     L.render_mask = take((size_t)G.total_pixels);
@@ -264,6 +265,7 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     b.ekeys = at<uint32_t>(ws, L->ekeys0);
     b.evals = at<uint32_t>(ws, L->evals0);
     b.entries = at<uint32_t>(ws, L->entries);
+    b.erect = at<uint2>(ws, L->erect);
     b.sorted_evals = at<uint32_t>(ws, L->evals0);   // 4 passes: the entry sort ends in buffer 0
     b.pkeys = at<uint32_t>(ws, L->keys0);
     b.pvals = at<uint32_t>(ws, L->vals0);
@@ -429,7 +431,7 @@ static cudaError_t run_composite_bwd(const gs_render_opts* opts, const gs_ws_lay
     b.order = at<uint32_t>(ws, L->tile_order);
     b.counters = at<Counters>(ws, L->counters);
     b.pair_mask = at<uint8_t>(ws, L->pair_mask);
-    b.entries = at<uint32_t>(ws, L->evals0);
+    b.entries = at<uint32_t>(ws, L->entries);
     b.T_final = at<float>(ws, L->T_final);
     b.n_contrib = at<uint32_t>(ws, L->n_contrib);
     b.dl_drgb = dl_drgb;

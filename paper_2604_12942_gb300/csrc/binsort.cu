@@ -134,16 +134,25 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t ltm;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(ltm));
-    const float* pf = reinterpret_cast<const float*>(a.proj);
     for (int k = 0; k < 32; k++) {
         const int lw = w * 32 + k;
         const uint32_t bw = s_word[lw];
         if ((bw >> lane) & 1u) {
             const uint32_t pos = s_off[lw] + (uint32_t)__popc(bw & ltm);
-            const int64_t idx = ((int64_t)blockIdx.x * kScanThreads + lw) * 32 + lane;
-            a.ekeys[pos] = __float_as_uint(__ldg(pf + 12 * idx + 2));   // z > 0: bits are monotone
-            a.evals[pos] = (uint32_t)idx;
-            a.entries[pos] = (uint32_t)idx;
+            const uint32_t idx = (uint32_t)(((int64_t)blockIdx.x * kScanThreads + lw) * 32 + lane);
+            const float4 r0 = __ldg(a.proj + 3 * (size_t)idx);
+            const int rx = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 1).w);
+            const int ry = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 2).w);
+            const View& V = a.views[idx / (uint32_t)a.n];
+            // the rectangle the projection counted (touched > 0: both spans are non-empty)
+            int xa = 0, xb = 0, ya = 0, yb = 0;
+            tile_span(r0.x, rx, a.tile, V.tiles_x, xa, xb);
+            tile_span(r0.y, ry, a.tile, V.tiles_y, ya, yb);
+            a.ekeys[pos] = __float_as_uint(r0.z);   // z > 0: bits are monotone
+            a.evals[pos] = pos;
+            a.entries[pos] = idx;
+            a.erect[pos] = make_uint2((uint32_t)(V.tile_off + ya * V.tiles_x + xa),
+                                      (uint32_t)(xb - xa + 1) | ((uint32_t)(yb - ya + 1) << 16));
         }
     }
 }
@@ -159,10 +168,14 @@ cudaError_t launch_entries(const BinArgs& a, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------------------------------------
-// Pair emission from the depth-sorted entries: the tiles-touched counts gathered in that
-// order are scanned into pair offsets (total = pair count), then each entry writes one
-// (global tile id, entry id) pair per covered tile, tiles in row-major order.
+// Pair emission from the depth-sorted entries: the tile counts of their rectangles, taken
+// in that order, are scanned into pair offsets (total = pair count), then each entry writes
+// one (global tile id, view * n + index) pair per covered tile, tiles in row-major order.
+// The rectangles and indices are read from the compact per-entry arrays of the compaction
+// (12 bytes an entry, which stay in L2), not from the projected records.
 // ----------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t rect_count(uint2 r) { return (r.y & 0xFFFFu) * (r.y >> 16); }
+
 __global__ void __launch_bounds__(kScanThreads) pair_count_kernel(BinArgs a) {
     __shared__ uint32_t s[33];
     const int64_t E = (int64_t)a.counters->n_entries;
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(kScanThreads) pair_count_kernel(BinArgs a) {
 #pragma unroll
         for (int k = 0; k < kScanItems; k++) {
             const int64_t j = base + (int64_t)k * kScanThreads + threadIdx.x;
-            if (j < E) sum += __ldg(a.touched + a.sorted_evals[j]);
+            if (j < E) sum += rect_count(a.erect[a.sorted_evals[j]]);
         }
     }
     sum = warp_sum(sum);
@@ -196,7 +209,7 @@ __global__ void __launch_bounds__(kScanThreads) pair_offsets_kernel(BinArgs a) {
     uint32_t t[kScanItems], sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
-        t[k] = base + k < E ? __ldg(a.touched + a.sorted_evals[base + k]) : 0u;
+        t[k] = base + k < E ? rect_count(a.erect[a.sorted_evals[base + k]]) : 0u;
         sum += t[k];
     }
     uint32_t tot;
@@ -220,8 +233,8 @@ __global__ void __launch_bounds__(kScanThreads) pair_offsets_kernel(BinArgs a) {
 // with very many tiles no longer serialise on one warp.
 __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
     static_assert(kEmitChunk == 8 * kEmitThreads, "each thread owns 8 consecutive slots of the chunk");
-    __shared__ uint32_t s_off[kEmitChunk + 1], s_row0[kEmitChunk + 1], s_id[kEmitChunk + 1];
-    __shared__ uint16_t s_x0[kEmitChunk + 1], s_wx[kEmitChunk + 1], s_tx[kEmitChunk + 1];
+    __shared__ uint32_t s_off[kEmitChunk + 1], s_t0[kEmitChunk + 1], s_id[kEmitChunk + 1];
+    __shared__ uint16_t s_wx[kEmitChunk + 1], s_tx[kEmitChunk + 1];
     __shared__ __align__(16) uint16_t s_own[kEmitChunk];   // slot -> local entry index
     __shared__ uint32_t s_wmax[kEmitThreads / 32];
     if (a.counters->status != 0) return;
@@ -239,21 +252,15 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
         __syncthreads();
         for (int j = threadIdx.x; j < ne; j += blockDim.x) {
             const int64_t e = e0 + j;
-            const uint32_t idx = a.sorted_evals[e];
-            const View& V = a.views[(int)(idx / a.n)];
-            const float4 r0 = __ldg(a.proj + 3 * (size_t)idx);
-            const int rx = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 1).w);
-            const int ry = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 2).w);
-            int xa, xb, ya, yb;
-            tile_span(r0.x, rx, a.tile, V.tiles_x, xa, xb);
-            tile_span(r0.y, ry, a.tile, V.tiles_y, ya, yb);
+            const uint32_t c = a.sorted_evals[e];
+            const uint32_t idx = a.entries[c];
+            const uint2 r = a.erect[c];
             const uint32_t off = a.poff[e];
             s_off[j] = off;
-            s_row0[j] = (uint32_t)(V.tile_off + ya * V.tiles_x);
+            s_t0[j] = r.x;
             s_id[j] = idx;
-            s_x0[j] = (uint16_t)xa;
-            s_wx[j] = (uint16_t)(xb - xa + 1);
-            s_tx[j] = (uint16_t)V.tiles_x;
+            s_wx[j] = (uint16_t)(r.y & 0xFFFFu);
+            s_tx[j] = (uint16_t)a.views[idx / (uint32_t)a.n].tiles_x;
             // the entry's first pair slot in this chunk (entry 0 starts at or before p0)
             if (j > 0 && off < p1) s_own[off - p0] = (uint16_t)j;
         }
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
             const uint32_t j = s_own[p - p0];
             const uint32_t kk = (uint32_t)p - s_off[j], wx = s_wx[j];
             const uint32_t ty = kk / wx, tx = kk - ty * wx;
-            a.pkeys[p] = s_row0[j] + ty * (uint32_t)s_tx[j] + (uint32_t)s_x0[j] + tx;
+            a.pkeys[p] = s_t0[j] + ty * (uint32_t)s_tx[j] + tx;
             a.pvals[p] = s_id[j];
         }
         __syncthreads();

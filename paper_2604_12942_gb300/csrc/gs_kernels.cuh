@@ -53,9 +53,10 @@ struct BinArgs {
     uint32_t* scan_tmp;           // block sums of the scans
     uint32_t* vis_bits;           // [ceil(n_views * n / 32)] scratch: one bit per (view, Gaussian) slot
     uint32_t* ekeys;              // compaction output: bits(z) of each entry
-    uint32_t* evals;              //   and its view * n + Gaussian index
-    uint32_t* entries;            //   a copy of evals kept in (view, Gaussian) order
-    const uint32_t* sorted_evals; // entries in depth order (input of the pair emission)
+    uint32_t* evals;              //   and its compact index (the value the depth sort carries)
+    uint32_t* entries;            //   view * n + Gaussian index of each entry, (view, Gaussian) order
+    uint2* erect;                 //   its tile rectangle: (first global tile id, wx | wy << 16)
+    const uint32_t* sorted_evals; // compact indices of the entries in depth order
     uint32_t* pkeys;              // emission output: global tile id of each pair
     uint32_t* pvals;              //   and the entry's view * n + Gaussian index
     uint32_t* poff;               // [n_views * n] pair offset of each depth-sorted entry
