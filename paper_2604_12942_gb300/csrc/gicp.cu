@@ -63,11 +63,17 @@ __device__ __forceinline__ uint32_t g_hash(int cx, int cy, int cz, uint32_t mask
 }
 __device__ __forceinline__ int g_cell(float p, double inv) { return (int)floor((double)p * inv); }
 
+// pts: the flagged target means in hash order, (x, y, z, row index bits), so that a candidate
+// of the nearest-mean search is one 16-byte load from a contiguous run of its cell
 struct GicpHash {
     uint64_t T;
-    uint32_t *count, *start, *cursor, *rows, *cell, *bsum;
+    uint32_t *count, *start, *cursor, *cell, *bsum;
+    float4* pts;
+    double* Rt;   // R (9) and t (3) of the current iteration
     GicpState* state;
 };
+
+static size_t hash_words(uint64_t T, int64_t n_tar) { return 3 * (size_t)T + (size_t)n_tar + (size_t)(T / 1024) + 2; }
 
 static GicpHash hash_layout(void* scratch, int64_t n_tar) {
     GicpHash h;
@@ -78,18 +84,21 @@ static GicpHash hash_layout(void* scratch, int64_t n_tar) {
     h.count = b;
     h.start = h.count + h.T;
     h.cursor = h.start + h.T;
-    h.rows = h.cursor + h.T;
-    h.cell = h.rows + n_tar;
+    h.cell = h.cursor + h.T;
     h.bsum = h.cell + n_tar;
+    uintptr_t q = reinterpret_cast<uintptr_t>(b + hash_words(h.T, n_tar));
+    q = (q + 15) & ~(uintptr_t)15;
+    h.pts = reinterpret_cast<float4*>(q);
+    h.Rt = reinterpret_cast<double*>(h.pts + n_tar);
     return h;
 }
 
 size_t gicp_scratch_bytes(int64_t n_tar) {
     uint64_t T = 1;
     while (T < (uint64_t)(2 * (n_tar > 0 ? n_tar : 1))) T <<= 1;
-    // hash words, then 12 doubles (R, t) after an 8-byte alignment
-    const size_t words = 3 * (size_t)T + 2 * (size_t)n_tar + (size_t)(T / 1024) + 2;
-    const size_t reg = sizeof(GicpState) + sizeof(uint32_t) * words + 8 + 12 * sizeof(double);
+    // hash words, then (16-byte aligned) the means in hash order, then 12 doubles (R, t)
+    const size_t reg = sizeof(GicpState) + sizeof(uint32_t) * hash_words(T, n_tar) + 15 +
+                       sizeof(float4) * (size_t)(n_tar > 0 ? n_tar : 0) + 12 * sizeof(double);
     // target set: the state, then the view table
     const size_t tgt = ((sizeof(GicpState) + 255) & ~(size_t)255) + sizeof(GicpView) * GS_MAX_VIEWS;
     return ((reg > tgt ? reg : tgt) + 255) & ~(size_t)255;
@@ -107,12 +116,14 @@ __global__ void __launch_bounds__(kGThreads) gicp_hash_count(GicpMap tar, const 
     }
 }
 
-__global__ void __launch_bounds__(kGThreads) gicp_hash_fill(int64_t n, const uint8_t* flag, const uint32_t* cell,
-                                                            const uint32_t* start, uint32_t* cursor, uint32_t* rows) {
+__global__ void __launch_bounds__(kGThreads) gicp_hash_fill(GicpMap tar, const uint8_t* flag, const uint32_t* cell,
+                                                            const uint32_t* start, uint32_t* cursor, float4* pts) {
+    const int64_t n = tar.n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (flag && !flag[i]) continue;
         const uint32_t h = cell[i];
-        rows[start[h] + atomicAdd(&cursor[h], 1u)] = (uint32_t)i;
+        pts[start[h] + atomicAdd(&cursor[h], 1u)] =
+            make_float4(tar.means[i], tar.means[n + i], tar.means[2 * n + i], __int_as_float((int)i));
     }
 }
 
@@ -141,7 +152,34 @@ __device__ void planar_cov(const GicpMap& g, int64_t i, double (&S)[6]) {
         }
 }
 
-__global__ void __launch_bounds__(kGThreads) gicp_normal_kernel(GicpMap src, const uint8_t* src_flag, GicpMap tar,
+// ---------------------------------------------------------------------------------------
+// Source list: the flagged source rows of [lo, hi) (hi - lo <= the hash size T), compacted
+// into the hash's cursor words, which are free once the hash is built, with their count in
+// the first scan word.  The normal equations then run on full warps: the FP64 pipe takes a
+// warp instruction at the same cost however few of its lanes are active, so a grid over every
+// row of the map (most not flagged) would pay about 32 times for each flagged row.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGThreads) gicp_src_compact(const uint8_t* flag, int64_t lo, int64_t hi,
+                                                              uint32_t* list, uint32_t* count) {
+    const int lane = threadIdx.x & 31;
+    uint32_t ltm;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(ltm));
+    // (base is the same for the 32 lanes of a warp, so the loop and the ballot are warp-uniform)
+    for (int64_t base = lo + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < hi;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = base + lane;
+        const bool f = m < hi && (!flag || flag[m] != 0);
+        const uint32_t bal = __ballot_sync(0xffffffffu, f);
+        if (!bal) continue;
+        uint32_t b = 0;
+        if (lane == 0) b = atomicAdd(count, (uint32_t)__popc(bal));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (f) list[b + __popc(bal & ltm)] = (uint32_t)(m - lo);
+    }
+}
+
+__global__ void __launch_bounds__(kGThreads) gicp_normal_kernel(GicpMap src, const uint32_t* list,
+                                                                const uint32_t* list_count, int64_t lo, GicpMap tar,
                                                                 double inv, uint32_t mask, float r2,
                                                                 GicpHash h, const double* Rd, const double* td,
                                                                 float Rf0, float Rf1, float Rf2, float Rf3, float Rf4,
@@ -153,8 +191,9 @@ __global__ void __launch_bounds__(kGThreads) gicp_normal_kernel(GicpMap src, con
 #pragma unroll
     for (int k = 0; k < 29; k++) acc[k] = 0.0;
     const int64_t ns = src.n, nt = tar.n;
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < ns; m += (int64_t)gridDim.x * blockDim.x) {
-        if (src_flag && !src_flag[m]) continue;
+    const int64_t cnt = (int64_t)*list_count;
+    for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < cnt; li += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = lo + list[li];
         const float s0 = src.means[m], s1 = src.means[ns + m], s2 = src.means[2 * ns + m];
         float q[3];
 #pragma unroll
@@ -170,9 +209,9 @@ __global__ void __launch_bounds__(kGThreads) gicp_normal_kernel(GicpMap src, con
                     const uint32_t hh = g_hash(cx + dx, cy + dy, cz + dz, mask);
                     const uint32_t b = h.start[hh], e = b + h.count[hh];
                     for (uint32_t t = b; t < e; t++) {
-                        const int64_t j = h.rows[t];
-                        const float ex = __fsub_rn(q[0], tar.means[j]), ey = __fsub_rn(q[1], tar.means[nt + j]);
-                        const float ez = __fsub_rn(q[2], tar.means[2 * nt + j]);
+                        const float4 P = h.pts[t];
+                        const int64_t j = __float_as_int(P.w);
+                        const float ex = __fsub_rn(q[0], P.x), ey = __fsub_rn(q[1], P.y), ez = __fsub_rn(q[2], P.z);
                         const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
                         if (d2 < best || (d2 == best && bi >= 0 && j < bi)) { best = d2; bi = j; }
                     }
@@ -218,7 +257,9 @@ __global__ void __launch_bounds__(kGThreads) gicp_normal_kernel(GicpMap src, con
         acc[27] += res[0] * Or[0] + res[1] * Or[1] + res[2] * Or[2];
         acc[28] += 1.0;
     }
-    // warp sums, then one FP64 atomic per value per warp
+    // warp sums, then one FP64 atomic per value per warp (warps without a correspondence add
+    // nothing)
+    if (!__any_sync(0xffffffffu, acc[28] != 0.0)) return;
 #pragma unroll
     for (int k = 0; k < 29; k++) {
         double v = acc[k];
@@ -249,18 +290,17 @@ cudaError_t launch_gicp_build(const GicpMap& tar, const uint8_t* tar_flag, float
     const uint32_t mask = (uint32_t)(h.T - 1);
     if (tar.n > 0) gicp_hash_count<<<g_grid(tar.n), kGThreads, 0, st>>>(tar, tar_flag, inv, mask, h.count, h.cell);
     if ((e = exclusive_scan_u32(h.count, (int64_t)h.T, h.start, h.bsum, nullptr, st)) != cudaSuccess) return e;
-    if (tar.n > 0) gicp_hash_fill<<<g_grid(tar.n), kGThreads, 0, st>>>(tar.n, tar_flag, h.cell, h.start, h.cursor, h.rows);
+    if (tar.n > 0) gicp_hash_fill<<<g_grid(tar.n), kGThreads, 0, st>>>(tar, tar_flag, h.cell, h.start, h.cursor, h.pts);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gicp_normal_eq(const GicpMap& src, const uint8_t* src_flag, const GicpMap& tar, float d_corr,
                                   const double* R, const double* t, void* scratch, double* acc_host, cudaStream_t st) {
     GicpHash h = hash_layout(scratch, tar.n);
-    // R and t (FP64) travel in the state block's tail, written from the host each iteration
+    // R and t (FP64) travel after the hashed means, written from the host each iteration
     cudaError_t e = cudaMemsetAsync(h.state, 0, sizeof(GicpState), st);
     if (e != cudaSuccess) return e;
-    double* Rt = reinterpret_cast<double*>(h.bsum + (h.T / 1024) + 2);
-    Rt = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(Rt) + 7) & ~(uintptr_t)7);
+    double* Rt = h.Rt;
     double host[12];
     for (int k = 0; k < 9; k++) host[k] = R[k];
     for (int k = 0; k < 3; k++) host[9 + k] = t[k];
@@ -268,11 +308,18 @@ cudaError_t launch_gicp_normal_eq(const GicpMap& src, const uint8_t* src_flag, c
     const double inv = 1.0 / (1.001 * (double)d_corr);
     const uint32_t mask = (uint32_t)(h.T - 1);
     const float r2 = d_corr * d_corr;
-    if (src.n > 0)
-        gicp_normal_kernel<<<g_grid(src.n), kGThreads, 0, st>>>(
-            src, src_flag, tar, inv, mask, r2, h, Rt, Rt + 9, (float)R[0], (float)R[1], (float)R[2], (float)R[3],
-            (float)R[4], (float)R[5], (float)R[6], (float)R[7], (float)R[8], (float)t[0], (float)t[1], (float)t[2]);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the source rows in segments of at most T rows (one segment when the source map is no
+    // larger than twice the target map)
+    for (int64_t lo = 0; lo < src.n; lo += (int64_t)h.T) {
+        const int64_t hi = src.n - lo < (int64_t)h.T ? src.n : lo + (int64_t)h.T;
+        if ((e = cudaMemsetAsync(h.bsum, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        gicp_src_compact<<<g_grid(hi - lo), kGThreads, 0, st>>>(src_flag, lo, hi, h.cursor, h.bsum);
+        gicp_normal_kernel<<<g_grid(hi - lo), kGThreads, 0, st>>>(
+            src, h.cursor, h.bsum, lo, tar, inv, mask, r2, h, Rt, Rt + 9, (float)R[0], (float)R[1], (float)R[2],
+            (float)R[3], (float)R[4], (float)R[5], (float)R[6], (float)R[7], (float)R[8], (float)t[0], (float)t[1],
+            (float)t[2]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if ((e = cudaMemcpyAsync(acc_host, h.state->acc, sizeof(double) * 29, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return e;
     return cudaStreamSynchronize(st);   // the host array must not go out of scope before the copy
