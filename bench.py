@@ -482,6 +482,11 @@ def f23_measure(step, cams, dev):
     prune_ms, (keep, nk) = timed(lambda: gs.prune_plan(planes, 3, 0.005, 0.01, scratch))
     dedup_ms, (acc, na) = timed(lambda: gs.dedup_plan(planes, 3, new[0:3], 0.05, scratch))
     upd_ms, _ = timed(lambda: gs.map_update(planes, step.m, step.v, 3, keep, new, acc, scratch=scratch))
+    # map update: kept rows move p, m and v (read + write), accepted new rows read p and write
+    # p, m, v; flags and scanned positions (5 B per row) once
+    pk, _ = peaks()
+    P = planes.shape[0]
+    upd_bytes = 4 * P * (6 * nk + 4 * na) + 5 * (n + n_new)
     gscr = gs.gicp_scratch(n, dev)
     views = cams[:4]
     tgt_ms, (tflag, nt) = timed(lambda: gs.gicp_target_set(planes, 3, views, 0.2, 20.0, None, gscr))
@@ -496,6 +501,11 @@ def f23_measure(step, cams, dev):
     return {"prune_plan_ms": round(prune_ms, 3), "rows": n, "pruned": n - nk,
             "dedup_plan_ms": round(dedup_ms, 3), "new_rows": n_new, "accepted": na,
             "map_update_ms": round(upd_ms, 3), "rows_out": nk + na,
+            "map_update_roofline": {"bound": "hbm", "bytes": upd_bytes,
+                                    "achieved": round(upd_bytes / (upd_ms * 1e-3) / 1e9, 1),
+                                    "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                    "frac": round(upd_bytes / (upd_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                                    "note": "public call (its scan, the copy kernel and the host sync)"},
             "gicp_target_set_ms": round(tgt_ms, 3), "target_rows": nt, "views": len(views),
             "gicp_register_ms": round(reg_ms, 3), "source_rows": int(src_flag.sum()),
             "gicp_translation_error_m": float(np.linalg.norm(np.asarray(T)[:3, 3])),

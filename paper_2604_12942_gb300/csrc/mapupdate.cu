@@ -246,8 +246,13 @@ cudaError_t exclusive_scan_u32(const uint32_t* x, int64_t n, uint32_t* out, uint
 // ---------------------------------------------------------------------------------------
 // Compaction: kept rows to their scanned positions, accepted new rows after them (with zero
 // moments).  Every plane is passed by its own base pointer (input stride n, new rows n_new,
-// output n_out).
+// output n_out).  One thread per row; the planes go in groups of 8, all 24 loads of a group
+// (parameters, m, v) before its stores, so that a row has that many reads in flight instead
+// of the three a plane at a time would give (the stores may alias later loads as far as the
+// compiler knows, so it cannot reorder them itself).
 // ---------------------------------------------------------------------------------------
+constexpr int kCompactGroup = 8;
+
 __global__ void __launch_bounds__(kMuThreads) compact_kernel(MapUpdateArgs a) {
     const int64_t total = a.n + a.n_new;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
@@ -255,10 +260,26 @@ __global__ void __launch_bounds__(kMuThreads) compact_kernel(MapUpdateArgs a) {
         const int64_t i = old ? r : r - a.n;
         if (old ? !a.keep[i] : (a.accept && !a.accept[i])) continue;
         const int64_t o = old ? (int64_t)a.pos_keep[i] : (int64_t)a.n_keep + (a.pos_new ? (int64_t)a.pos_new[i] : i);
-        for (int p = 0; p < a.n_planes; p++) {
-            a.out[p][o] = old ? a.in[p][i] : a.nw[p][i];
-            a.m_out[p][o] = old ? a.m_in[p][i] : 0.f;
-            a.v_out[p][o] = old ? a.v_in[p][i] : 0.f;
+        for (int p0 = 0; p0 < a.n_planes; p0 += kCompactGroup) {
+            float x[kCompactGroup], mm[kCompactGroup], vv[kCompactGroup];
+#pragma unroll
+            for (int k = 0; k < kCompactGroup; k++) {
+                const int p = p0 + k;
+                if (p < a.n_planes) {
+                    x[k] = old ? a.in[p][i] : a.nw[p][i];
+                    mm[k] = old ? a.m_in[p][i] : 0.f;
+                    vv[k] = old ? a.v_in[p][i] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kCompactGroup; k++) {
+                const int p = p0 + k;
+                if (p < a.n_planes) {
+                    a.out[p][o] = x[k];
+                    a.m_out[p][o] = mm[k];
+                    a.v_out[p][o] = vv[k];
+                }
+            }
         }
         if (a.tags_out) a.tags_out[o] = old ? (a.tags_in ? a.tags_in[i] : 0u) : (a.new_tags ? a.new_tags[i] : 0u);
     }
