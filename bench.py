@@ -548,11 +548,12 @@ def roofline_table(stage, w, pk, pk_kind):
     B = {
         # geometry of every row, SH of the rows some view sees
         "project": 44 * n + 192 * w["visible_gaussians"] + 4 * VN + 48 * E,
-        # entry count + compaction (touched once, its bit words written and read, z, entry
-        # write), depth sort (20 B per
-        # entry per pass), pair count + emission (entry id, touched, record u v rx ry, pair
-        # write), tile sort (20 B per pair per pass), ranges (tile ids)
-        "bin_sort": 4 * VN + VN // 4 + 12 * E + w["depth_sort_passes"] * 20 * E + 8 * E + 24 * E + 8 * P
+        # entry count (touched once, bit words written) and compaction (bit words read; per
+        # entry 24 B of its record read, key, value, index and tile rectangle written: 20 B),
+        # depth sort (20 B per entry per pass), pair count and offsets (sorted id and rectangle
+        # twice, offset written: 28 B per entry), emission (sorted id, index, rectangle, offset:
+        # 20 B per entry; 8 B per pair written), tile sort (20 B per pair per pass), ranges
+        "bin_sort": 4 * VN + VN // 4 + 44 * E + w["depth_sort_passes"] * 20 * E + 48 * E + 8 * P
                     + w["tile_sort_passes"] * 20 * P + 4 * P,
         # fused projection backward + Adam, rows visible in some view: parameters, m and v
         # read, parameters, m and v written (6 x 236 B); visibility and touched flags of every
