@@ -768,26 +768,41 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(BwdArgs a) {
             const float4 r0 = s_rec[b][t][0], r1 = s_rec[b][t][1];
             const float2 bx = make_float2(r0.x, r0.y);
             const float4 co = make_float4(r1.x, r1.y, r1.z, r0.w);
+            // the alphas of the lane's pixels first: a record that no pixel of the warp adds
+            // (all below alpha_min or past their pixels' last fragment) changes nothing and is
+            // skipped whole
+            float dxq[kPPT], dyq[kPPT], hxq[kPPT], hyq[kPPT], Gq[kPPT], a0q[kPPT], alq[kPPT];
+            bool cq[kPPT];
+            bool contrib = false;
+#pragma unroll
+            for (int q = 0; q < kPPT; q++) {
+                const bool live = (uint32_t)j < last[q];
+                dxq[q] = px[q] - bx.x;
+                dyq[q] = py[q] - bx.y;
+                const FragE fe = frag_exponent(dxq[q], dyq[q], co.x, co.y, co.z);
+                hxq[q] = fe.hx;
+                hyq[q] = fe.hy;
+                Gq[q] = ex2_approx(fe.e);
+                a0q[q] = co.w * Gq[q];
+                alq[q] = fminf(amax, a0q[q]);
+                cq[q] = live && !(alq[q] < amin);
+                if constexpr (COUNT) {
+                    n_eval += live;
+                    n_add += cq[q];
+                }
+                contrib |= cq[q];
+            }
+            if (!__any_sync(0xffffffffu, contrib)) continue;
             float val[10];
 #pragma unroll
             for (int q = 0; q < 10; q++) val[q] = 0.f;
-            bool contrib = false;
             const float4 r2 = s_rec[b][t][2];
             const float4 cz = make_float4(r2.x, r2.y, r2.z, r0.z);
 #pragma unroll
             for (int q = 0; q < kPPT; q++) {
-                const bool live = (uint32_t)j < last[q];
-                const float dx = px[q] - bx.x, dy = py[q] - bx.y;
-                const FragE fe = frag_exponent(dx, dy, co.x, co.y, co.z);
-                const float G = ex2_approx(fe.e);
-                const float a0 = co.w * G;
-                const float alpha = fminf(amax, a0);
-                const bool c = live && !(alpha < amin);
-                if constexpr (COUNT) {
-                    n_eval += live;
-                    n_add += c;
-                }
-                contrib |= c;
+                const float dx = dxq[q], dy = dyq[q], G = Gq[q], a0 = a0q[q], alpha = alq[q];
+                const FragE fe = {hxq[q], hyq[q], 0.f};
+                const bool c = cq[q];
                 const float rom = rcp_approx(1.f - alpha);
                 const float Tn = T[q] * rom;
                 const float wgt = alpha * Tn;
