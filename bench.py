@@ -36,10 +36,10 @@ METRIC = "fwd+bwd render Mpix/s and iters/s at 2M Gaussians; secs-to-PSNR learne
 # (key tile = chunk = 0).  Once a kernel changes these must be captured again; a shape without an
 # entry reports null.
 NCU_TRAFFIC = {
-    ("render_bwd_warp_kernel", 16, 0): 320_741_376 + 62_899_200,
-    ("render_fwd_kernel", 16, 256): 221_431_552 + 200_414_976,
-    ("project_bwd_entry_kernel", 0, 0): 159_156_736 + 52_907_264,
-    ("project_bwd_kernel", 0, 0): 1_195_792_128 + 861_713_408,
+    ("render_bwd_warp_kernel", 16, 0): 322_142_976 + 62_984_192,
+    ("render_fwd_kernel", 16, 256): 223_078_144 + 200_414_976,
+    ("project_bwd_entry_kernel", 0, 0): 159_240_448 + 51_640_832,
+    ("project_bwd_kernel", 0, 0): 1_195_726_080 + 861_915_136,
 }
 
 
