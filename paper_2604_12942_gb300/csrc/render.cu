@@ -304,10 +304,11 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
         if (__syncthreads_count(!done) == 0) break;   // (also: every warp is done with buffer b ^ 1)
         stage(c + 1, b ^ 1);
         fetch_ids(c + 2);
-        cp_async_wait_prior();   // chunk c has landed (chunk c + 1 may still be in flight)
-        __syncthreads();
+        cp_async_wait_prior();   // this thread's copies of chunk c have landed (c + 1 may be in flight)
         const int m = min(CHUNK, n - base);
-        // warp-region masks of the chunk's records, kept per pair for the backward
+        // warp-region masks of the chunk's records, kept per pair for the backward.  Thread t
+        // takes the records it copied itself (stage gives record k to thread k mod NT), which
+        // its own wait has made visible to it: no barrier before this loop.
         for (int k = threadIdx.x; k < m; k += NT) {
             const float4 r0 = s_rec[b][k][0], r1 = s_rec[b][k][1];
             const float rxf = (float)__float_as_int(r1.w), ryf = (float)__float_as_int(s_rec[b][k][2].w);
