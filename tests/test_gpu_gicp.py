@@ -95,3 +95,36 @@ def test_register_with_flags_uses_only_flagged_rows():
     T_ref, cost, cnt, it, conv = gicp.register(P[0:3, s_idx], covs, P[0:3, t_idx], covt, np.eye(4), 0.5, 10, 1e-7)
     assert res.n_corr == cnt and res.iters == it
     np.testing.assert_allclose(T, T_ref, atol=1e-6)
+
+
+def test_register_source_map_larger_than_target_hash():
+    """A source map of 5000 rows against 600 target rows (hash of 2048 cells): the flagged
+    source rows are listed and summed in three segments of the source map; the result is the
+    oracle's on the flagged rows alone."""
+    rng = np.random.default_rng(9)
+    means, quats, ls = _planar_map(rng, 600)
+    tar = _planes_of(means, quats, ls)
+    T_gt = gicp.se3_exp(np.array([0.1, 0.05, -0.06, -0.02, 0.03, 0.01]))
+    Ti = np.linalg.inv(T_gt)
+    n_src, sel = 5000, rng.choice(tar.shape[1], 400, replace=False)
+    rows = np.sort(rng.choice(n_src, 400, replace=False))        # spread over every segment
+    src = _planes_of(rng.uniform(500, 600, (3, n_src)), np.tile([[1.0], [0], [0], [0]], (1, n_src)),
+                     np.full((3, n_src), -2.0))                   # unflagged rows far away
+    src[0:3, rows] = Ti[:3, :3] @ tar[0:3, sel].astype(np.float64) + Ti[:3, 3:]
+    src_R = Ti[:3, :3] @ np.stack([gicp.quat_to_R(q) for q in tar[6:10, sel].T])
+    q_xyzw = Rotation.from_matrix(src_R).as_quat()
+    src[6:10, rows] = np.stack([q_xyzw[:, 3], q_xyzw[:, 0], q_xyzw[:, 1], q_xyzw[:, 2]])
+    src[3:6, rows] = tar[3:6, sel]
+    flag = np.zeros(n_src, np.uint8)
+    flag[rows] = 1
+    T, res = gs.gicp_register(torch.as_tensor(src, device="cuda"), torch.as_tensor(flag, device="cuda"),
+                              torch.as_tensor(tar, device="cuda"), None, 0, np.eye(4), d_corr=1.0, max_iters=30,
+                              eps=1e-7)
+    s = src[:, rows]
+    covs = [gicp.planar_covariance(s[6:10, m], s[3:6, m]) for m in range(s.shape[1])]
+    covt = [gicp.planar_covariance(tar[6:10, m], tar[3:6, m]) for m in range(tar.shape[1])]
+    T_ref, cost, cnt, it, conv = gicp.register(s[0:3], covs, tar[0:3], covt, np.eye(4), 1.0, 30, 1e-7)
+    assert res.n_corr == cnt and res.iters == it and res.converged == int(conv)
+    np.testing.assert_allclose(T, T_ref, atol=1e-6)
+    np.testing.assert_allclose(T, T_gt, atol=1e-4)
+    assert abs(res.cost - cost) <= 1e-5 * max(1.0, cost)
