@@ -54,7 +54,8 @@ class _Opts(C.Structure):
 class _Proj(C.Structure):
     _fields_ = [("visible", C.c_void_p), ("u", C.c_void_p), ("v", C.c_void_p), ("z", C.c_void_p),
                 ("cov2d", C.c_void_p), ("conic", C.c_void_p), ("opacity", C.c_void_p),
-                ("rgb", C.c_void_p), ("rx", C.c_void_p), ("ry", C.c_void_p), ("fragile", C.c_void_p)]
+                ("rgb", C.c_void_p), ("rx", C.c_void_p), ("ry", C.c_void_p), ("fragile", C.c_void_p),
+                ("zkey", C.c_void_p)]
 
 
 def lib():
@@ -137,15 +138,18 @@ def _params(scene):
             _f64(scene.opacity_logits), _f64(scene.sh))
 
 
+_PROJ_FIELDS = ("visible", "u", "v", "z", "cov2d", "conic", "opacity", "rgb", "rx", "ry", "fragile", "zkey")
+
+
 def project(scene, cam, opts: Opts = Opts()):
-    """Per-Gaussian projection into one view.  Returns a dict of arrays."""
+    """Per-Gaussian projection into one view.  Returns a dict of arrays; `zkey` is the FP32
+    depth key that orders the compositing (front to back, equal keys by index)."""
     n = scene.n
     out = dict(visible=np.zeros(n, np.int32), u=np.zeros(n), v=np.zeros(n), z=np.zeros(n),
                cov2d=np.zeros(3 * n), conic=np.zeros(3 * n), opacity=np.zeros(n),
                rgb=np.zeros(3 * n), rx=np.zeros(n, np.int32), ry=np.zeros(n, np.int32),
-               fragile=np.zeros(n, np.int32))
-    pr = _Proj(*[_p(out[k]).value for k in ("visible", "u", "v", "z", "cov2d", "conic", "opacity",
-                                              "rgb", "rx", "ry", "fragile")])
+               fragile=np.zeros(n, np.int32), zkey=np.zeros(n, np.float32))
+    pr = _Proj(*[_p(out[k]).value for k in _PROJ_FIELDS])
     ps = _params(scene)
     lib().or_project(n, scene.sh_degree, *[_p(a) for a in ps], C.byref(_cam(cam)), C.byref(opts.c()),
                      C.byref(pr))
@@ -159,8 +163,8 @@ def project(scene, cam, opts: Opts = Opts()):
 def _proj_struct(pr):
     for k in ("cov2d", "conic", "rgb"):
         assert pr[k].flags.c_contiguous
-    return _Proj(*[_p(pr[k]).value for k in ("visible", "u", "v", "z", "cov2d", "conic", "opacity",
-                                              "rgb", "rx", "ry", "fragile")])
+    assert pr["zkey"].dtype == np.float32
+    return _Proj(*[_p(pr[k]).value for k in _PROJ_FIELDS])
 
 
 def render(pr, cam, opts: Opts = Opts(), margin=1e-4, use_square=True):

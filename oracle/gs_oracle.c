@@ -60,6 +60,7 @@ typedef struct {
     double *rgb;       /* [3n] */
     int32_t *rx, *ry;  /* half-extents (px) of the alpha >= alpha_min box, 0 if culled */
     int32_t *fragile;  /* 1 if a cull decision lies within a relative 1e-5 of its threshold */
+    float *zkey;       /* FP32 depth key that orders the compositing (see depth_key) */
 } or_proj;
 
 /* ------------------------------------------------------------------------------------ */
@@ -173,6 +174,7 @@ typedef struct {
     double M[9];           /* Rq * diag(s) */
     double Sigma[9];       /* world covariance */
     double pc[3];          /* camera-frame centre */
+    float zkey;            /* FP32 depth key (depth_key) */
     double tx, ty;         /* clamped x/z, y/z */
     int clx, cly;          /* 1 if clamped */
     double J[6];           /* 2x3 */
@@ -189,6 +191,21 @@ typedef struct {
     int32_t rx, ry;
 } proj1;
 
+/* The front-to-back order of the compositing (§III-C; ties and precision are not stated by
+ * the paper).  Reading: Gaussians are ordered by the IEEE single-precision camera depth
+ *   z32 = fma(R22, mu_z, fma(R21, mu_y, R20 * mu_x)) + t_z
+ * with every operation rounded to FP32 (fmaf rounds once), taken on the FP32 values of the
+ * pose (third row of R_cw, t_cw) and of the mean, and equal keys in ascending Gaussian index.  The order is an integer decision made from floating point, so
+ * it is fixed in the precision of the FP32 step, exactly, with this operation order; the
+ * continuous quantities (the depth D, the weights) stay in double. */
+static float depth_key(const double *W, const double *t, const double *mu) {
+    const float r20 = (float)W[6], r21 = (float)W[7], r22 = (float)W[8], tz = (float)t[2];
+    const float m0 = (float)mu[0], m1 = (float)mu[1], m2 = (float)mu[2];
+    const float p = r20 * m0;                 /* rounded product (no contraction: -ffp-contract=off) */
+    const float s = fmaf(r22, m2, fmaf(r21, m1, p));
+    return s + tz;
+}
+
 static void project_one(const double *mu, const double *ls, const double *q, double logit,
                         const double *shc /* [K][3] */, int deg, const or_camera *cam,
                         const or_opts *opt, proj1 *P) {
@@ -199,6 +216,7 @@ static void project_one(const double *mu, const double *ls, const double *q, dou
     for (int i = 0; i < 3; i++) cw[i] = -(W[0 * 3 + i] * cam->t[0] + W[1 * 3 + i] * cam->t[1] + W[2 * 3 + i] * cam->t[2]);
     /* camera-frame centre */
     for (int i = 0; i < 3; i++) P->pc[i] = W[i * 3 + 0] * mu[0] + W[i * 3 + 1] * mu[1] + W[i * 3 + 2] * mu[2] + cam->t[i];
+    P->zkey = depth_key(W, cam->t, mu);
     const double x = P->pc[0], y = P->pc[1], z = P->pc[2];
     if (fabs(z - opt->near_z) <= 1e-5 * fabs(opt->near_z) + 1e-12) P->fragile = 1;
     if (!(z > opt->near_z)) { P->culled = 1; return; }
@@ -290,6 +308,7 @@ void or_project(int64_t n, int deg, const double *means, const double *log_scale
         out->rx[i] = P.culled ? 0 : P.rx;
         out->ry[i] = P.culled ? 0 : P.ry;
         out->u[i] = P.u; out->v[i] = P.v; out->z[i] = P.pc[2];
+        out->zkey[i] = P.zkey;
         out->opacity[i] = P.o;
         for (int k = 0; k < 3; k++) {
             out->conic[3 * i + k] = P.culled ? 0 : P.conic[k];
@@ -304,7 +323,7 @@ void or_project(int64_t n, int deg, const double *means, const double *log_scale
 /* ------------------------------------------------------------------------------------ */
 /* Brute-force compositing.                                                              */
 /* ------------------------------------------------------------------------------------ */
-typedef struct { double z; int64_t id; } zid;
+typedef struct { float z; int64_t id; } zid;
 static int cmp_zid(const void *a, const void *b) {
     const zid *x = (const zid *)a, *y = (const zid *)b;
     if (x->z < y->z) return -1;
@@ -312,12 +331,13 @@ static int cmp_zid(const void *a, const void *b) {
     return (x->id > y->id) - (x->id < y->id);
 }
 
-/* Visible Gaussians in front-to-back order: ascending depth, ties by index. */
+/* Visible Gaussians in front-to-back order: ascending FP32 depth key (depth_key), equal keys
+ * by ascending index. */
 static int64_t depth_order(int64_t n, const or_proj *pr, int64_t *order) {
     zid *tmp = (zid *)malloc(sizeof(zid) * (size_t)(n > 0 ? n : 1));
     int64_t m = 0;
     for (int64_t i = 0; i < n; i++)
-        if (pr->visible[i]) { tmp[m].z = pr->z[i]; tmp[m].id = i; m++; }
+        if (pr->visible[i]) { tmp[m].z = pr->zkey[i]; tmp[m].id = i; m++; }
     qsort(tmp, (size_t)m, sizeof(zid), cmp_zid);
     for (int64_t k = 0; k < m; k++) order[k] = tmp[k].id;
     free(tmp);
@@ -340,10 +360,10 @@ static double frag_alpha(const or_proj *pr, int64_t g, double px, double py, con
 
 /* Per pixel: C = sum_i c_i alpha_i T_i + T_final bg, D = sum_i z_i alpha_i T_i,
  * T_final, the number of added fragments, and a fragility flag: 1 if a decision taken at
- * this pixel (alpha vs alpha_min, T(1-alpha) vs T_min, alpha vs the alpha_max clamp, the
- * depth order of two added neighbours, a cull decision of an added Gaussian) lies within a
- * relative `margin` of its threshold, so that a correct FP32 implementation may take the
- * other branch.  Gaussians whose screen box (half-extents rx, ry) does not contain the pixel
+ * this pixel (alpha vs alpha_min, T(1-alpha) vs T_min, alpha vs the alpha_max clamp, a cull
+ * decision of an added Gaussian) lies within a relative `margin` of its threshold, so that a
+ * correct FP32 implementation may take the other branch.  The depth order is no such
+ * decision: it is defined exactly on the FP32 key (depth_key).  Gaussians whose screen box (half-extents rx, ry) does not contain the pixel
  * centre are skipped: outside the box alpha < alpha_min by construction (tested). */
 void or_render(int64_t n, const or_proj *pr, const or_camera *cam, const or_opts *opt,
                double margin, int use_square, double *C, double *D, double *T_out,
@@ -357,8 +377,6 @@ void or_render(int64_t n, const or_proj *pr, const or_camera *cam, const or_opts
             const double cx = px + 0.5, cy = py + 0.5;
             double T = 1.0, c[3] = {0, 0, 0}, d = 0;
             int cnt = 0, fr = 0;
-            double last_z = -1;
-            int64_t last_g = -1;
             for (int64_t k = 0; k < m; k++) {
                 const int64_t g = order[k];
                 if (use_square) {
@@ -373,14 +391,11 @@ void or_render(int64_t n, const or_proj *pr, const or_camera *cam, const or_opts
                 if (fabs(test_T - opt->T_min) <= margin * opt->T_min) fr = 1;
                 if (test_T < opt->T_min) break;
                 if (pr->fragile[g]) fr = 1;
-                if (last_g >= 0 && fabs(pr->z[g] - last_z) <= margin * 0.1 * fabs(last_z)) fr = 1;
                 const double w = a * T;
                 for (int ch = 0; ch < 3; ch++) c[ch] += w * pr->rgb[3 * g + ch];
                 d += w * pr->z[g];
                 T = test_T;
                 cnt++;
-                last_z = pr->z[g];
-                last_g = g;
             }
             const int64_t p = (int64_t)py * W + px;
             for (int ch = 0; ch < 3; ch++) C[(int64_t)ch * W * H + p] = c[ch] + T * opt->bg[ch];

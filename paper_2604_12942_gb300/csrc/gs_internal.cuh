@@ -288,9 +288,14 @@ __device__ __forceinline__ void project_view(const float* mu, const Cov3& cv, fl
     // Every field is computed (no early exit) so the backward, which recomputes this for
     // the pairs the forward kept, never reads an unset value.
     const float* W = V.R;
-    P.pc[0] = W[0] * mu[0] + W[1] * mu[1] + W[2] * mu[2] + V.t[0];
-    P.pc[1] = W[3] * mu[0] + W[4] * mu[1] + W[5] * mu[2] + V.t[1];
-    P.pc[2] = W[6] * mu[0] + W[7] * mu[1] + W[8] * mu[2] + V.t[2];
+    // Camera-frame centre, each row as fma(R_k2, mu_z, fma(R_k1, mu_y, R_k0 mu_x)) + t_k with
+    // every operation rounded once.  The depth's FP32 bits are the compositing order's sort
+    // key, so its operation order is part of the definition of that order; the intrinsics
+    // keep the compiler from contracting it any other way.
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        P.pc[k] = __fadd_rn(__fmaf_rn(W[3 * k + 2], mu[2], __fmaf_rn(W[3 * k + 1], mu[1], __fmul_rn(W[3 * k], mu[0]))),
+                            V.t[k]);
     const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
     const bool front = z > op.near_z;
     const float iz = 1.0f / (front ? z : 1.0f);

@@ -1,12 +1,25 @@
-"""Parity at the benchmark's full size: the 2M-Gaussian SH-3 LiDAR loop scene with its 8 views of
-uneven size, in the launch configuration bench.py times (8x8 tiles, chunks of 64), checked on
-samples the FP64 oracle can compute: every pixel of one crop per image-size class (brute force
-over all 2M Gaussians), and every parameter gradient and pose twist when the upstream gradient
-is restricted to those crops.
+"""Parity at full size, in the launch shapes the bench times.
+
+Workloads (seeded, synthetic LiDAR-camera scenes, SH degree 3):
+  * batched_2M: the bench's 2M-Gaussian loop scene with its 8 views 2 x {640x480, 960x540,
+    1280x720, 1280x1024};
+  * single_500k: 500k Gaussians of a line scene seen by one 1280x720 camera;
+  * single_1M: 1M Gaussians of a line scene seen by one 1024x768 camera.
+The GPU renders the whole views in the bench's autotuned shape (16x16 tiles, chunks of 256)
+and, for the 2M batch, also in 8x8 tiles with chunks of 64.  The FP64 oracle computes what it
+can at this size: every pixel of a few crops per workload (brute force over all Gaussians),
+and every parameter gradient and pose twist when the upstream gradient is restricted to
+those crops.
 
 A crop is the view's camera with the principal point moved by the crop offset; the Jacobian
 clamp limit clamp_fov (W/2)/fx is kept equal to the full view's by scaling clamp_fov with
-W / w, which holds for x and y alike because each crop has its view's aspect ratio."""
+W / w, which holds for x and y alike because each crop has its view's aspect ratio.
+
+The compositing order is the FP32 depth key on both sides (ties by index), so only the
+pixels with an FP32 branch within a relative 1e-4 of its threshold (alpha vs alpha_min,
+T (1 - alpha) vs T_min, the 0.99 clamp, a cull) are fragile: at most 5% per crop, checked
+for validity only and left out of the gradient comparison.  All other pixels meet the
+images' max-abs 1e-4 and the gradients' relative L2 1e-3."""
 import numpy as np
 import pytest
 import torch
@@ -18,92 +31,136 @@ from tests.gpu_helpers import GROUPS, rel_l2
 
 pytestmark = pytest.mark.gpu
 
+IMG_TOL = 1e-4
 GRAD_TOL = 1e-3
-# view -> crop size (one view of each size class; the crop keeps the view's aspect ratio)
-CROPS = {0: (64, 48), 2: (64, 36), 4: (64, 36), 6: (80, 64)}
+MAX_FRAGILE = 0.05
 
 
-def _crop(cam, w, h):
-    """Centred w x h crop of `cam` and its oracle options (clamp limit of the full view)."""
-    x0, y0 = (cam["width"] - w) // 2, (cam["height"] - h) // 2
+def _batched_2m():
+    import bench
+    sc, _, cams = bench.make_workload(2_000_000, 0)
+    # view -> crops (w, h, x0, y0 or None = centred); one view of each size class
+    crops = {0: [(64, 48, None)], 2: [(64, 36, None)], 4: [(64, 36, None)], 6: [(80, 64, None), (80, 64, 96, 700)]}
+    return sc, cams, crops
+
+
+def _single(seed, n, size, pose, crops):
+    sc = synth.lidar_scene(seed=seed, n=n, sh_degree=3, kind="line")
+    cams = synth.trajectory_cameras(sc, [size], [pose])
+    return sc, cams, {0: crops}
+
+
+WORKLOADS = {
+    "batched_2M": _batched_2m,
+    "single_500k": lambda: _single(2, 500_000, (1280, 720), 120, [(64, 36, None), (96, 54, 200, 500)]),
+    "single_1M": lambda: _single(4, 1_000_000, (1024, 768), 60, [(64, 48, None), (96, 72, 800, 80)]),
+}
+# (workload, tile, chunk): the bench's autotuned shape everywhere, 8x8 / 64 on the batch too
+CASES = [("batched_2M", 16, 256), ("batched_2M", 8, 64), ("single_500k", 16, 256), ("single_1M", 16, 256)]
+
+
+def _crop(cam, crop):
+    """A w x h crop of `cam` (centred, or at (x0, y0)) and its oracle options."""
+    w, h = crop[0], crop[1]
+    if crop[2] is None:
+        x0, y0 = (cam["width"] - w) // 2, (cam["height"] - h) // 2
+    else:
+        x0, y0 = crop[2], crop[3]
     c = dict(cam)
     c["cx"] = cam["cx"] - x0
     c["cy"] = cam["cy"] - y0
     c["width"], c["height"] = w, h
     assert cam["width"] * h == cam["height"] * w
+    assert 0 <= x0 and x0 + w <= cam["width"] and 0 <= y0 and y0 + h <= cam["height"]
     return c, oracle.Opts(clamp_fov=1.3 * cam["width"] / w), x0, y0
 
 
-@pytest.fixture(scope="module")
-def full():
-    import bench
-    sc, _, cams = bench.make_workload(2_000_000, 0)
-    opts = gs.default_opts(tile=8, chunk=64)
+_ORACLE = {}
+
+
+def _oracle_case(name):
+    """Scene, cameras and the oracle's crops of one workload (computed once per module)."""
+    if name not in _ORACLE:
+        sc, cams, crops = WORKLOADS[name]()
+        out = []
+        for v, lst in crops.items():
+            for crop in lst:
+                cam, o_opts, x0, y0 = _crop(cams[v], crop)
+                pr = oracle.project(sc, cam, o_opts)
+                img = oracle.render(pr, cam, o_opts)
+                out.append((v, cam, o_opts, x0, y0, pr, img))
+        _ORACLE[name] = (sc, cams, out)
+    return _ORACLE[name]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[f"{w}-{t}x{c}" for w, t, c in CASES])
+def full(request):
+    name, tile, chunk = request.param
+    sc, cams, crops = _oracle_case(name)
+    opts = gs.default_opts(tile=tile, chunk=chunk)
     ws = gs.Workspace(sc.n, cams, opts, 64_000_000)
     planes = torch.as_tensor(sc.planes(), device="cuda").contiguous()
     P = ws.layout.total_pixels
     rgb = torch.zeros(3 * P, device="cuda")
     depth = torch.zeros(P, device="cuda")
+    T = torch.zeros(P, device="cuda")
     ws.project(planes, 3)
     ws.bin_sort()
-    ws.render_fwd(rgb, depth)
+    ws.render_fwd(rgb, depth, T)
     torch.cuda.synchronize()
     c = ws.counters()
-    assert c.status == 0 and c.n_pairs > 20_000_000
-    crops = {}
-    for v, (w, h) in CROPS.items():
-        cam, o_opts, x0, y0 = _crop(cams[v], w, h)
-        pr = oracle.project(sc, cam, o_opts)
-        img = oracle.render(pr, cam, o_opts)
-        crops[v] = (cam, o_opts, x0, y0, pr, img)
-    return sc, cams, ws, planes, rgb, depth, crops
+    assert c.status == 0 and c.n_pairs > 1_000_000, (c.status, c.n_pairs)
+    yield sc, cams, ws, planes, rgb, depth, T, crops
+    del ws
+    torch.cuda.empty_cache()
 
 
 def test_fullsize_forward_crops_match_oracle(full):
-    sc, cams, ws, planes, rgb, depth, crops = full
+    sc, cams, ws, planes, rgb, depth, T, crops = full
     C = gs.unpack_rgb(rgb, cams)
     D = gs.unpack_plane(depth, cams)
-    for v, (cam, o_opts, x0, y0, pr, img) in crops.items():
+    Tv = gs.unpack_plane(T, cams)
+    for v, cam, o_opts, x0, y0, pr, img in crops:
         w, h = cam["width"], cam["height"]
         Cg = C[v][:, y0:y0 + h, x0:x0 + w].cpu().numpy()
         Dg = D[v][y0:y0 + h, x0:x0 + w].cpu().numpy()
-        # At this density most pixels are "fragile": two of their added fragments lie at depths
-        # within 1e-5 (relative) of each other -- Gaussians on one facade -- and FP32 depths may
-        # order them either way.  Those pixels are checked for validity, the others exactly.
-        ok = ~img["fragile"]
-        assert ok.sum() > 200, (v, ok.mean())
-        assert np.abs(Cg - img["C"])[:, ok].max() < 1e-4, v
-        assert (np.abs(Dg - img["D"]) / np.maximum(1.0, np.abs(img["D"])))[ok].max() < 1e-4, v
-        assert np.isfinite(Cg).all() and (Cg >= -1e-6).all()
-        err = np.abs(Cg - img["C"]).max(axis=0)
-        assert np.mean(err < 0.02) > 0.95 and np.median(err) < 1e-3, (v, np.mean(err < 0.02), np.median(err))
+        Tg = Tv[v][y0:y0 + h, x0:x0 + w].cpu().numpy()
+        fr = img["fragile"]
+        assert fr.mean() <= MAX_FRAGILE, (v, fr.mean())
+        ok = ~fr
+        assert np.abs(Cg - img["C"])[:, ok].max() < IMG_TOL, (v, np.abs(Cg - img["C"])[:, ok].max())
+        assert np.abs(Tg - img["T"])[ok].max() < IMG_TOL, v
+        assert (np.abs(Dg - img["D"]) / np.maximum(1.0, np.abs(img["D"])))[ok].max() < IMG_TOL, v
+        # fragile pixels: valid values (finite, non-negative colour, transmittance in [0, 1])
+        assert np.isfinite(Cg).all() and (Cg >= -1e-6).all() and np.isfinite(Dg).all()
+        assert (Tg >= 0).all() and (Tg <= 1).all()
 
 
 def test_fullsize_backward_crops_match_oracle(full):
-    sc, cams, ws, planes, rgb, depth, crops = full
+    sc, cams, ws, planes, rgb, depth, T, crops = full
     P = ws.layout.total_pixels
     off = gs.pixel_offsets(cams)
     dl_rgb = torch.zeros(3 * P, device="cuda")
     dl_d = torch.zeros(P, device="cuda")
-    ups = synth.random_upstream(21, [crops[v][0] for v in CROPS])
+    ups = synth.random_upstream(21, [c[1] for c in crops])
     grads_ref = None
     tw_ref = np.zeros((len(cams), 6))
-    for (v, (cam, o_opts, x0, y0, pr, img)), up in zip(crops.items(), ups):
+    views = set()
+    for (v, cam, o_opts, x0, y0, pr, img), up in zip(crops, ups):
         # the crop's upstream gradient, zero at pixels whose FP32 branches may differ
         up["gC"][:, img["fragile"]] = 0.0
         up["gD"][img["fragile"]] = 0.0
         W, H = cams[v]["width"], cams[v]["height"]
-        full_c = np.zeros((3, H, W), np.float32)
-        full_d = np.zeros((H, W), np.float32)
-        full_c[:, y0:y0 + cam["height"], x0:x0 + cam["width"]] = up["gC"]
-        full_d[y0:y0 + cam["height"], x0:x0 + cam["width"]] = up["gD"]
         o, px = off[v], W * H
-        dl_rgb[3 * o:3 * o + 3 * px] = torch.as_tensor(full_c.reshape(-1), device="cuda")
-        dl_d[o:o + px] = torch.as_tensor(full_d.reshape(-1), device="cuda")
+        full_c = dl_rgb[3 * o:3 * o + 3 * px].view(3, H, W)
+        full_d = dl_d[o:o + px].view(H, W)
+        full_c[:, y0:y0 + cam["height"], x0:x0 + cam["width"]] = torch.as_tensor(up["gC"], device="cuda")
+        full_d[y0:y0 + cam["height"], x0:x0 + cam["width"]] = torch.as_tensor(up["gD"], device="cuda")
         g2d = oracle.render_backward(pr, cam, up["gC"], up["gD"], o_opts)
         g, tw = oracle.project_backward(sc, cam, g2d, o_opts)
         grads_ref = g if grads_ref is None else grads_ref + g
-        tw_ref[v] = tw
+        tw_ref[v] += tw
+        views.add(v)
     grads = torch.zeros_like(planes)
     twist = torch.zeros(len(cams), 6, device="cuda")
     ws.render_bwd(planes, 3, grads, dl_rgb, dl_d, twist)
@@ -113,8 +170,9 @@ def test_fullsize_backward_crops_match_oracle(full):
     for name, sl in GROUPS.items():
         e = rel_l2(g[sl], grads_ref[sl])
         assert e < GRAD_TOL, (name, e)
-    for v in CROPS:
+    for v in views:
         e = rel_l2(twist[v].cpu().numpy(), tw_ref[v])
         assert e < GRAD_TOL, ("twist", v, e)
-    others = [v for v in range(len(cams)) if v not in CROPS]
-    assert float(twist[others].abs().max()) == 0.0
+    others = [v for v in range(len(cams)) if v not in views]
+    if others:
+        assert float(twist[others].abs().max()) == 0.0

@@ -211,6 +211,64 @@ def test_depth_order_swaps_contributions():
     np.testing.assert_allclose(B["C"][:, px[0], px[1]], c2 * b2 + c1 * b1 * (1 - b2), atol=1e-12)
 
 
+def _two_gaussians(a, b):
+    return synth.Scene(np.concatenate([a.means, b.means], 1), np.concatenate([a.log_scales, b.log_scales], 1),
+                       np.concatenate([a.quats, b.quats], 1), np.concatenate([a.opacity_logits, b.opacity_logits]),
+                       np.concatenate([a.sh, b.sh], 1), a.sh_degree)
+
+
+def test_equal_fp32_depth_keys_composite_in_index_order():
+    """Two Gaussians whose depths differ below FP32 resolution: the front-to-back order is that
+    of their FP32 depth keys, and equal keys go in index order -- even where the FP64 depths
+    order them the other way.  Camera turned about y by theta = 2^-20 rad: Gaussian 0 at
+    (-2^-5, 0, 3) has depth 3 cos(theta) + 2^-5 sin(theta), Gaussian 1 at (0, 0, 3) depth
+    3 cos(theta), so Gaussian 1 is nearer by ~3e-8 m in FP64; in FP32 sin(theta) = 2^-20,
+    cos(theta) = 1 and 3 + 2^-25 rounds to 3 (one ulp at 3 is 2^-22): equal keys."""
+    th = 2.0 ** -20
+    R = np.array([[math.cos(th), 0, math.sin(th)], [0, 1, 0], [-math.sin(th), 0, math.cos(th)]])
+    cam = synth.camera(16, 16, 20.0, R=R)
+    ca, cb = np.array([1.0, 0, 0]), np.array([0, 0, 1.0])
+    a = _one_gaussian((-2.0 ** -5, 0, 3.0), math.log(0.3), logit=0.5, colour=ca)
+    b = _one_gaussian((0, 0, 3.0), math.log(0.3), logit=0.5, colour=cb)
+    sc = _two_gaussians(a, b)
+    pr = oracle.project(sc, cam)
+    assert pr["z"][0] > pr["z"][1]                      # FP64: Gaussian 1 is in front
+    assert pr["zkey"][0] == pr["zkey"][1] == np.float32(3.0)
+    img = oracle.render(pr, cam)
+    # each Gaussian's alpha at the centre pixel from its own single-Gaussian image (C = alpha c)
+    py = px = 8
+    al = [oracle.render(oracle.project(s, cam), cam)["C"][ch, py, px]
+          for s, ch in ((a, 0), (b, 2))]
+    got = img["C"][:, py, px]
+    np.testing.assert_allclose(got, ca * al[0] + cb * al[1] * (1 - al[0]), atol=1e-12)   # index order
+    assert np.abs(got - (cb * al[1] + ca * al[0] * (1 - al[1]))).max() > 1e-2             # not FP64 order
+
+
+def test_depth_key_is_the_fp32_depth():
+    """The key is the camera depth rounded through FP32 arithmetic: within a few FP32 ulps of
+    the FP64 depth (so no term, sign or row of the pose is lost), ascending with it wherever
+    the FP64 depths differ by more than that, and exactly the FP32 value when every product
+    and sum is exact (dyadic inputs)."""
+    R = _rot([0.3, -1.0, 0.4], 0.7)
+    cam = synth.camera(320, 240, 300.0, R=R, t=[0.4, -0.3, 7.5])
+    sc = synth.uniform_box_scene(5, 3000, sh_degree=0)
+    pr = oracle.project(sc, cam)
+    z32 = pr["zkey"].astype(np.float64)
+    z = pr["z"]
+    bound = 4 * 2.0 ** -24 * (np.abs(R[2]) @ np.abs(sc.means) + 7.5)
+    assert np.all(np.abs(z32 - z) <= bound)
+    o = np.argsort(z)
+    dz = np.diff(z[o])
+    far = dz > bound[o][1:] + bound[o][:-1]
+    assert np.all(np.diff(z32[o])[far] > 0)
+    # dyadic rotation rows and means: every operation exact, key == the exact depth
+    Rd = np.array([[0.6, 0.0, -0.8], [0.0, 1.0, 0.0], [0.8, 0.0, 0.6]])
+    Rd[2] = [0.75, 0.0, 0.5]                              # only the third row enters the key
+    camd = synth.camera(64, 48, 60.0, R=Rd, t=[0, 0, 0.25])
+    s = _one_gaussian((1.5, 0.25, 2.125), -3.0)
+    assert oracle.project(s, camd)["zkey"][0] == np.float32(0.75 * 1.5 + 0.5 * 2.125 + 0.25)
+
+
 def test_screen_box_bounds_every_kept_fragment():
     """Outside a Gaussian's screen box (half-extents rx, ry) alpha < alpha_min, so
     restricting each pixel to the Gaussians whose box contains it changes nothing (the tiled
