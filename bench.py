@@ -29,31 +29,34 @@ sys.path.insert(0, ROOT)
 
 SIZES = [(640, 480), (640, 480), (960, 540), (960, 540), (1280, 720), (1280, 720), (1280, 1024), (1280, 1024)]
 METRIC = "fwd+bwd render Mpix/s and iters/s at 2M Gaussians; secs-to-PSNR learned vs plain"
-# DRAM bytes (read + write) per launch of the compositing kernels on this workload, from one
-# ncu capture of dram__bytes_read.sum / dram__bytes_write.sum (a one-pass metric set) of the
-# full 2M-Gaussian step; the command and figures are in profiles/launches_c3_2M_8views.md.
-# Keyed by (kernel, tile, chunk); the projection backward does not depend on the tile shape
-# (key tile = chunk = 0).  Once a kernel changes these must be captured again; a shape without an
-# entry reports null.
-NCU_TRAFFIC = {
-    ("render_bwd_warp_kernel", 16, 0): 322_142_976 + 62_984_192,
-    ("render_fwd_kernel", 16, 256): 223_078_144 + 200_414_976,
-    ("project_bwd_entry_kernel", 0, 0): 159_240_448 + 51_640_832,
-    ("project_bwd_kernel", 0, 0): 1_195_726_080 + 861_915_136,
-}
+# DRAM bytes (read + write) per launch of the dominant kernels of each stage, measured with
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 2M-Gaussian workload in the shape
+# below.  `digest` is the SHA-256 of the library's CUDA sources when the figures were taken:
+# once any kernel source changes the figures no longer describe the build, and every stage
+# reports traffic null until they are captured again.
+TRAFFIC = {"digest": None, "n": 2_000_000, "tile": 16, "chunk": 256, "bytes": {}}
+
+
+def source_digest():
+    """SHA-256 over the library's CUDA sources and public header, in name order."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2604_12942_gb300", "csrc", "*.cu*")))
+    files.append(os.path.join(ROOT, "include", "gs.h"))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
 
 
 def stage_traffic(stage, tile, chunk, n):
-    """Captured DRAM bytes of one stage's kernels on the 2M-Gaussian workload, or None when a
-    kernel has no entry or the workload is another one."""
-    if n != 2_000_000:
+    """Measured DRAM bytes of one stage's kernels, or None when the figures do not describe
+    this build (sources changed since the capture) or this workload."""
+    if (TRAFFIC["digest"] != source_digest() or n != TRAFFIC["n"] or tile != TRAFFIC["tile"]
+            or chunk != TRAFFIC["chunk"]):
         return None
-    ks = {"composite_bwd": [("render_bwd_warp_kernel", tile, 0) if tile == 16 else ("render_bwd_kernel", tile, chunk)],
-          "render_fwd": [("render_fwd_kernel", tile, chunk)],
-          "project_bwd_adam": [("project_bwd_entry_kernel", 0, 0), ("project_bwd_kernel", 0, 0)]}.get(stage)
-    if not ks or any(k not in NCU_TRAFFIC for k in ks):
-        return None
-    return sum(NCU_TRAFFIC[k] for k in ks)
+    return TRAFFIC["bytes"].get(stage)
 
 
 def parse():
@@ -67,6 +70,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="32, 64, 128 or 256; 0 = autotune")
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--core-only", action="store_true",
+                    help="only the timed step and its stage breakdown (no f1/f2/f3 calls, end-to-end run or CPU "
+                         "baseline): a short command for profilers")
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--learned", action="store_true",
                     help="secs-to-PSNR of learned init + batched views vs plain init + one view per step")
@@ -96,67 +102,126 @@ def workload_config(args):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock, power and clock-event reasons DURING the timed region.  NVML is read (read-only
+    queries) from a background thread every 2 ms, so even a region of a few tens of ms holds
+    samples; where NVML cannot be loaded, nvidia-smi samples every 100 ms into a temporary
+    file instead."""
 
-    def __init__(self, index=0):
+    # clock-event reason bits of NVML's public API
+    REASONS = {0x8: "hw_slowdown", 0x80: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap"}
+
+    def __init__(self, torch_device):
+        self.dev = torch_device
+        self.rows = []          # (host time, sm MHz, max sm MHz, [reason names])
         self.proc = None
-        self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.thread = None
+        self.source = None
+
+    def _nvml_handle(self):
+        import ctypes
+        import torch
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        pr = torch.cuda.get_device_properties(self.dev)
+        bus = f"{getattr(pr, 'pci_domain_id', 0):08X}:{getattr(pr, 'pci_bus_id', 0):02X}:" \
+              f"{getattr(pr, 'pci_device_id', 0):02X}.0"
+        if lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+            cnt = ctypes.c_uint()
+            lib.nvmlDeviceGetCount_v2(ctypes.byref(cnt))
+            idx = 0 if cnt.value == 1 else self.dev.index
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
+
+    def _nvml_loop(self, lib, h, reasons_fn):
+        import ctypes
+        mhz, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.done:
+            ok = (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and
+                  lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                  reasons_fn(h, ctypes.byref(rs)) == 0)
+            if ok:
+                names = sorted({v for b, v in self.REASONS.items() if rs.value & b})
+                self.rows.append((time.perf_counter(), float(mhz.value), float(mx.value), names))
+            time.sleep(0.002)
 
     def __enter__(self):
+        import threading
+        self.done = False
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            lib, h, rf = self._nvml_handle()
+            self.thread = threading.Thread(target=self._nvml_loop, args=(lib, h, rf), daemon=True)
+            self.thread.start()
+            self.source = "nvml, 2 ms"
+            t_end = time.time() + 2.0
+            while not self.rows and time.time() < t_end:
+                time.sleep(0.001)
+        except Exception:
+            self.thread = None
+            self._start_smi()
+        return self
+
+    def _start_smi(self):
+        import tempfile
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}",
-                 "--query-gpu=timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
-            # the timed region starts only once the sampler is producing rows
+                ["nvidia-smi", f"--id={self.dev.index}",
+                 "--query-gpu=timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi, 100 ms"
             t_end = time.time() + 5.0
-            while time.time() < t_end and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+            while time.time() < t_end and os.path.getsize(self.f.name) == 0 and self.proc.poll() is None:
                 time.sleep(0.01)
         except Exception:
             self.proc = None
-        return self
 
     def mark(self, which):
-        """Wall-clock bounds of the timed region (host time, same clock as nvidia-smi's)."""
-        setattr(self, which, datetime.datetime.now())
+        """Host-clock bounds of the timed region."""
+        setattr(self, which, time.perf_counter())
 
     def __exit__(self, *a):
+        if self.thread is not None:
+            time.sleep(0.005)
+            self.done = True
+            self.thread.join(timeout=2)
         if self.proc:
-            time.sleep(0.15)   # one more sample after the region
+            time.sleep(0.15)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
             self.f.close()
-
-    def summary(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
-            p = [x.strip() for x in line.split(",")]
-            if len(p) >= 10:
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            now_wall, now_perf = datetime.datetime.now(), time.perf_counter()
+            for line in open(self.f.name):
+                p = [x.strip() for x in line.split(",")]
                 try:
                     ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f")
-                    rows.append((ts, float(p[2]), float(p[3]), p[6:10]))
-                except ValueError:
+                    t = now_perf - (now_wall - ts).total_seconds()
+                    self.rows.append((t, float(p[1]), float(p[2]),
+                                      sorted({names[i] for i, x in enumerate(p[3:7]) if x.lower() == "active"})))
+                except (ValueError, IndexError):
                     pass
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            os.unlink(self.f.name)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock samples"], "source": self.source}
         t0, t1 = getattr(self, "start", None), getattr(self, "stop", None)
-        inside = [r for r in rows if t0 is not None and t1 is not None and t0 <= r[0] <= t1]
-        # a region shorter than the sampling period may hold no row: take the row nearest to it
-        use = inside or [min(rows, key=lambda r: abs((r[0] - (t0 or r[0])).total_seconds()))]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, _, r in use for i, x in enumerate(r) if x.lower() == "active"})
+        inside = [r for r in self.rows if t0 is not None and t1 is not None and t0 <= r[0] <= t1]
+        use = inside or [min(self.rows, key=lambda r: abs(r[0] - (t0 or r[0])))]
+        reasons = sorted({x for r in use for x in r[3]})
         return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": max(r[2] for r in use),
-                "reasons": reasons, "samples": len(inside), "samples_total": len(rows)}
+                "reasons": reasons, "samples": len(inside), "samples_total": len(self.rows), "source": self.source}
 
 
 def peaks():
@@ -292,7 +357,7 @@ def run_gpu(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(dev.index) as clk:
+    with Clocks(dev) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         clk.mark("start")
@@ -327,6 +392,14 @@ def run_gpu(args, rank, world):
     # The f1 option (interior mask of the step's rendering + SSIM term), measured beside the
     # headline: its kernels alone on the rendered C3 images, and a whole graph-replayed step
     # with it switched on.
+    if args.core_only:
+        adam_steps = int(step.ws.counters().adam_step)
+        step.release()
+        return dict(f1=None, f23=None, total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0,
+                    loss_end=loss_end, tune=tune, adam_steps=adam_steps, eager_ms=None, h2d_ms=None, work=work,
+                    clocks=clk.summary(), e2e_s=None, px=sum(w * h for w, h in SIZES), h2d=0, d2h=0, sc=sc,
+                    cams=cams, trgb=trgb, tdep=tdep, n=n, kernels=kernels_per_step(step.ws.layout),
+                    sms=torch.cuda.get_device_properties(dev).multi_processor_count)
     f1 = f1_measure(args, step, cams, trgb, tdep, planes0, cap, st, dev)
     f23 = f23_measure(step, cams, dev)
     # End to end through the public API: every step's targets are uploaded from pinned host
@@ -394,7 +467,8 @@ def run_gpu(args, rank, world):
                 tune=tune, adam_steps=adam_steps, eager_ms=eager_ms, h2d_ms=h2d_ms, work=work,
                 clocks=clk.summary(), e2e_s=e_dt, px=px, h2d=int(h_rgb.numel() * 4 + h_dep.numel() * 4),
                 d2h=int(h_loss.numel() * 4), sc=sc, cams=cams, trgb=trgb, tdep=tdep, n=n,
-                kernels=kernels_per_step(step.ws.layout))
+                kernels=kernels_per_step(step.ws.layout),
+                sms=torch.cuda.get_device_properties(dev).multi_processor_count)
 
 
 F1_LAMBDA_SSIM, F1_ERODE = 0.2, 2
@@ -453,7 +527,7 @@ def f1_measure(args, step, cams, trgb, tdep, planes0, cap, st, dev):
                                    "peak": pk["hbm_gbs"], "unit": "GB/s",
                                    "frac": round(B / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)},
             "step_ms": round(step_ms, 4), "step_mpix_s": round(sum(w * h for w, h in SIZES) / (step_ms * 1e-3) / 1e6, 2),
-            "note": "option of the step (the paper's full objective); the headline keeps the north-star loss"}
+            "note": "option of the step (the paper's full objective); the headline keeps the L1 colour + depth loss"}
 
 
 def _se3_exp(xi):
@@ -566,19 +640,31 @@ def kernels_per_step(L):
     return 1 + 1 + 3 + 3 * 4 + 3 + 3 * tile_sort_passes(L) + 1 + 3 + 3 + 3 + 2
 
 
-# Algorithmic work per unit (kernel table):
-#   FP32 operations per evaluated fragment (FMA = 2): dx, dy 2; h_x, h_y, e 9; ex2 1; o*G 1;
-#   clamp 1 -> 14.  Added in the forward: 1 - alpha, T (1 - alpha), w, 4 FMA -> +11.  Added in
-#   the backward: 1 - alpha, rcp, T update, w (4), g.c (7), dL/dalpha (3), S (2), 4 colour /
-#   depth FMA (8), h, h dx (2), 5 geometry terms (11), dL/do (2) and the 10 additions that sum
-#   the fragment into its Gaussian's totals -> +49.
+# Algorithmic FP32 work per evaluated fragment, (pixel, Gaussian) pairs tested: 20 operations in
+# the forward (offset, quadratic form, exponent scaling, alpha, tests, transmittance update,
+# weight, three colour and one depth FMA) and 60 in the backward (the forward's plus the
+# transmittance recompute, colour / depth / alpha adjoints and the conic and mean terms), one
+# SFU exponential in each.  The kernels' own count (14 per evaluated fragment, +11 per added
+# one in the forward and +49 in the backward, from the instructions they execute on every
+# fragment and on the added ones) is reported beside it as `flops_kernel_count`.
+FLOP_FWD, FLOP_BWD = 20, 60
 FLOP_EVAL, FLOP_FWD_ADD, FLOP_BWD_ADD = 14, 11, 49
+SFU_PER_SM_CLK = 16     # MUFU results per SM per clock (4 per sub-partition)
 
 
-def roofline_table(stage, w, pk, pk_kind):
-    """Bound, algorithmic work and achieved fraction of every stage."""
+def compute_peaks(pk, sms):
+    """FP32 and SFU peaks derived from the SM count and the maximum SM clock."""
+    ghz = pk.get("sm_max_mhz", 2070.0) / 1e3
+    return {"fp32_tflops": sms * 128 * 2 * ghz / 1e3, "sfu_tops": sms * SFU_PER_SM_CLK * ghz / 1e3, "sms": sms,
+            "sm_max_mhz": pk.get("sm_max_mhz", 2070.0)}
+
+
+def roofline_table(stage, w, pk, sms):
+    """Bound, algorithmic work and achieved fraction of every stage, and the stage's lower
+    bound time t_star_ms = max(bytes / HBM, FP32 ops / FP32 peak, SFU ops / SFU peak)."""
     hbm = pk["hbm_gbs"]
-    fp32 = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    cp = compute_peaks(pk, sms)
+    fp32, sfu = cp["fp32_tflops"], cp["sfu_tops"]
     n, V, P, E = w["n"], w["views"], w["pairs"], w["visible_entries"]
     VN = V * n
     B = {
@@ -596,21 +682,30 @@ def roofline_table(stage, w, pk, pk_kind):
         # row; screen-space sums of the visible entries
         "project_bwd_adam": 6 * 236 * w["visible_gaussians"] + n + 4 * VN + 48 * E,
     }
-    F = {
-        "render_fwd": FLOP_EVAL * w["frag_fwd_eval"] + FLOP_FWD_ADD * w["frag_fwd_add"],
-        "composite_bwd": FLOP_EVAL * w["frag_bwd_eval"] + FLOP_BWD_ADD * w["frag_bwd_add"],
-    }
+    F = {"render_fwd": FLOP_FWD * w["frag_fwd_eval"], "composite_bwd": FLOP_BWD * w["frag_bwd_eval"]}
+    Fk = {"render_fwd": FLOP_EVAL * w["frag_fwd_eval"] + FLOP_FWD_ADD * w["frag_fwd_add"],
+          "composite_bwd": FLOP_EVAL * w["frag_bwd_eval"] + FLOP_BWD_ADD * w["frag_bwd_add"]}
+    S = {"render_fwd": w["frag_fwd_eval"], "composite_bwd": w["frag_bwd_eval"] + w["frag_bwd_add"]}
     out = {}
     for k, ms in stage.items():
         if k in B:
             ach = B[k] / (ms * 1e-3) / 1e9
             out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                      "frac": round(ach / hbm, 4), "bytes": int(B[k]), "ms": round(ms, 4)}
+                      "frac": round(ach / hbm, 4), "bytes": int(B[k]), "ms": round(ms, 4),
+                      "t_star_ms": round(B[k] / hbm / 1e6, 4)}
         else:
             ach = F[k] / (ms * 1e-3) / 1e12
+            t_star = max(F[k] / fp32 / 1e9, S[k] / sfu / 1e9)
             out[k] = {"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32, 1), "unit": "TFLOP/s",
-                      "frac": round(ach / fp32, 4), "flops": int(F[k]), "ms": round(ms, 4)}
+                      "frac": round(ach / fp32, 4), "flops": int(F[k]), "ms": round(ms, 4),
+                      "flops_kernel_count": int(Fk[k]), "sfu_ops": int(S[k]), "t_star_ms": round(t_star, 4)}
     return out
+
+
+def composite_fraction(table, ms_step):
+    """T* / T: the sum of the stages' lower-bound times over the measured step time."""
+    t_star = sum(v["t_star_ms"] for v in table.values())
+    return {"t_star_ms": round(t_star, 4), "t_ms": round(ms_step, 4), "frac": round(t_star / ms_step, 4)}
 
 
 def run_learned(args):
@@ -697,9 +792,10 @@ def main():
     pk, pk_kind = peaks()
     stage = r["stage_ms"]
     dom = max(stage, key=stage.get)
-    table = roofline_table(stage, r["work"], pk, pk_kind)
+    table = roofline_table(stage, r["work"], pk, r["sms"])
     for k in table:
         table[k]["traffic"] = stage_traffic(k, args.tile, args.chunk, args.n)
+    cp = compute_peaks(pk, r["sms"])
     roof = dict(table[dom])
     roof.update({"kernel": {"composite_bwd": "render_bwd_warp_kernel" if args.tile == 16 else "render_bwd_kernel",
                             "render_fwd": "render_fwd_kernel",
@@ -707,7 +803,9 @@ def main():
                             "bin_sort": "scan/emit/radix/ranges kernels"}[dom],
                  "traffic": stage_traffic(dom, args.tile, args.chunk, args.n),
                  "peak_kind": (pk_kind + " HBM copy") if roof["bound"] == "hbm" else
-                 "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock " + str(pk.get("sm_max_mhz", 2070.0)) + " MHz"})
+                 f"derived: {cp['sms']} SMs (device properties) x 128 FP32 lanes x 2 x max SM clock "
+                 f"{cp['sm_max_mhz']} MHz",
+                 "composite": composite_fraction(table, ms_step)})
     line = {
         "metric": METRIC, "value": round(mpix, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "iters_per_s": round(1e3 / ms_step, 2),
@@ -716,7 +814,8 @@ def main():
         "stage_ms": {k: round(v, 4) for k, v in stage.items()}, "n_pairs": r["n_pairs"],
         "loss": [round(r["loss0"], 6), round(r["loss_end"], 6)],
         "roofline": roof, "roofline_stages": table, "work": r["work"], "clocks": r["clocks"],
-        "e2e": {"value": round(r["px"] / r["e2e_s"] / 1e6, 2), "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
+        "e2e": None if r["e2e_s"] is None else {
+                "value": round(r["px"] / r["e2e_s"] / 1e6, 2), "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"], "ms_per_step": round(1e3 * r["e2e_s"], 3),
                 "eager_device_ms_per_step": round(r["eager_ms"], 3), "h2d_ms_per_step": round(r["h2d_ms"], 3),
                 "path": "pinned host targets -> copy stream (next step's upload overlaps this step) -> graph "
@@ -726,7 +825,7 @@ def main():
         "kernel_shape": {"tile": args.tile, "chunk": args.chunk},
         "autotune": r["tune"],
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and not args.core_only and world == 1:
         tg = [{"rgb": t[0].cpu().numpy(), "depth": t[1].cpu().numpy()} for t in
               zip(__import__("paper_2604_12942_gb300").unpack_rgb(r["trgb"], r["cams"]),
                   __import__("paper_2604_12942_gb300").unpack_plane(r["tdep"], r["cams"]))]

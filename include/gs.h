@@ -368,6 +368,22 @@ gs_status gs_project_bwd(const gs_gaussians *g, const gs_camera *cams, const gs_
                          const gs_ws_layout *L, void *ws, gs_gaussians *grads, float *grad_twist,
                          void *stream);
 
+/* Pose twists of the differentiable rendering (§III-C: the optimisation refines keyframe
+ * poses with the map; here a pose increment xi = (rho, phi), rho the translation part, acts on
+ * the left, T_cw <- Exp(xi) T_cw).  Host-side helpers of the autograd form, all arrays HOST
+ * memory, n_views in 1..GS_MAX_VIEWS.
+ *   gs_twist_cameras: out[v] = cams[v] with (R_cw, t_cw) replaced by Exp(xi_v) (R_cw, t_cw),
+ *     computed in double (Rodrigues rotation, t = V(phi) rho) and rounded to float; out may
+ *     equal cams.  xi: [n_views][6].
+ *   gs_twist_grad: g_xi_v = J(xi_v)^T g_left_v, with J the left Jacobian of SE(3)
+ *     (Exp(xi + d) = Exp(J(xi) d) Exp(xi) to first order, summed as its power series in the
+ *     6 x 6 adjoint of xi) and g_left the gradient w.r.t. a left perturbation of the already
+ *     moved pose (gs_render_bwd's grad_twist); so g_xi is the gradient w.r.t. xi itself
+ *     (J = I at xi = 0).  xi, g_left, g_xi: [n_views][6]; g_xi may equal g_left.
+ * A non-finite xi returns GS_ERR_NONFINITE. */
+gs_status gs_twist_cameras(const gs_camera *cams, const float *xi, int32_t n_views, gs_camera *out);
+gs_status gs_twist_grad(const float *xi, const float *g_left, int32_t n_views, float *g_xi);
+
 /* a8 -- Fused masked Adam (§III-C: visible and unfrozen Gaussians are refined by a sparse
  * gradient-based optimiser; only the most recent segments are updated).  Row i is updated
  * iff (update_mask == NULL or update_mask[i]) and (visible == NULL or visible[i]);
@@ -492,11 +508,12 @@ gs_status gs_init_cascade(const float *pts, const float *rgb, int64_t n, const f
  * per pass), the same sort gs_bin_sort applies to its (tile, depth) pairs, for callers that
  * cannot allocate device memory -- e.g. code running under a no-allocation policy, inside
  * a host callback, or as a plug-in of an application that owns all device allocations.
- * Its scratch is a fixed array inside the library (about 13 MB per device, held by every
- * GPU that loads the library until the process exits), so a call sorts at most 1048576
- * pairs; larger n returns GS_ERR_INVALID_ARG.  The call allocates nothing.
+ * Its scratch is a fixed array inside the library (13,108,480 bytes = 12.5 MiB per device,
+ * held by every GPU that loads the library until the process exits), so a call sorts at
+ * most 1048576 pairs; larger n returns GS_ERR_INVALID_ARG.  The call allocates nothing.
  *   keys_in [n], vals_in [n]   device input, not modified
- *   keys_out [n], vals_out [n] device output; must not alias the inputs
+ *   keys_out [n], vals_out [n] device output; the byte ranges of the two outputs must not
+ *                              overlap each other or either input (GS_ERR_INVALID_ARG)
  * The first call on a device (with that device current) looks up the scratch address with
  * cudaGetSymbolAddress, which can load the library's device code; make that first call
  * before any stream capture.  All calls share the scratch and it keeps the previous call's

@@ -352,3 +352,5 @@ from .objective import (erode, gaussian_window, masked_objective, render_mask,  
 from .mapupdate import apply_update, dedup_plan, logit_threshold, prune_plan  # noqa: E402,F401
 # Gaussian-GICP loop registration (target set, planar covariances, Gauss-Newton on SE(3)).
 from . import gicp  # noqa: E402,F401
+# SE(3) pose increments (Exp, left Jacobian) of the differentiable rendering's pose gradient.
+from . import se3  # noqa: E402,F401

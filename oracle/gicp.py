@@ -8,7 +8,7 @@ planar form with eigenvalues (1, 1, 1e-3); the loop pose minimises the sum over 
 of r^T (Sigma~_n + R Sigma~_m R^T)^-1 r with r = mu_n - T mu_m (residual, covariance and
 objective equations).
 
-Readings (also listed in the design doc):
+Readings where the paper is silent:
   * in the image: z > near_z (0.2 m), 0 <= u < W and 0 <= v < H for u = fx x / z + cx,
     v = fy y / z + cy, all in FP32 with the kernel's operation order; the distance to the view's
     position (its camera centre) is compared squared, in FP32; d_max = 20 m;

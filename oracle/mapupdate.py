@@ -5,7 +5,7 @@ RMGS-SLAM §III-C: new Gaussians pass a 3-D Euclidean proximity test before inse
 ones in revisited regions are filtered out), and low-opacity Gaussians are pruned under a
 bounded removal ratio.
 
-Readings (the paper gives neither constant nor rule beyond this; also listed in the design doc):
+Readings (the paper gives neither constant nor rule beyond this):
   * prune candidates: opacity sigmoid(logit) < opacity_min, decided on the FP32 logit against
     the FP32 logit of opacity_min (the sigmoid is monotone), opacity_min = 0.005;
   * bounded ratio: at most floor(max_ratio * n) rows go per call (max_ratio = 0.01); when more

@@ -5,7 +5,7 @@ RMGS-SLAM §III-C, "Optimization": the supervision is restricted to an interior 
 eroding a geometric support mask taken from the accumulated opacity of the current rendering,
 and the objective is lambda_rgb L_rgb + lambda_ssim L_ssim + lambda_depth L_depth over that mask.
 
-Readings of what the paper leaves open (listed in the design doc as well):
+Readings of what the paper leaves open:
   * M_geo(x) = [1 - T_final(x) >= tau], tau = 0.5, decided on the FP32 T_final in FP32.
   * Erode(M, r): binary erosion with a disk of radius r (offsets with dx^2 + dy^2 <= r^2);
     pixels outside the image count as outside M, so a band of width r at the border erodes.

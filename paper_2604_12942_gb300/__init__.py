@@ -4,10 +4,10 @@ front-to-back compositing of colour and depth, L1 photometric + depth loss, anal
 backward including keyframe SE(3) pose twists, and a masked Adam step -- hand-written CUDA
 behind the C ABI of include/gs.h, driven from PyTorch device memory and streams.
 """
-from .core import (LR_DEFAULT, MappingStep, StepResult, Workspace, adam_step, camera_array, default_opts,
+from .core import (LR_DEFAULT, MappingStep, RenderFn, Renderer, StepResult, Workspace, adam_step, camera_array, default_opts,
                    dedup_plan, gaussians_struct, gicp_register, gicp_scratch, gicp_target_set, map_update, map_update_scratch, n_planes, pack_plane, pack_rgb,
                    pixel_offsets, prune_plan, unpack_plane, unpack_rgb)
 
-__all__ = ["LR_DEFAULT", "MappingStep", "StepResult", "Workspace", "adam_step", "camera_array", "default_opts",
+__all__ = ["LR_DEFAULT", "MappingStep", "RenderFn", "Renderer", "StepResult", "Workspace", "adam_step", "camera_array", "default_opts",
            "dedup_plan", "gaussians_struct", "gicp_register", "gicp_scratch", "gicp_target_set", "map_update", "map_update_scratch", "n_planes", "pack_plane", "pack_rgb",
            "pixel_offsets", "prune_plan", "unpack_plane", "unpack_rgb"]

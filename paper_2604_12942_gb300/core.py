@@ -197,6 +197,104 @@ class Workspace:
         return self.region("visible", torch.uint8, self.n)
 
 
+class Renderer:
+    """Differentiable rendering of the Gaussian map into a batch of keyframes (§III-C: colour
+    and depth composited front to back; gradients to every Gaussian parameter and to each
+    keyframe pose), usable inside any PyTorch computation:
+
+        r = Renderer(n, cams, sh_degree)
+        rgb, depth, T = r(planes, twist)          # RenderFn.apply(planes, twist, r)
+        loss = my_objective(rgb, depth)
+        loss.backward()                           # planes.grad, twist.grad
+
+    `planes` is the packed [11 + 3K, n] float32 CUDA tensor of gs.h (means, log-scales,
+    quaternions, opacity logit, SH).  `twist` (may be None) is a [V, 6] float32 tensor on any
+    device: pose increments xi = (rho, phi) applied on the left, T_cw <- Exp(xi) T_cw, to the
+    cameras given here; its gradient is the exact gradient w.r.t. xi.  The outputs are the
+    packed images of gs.h (rgb [3P] planar per view, depth [P], final transmittance T [P];
+    unpack with unpack_rgb / unpack_plane); T carries no gradient.
+
+    The forward reads the twist on the host and checks the workspace's status word (both
+    synchronise the stream); the backward reads the pose gradient back the same way.  One
+    workspace holds the state of one forward: a second forward through the same Renderer
+    before the first one's backward makes that backward raise."""
+
+    def __init__(self, n, cams, sh_degree, opts: N.RenderOpts | None = None, max_pairs=None, device="cuda"):
+        self.ws = Workspace(n, cams, opts or default_opts(), max_pairs or max(1 << 20, 64 * n * len(cams)), device)
+        self.base_cams = camera_array(cams)
+        self.sh_degree = sh_degree
+        self.generation = 0
+
+    def __call__(self, planes, twist=None):
+        return RenderFn.apply(planes, twist, self)
+
+
+class RenderFn(torch.autograd.Function):
+    """forward: gs_twist_cameras (if a twist is given), gs_project, gs_bin_sort, gs_render_fwd;
+    backward: gs_render_bwd for the upstream dL/dC, dL/dD, then gs_twist_grad for the poses.
+    Marshalling only: every step runs in the library."""
+
+    @staticmethod
+    def forward(ctx, planes, twist, r: Renderer):
+        ws = r.ws
+        V = ws.V
+        xi = None
+        cams = r.base_cams
+        if twist is not None:
+            if tuple(twist.shape) != (V, 6):
+                raise ValueError(f"twist must be [{V}, 6], got {tuple(twist.shape)}")
+            xi = twist.detach().to("cpu", torch.float32).contiguous()
+            cams = (N.Camera * V)()
+            N.check(N.lib().gs_twist_cameras(r.base_cams, C.c_void_p(xi.data_ptr()), V, cams), "gs_twist_cameras")
+        ws.cams_c = cams
+        P = ws.layout.total_pixels
+        dev = planes.device
+        rgb = torch.empty(3 * P, device=dev)
+        depth = torch.empty(P, device=dev)
+        T = torch.empty(P, device=dev)
+        ws.project(planes, r.sh_degree)
+        ws.bin_sort()
+        ws.render_fwd(rgb, depth, T)
+        c = ws.counters()
+        if c.status != 0:
+            raise N.GsError(f"render: device status {N.STATUS.get(c.status, c.status)} ({c.n_pairs} pairs for "
+                            f"a workspace of {ws.layout.max_pairs}); make the Renderer with a larger max_pairs")
+        r.generation += 1
+        ctx.generation = r.generation
+        ctx.r, ctx.cams, ctx.xi = r, cams, xi
+        ctx.twist_device = None if twist is None else twist.device
+        ctx.save_for_backward(planes)
+        ctx.mark_non_differentiable(T)
+        return rgb, depth, T
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_T):
+        r = ctx.r
+        if r.generation != ctx.generation:
+            raise RuntimeError("RenderFn.backward: the Renderer's workspace was used by a later forward; "
+                               "use one Renderer per forward whose backward is still pending")
+        (planes,) = ctx.saved_tensors
+        ws = r.ws
+        ws.cams_c = ctx.cams
+        V = ws.V
+        P = ws.layout.total_pixels
+        dev = planes.device
+        want_twist = ctx.xi is not None and ctx.needs_input_grad[1]
+        grads = torch.zeros_like(planes)
+        g_left = torch.zeros(V, 6, device=dev) if want_twist else None
+        g_rgb = torch.zeros(3 * P, device=dev) if g_rgb is None else g_rgb.contiguous().to(torch.float32)
+        g_depth = None if g_depth is None else g_depth.contiguous().to(torch.float32)
+        ws.render_bwd(planes, r.sh_degree, grads, g_rgb, g_depth, g_left)
+        g_xi = None
+        if want_twist:
+            gl = g_left.cpu()
+            gx = torch.empty(V, 6)
+            N.check(N.lib().gs_twist_grad(C.c_void_p(ctx.xi.data_ptr()), C.c_void_p(gl.data_ptr()), V,
+                                          C.c_void_p(gx.data_ptr())), "gs_twist_grad")
+            g_xi = gx.to(ctx.twist_device)
+        return (grads if ctx.needs_input_grad[0] else None), g_xi, None
+
+
 def adam_step(planes, grads, m, v, sh_degree, step, lr, update_mask=None, visible=None, b1=0.9, b2=0.999,
               eps=1e-15):
     gp, gg, gm, gv = (gaussians_struct(t, sh_degree) for t in (planes, grads, m, v))

@@ -1090,6 +1090,83 @@ static void se3_exp(const double xi[6], double T[16]) {
     T[15] = 1;
 }
 
+// Left Jacobian of SE(3) at xi = (rho, phi): J = sum_k ad^k / (k+1)! with the 6 x 6 adjoint
+// ad = [[phi^, rho^], [0, phi^]], so that Exp(xi + d) = Exp(J d) Exp(xi) to first order.
+// The series is summed until its terms fall below double rounding (at most 120 terms: the
+// k-th term is bounded by |xi|^k / (k+1)!).
+static void se3_left_jacobian(const double xi[6], double J[36]) {
+    double ad[36] = {0};
+    auto hat = [&](const double* w, int r0, int c0) {
+        ad[6 * (r0 + 0) + c0 + 1] = -w[2]; ad[6 * (r0 + 0) + c0 + 2] = w[1];
+        ad[6 * (r0 + 1) + c0 + 0] = w[2];  ad[6 * (r0 + 1) + c0 + 2] = -w[0];
+        ad[6 * (r0 + 2) + c0 + 0] = -w[1]; ad[6 * (r0 + 2) + c0 + 1] = w[0];
+    };
+    hat(xi + 3, 0, 0);
+    hat(xi, 0, 3);
+    hat(xi + 3, 3, 3);
+    double term[36], next[36];
+    for (int k = 0; k < 36; k++) term[k] = J[k] = (k % 7 == 0) ? 1.0 : 0.0;
+    for (int m = 1; m <= 120; m++) {
+        double mx = 0;
+        for (int r = 0; r < 6; r++)
+            for (int c = 0; c < 6; c++) {
+                double s = 0;
+                for (int e = 0; e < 6; e++) s += term[6 * r + e] * ad[6 * e + c];
+                next[6 * r + c] = s / (double)(m + 1);
+                mx = fmax(mx, fabs(next[6 * r + c]));
+            }
+        for (int k = 0; k < 36; k++) { term[k] = next[k]; J[k] += next[k]; }
+        if (mx < 1e-18) break;
+    }
+}
+
+static bool finite_twist(const float* xi, int32_t n_views) {
+    for (int k = 0; k < 6 * n_views; k++)
+        if (!std::isfinite(xi[k])) return false;
+    return true;
+}
+
+gs_status gs_twist_cameras(const gs_camera* cams, const float* xi, int32_t n_views, gs_camera* out) {
+    if (!cams || !xi || !out) return fail(GS_ERR_INVALID_ARG, "cams, xi and out are required");
+    if (n_views < 1 || n_views > GS_MAX_VIEWS) return fail(GS_ERR_INVALID_ARG, "need 1..%d views", GS_MAX_VIEWS);
+    if (!finite_twist(xi, n_views)) return fail(GS_ERR_NONFINITE, "a twist component is not finite");
+    for (int v = 0; v < n_views; v++) {
+        double x[6], E[16];
+        for (int k = 0; k < 6; k++) x[k] = xi[6 * v + k];
+        se3_exp(x, E);
+        gs_camera c = cams[v];
+        for (int r = 0; r < 3; r++) {
+            double t = E[4 * r + 3];
+            for (int e = 0; e < 3; e++) t += E[4 * r + e] * (double)cams[v].t_cw[e];
+            c.t_cw[r] = (float)t;
+            for (int col = 0; col < 3; col++) {
+                double s = 0;
+                for (int e = 0; e < 3; e++) s += E[4 * r + e] * (double)cams[v].R_cw[3 * e + col];
+                c.R_cw[3 * r + col] = (float)s;
+            }
+        }
+        out[v] = c;
+    }
+    return GS_OK;
+}
+
+gs_status gs_twist_grad(const float* xi, const float* g_left, int32_t n_views, float* g_xi) {
+    if (!xi || !g_left || !g_xi) return fail(GS_ERR_INVALID_ARG, "xi, g_left and g_xi are required");
+    if (n_views < 1 || n_views > GS_MAX_VIEWS) return fail(GS_ERR_INVALID_ARG, "need 1..%d views", GS_MAX_VIEWS);
+    if (!finite_twist(xi, n_views)) return fail(GS_ERR_NONFINITE, "a twist component is not finite");
+    for (int v = 0; v < n_views; v++) {
+        double x[6], J[36];
+        for (int k = 0; k < 6; k++) x[k] = xi[6 * v + k];
+        se3_left_jacobian(x, J);
+        for (int c = 0; c < 6; c++) {
+            double s = 0;
+            for (int r = 0; r < 6; r++) s += J[6 * r + c] * (double)g_left[6 * v + r];
+            g_xi[6 * v + c] = (float)s;
+        }
+    }
+    return GS_OK;
+}
+
 // Solves H x = b (6 x 6, symmetric positive definite) by Cholesky; false if not positive.
 static bool solve6(const double H[36], const double b[6], double x[6]) {
     double L[36] = {0};

@@ -584,30 +584,27 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) sort_downsweep
     }
 }
 
-static int g_sort_grid = 0;
+static int g_sort_grid[kMaxDevices] = {};
 int sort_grid() {
-    if (g_sort_grid == 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int g = (sms > 0 ? sms : 148) * kSortBlocksPerSM;
-        g_sort_grid = g < kSortMaxGrid ? g : kSortMaxGrid;
-    }
-    return g_sort_grid;
+    const int d = current_device();
+    if (d >= 0 && g_sort_grid[d] > 0) return g_sort_grid[d];
+    const int g = device_sms() * kSortBlocksPerSM;
+    const int grid = g < kSortMaxGrid ? g : kSortMaxGrid;
+    if (d >= 0) g_sort_grid[d] = grid;
+    return grid;
 }
 
 // One pass (in_buf -> in_buf ^ 1) with BITS-bit digits at `shift`.
 template <typename K, int BITS>
 static cudaError_t launch_pass(const SortArgs& a, int in_buf, int shift, cudaStream_t st) {
-    static bool attr_set = false;
+    static bool attr_set[kMaxDevices] = {};
     const size_t smem = sizeof(SortSmem<K, BITS>);
     if (a.grid < 1 || a.grid > kSortMaxGrid) return cudaErrorInvalidValue;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sort_downsweep_kernel<K, BITS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = once_per_device(attr_set, [&] {
+        return cudaFuncSetAttribute(sort_downsweep_kernel<K, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    });
+    if (e != cudaSuccess) return e;
     sort_upsweep_kernel<K, BITS><<<a.grid, kUpThreads, 0, st>>>(a, in_buf, shift);
     sort_scan_kernel<<<(1 << BITS) / 8, 256, 0, st>>>(a);
     sort_downsweep_kernel<K, BITS><<<a.grid, kSortThreads, smem, st>>>(a, in_buf, shift);

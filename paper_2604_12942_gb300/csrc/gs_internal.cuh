@@ -24,6 +24,31 @@ constexpr int kScanBlock = kScanThreads * kScanItems;
 constexpr int kEmitThreads = 256;
 constexpr int kEmitChunk = 2048;                  // pairs per chunk of the balanced emission
 
+// Launch attributes (a kernel's dynamic shared-memory limit) and grid sizes taken from device
+// properties belong to one device: the library keeps them per device, so it works on every
+// device it is used on.  Concurrent first calls may both set an attribute (harmless).
+constexpr int kMaxDevices = 64;
+inline int current_device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+    return d;
+}
+// Runs set() once per device; a failed attempt is retried on the next call.
+template <class F>
+inline cudaError_t once_per_device(bool (&done)[kMaxDevices], F set) {
+    const int d = current_device();
+    if (d >= 0 && done[d]) return cudaSuccess;
+    const cudaError_t e = set();
+    if (e == cudaSuccess && d >= 0) done[d] = true;
+    return e;
+}
+inline int device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 148;
+}
+
 // Per-view table held in the workspace.
 struct View {
     int32_t W, H, tiles_x, tiles_y;

@@ -285,23 +285,24 @@ __global__ void mlp_adam_kernel(float* master, bf16* wq, float* bias, float* gw,
 }
 
 static int mlp_grid(int64_t n) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sms();
     const int64_t blocks = (n + kRows - 1) / kRows;
     return (int)(blocks < sms ? (blocks > 0 ? blocks : 1) : sms);
 }
 
-static bool g_mlp_attr = false;
+static bool g_mlp_attr[kMaxDevices] = {};
 static cudaError_t mlp_attrs() {
-    if (g_mlp_attr) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(mlp_train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(mlp_train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem));
-    g_mlp_attr = e == cudaSuccess;
-    return e;
+    return once_per_device(g_mlp_attr, [] {
+        cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(MlpSmem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mlp_train_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(MlpSmem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mlp_train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(BwdSmem));
+        return e;
+    });
 }
 
 __global__ void mlp_loss_finalize_kernel(const double* s, int64_t n, float* out) {

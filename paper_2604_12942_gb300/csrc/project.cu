@@ -488,13 +488,12 @@ cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st) {
 template <int DEG, bool FUSED_ADAM>
 static cudaError_t launch_project_bwd_d(const ProjectBwdArgs& a, unsigned blocks, cudaStream_t st) {
     constexpr size_t smem = sizeof(float) * 2 * 3 * (DEG + 1) * (DEG + 1) * kProjBwdThreads;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(project_bwd_kernel<DEG, FUSED_ADAM>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static bool attr_set[kMaxDevices] = {};
+    cudaError_t e = once_per_device(attr_set, [&] {
+        return cudaFuncSetAttribute(project_bwd_kernel<DEG, FUSED_ADAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    });
+    if (e != cudaSuccess) return e;
     project_bwd_kernel<DEG, FUSED_ADAM><<<blocks, kProjBwdThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

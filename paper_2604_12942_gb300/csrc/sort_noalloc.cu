@@ -8,8 +8,8 @@
 // caller-allocated workspace; this entry point keeps it in a fixed array compiled into the
 // library instead, so the caller passes only the input and output buffers.
 //
-// The scratch is one file-scope __device__ array of kNoAllocBytes (about 13.1 MB), which
-// every GPU that loads the library holds until the process exits.  It bounds a call to
+// The scratch is one file-scope __device__ array of kNoAllocBytes (13,108,480 bytes, 12.5 MiB),
+// which every GPU that loads the library holds until the process exits.  It bounds a call to
 // kNoAllocMaxPairs pairs.  All calls share it and it keeps the last call's contents, so
 // calls that overlap on the GPU (different streams, or different host threads without
 // ordering) race with each other and must be serialised by the caller.
@@ -20,12 +20,17 @@
 namespace gs {
 
 constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 20;
-constexpr int kNoAllocMaxGrid = 1024;
+// The sort grid never exceeds kSortMaxGrid blocks (sort_grid() caps it), and each block of a
+// pass owns one histogram row: the scratch holds exactly that many rows.
+constexpr int kNoAllocMaxGrid = kSortMaxGrid;
 constexpr size_t kNoAllocCounters = 256;
 constexpr size_t kNoAllocHist = sizeof(uint32_t) * ((size_t)kSortBins * kNoAllocMaxGrid + kSortBins);
 constexpr size_t kNoAllocKeys = sizeof(unsigned long long) * (size_t)kNoAllocMaxPairs;
 constexpr size_t kNoAllocVals = sizeof(uint32_t) * (size_t)kNoAllocMaxPairs;
 constexpr size_t kNoAllocBytes = kNoAllocCounters + kNoAllocHist + kNoAllocKeys + kNoAllocVals;
+
+static_assert(kNoAllocBytes == 13108480, "the size stated in gs.h");
+static_assert(sizeof(Counters) <= kNoAllocCounters, "counter block");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -63,6 +68,12 @@ __global__ void noalloc_init_kernel(Counters* c, unsigned long long n) {
 
 gs_status record_error(gs_status s, const char* msg);
 
+// True if the byte ranges [a, a + na) and [b, b + nb) share a byte.
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -78,8 +89,14 @@ extern "C" gs_status gs_sort_pairs_noalloc(const uint64_t* keys_in, const uint32
     if (key_bits < 1 || key_bits > 64) return record_error(GS_ERR_INVALID_ARG, "key_bits must be in [1, 64]");
     if (n == 0) return GS_OK;
     if (!keys_in || !vals_in || !keys_out || !vals_out) return record_error(GS_ERR_INVALID_ARG, "NULL buffer");
-    if ((const void*)keys_in == (const void*)keys_out || (const void*)vals_in == (const void*)vals_out)
-        return record_error(GS_ERR_INVALID_ARG, "input and output buffers must not alias");
+    {
+        const size_t kb = sizeof(uint64_t) * (size_t)n, vb = sizeof(uint32_t) * (size_t)n;
+        if (overlap(keys_out, kb, keys_in, kb) || overlap(keys_out, kb, vals_in, vb) ||
+            overlap(vals_out, vb, keys_in, kb) || overlap(vals_out, vb, vals_in, vb) ||
+            overlap(keys_out, kb, vals_out, vb))
+            return record_error(GS_ERR_INVALID_ARG,
+                                "the output buffers must not overlap each other or the inputs");
+    }
     void* base = nullptr;
     cudaError_t e = noalloc_scratch(&base);
     if (e != cudaSuccess) return record_error(GS_ERR_CUDA, cudaGetErrorString(e));
@@ -101,7 +118,7 @@ extern "C" gs_status gs_sort_pairs_noalloc(const uint64_t* keys_in, const uint32
     a.digit_tot = hist + (size_t)kSortBins * kNoAllocMaxGrid;
     a.counters = cnt;
     a.count = &cnt->n_pairs;
-    a.grid = sort_grid() < kNoAllocMaxGrid ? sort_grid() : kNoAllocMaxGrid;
+    a.grid = sort_grid();   // <= kSortMaxGrid = kNoAllocMaxGrid
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
         if (p == 0) {
