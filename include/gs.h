@@ -488,6 +488,25 @@ gs_status gs_mlp_train_step(float *w_master, uint16_t *w_bf16, float *bias, floa
                             int64_t n, float lr, float b1, float b2, float eps, int64_t step,
                             void *scratch, size_t scratch_bytes, float *loss_out, void *stream);
 
+/* a12 -- Training pairs of the initialiser from the plain mapping loop (§III-B's learned
+ * branch; its targets here are what the plain loop changes).  For every row i with
+ * has_feature[i] != 0 and inside[i] != 0 (either may be NULL = every row), in row order, row
+ * k of the outputs is x_out[k] = x[i] (16 features, as gs_voxel_pca writes them) and
+ * y_out[k] = the residual of the optimised map `opt` against the initial map `init` in the
+ * MLP's output units (FP32, each operation rounded once):
+ *   y[0..2] = log-scale(opt) - log-scale(init);
+ *   y[3..6] = q(opt)/|q(opt)| - q(init)/|q(init)|, each normalised quaternion multiplied by -1
+ *             first if its w component is negative (w >= 0 forms);
+ *   y[7] = logit(opt) - logit(init);  y[8..10] = (SH DC(opt) - SH DC(init)) * Y00 (colour
+ *   units, Y00 = 1 / (2 sqrt(pi)));  y[11..15] = 0.
+ * init, opt: the same n and sh_degree; x [n][16], x_out / y_out [n][16] device, 16-byte
+ * aligned; *n_out (host) receives the rows written.  scratch: gs_init_residuals_scratch_bytes(n)
+ * device bytes.  Synchronises `stream` (to read the count). */
+size_t gs_init_residuals_scratch_bytes(int64_t n);
+gs_status gs_init_residuals(const gs_gaussians *init, const gs_gaussians *opt, const float *x,
+                            const uint8_t *has_feature, const uint8_t *inside, float *x_out, float *y_out,
+                            int64_t *n_out, void *scratch, size_t scratch_bytes, void *stream);
+
 /* Cascaded initialisation (§III-B equations): per point, the model branch where the MLP output
  * y (may be NULL: no model) is valid -- the point has a feature, lies inside the loopframe,
  * the outputs are finite and |log-scale residual| < 3 -- giving log-scale s_pca + dy,

@@ -12,6 +12,8 @@ accumulation on the GPU).  This module restates, in double precision:
   mlp_backward() mean-squared-error gradients of every weight and bias
   adam()         Adam on FP32 master weights
   cascade()      the three-way choice and the initial parameters (§III-B equations)
+  residual_pairs() the model's training targets: optimised minus initial parameters of the
+                 rows with a feature inside the loopframe, in the model's output units
 
 Readings (the paper is silent): lambda is floored at (0.01 m)^2 before the logarithm;
 the model output is a residual added to the PCA initialisation (log-scale, quaternion
@@ -211,3 +213,33 @@ def cascade(points, colours, pca, depth, inside, fx, y=None):
             q[i] = [1.0, 0, 0, 0]
     return dict(log_scales=ls.T, quats=q.T, opacity_logits=lo, dc=((col - 0.5) / Y00).T, branch=branch,
                 beta=beta, valid=valid)
+
+
+def _unit_w_nonneg(q):
+    """Quaternions [4, n] (w, x, y, z) normalised, then negated where w < 0 (q and -q are the
+    same rotation; the w >= 0 form makes the residual between two of them well defined)."""
+    q = np.asarray(q, np.float64)
+    u = q / np.linalg.norm(q, axis=0, keepdims=True)
+    return np.where(u[0:1] < 0, -u, u)
+
+
+def residual_pairs(init, opt, x, has_feature=None, inside=None):
+    """Training pairs of the initialiser from one run of the plain loop: for the rows with a
+    voxel feature that lie inside the loopframe, in row order, the features x and the target
+    y [k, 16] = (log-scale_opt - log-scale_init (3), unit_w>=0(q_opt) - unit_w>=0(q_init) (4),
+    logit_opt - logit_init, (SH DC_opt - SH DC_init) * Y00 (3, colour units), 0 (5)).
+    init, opt: parameter planes [11 + 3K, n] (means, log-scales, quaternion, logit, SH)."""
+    init = np.asarray(init, np.float64)
+    opt = np.asarray(opt, np.float64)
+    n = init.shape[1]
+    keep = np.ones(n, bool)
+    if has_feature is not None:
+        keep &= np.asarray(has_feature) != 0
+    if inside is not None:
+        keep &= np.asarray(inside) != 0
+    y = np.zeros((n, 16))
+    y[:, 0:3] = (opt[3:6] - init[3:6]).T
+    y[:, 3:7] = (_unit_w_nonneg(opt[6:10]) - _unit_w_nonneg(init[6:10])).T
+    y[:, 7] = opt[10] - init[10]
+    y[:, 8:11] = ((opt[11:14] - init[11:14]) * Y00).T
+    return np.asarray(x, np.float64)[keep], y[keep]

@@ -124,6 +124,9 @@ _SIGS = {
                              C.c_void_p, C.POINTER(Gaussians), C.POINTER(Gaussians), C.c_void_p,
                              C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float, C.c_int64, C.c_void_p,
                              C.c_void_p], C.c_int),
+    "gs_init_residuals_scratch_bytes": ([C.c_int64], C.c_size_t),
+    "gs_init_residuals": ([C.POINTER(Gaussians), C.POINTER(Gaussians)] + [C.c_void_p] * 5 +
+                          [C.POINTER(C.c_int64), C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "gs_twist_cameras": ([C.POINTER(Camera), C.c_void_p, C.c_int32, C.POINTER(Camera)], C.c_int),
     "gs_twist_grad": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "gs_sort_pairs_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p],

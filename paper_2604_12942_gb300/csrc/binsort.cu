@@ -342,9 +342,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// The pass's digit: BITS bits of the key from `shift`, restricted by the pass's digit mask (a
+// sort by the low b bits ends with a pass whose mask keeps only the bits below b).
 template <int BITS, typename K>
-__device__ __forceinline__ uint32_t digit_of(K k, int shift) {
-    return (uint32_t)(k >> shift) & ((1u << BITS) - 1u);
+__device__ __forceinline__ uint32_t digit_of(K k, int shift, uint32_t mask) {
+    return (uint32_t)(k >> shift) & ((1u << BITS) - 1u) & mask;
 }
 
 // Per-block digit histograms over the block's chunks: every thread loads its kUpItems keys of
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kUpThreads) sort_upsweep_kernel(SortArgs a, in
 #pragma unroll
         for (int j = 0; j < kUpItems; j++) {
             const int64_t idx = base + (int64_t)j * kUpThreads + threadIdx.x;
-            if (idx < hi) atomicAdd(&hw[digit_of<BITS>(k[j], shift)], 1u);
+            if (idx < hi) atomicAdd(&hw[digit_of<BITS>(k[j], shift, a.digit_mask)], 1u);
         }
     }
     __syncthreads();
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) sort_downsweep
         for (int j = 0; j < kSortItems; j++) {
             const int item = w * kItemsPerWarp + j * 32 + lane;
             const bool valid = item < m;
-            const uint32_t d = valid ? digit_of<BITS>(key[j], shift) : (uint32_t)BINS;
+            const uint32_t d = valid ? digit_of<BITS>(key[j], shift, a.digit_mask) : (uint32_t)BINS;
             // lanes holding the same digit: one ballot per digit bit, and one for validity (a
             // fixed cost; __match_any_sync is slower when a warp holds many distinct digits)
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) sort_downsweep
         for (int j = 0; j < kSortItems; j++) {
             const int item = w * kItemsPerWarp + j * 32 + lane;
             if (item < m) {
-                const uint32_t d = digit_of<BITS>(key[j], shift);
+                const uint32_t d = digit_of<BITS>(key[j], shift, a.digit_mask);
                 const int pos = skew((int)(S.cstart[dix(d)] + S.wcnt[w][dix(d)] + rank[j]));
                 S.keys[pos] = key[j];
                 S.vals[pos] = val[j];
@@ -573,7 +575,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSM) sort_downsweep
         __syncthreads();
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
             const K kk = S.keys[skew(k)];
-            const uint32_t d = digit_of<BITS>(kk, shift);
+            const uint32_t d = digit_of<BITS>(kk, shift, a.digit_mask);
             const int64_t g = (int64_t)S.run[dix(d)] + (k - (int)S.cstart[dix(d)]);
             kout[g] = kk;
             vout[g] = S.vals[skew(k)];

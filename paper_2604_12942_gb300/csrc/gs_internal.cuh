@@ -140,6 +140,22 @@ __device__ __forceinline__ FragE frag_exponent(float dx, float dy, float a, floa
     return f;
 }
 
+// Two exponents at once in packed FP32 pairs (sm_100+ f32x2 arithmetic): component by
+// component the same correctly rounded operations as frag_exponent, so bit-identical.
+struct FragE2 {
+    float2 hx, hy, e;
+};
+
+__device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ FragE2 frag_exponent2(float2 dx, float2 dy, float2 a, float2 b, float2 c) {
+    FragE2 f;
+    f.hx = __ffma2_rn(a, dx, __fmul2_rn(b, dy));
+    f.hy = __ffma2_rn(c, dy, __fmul2_rn(b, dx));
+    f.e = __ffma2_rn(dx, f.hx, __fmul2_rn(dy, f.hy));
+    return f;
+}
+
 constexpr float kConicScale = -0.5f * kLog2e;
 
 // 2^x by the hardware ex2 instruction (flush-to-zero for tiny results).

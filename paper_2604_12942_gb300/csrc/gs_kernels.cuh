@@ -74,6 +74,7 @@ struct SortArgs {
     const Counters* counters;  // status word (a set status skips the sort)
     const unsigned long long* count;   // element count, read on the device
     int grid;
+    uint32_t digit_mask = 0xFFFFFFFFu;  // ANDed into every digit of the pass (a partial top digit)
 };
 
 struct RangeArgs {

@@ -130,6 +130,9 @@ extern "C" gs_status gs_sort_pairs_noalloc(const uint64_t* keys_in, const uint32
         }
         a.keys[1] = kdst[p & 1];
         a.vals[1] = vdst[p & 1];
+        // the last pass takes only the key bits below key_bits
+        const int top = key_bits - shift;
+        a.digit_mask = top >= 8 ? 0xFFFFFFFFu : (1u << top) - 1u;
         e = launch_sort64(a, 1, &shift, st);
         if (e != cudaSuccess) return record_error(GS_ERR_CUDA, cudaGetErrorString(e));
     }

@@ -92,6 +92,23 @@ class MLP:
         return self.loss
 
 
+def residual_pairs(init: torch.Tensor, opt: torch.Tensor, sh_degree: int, pca):
+    """Training pairs (x [k, 16], y [k, 16]) of the initialiser: the features and the
+    optimised-minus-initial residuals of the rows with a voxel feature inside the loopframe
+    (gs_init_residuals)."""
+    n = init.shape[1]
+    dev = init.device
+    gi, go = gaussians_struct(init.contiguous(), sh_degree), gaussians_struct(opt.contiguous(), sh_degree)
+    x_out = torch.empty(max(n, 1), 16, device=dev)
+    y_out = torch.empty(max(n, 1), 16, device=dev)
+    scratch = torch.empty(int(N.lib().gs_init_residuals_scratch_bytes(n)), dtype=torch.uint8, device=dev)
+    k = C.c_int64()
+    N.check(N.lib().gs_init_residuals(C.byref(gi), C.byref(go), _ptr(pca["x"].contiguous()), _ptr(pca["has_feature"]),
+                                      _ptr(pca["inside"]), _ptr(x_out), _ptr(y_out), C.byref(k), _ptr(scratch),
+                                      scratch.numel(), _stream()), "gs_init_residuals")
+    return x_out[:k.value], y_out[:k.value]
+
+
 def cascade(points, colours, pca, fx, y=None, sh_degree=3, opacity_init=0.1):
     """Initial Gaussian map [11 + 3K, n] by the cascade; returns (planes, branch, beta)."""
     n = points.shape[1]

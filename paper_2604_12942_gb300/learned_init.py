@@ -8,7 +8,8 @@ plain mapping loop itself produces:
   init      the cascade without the model (PCA where reliable, else the depth heuristic)
   optimise  the plain loop (gs_step) from that init for a number of iterations
   pairs     (x, residual) with residual = optimised - init in the model's output units:
-            log-scale (3), quaternion (4, both with w >= 0), opacity logit (1), colour (3)
+            log-scale (3), quaternion (4, both with w >= 0), opacity logit (1), colour (3),
+            formed by gs_init_residuals
 
 The evaluation compares wall seconds to a held-out PSNR for plain init + one view per step
 against learned init + a batch of views per step (§III-C samples several views per
@@ -120,21 +121,6 @@ class Optimizer:
         return self.step.planes
 
 
-def residuals(init: torch.Tensor, opt: torch.Tensor, sh_degree: int) -> torch.Tensor:
-    """Model targets [n, 16]: optimised - initial in the model's output units."""
-    n = init.shape[1]
-    y = torch.zeros(n, 16, device=init.device)
-    y[:, 0:3] = (opt[3:6] - init[3:6]).T
-    qi = init[6:10] / init[6:10].norm(dim=0, keepdim=True)
-    qo = opt[6:10] / opt[6:10].norm(dim=0, keepdim=True)
-    qi = qi * torch.where(qi[0:1] < 0, -1.0, 1.0)
-    qo = qo * torch.where(qo[0:1] < 0, -1.0, 1.0)
-    y[:, 3:7] = (qo - qi).T
-    y[:, 7] = opt[10] - init[10]
-    y[:, 8:11] = ((opt[11:14] - init[11:14]) * Y00).T
-    return y
-
-
 def training_pairs(seeds, n, iters=200, views=8, sh_degree=1):
     """(x, y) pairs from the plain loop on the scenes `seeds`."""
     xs, ys = [], []
@@ -142,9 +128,9 @@ def training_pairs(seeds, n, iters=200, views=8, sh_degree=1):
         sd = make_scene(s, n, sh_degree)
         init, pca, branch = initial_map(sd, None)
         opt = Optimizer(init.clone(), sd, views, seed=s).run(iters)
-        ok = (pca["has_feature"] > 0) & (pca["inside"] > 0)
-        xs.append(pca["x"][ok])
-        ys.append(residuals(init, opt, sh_degree)[ok])
+        x, y = learned.residual_pairs(init, opt, sh_degree, pca)
+        xs.append(x)
+        ys.append(y)
     return torch.cat(xs), torch.cat(ys)
 
 

@@ -177,3 +177,27 @@ def test_cascade_matches_oracle():
     np.testing.assert_allclose(P[10], ref["opacity_logits"], atol=2e-5)
     np.testing.assert_allclose(P[11:14], ref["dc"], atol=2e-5)
     assert np.all(P[14:] == 0)
+
+
+@pytest.mark.parametrize("n,deg", [(5003, 1), (70_001, 3), (1, 0), (0, 1)])
+def test_residual_pairs_match_oracle(n, deg):
+    """gs_init_residuals (training pairs of the initialiser) against the oracle: the kept rows
+    (feature and inside flags) in row order bit-exactly, the residuals within FP32 rounding;
+    quaternions with either sign of w, ragged sizes, a single row and none."""
+    rng = np.random.default_rng(n + deg)
+    P = 11 + 3 * (deg + 1) ** 2
+    init = rng.normal(size=(P, n)).astype(np.float32)
+    opt = (init + 0.3 * rng.normal(size=(P, n))).astype(np.float32)
+    flip = rng.uniform(size=n) < 0.5
+    opt[6:10, flip] *= -1.7                                  # same rotation, other sign and norm
+    x = rng.normal(size=(n, 16)).astype(np.float32)
+    has = (rng.uniform(size=n) < 0.8).astype(np.uint8)
+    ins = (rng.uniform(size=n) < 0.7).astype(np.uint8)
+    pca = {"x": torch.as_tensor(x).cuda(), "has_feature": torch.as_tensor(has).cuda(),
+           "inside": torch.as_tensor(ins).cuda()}
+    xg, yg = learned.residual_pairs(torch.as_tensor(init).cuda(), torch.as_tensor(opt).cuda(), deg, pca)
+    xr, yr = im.residual_pairs(init, opt, x, has, ins)
+    assert xg.shape[0] == xr.shape[0] == int(((has != 0) & (ins != 0)).sum())
+    np.testing.assert_array_equal(xg.cpu().numpy(), xr.astype(np.float32))
+    if n:
+        np.testing.assert_allclose(yg.cpu().numpy(), yr, rtol=0, atol=2e-6)

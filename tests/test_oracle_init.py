@@ -157,3 +157,39 @@ def test_cascade_branches_and_beta():
     np.testing.assert_allclose(out["log_scales"][:, 1], 0.5 * np.log([1e-3, 4e-3, 9e-3]) + math.log(out["beta"]))
     np.testing.assert_allclose(out["quats"][:, 3], [1, 0, 0, 0])
     np.testing.assert_allclose(out["opacity_logits"][1], math.log(0.1 / 0.9))
+
+
+def test_residual_pairs_hand_case():
+    """Training targets of the initialiser on three hand-made rows.
+    Row 0: the optimised quaternion is the initial one scaled by -2.5 (the same rotation), so
+    its rotation residual is exactly 0; scales, logit and colour move by known amounts.
+    Row 1: the initial quaternion is stored as (-1, 0, 0, 0), whose w >= 0 form is the
+    identity; the optimised one is a rotation by 60 degrees about z, unnormalised (x 3): the
+    residual is (cos 30 - 1, 0, 0, sin 30).
+    Row 2: no voxel feature, dropped (and row order kept for the others)."""
+    n, K = 3, 4                     # SH degree 1: 11 + 12 planes
+    init = np.zeros((11 + 3 * K, n))
+    init[6:10, :] = [[1.0, -1.0, 1.0], [0, 0, 0], [0, 0, 0], [0, 0, 0]]   # row 1 stored as -identity
+    opt = init.copy()
+    q0 = np.array([0.3, -0.5, 0.2, 0.7])
+    init[6:10, 0] = q0
+    opt[6:10, 0] = -2.5 * q0
+    c, s = math.cos(math.pi / 6), math.sin(math.pi / 6)
+    opt[6:10, 1] = 3.0 * np.array([c, 0, 0, s])
+    init[3:6, 0] = [-3.0, -2.5, -4.0]
+    opt[3:6, 0] = [-2.75, -2.5, -4.5]
+    init[10, 0], opt[10, 0] = -2.0, 0.5
+    init[11:14, 0] = [0.1, 0.2, 0.3]
+    opt[11:14, 0] = [0.1 + 1.0 / im.Y00, 0.2, 0.3 - 0.5 / im.Y00]   # colour +1 and -0.5 after * Y00
+    opt[14:, 0] = 7.0               # higher SH: not a target
+    x = np.arange(3 * 16, dtype=float).reshape(3, 16)
+    xs, y = im.residual_pairs(init, opt, x, has_feature=np.array([1, 1, 0]), inside=np.array([1, 1, 1]))
+    assert xs.shape == (2, 16) and np.array_equal(xs, x[:2])
+    np.testing.assert_allclose(y[0, 0:3], [0.25, 0.0, -0.5], atol=1e-15)
+    np.testing.assert_allclose(y[0, 3:7], 0.0, atol=1e-15)
+    assert y[0, 7] == 2.5
+    np.testing.assert_allclose(y[0, 8:11], [1.0, 0.0, -0.5], atol=1e-14)
+    np.testing.assert_allclose(y[1, 3:7], [c - 1.0, 0.0, 0.0, s], atol=1e-15)
+    assert np.all(y[:, 11:] == 0)
+    # without the flags every row is kept
+    assert im.residual_pairs(init, opt, x)[1].shape == (3, 16)
