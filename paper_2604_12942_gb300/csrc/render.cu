@@ -729,6 +729,11 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(BwdArgs a) {
         mylast = max(mylast, last[q]);
     }
     const int wtop = (int)__reduce_max_sync(0xffffffffu, mylast);
+    // the lane's two pixels (rows y and y + 4 of the region) as packed pairs
+    const float2 px2 = make_float2(px[0], px[1]), py2 = make_float2(py[0], py[1]);
+    const float2 g0 = make_float2(gc0[0], gc0[1]), g1 = make_float2(gc1[0], gc1[1]);
+    const float2 g2 = make_float2(gc2[0], gc2[1]), gd2 = make_float2(gd[0], gd[1]);
+    float2 T2 = make_float2(T[0], T[1]), S2 = make_float2(S[0], S[1]);
     uint32_t ltm;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(ltm));
     // window starting (from the back) at position k0: this warp's hits, copied into buffer b
@@ -765,67 +770,57 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(BwdArgs a) {
         __syncwarp();
         if constexpr (COUNT) n_visit += cnt;
         for (int t = 0; t < cnt; t++) {
-            const int j = s_pos[b][t];
+            const uint32_t j = (uint32_t)s_pos[b][t];
             const float4 r0 = s_rec[b][t][0], r1 = s_rec[b][t][1];
-            const float2 bx = make_float2(r0.x, r0.y);
-            const float4 co = make_float4(r1.x, r1.y, r1.z, r0.w);
-            // the alphas of the lane's pixels first: a record that no pixel of the warp adds
-            // (all below alpha_min or past their pixels' last fragment) changes nothing and is
-            // skipped whole
-            float dxq[kPPT], dyq[kPPT], hxq[kPPT], hyq[kPPT], Gq[kPPT], a0q[kPPT], alq[kPPT];
-            bool cq[kPPT];
-            bool contrib = false;
-#pragma unroll
-            for (int q = 0; q < kPPT; q++) {
-                const bool live = (uint32_t)j < last[q];
-                dxq[q] = px[q] - bx.x;
-                dyq[q] = py[q] - bx.y;
-                const FragE fe = frag_exponent(dxq[q], dyq[q], co.x, co.y, co.z);
-                hxq[q] = fe.hx;
-                hyq[q] = fe.hy;
-                Gq[q] = ex2_approx(fe.e);
-                a0q[q] = co.w * Gq[q];
-                alq[q] = fminf(amax, a0q[q]);
-                cq[q] = live && !(alq[q] < amin);
-                if constexpr (COUNT) {
-                    n_eval += live;
-                    n_add += cq[q];
-                }
-                contrib |= cq[q];
+            // the alphas of the lane's two pixels first, as one packed pair: a record that no
+            // pixel of the warp adds (all below alpha_min or past their pixels' last fragment)
+            // changes nothing and is skipped whole
+            const float2 dx = __fadd2_rn(px2, dup2(-r0.x));
+            const float2 dy = __fadd2_rn(py2, dup2(-r0.y));
+            const FragE2 fe = frag_exponent2(dx, dy, dup2(r1.x), dup2(r1.y), dup2(r1.z));
+            const float2 G = make_float2(ex2_approx(fe.e.x), ex2_approx(fe.e.y));
+            const float2 a0 = __fmul2_rn(dup2(r0.w), G);
+            const float2 al = make_float2(fminf(amax, a0.x), fminf(amax, a0.y));
+            const bool c0 = j < last[0] && !(al.x < amin);
+            const bool c1 = j < last[1] && !(al.y < amin);
+            const bool contrib = c0 || c1;
+            if constexpr (COUNT) {
+                n_eval += (j < last[0]) + (j < last[1]);
+                n_add += c0 + c1;
             }
             if (!__any_sync(0xffffffffu, contrib)) continue;
+            const float4 r2 = s_rec[b][t][2];
+            // back to front: T in front of the fragment from the one behind it, weight, the
+            // colour / depth adjoint and dL/dalpha; pixels that do not add it keep T and S
+            const float2 om = __fadd2_rn(dup2(1.f), make_float2(-al.x, -al.y));
+            const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+            const float2 Tn = __fmul2_rn(T2, rom);
+            const float2 wgt = __fmul2_rn(al, Tn);
+            const float2 gcz = __ffma2_rn(gd2, dup2(r0.z),
+                                          __ffma2_rn(g2, dup2(r2.z), __ffma2_rn(g1, dup2(r2.y), __fmul2_rn(g0, dup2(r2.x)))));
+            const float2 dLda = __ffma2_rn(Tn, gcz, __fmul2_rn(make_float2(-S2.x, -S2.y), rom));
+            const float2 Sn = __ffma2_rn(gcz, wgt, S2);
+            S2 = make_float2(c0 ? Sn.x : S2.x, c1 ? Sn.y : S2.y);
+            T2 = make_float2(c0 ? Tn.x : T2.x, c1 ? Tn.y : T2.y);
+            const float2 wc = make_float2(c0 ? wgt.x : 0.f, c1 ? wgt.y : 0.f);
+            // the 0.99 clamp stops the gradient through the exponent and the opacity
+            const float2 gl = make_float2((c0 && a0.x < amax) ? dLda.x : 0.f, (c1 && a0.y < amax) ? dLda.y : 0.f);
+            const float2 h = __fmul2_rn(gl, a0);
+            const float2 hdx = __fmul2_rn(h, dx);
+            float2 v2[10];
+            v2[0] = __fmul2_rn(h, fe.hx);
+            v2[1] = __fmul2_rn(h, fe.hy);
+            v2[2] = __fmul2_rn(hdx, dx);
+            v2[3] = __fmul2_rn(hdx, dy);
+            v2[4] = __fmul2_rn(__fmul2_rn(h, dy), dy);
+            v2[5] = __fmul2_rn(gl, G);
+            v2[6] = __fmul2_rn(gd2, wc);
+            v2[7] = __fmul2_rn(g0, wc);
+            v2[8] = __fmul2_rn(g1, wc);
+            v2[9] = __fmul2_rn(g2, wc);
             float val[10];
 #pragma unroll
-            for (int q = 0; q < 10; q++) val[q] = 0.f;
-            const float4 r2 = s_rec[b][t][2];
-            const float4 cz = make_float4(r2.x, r2.y, r2.z, r0.z);
-#pragma unroll
-            for (int q = 0; q < kPPT; q++) {
-                const float dx = dxq[q], dy = dyq[q], G = Gq[q], a0 = a0q[q], alpha = alq[q];
-                const FragE fe = {hxq[q], hyq[q], 0.f};
-                const bool c = cq[q];
-                const float rom = rcp_approx(1.f - alpha);
-                const float Tn = T[q] * rom;
-                const float wgt = alpha * Tn;
-                const float gcz = gc0[q] * cz.x + gc1[q] * cz.y + gc2[q] * cz.z + gd[q] * cz.w;
-                const float dLda = Tn * gcz - S[q] * rom;
-                S[q] = c ? fmaf(gcz, wgt, S[q]) : S[q];
-                T[q] = c ? Tn : T[q];
-                const float wc = c ? wgt : 0.f;
-                val[7] = fmaf(gc0[q], wc, val[7]);
-                val[8] = fmaf(gc1[q], wc, val[8]);
-                val[9] = fmaf(gc2[q], wc, val[9]);
-                val[6] = fmaf(gd[q], wc, val[6]);
-                const float gl = (c && a0 < amax) ? dLda : 0.f;   // the 0.99 clamp stops the gradient
-                const float h = gl * a0;
-                const float hdx = h * dx;
-                val[0] = fmaf(h, fe.hx, val[0]);
-                val[1] = fmaf(h, fe.hy, val[1]);
-                val[2] = fmaf(hdx, dx, val[2]);
-                val[3] = fmaf(hdx, dy, val[3]);
-                val[4] = fmaf(h * dy, dy, val[4]);
-                val[5] = fmaf(gl, G, val[5]);
-            }
+            for (int q = 0; q < 10; q++) val[q] = v2[q].x + v2[q].y;
             const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
             if (cmask) {
                 float4* rec4 = a.grad2d + 3 * (size_t)s_id[b][t];
