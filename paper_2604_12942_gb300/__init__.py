@@ -11,3 +11,6 @@ from .core import (LR_DEFAULT, MappingStep, RenderFn, Renderer, StepResult, Work
 __all__ = ["LR_DEFAULT", "MappingStep", "RenderFn", "Renderer", "StepResult", "Workspace", "adam_step", "camera_array", "default_opts",
            "dedup_plan", "gaussians_struct", "gicp_register", "gicp_scratch", "gicp_target_set", "map_update", "map_update_scratch", "n_planes", "pack_plane", "pack_rgb",
            "pixel_offsets", "prune_plan", "unpack_plane", "unpack_rgb"]
+from .viewshard import ViewParallelStep, allreduce_step_state, partition_views  # noqa: E402
+
+__all__ += ["ViewParallelStep", "allreduce_step_state", "partition_views"]
