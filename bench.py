@@ -395,13 +395,14 @@ def run_gpu(args, rank, world):
     if args.core_only:
         adam_steps = int(step.ws.counters().adam_step)
         step.release()
-        return dict(f1=None, f23=None, total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0,
+        return dict(f1=None, f23=None, a9=None, total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0,
                     loss_end=loss_end, tune=tune, adam_steps=adam_steps, eager_ms=None, h2d_ms=None, work=work,
                     clocks=clk.summary(), e2e_s=None, px=sum(w * h for w, h in SIZES), h2d=0, d2h=0, sc=sc,
                     cams=cams, trgb=trgb, tdep=tdep, n=n, kernels=kernels_per_step(step.ws.layout),
                     sms=torch.cuda.get_device_properties(dev).multi_processor_count)
     f1 = f1_measure(args, step, cams, trgb, tdep, planes0, cap, st, dev)
     f23 = f23_measure(step, cams, dev)
+    a9 = a9_measure(args, planes0, cams, trgb, tdep, cap, st, total_ms / args.steps)
     # End to end through the public API: every step's targets are uploaded from pinned host
     # memory and its loss is read back before the next step starts.  The upload of step k + 1
     # runs on a copy stream into a staging buffer while step k computes (double buffering, as
@@ -463,7 +464,7 @@ def run_gpu(args, rank, world):
     px = sum(w * h for w, h in SIZES)
     adam_steps = int(step.ws.counters().adam_step)
     step.release()
-    return dict(f1=f1, f23=f23, total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=loss_end,
+    return dict(f1=f1, f23=f23, a9=a9, total_ms=total_ms, stage_ms=stage_ms, n_pairs=n_pairs, loss0=loss0, loss_end=loss_end,
                 tune=tune, adam_steps=adam_steps, eager_ms=eager_ms, h2d_ms=h2d_ms, work=work,
                 clocks=clk.summary(), e2e_s=e_dt, px=px, h2d=int(h_rgb.numel() * 4 + h_dep.numel() * 4),
                 d2h=int(h_loss.numel() * 4), sc=sc, cams=cams, trgb=trgb, tdep=tdep, n=n,
@@ -528,6 +529,37 @@ def f1_measure(args, step, cams, trgb, tdep, planes0, cap, st, dev):
                                    "frac": round(B / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)},
             "step_ms": round(step_ms, 4), "step_mpix_s": round(sum(w * h for w, h in SIZES) / (step_ms * 1e-3) / 1e6, 2),
             "note": "option of the step (the paper's full objective); the headline keeps the L1 colour + depth loss"}
+
+
+def a9_measure(args, planes0, cams, trgb, tdep, cap, st, graph_ms):
+    """The persistent form of the step (forward, backward, projection backward and Adam as one
+    cooperative kernel with bounded grid barriers), graph-replayed like the headline, on a copy
+    of the map: its time per step beside the headline's stage-per-kernel graph."""
+    import torch
+
+    import paper_2604_12942_gb300 as gs
+    if args.tile != 16 or args.chunk != 256:
+        return {"note": f"persistent form needs 16x256 (the autotuned shape is {args.tile}x{args.chunk})"}
+    opts = gs.default_opts(tile=16, chunk=256, persistent=1)
+    ps = gs.MappingStep(planes0.clone(), 3, cams, opts, max_pairs=cap)
+    for _ in range(2):
+        ps(trgb, tdep)
+    ps.capture(trgb, tdep)
+    for _ in range(3):
+        ps.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(st)
+    for _ in range(reps):
+        ps.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ok = ps.ws.counters().status == 0
+    ps.release()
+    return {"persistent_step_ms": round(ms, 4), "graph_step_ms": round(graph_ms, 4), "status_ok": ok,
+            "kernels_replaced": "render_fwd, loss finalize, grad-record clear, render_bwd, Adam counter, "
+                                "projection backward entry and row (+Adam) -> 1 cooperative kernel"}
 
 
 def _se3_exp(xi):
@@ -821,7 +853,7 @@ def main():
                 "path": "pinned host targets -> copy stream (next step's upload overlaps this step) -> graph "
                         "input buffers -> gs_step graph replay -> loss read back, every step"},
         "gpu_launches": r["kernels"] * args.steps, "timed": "CUDA-graph replay of gs_step",
-        "f1_ssim_and_mask": r["f1"], "f2_f3_calls": r["f23"],
+        "f1_ssim_and_mask": r["f1"], "f2_f3_calls": r["f23"], "a9_persistent": r["a9"],
         "kernel_shape": {"tile": args.tile, "chunk": args.chunk},
         "autotune": r["tune"],
     }

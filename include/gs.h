@@ -52,7 +52,9 @@ typedef enum {
     GS_ERR_CUDA = 2,         /* a CUDA runtime call failed (message in gs_last_error) */
     GS_ERR_CAPACITY = 3,     /* more (tile, Gaussian) pairs than the workspace holds */
     GS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
-    GS_ERR_NONFINITE = 5,    /* a non-finite value was detected */
+    GS_ERR_NONFINITE = 5,    /* a non-finite value was detected: a camera value (returned by
+                                the call) or a Gaussian parameter (the projection sets the
+                                status word; the later stages of the step then do nothing) */
     GS_ERR_UNSUPPORTED = 6   /* a valid request this build does not implement */
 } gs_status;
 
@@ -105,6 +107,17 @@ typedef struct {
     int32_t mask_erode;      /* >= 0: the step supervises inside M_int = Erode(M_geo, disk of this
                                 radius, 0..16) of its own rendering, intersected with the caller's
                                 mask; -1 (default): the caller's mask alone */
+    /* Launch form of gs_step's compositing, backward and update stages (a9):                   */
+    int32_t persistent;      /* 1: forward compositing, backward compositing, projection backward
+                                and Adam run as ONE cooperative persistent kernel whose phases are
+                                separated by bounded grid barriers (needs tile 16, chunk 256, the
+                                fused L1 loss and optimize = 1; else gs_step returns
+                                GS_ERR_UNSUPPORTED); 0 (default): one kernel per stage */
+    int32_t sync_spin_limit; /* polls (about 0.1 us apart) before a grid-barrier wait gives up and
+                                sets GS_ERR_TIMEOUT; 0 (default): 10,000,000 (about a second) */
+    int32_t sync_skip_block; /* diagnostic: this block of the persistent kernel does not arrive at
+                                its first grid barrier, so that the others' waits time out (tests
+                                the bounded wait); -1 (default): none */
 } gs_render_opts;
 
 /* Byte offsets of the workspace regions (all 256-byte aligned) -- exposed so callers and
@@ -207,6 +220,12 @@ gs_status gs_read_counters(const gs_ws_layout *L, const void *ws, gs_counters *o
 /* Clears the device counters (status, pair count, the Adam step of gs_step).  Call once after
  * allocating a workspace (asynchronous on `stream`). */
 gs_status gs_workspace_init(const gs_ws_layout *L, void *ws, void *stream);
+
+/* Device-side failures.  The projection clears the status word; a stage that fails sets it
+ * (GS_ERR_CAPACITY from the binning, GS_ERR_NONFINITE from the projection on a NaN or infinite
+ * parameter) and every later stage of the step -- binning, compositing, backward, projection
+ * backward, the fused Adam update and its step counter -- then does nothing, so a failed
+ * step leaves the parameters, moments and Adam step unchanged.  gs_read_counters reports it. */
 
 /* a1 -- EWA projection with SH colour (§III-C "standard differentiable Gaussian splatting";
  * tile-based rasterizer of §II-A).  For every view v and Gaussian i: q = q/|q| -> R,

@@ -32,7 +32,8 @@ class RenderOpts(C.Structure):
                 ("T_min", C.c_float), ("clamp_fov", C.c_float), ("bg", C.c_float * 3), ("lambda_rgb", C.c_float),
                 ("lambda_depth", C.c_float), ("tile", C.c_int32), ("chunk", C.c_int32),
                 ("count_fragments", C.c_int32), ("lambda_ssim", C.c_float), ("mask_opacity", C.c_float),
-                ("mask_erode", C.c_int32)]
+                ("mask_erode", C.c_int32), ("persistent", C.c_int32), ("sync_spin_limit", C.c_int32),
+                ("sync_skip_block", C.c_int32)]
 
 
 class GicpResult(C.Structure):

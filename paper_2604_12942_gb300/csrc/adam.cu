@@ -15,11 +15,7 @@ __device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v,
 // Advances the device-side Adam step counter and stores the bias corrections of that step
 // (one thread; lets a captured graph run many steps without host-side parameters).
 __global__ void adam_step_counter_kernel(Counters* c, float b1, float b2) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const unsigned long long t = c->adam_step + 1;
-    c->adam_step = t;
-    c->adam_bc1 = (float)(1.0 - pow((double)b1, (double)t));
-    c->adam_bc2 = (float)(1.0 - pow((double)b2, (double)t));
+    if (threadIdx.x == 0 && blockIdx.x == 0) adam_step_advance(c, b1, b2);
 }
 
 cudaError_t launch_adam_step_counter(Counters* c, float b1, float b2, cudaStream_t st) {

@@ -53,6 +53,9 @@ static gs_status check_opts(const gs_render_opts* o) {
     if (!(o->lambda_ssim >= 0.f) || !(o->mask_opacity >= 0.f && o->mask_opacity <= 1.f) || o->mask_erode < -1 ||
         o->mask_erode > 16)
         return fail(GS_ERR_INVALID_ARG, "need lambda_ssim >= 0, mask_opacity in [0, 1], mask_erode in [-1, 16]");
+    if (o->persistent != 0 && o->persistent != 1) return fail(GS_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    if (o->sync_spin_limit < 0 || o->sync_skip_block < -1)
+        return fail(GS_ERR_INVALID_ARG, "need sync_spin_limit >= 0 and sync_skip_block >= -1");
     return GS_OK;
 }
 
@@ -68,6 +71,10 @@ static gs_status make_geometry(int32_t n_views, const gs_camera* cams, const gs_
         if (c.width <= 0 || c.height <= 0 || c.width > 16384 || c.height > 16384)
             return fail(GS_ERR_INVALID_ARG, "view %d: bad size %dx%d", v, c.width, c.height);
         if (!(c.fx > 0.f) || !(c.fy > 0.f)) return fail(GS_ERR_INVALID_ARG, "view %d: focal lengths must be > 0", v);
+        bool finite = std::isfinite(c.fx) && std::isfinite(c.fy) && std::isfinite(c.cx) && std::isfinite(c.cy);
+        for (int k = 0; k < 9; k++) finite = finite && std::isfinite(c.R_cw[k]);
+        for (int k = 0; k < 3; k++) finite = finite && std::isfinite(c.t_cw[k]);
+        if (!finite) return fail(GS_ERR_NONFINITE, "view %d: a camera value is not finite", v);
         View& V = G.views[v];
         memset(&V, 0, sizeof(V));
         V.W = c.width;
@@ -248,6 +255,7 @@ static cudaError_t run_project(const gs_gaussians* g, const gs_render_opts* opts
     a.proj = at<float4>(ws, L->proj);
     a.touched = at<uint32_t>(ws, L->touched);
     a.visible = at<uint8_t>(ws, L->visible);
+    a.counters = at<Counters>(ws, L->counters);
     return launch_project(a, g->sh_degree, st);
 }
 
@@ -362,6 +370,58 @@ static cudaError_t run_objective(const gs_render_opts* opts, const gs_ws_layout*
                                 target_depth != nullptr, loss_out, st);
 }
 
+// Arguments of the forward compositing (its loss epilogue is off when tgt_rgb is NULL).
+static FwdArgs fwd_args(const gs_render_opts* opts, const gs_ws_layout* L, void* ws, float* out_rgb, float* out_depth,
+                        float* out_T, const float* tgt_rgb, const float* tgt_depth, const uint8_t* mask,
+                        float* dl_drgb, float* dl_ddepth) {
+    double* sums = at<double>(ws, L->loss_acc);
+    FwdArgs a;
+    a.n_views = L->n_views;
+    a.views = at<View>(ws, L->views);
+    a.op = to_opts(opts);
+    a.proj = at<float4>(ws, L->proj);
+    a.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
+    a.ranges = at<uint2>(ws, L->ranges);
+    a.order = at<uint32_t>(ws, L->tile_order);
+    a.counters = at<Counters>(ws, L->counters);
+    a.pair_mask = at<uint8_t>(ws, L->pair_mask);
+    a.T_final = at<float>(ws, L->T_final);
+    a.n_contrib = at<uint32_t>(ws, L->n_contrib);
+    a.out_rgb = out_rgb;
+    a.out_depth = out_depth;
+    a.out_T = out_T;
+    a.tgt_rgb = tgt_rgb;
+    a.tgt_depth = tgt_depth;
+    a.mask = mask;
+    a.dl_drgb = dl_drgb;
+    a.dl_ddepth = dl_ddepth;
+    a.loss_sums = sums;
+    a.loss_counts = reinterpret_cast<uint32_t*>(sums + 3 * GS_MAX_VIEWS);
+    return a;
+}
+
+// Arguments of the backward compositing for upstream gradients dl_drgb, dl_ddepth.
+static BwdArgs bwd_args(const gs_render_opts* opts, const gs_ws_layout* L, void* ws, const float* dl_drgb,
+                        const float* dl_ddepth) {
+    BwdArgs b;
+    b.n_views = L->n_views;
+    b.views = at<View>(ws, L->views);
+    b.op = to_opts(opts);
+    b.proj = at<float4>(ws, L->proj);
+    b.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
+    b.ranges = at<uint2>(ws, L->ranges);
+    b.order = at<uint32_t>(ws, L->tile_order);
+    b.counters = at<Counters>(ws, L->counters);
+    b.pair_mask = at<uint8_t>(ws, L->pair_mask);
+    b.entries = at<uint32_t>(ws, L->entries);
+    b.T_final = at<float>(ws, L->T_final);
+    b.n_contrib = at<uint32_t>(ws, L->n_contrib);
+    b.dl_drgb = dl_drgb;
+    b.dl_ddepth = dl_ddepth;
+    b.grad2d = at<float4>(ws, L->grad2d);
+    return b;
+}
+
 // Forward compositing.  With a target and neither the SSIM term nor the render-derived mask,
 // the L1 loss is fused into the compositing epilogue; otherwise the forward only renders and
 // the mask and the objective follow as separate kernels.
@@ -380,28 +440,9 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
             cudaSuccess)
             return e;
     }
-    FwdArgs a;
-    a.n_views = L->n_views;
-    a.views = at<View>(ws, L->views);
-    a.op = to_opts(opts);
-    a.proj = at<float4>(ws, L->proj);
-    a.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
-    a.ranges = at<uint2>(ws, L->ranges);
-    a.order = at<uint32_t>(ws, L->tile_order);
-    a.counters = at<Counters>(ws, L->counters);
-    a.pair_mask = at<uint8_t>(ws, L->pair_mask);
-    a.T_final = at<float>(ws, L->T_final);
-    a.n_contrib = at<uint32_t>(ws, L->n_contrib);
-    a.out_rgb = out_rgb;
-    a.out_depth = out_depth;
-    a.out_T = out_T;
-    a.tgt_rgb = fused ? target_rgb : nullptr;
-    a.tgt_depth = fused ? target_depth : nullptr;
-    a.mask = fused ? mask : nullptr;
-    a.dl_drgb = fused ? dl_drgb : nullptr;
-    a.dl_ddepth = fused ? dl_ddepth : nullptr;
-    a.loss_sums = sums;
-    a.loss_counts = counts;
+    const FwdArgs a = fwd_args(opts, L, ws, out_rgb, out_depth, out_T, fused ? target_rgb : nullptr,
+                               fused ? target_depth : nullptr, fused ? mask : nullptr, fused ? dl_drgb : nullptr,
+                               fused ? dl_ddepth : nullptr);
     if ((e = launch_render_fwd(a, L->total_tiles, st)) != cudaSuccess) return e;
     if (fused)
         return launch_loss_finalize(sums, counts, L->n_views, opts->lambda_rgb, opts->lambda_depth, 0.f,
@@ -421,23 +462,7 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
 
 static cudaError_t run_composite_bwd(const gs_render_opts* opts, const gs_ws_layout* L, void* ws, const float* dl_drgb,
                                      const float* dl_ddepth, cudaStream_t st) {
-    BwdArgs b;
-    b.n_views = L->n_views;
-    b.views = at<View>(ws, L->views);
-    b.op = to_opts(opts);
-    b.proj = at<float4>(ws, L->proj);
-    b.vals = at<uint32_t>(ws, L->sorted_buf ? L->vals1 : L->vals0);
-    b.ranges = at<uint2>(ws, L->ranges);
-    b.order = at<uint32_t>(ws, L->tile_order);
-    b.counters = at<Counters>(ws, L->counters);
-    b.pair_mask = at<uint8_t>(ws, L->pair_mask);
-    b.entries = at<uint32_t>(ws, L->entries);
-    b.T_final = at<float>(ws, L->T_final);
-    b.n_contrib = at<uint32_t>(ws, L->n_contrib);
-    b.dl_drgb = dl_drgb;
-    b.dl_ddepth = dl_ddepth;
-    b.grad2d = at<float4>(ws, L->grad2d);
-    return launch_render_bwd(b, L->total_tiles, st);
+    return launch_render_bwd(bwd_args(opts, L, ws, dl_drgb, dl_ddepth), L->total_tiles, st);
 }
 
 // Adam settings of the fused projection backward (a7 + a8).
@@ -450,9 +475,8 @@ struct FusedAdam {
     const Counters* step_dev;
 };
 
-static cudaError_t run_project_bwd(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
-                                   gs_gaussians* grads, float* grad_twist, cudaStream_t st,
-                                   const FusedAdam* fa = nullptr) {
+static ProjectBwdArgs pbwd_args(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                                gs_gaussians* grads, float* grad_twist, const FusedAdam* fa) {
     ProjectBwdArgs p;
     memset(&p, 0, sizeof(p));
     p.n = L->n;
@@ -488,7 +512,13 @@ static cudaError_t run_project_bwd(const gs_gaussians* g, const gs_render_opts* 
         p.bc2 = fa->step > 0 ? (float)(1.0 - pow((double)fa->b2, (double)fa->step)) : 1.f;
         p.step_dev = fa->step_dev;
     }
-    return launch_project_bwd(p, g->sh_degree, st);
+    return p;
+}
+
+static cudaError_t run_project_bwd(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
+                                   gs_gaussians* grads, float* grad_twist, cudaStream_t st,
+                                   const FusedAdam* fa = nullptr) {
+    return launch_project_bwd(pbwd_args(g, opts, L, ws, grads, grad_twist, fa), g->sh_degree, st);
 }
 
 static cudaError_t run_bwd(const gs_gaussians* g, const gs_render_opts* opts, const gs_ws_layout* L, void* ws,
@@ -557,6 +587,26 @@ static gs_status run_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussian
     if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
     GS_CUDA(run_project(params, opts, L, ws, st));
     GS_CUDA(run_bin_sort(opts, L, ws, st));
+    if (opts->persistent) {
+        // loss normalisers first (the forward's epilogue reads them), then one persistent
+        // kernel for forward, backward, projection backward and Adam
+        double* sums = at<double>(ws, L->loss_acc);
+        uint32_t* counts = reinterpret_cast<uint32_t*>(sums + 3 * GS_MAX_VIEWS);
+        GS_CUDA(cudaMemsetAsync(sums, 0, kLossAccBytes, st));
+        GS_CUDA(launch_loss_count(at<View>(ws, L->views), L->n_views, G.pix, io->target_depth, io->mask, counts, st));
+        if (io->grad_twist) GS_CUDA(cudaMemsetAsync(io->grad_twist, 0, sizeof(float) * 6 * L->n_views, st));
+        const float* dl_dd = io->target_depth ? io->dl_ddepth : nullptr;
+        const FwdArgs fa_ = fwd_args(opts, L, ws, io->out_rgb, io->out_depth, nullptr, io->target_rgb, io->target_depth,
+                                     io->mask, io->dl_drgb, io->target_depth ? io->dl_ddepth : nullptr);
+        Counters* c = at<Counters>(ws, L->counters);
+        FusedAdam fad{params, m, v, io->update_mask, io->lr, io->b1, io->b2, io->eps, 0, c};
+        GS_CUDA(launch_step_persistent(fa_, bwd_args(opts, L, ws, io->dl_drgb, dl_dd),
+                                       pbwd_args(params, opts, L, ws, nullptr, io->grad_twist, &fad), params->sh_degree,
+                                       L->total_tiles, opts->lambda_rgb, opts->lambda_depth, io->target_depth != nullptr,
+                                       io->loss_out, io->b1, io->b2, opts->sync_spin_limit, opts->sync_skip_block, st,
+                                       nullptr));
+        return GS_OK;
+    }
     GS_CUDA(run_fwd(opts, L, G, ws, io->out_rgb, io->out_depth, nullptr, io->target_rgb, io->target_depth, io->mask,
                     io->dl_drgb, io->target_depth ? io->dl_ddepth : nullptr, io->loss_out, st));
     if (io->grad_twist) GS_CUDA(cudaMemsetAsync(io->grad_twist, 0, sizeof(float) * 6 * L->n_views, st));
@@ -581,6 +631,11 @@ static gs_status check_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussi
     if ((s = check_step_io(io)) != GS_OK) return s;
     if ((s = check_adam(params, grads, m, v, io->lr, io->b1, io->b2, io->eps)) != GS_OK) return s;
     if (params->n != L->n) return fail(GS_ERR_INVALID_ARG, "n does not match the layout");
+    if (opts->persistent &&
+        (opts->tile != 16 || opts->chunk != 256 || !io->optimize || opts->lambda_ssim > 0.f || opts->mask_erode >= 0 ||
+         opts->count_fragments))
+        return fail(GS_ERR_UNSUPPORTED, "the persistent step needs tile 16, chunk 256, optimize = 1, the fused L1 loss "
+                                        "and no fragment counters");
     return geometry_for(L, cams, opts, G);
 }
 
@@ -625,6 +680,9 @@ void gs_default_opts(gs_render_opts* o) {
     o->lambda_ssim = 0.0f;
     o->mask_opacity = 0.5f;
     o->mask_erode = -1;
+    o->persistent = 0;
+    o->sync_spin_limit = 0;
+    o->sync_skip_block = -1;
 }
 
 size_t gs_workspace_size(int64_t n, int32_t n_views, const gs_camera* cams, const gs_render_opts* opts,

@@ -120,6 +120,33 @@ struct Opts {
 
 __device__ __forceinline__ void set_status(Counters* c, uint32_t s) { atomicCAS(&c->status, 0u, s); }
 
+// Advances the device-side Adam step counter and stores the bias corrections of that step
+// (one thread); a failed step (status set) takes no Adam step.
+__device__ __forceinline__ void adam_step_advance(Counters* c, float b1, float b2) {
+    if (c->status != 0) return;
+    const unsigned long long t = c->adam_step + 1;
+    c->adam_step = t;
+    c->adam_bc1 = (float)(1.0 - pow((double)b1, (double)t));
+    c->adam_bc2 = (float)(1.0 - pow((double)b2, (double)t));
+}
+
+// The loss terms of every view and their mean from the accumulated masked sums (one thread):
+// lambda_rgb L1 / |M| + lambda_depth L1_D / |M_D| + lambda_ssim (1 - mean SSIM over M).
+__device__ __forceinline__ void loss_finalize_one(const double* sums, const uint32_t* counts, int n_views,
+                                                  float lambda_rgb, float lambda_depth, float lambda_ssim,
+                                                  int has_depth, float* loss_out) {
+    double tot = 0;
+    for (int v = 0; v < n_views; v++) {
+        const double cm = counts[2 * v], cd = counts[2 * v + 1];
+        double l = cm > 0 ? lambda_rgb * sums[3 * v] / cm : 0.0;
+        if (has_depth && cd > 0) l += lambda_depth * sums[3 * v + 1] / cd;
+        if (lambda_ssim > 0.f && cm > 0) l += lambda_ssim * (1.0 - sums[3 * v + 2] / (3.0 * cm));
+        loss_out[v] = (float)l;
+        tot += l;
+    }
+    loss_out[n_views] = (float)(tot / n_views);
+}
+
 // ---------------------------------------------------------------------------------------
 // Compositing exponent.  The record stores the inverse 2-D covariance [[A, B], [B, C]]
 // scaled by k = -log2(e)/2, (a, b, c) = k (A, B, C), so that alpha = o * 2^e with

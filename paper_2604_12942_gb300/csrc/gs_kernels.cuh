@@ -14,6 +14,7 @@ struct ProjectArgs {
     float4* proj;          // [V*n][3]
     uint32_t* touched;     // [V*n]
     uint8_t* visible;      // [n]
+    Counters* counters;    // status word: GS_ERR_NONFINITE on a non-finite parameter
 };
 
 struct ProjectBwdArgs {
@@ -235,6 +236,12 @@ cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int
 cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st);
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t st);
 cudaError_t launch_adam_step_counter(Counters* c, float b1, float b2, cudaStream_t st);
+// The persistent form of forward -> backward -> projection backward + Adam (render.cu); the
+// grid state lives 128 bytes into the counters' 256-byte slot of the workspace.
+cudaError_t launch_step_persistent(const FwdArgs& fwd, const BwdArgs& bwd, const ProjectBwdArgs& pb, int deg,
+                                   int total_tiles, float lambda_rgb, float lambda_depth, int has_depth,
+                                   float* loss_out, float b1, float b2, long long spin_limit, int skip_block,
+                                   cudaStream_t st, int* grid_out);
 cudaError_t launch_setup_views(View* dst, const View* src_host, int n_views, cudaStream_t st);
 
 int sort_grid();

@@ -7,6 +7,7 @@
 // list is walked in chunks staged in shared memory (records gathered once per chunk by
 // the whole CTA); the inner loop then reads broadcast shared memory only.
 #include "gs_kernels.cuh"
+#include "project_bwd.cuh"
 
 namespace gs {
 
@@ -54,17 +55,8 @@ cudaError_t launch_loss_count(const View* views, int n_views, const int64_t* pix
 
 __global__ void loss_finalize_kernel(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
                                      float lambda_depth, float lambda_ssim, int has_depth, float* loss_out) {
-    if (threadIdx.x != 0) return;
-    double tot = 0;
-    for (int v = 0; v < n_views; v++) {
-        const double cm = counts[2 * v], cd = counts[2 * v + 1];
-        double l = cm > 0 ? lambda_rgb * sums[3 * v] / cm : 0.0;
-        if (has_depth && cd > 0) l += lambda_depth * sums[3 * v + 1] / cd;
-        if (lambda_ssim > 0.f && cm > 0) l += lambda_ssim * (1.0 - sums[3 * v + 2] / (3.0 * cm));
-        loss_out[v] = (float)l;
-        tot += l;
-    }
-    loss_out[n_views] = (float)(tot / n_views);
+    if (threadIdx.x == 0)
+        loss_finalize_one(sums, counts, n_views, lambda_rgb, lambda_depth, lambda_ssim, has_depth, loss_out);
 }
 
 cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
@@ -192,24 +184,36 @@ __device__ __forceinline__ void load_record(const float4* proj, uint32_t gid, fl
 // bound and gains more from occupancy than from the few registers the staging code wants.
 constexpr int kFwdThreadsPerSM = 1280;
 
+// Shared memory of one forward tile: two chunk buffers of raw records (u, v, z, o),
+// (a, b, c, rx), (r, g, b, ry) -- while the warps composite one, cp.async fills the other --,
+// the chunk's region masks, per-warp record lists, loss partials and the pixels' targets.
+template <int TILE, int CHUNK>
+struct FwdSmem {
+    static constexpr int NT = TileMap<TILE, kFwdPPT>::NT;
+    static constexpr int NW = NT / 32;
+    float4 rec[2][CHUNK][3];
+    uint32_t mask[CHUNK];
+    uint16_t list[NW][CHUNK];   // per warp: the chunk's records that reach its region
+    double red[2][NW];
+    float tgt[4][NT];           // target r, g, b, depth of each thread's pixel
+};
+
+// The forward of work item `item` (the item-th tile of the work order), by the CTA's NT threads.
 // COUNT: fill the fragment and visit counters (a diagnostic option; off in the step).
 template <int TILE, int CHUNK, bool COUNT>
-__global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM / TileMap<TILE, kFwdPPT>::NT)
-    render_fwd_kernel(FwdArgs a) {
+__device__ __forceinline__ void render_fwd_tile(const FwdArgs& a, int item, FwdSmem<TILE, CHUNK>& S) {
     using TM = TileMap<TILE, kFwdPPT>;
     constexpr int NT = TM::NT;
     constexpr int NW = NT / 32;
-    // two chunk buffers of raw records (u, v, z, o), (a, b, c, rx), (r, g, b, ry): while the
-    // warps composite one, cp.async fills the other
-    __shared__ float4 s_rec[2][CHUNK][3];
-    __shared__ uint32_t s_mask[CHUNK];
-    __shared__ uint16_t s_list[NW][CHUNK];   // per warp: the chunk's records that reach its region
-    __shared__ double s_red[2][NW];
-    __shared__ float s_tgt[4][NT];           // target r, g, b, depth of each thread's pixel
+    auto& s_rec = S.rec;
+    auto& s_mask = S.mask;
+    auto& s_list = S.list;
+    auto& s_red = S.red;
+    auto& s_tgt = S.tgt;
     // (loads ordered so that the dependent chain order -> ranges / view -> ids -> records is
     // as short as possible: CTAs are short and this latency is paid once per tile)
     const uint32_t status = a.counters->status;
-    const int gt = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
+    const int gt = a.order ? (int)a.order[item] : item;
     if (status != 0) return;
     const uint2 rg = a.ranges[gt];
     const int v = view_of_tile(a.views, a.n_views, gt);
@@ -405,6 +409,13 @@ __global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM /
             if (sd != 0.0) atomicAdd(&a.loss_sums[3 * v + 1], sd);
         }
     }
+}
+
+template <int TILE, int CHUNK, bool COUNT>
+__global__ void __launch_bounds__(TileMap<TILE, kFwdPPT>::NT, kFwdThreadsPerSM / TileMap<TILE, kFwdPPT>::NT)
+    render_fwd_kernel(FwdArgs a) {
+    __shared__ FwdSmem<TILE, CHUNK> S;
+    render_fwd_tile<TILE, CHUNK, COUNT>(a, blockIdx.x, S);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -683,15 +694,24 @@ __global__ void __launch_bounds__(TileMap<TILE, kBwdPPT>::NT) render_bwd_kernel(
 // ----------------------------------------------------------------------------------------
 constexpr int kWin = 32;   // list positions per window
 
+// A warp's shared memory: its two windows of staged records, their ids and list positions.
+struct BwdWarpSmem {
+    float4 rec[2][kWin][3];
+    uint32_t id[2][kWin];
+    int pos[2][kWin];
+};
+
+// The backward of work item `item` = 4 t + w: region w of the t-th tile of the work order, by
+// one warp with its own shared memory S.
 template <bool COUNT>
-__global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(BwdArgs a) {
+__device__ __forceinline__ void render_bwd_region(const BwdArgs& a, int item, BwdWarpSmem& W) {
     constexpr int TILE = 16, kPPT = kBwdPPT;
-    __shared__ float4 s_rec[2][kWin][3];
-    __shared__ uint32_t s_id[2][kWin];
-    __shared__ int s_pos[2][kWin];
+    auto& s_rec = W.rec;
+    auto& s_id = W.id;
+    auto& s_pos = W.pos;
     const uint32_t status = a.counters->status;
-    const int gt = a.order ? (int)a.order[blockIdx.x >> 2] : (int)(blockIdx.x >> 2);
-    const int w = blockIdx.x & 3;   // region: column w % 2, row w / 2 (the forward's mask order)
+    const int gt = a.order ? (int)a.order[item >> 2] : (item >> 2);
+    const int w = item & 3;   // region: column w % 2, row w / 2 (the forward's mask order)
     if (status != 0) return;
     const uint2 rg = a.ranges[gt];
     const int v = view_of_tile(a.views, a.n_views, gt);
@@ -854,6 +874,12 @@ __global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(BwdArgs a) {
     }
 }
 
+template <bool COUNT>
+__global__ void __launch_bounds__(32, 32) render_bwd_warp_kernel(BwdArgs a) {
+    __shared__ BwdWarpSmem S;
+    render_bwd_region<COUNT>(a, blockIdx.x, S);
+}
+
 template <int TILE, int CHUNK>
 static void launch_fwd_c(const FwdArgs& a, int total_tiles, cudaStream_t st) {
     constexpr int NT = TileMap<TILE, kFwdPPT>::NT;
@@ -917,6 +943,202 @@ cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st
     }
     return a.op.tile == 8 ? launch_bwd_t<8>(a, total_tiles, a.op.chunk, st)
                           : launch_bwd_t<16>(a, total_tiles, a.op.chunk, st);
+}
+
+// ----------------------------------------------------------------------------------------
+// a9, persistent form of the step's last stages: forward compositing (with the fused L1 loss),
+// backward compositing, the projection backward's entry and row parts and the fused Adam update
+// as ONE cooperative kernel whose blocks are all resident, the phases separated by grid
+// barriers:
+//   phase 0  zero the screen-space gradient records of the visible entries
+//   phase 1  forward tiles, taken from a queue in the largest-first work order
+//   -- barrier --  (one thread: the loss terms and the Adam step counter)
+//   phase 2  backward (tile, 8 x 8 region) items, one per warp, from a second queue
+//   -- barrier --
+//   phase 3  projection backward, entry part (grid-stride over the visible entries)
+//   -- barrier --
+//   phase 4  projection backward, row part, with the masked Adam update
+// Every wait at a barrier is bounded: after `spin_limit` polls the block sets GS_ERR_TIMEOUT
+// in the status word and returns, and so does every block that then finds the status set, so
+// the kernel always ends.  The phases are the same device code as the stage kernels; the
+// register budget of the kernel is that of its heaviest phase (the row part).
+// ----------------------------------------------------------------------------------------
+struct GridSync {
+    unsigned int count;   // blocks arrived at the current barrier
+    unsigned int gen;     // barriers completed
+    unsigned int q_fwd;   // next forward work item
+    unsigned int q_bwd;   // next backward work item
+};
+static_assert(sizeof(Counters) + sizeof(GridSync) <= 256, "the grid state follows the counters in their slot");
+
+struct PersistentArgs {
+    FwdArgs fwd;
+    BwdArgs bwd;
+    ProjectBwdArgs pb;
+    Counters* counters;
+    GridSync* sync;
+    int total_tiles;
+    float lambda_rgb, lambda_depth;
+    int has_depth;
+    float* loss_out;
+    float b1, b2;
+    unsigned long long spin_limit;
+    int skip_block;   // diagnostic: this block does not arrive at the first barrier (-1: none)
+};
+
+constexpr int kPersistThreads = 256;
+constexpr int kPersistWarps = kPersistThreads / 32;
+static_assert(kPersistThreads == kEntryThreads, "the entry part runs with the persistent block");
+static_assert(kPersistThreads == TileMap<16, kFwdPPT>::NT, "a forward tile is one persistent block");
+
+template <int DEG>
+struct PersistSmem {
+    union {
+        FwdSmem<16, 256> fwd;
+        BwdWarpSmem bwd[kPersistWarps];
+        float rows[2 * 3 * (DEG + 1) * (DEG + 1) * kPersistThreads];
+    } u;
+    float tw[GS_MAX_VIEWS * 6];
+    unsigned int item;
+    int ok;
+};
+
+// Grid barrier with a bounded wait.  Thread 0 of each block reads the generation, arrives
+// (unless `arrive` is false), and the last block to arrive resets the count and advances the
+// generation; the others poll it, at most spin_limit times, about 0.1 us apart.  Returns false
+// (for the whole block) if the wait gave up or the status word is set.
+template <int DEG>
+__device__ __forceinline__ bool grid_barrier(const PersistentArgs& P, bool arrive, PersistSmem<DEG>& S) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        GridSync* g = P.sync;
+        volatile unsigned int* vgen = &g->gen;
+        const unsigned int g0 = *vgen;
+        __threadfence();
+        bool released = false;
+        if (arrive && atomicAdd(&g->count, 1u) + 1u == gridDim.x) {
+            atomicExch(&g->count, 0u);
+            __threadfence();
+            atomicAdd(&g->gen, 1u);
+            released = true;
+        }
+        int ok = 1;
+        if (!released) {
+            unsigned long long polls = 0;
+            while (*vgen == g0) {
+                if (++polls > P.spin_limit) {
+                    set_status(P.counters, GS_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        S.ok = ok && *(volatile uint32_t*)&P.counters->status == 0u;
+    }
+    __syncthreads();
+    return S.ok != 0;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kPersistThreads, 2) step_persistent_kernel(PersistentArgs P) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    PersistSmem<DEG>& S = *reinterpret_cast<PersistSmem<DEG>*>(s_raw);
+    if (P.counters->status != 0) return;   // failed earlier stage: every block leaves at once
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {   // phase 0
+        const int64_t E = (int64_t)P.counters->n_entries;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t e = (int64_t)blockIdx.x * kPersistThreads + threadIdx.x; e < 3 * E;
+             e += (int64_t)gridDim.x * kPersistThreads)
+            P.bwd.grad2d[3 * (size_t)P.bwd.entries[e / 3] + (size_t)(e % 3)] = z;
+    }
+    for (;;) {   // phase 1
+        if (threadIdx.x == 0) S.item = atomicAdd(&P.sync->q_fwd, 1u);
+        __syncthreads();
+        const unsigned int t = S.item;
+        __syncthreads();
+        if (t >= (unsigned int)P.total_tiles) break;
+        render_fwd_tile<16, 256, false>(P.fwd, (int)t, S.u.fwd);
+    }
+    if (!grid_barrier<DEG>(P, (int)blockIdx.x != P.skip_block, S)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (P.loss_out)
+            loss_finalize_one(P.fwd.loss_sums, P.fwd.loss_counts, P.fwd.n_views, P.lambda_rgb, P.lambda_depth, 0.f,
+                              P.has_depth, P.loss_out);
+        adam_step_advance(P.counters, P.b1, P.b2);
+    }
+    for (;;) {   // phase 2
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(&P.sync->q_bwd, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= 4u * (unsigned int)P.total_tiles) break;
+        render_bwd_region<false>(P.bwd, (int)item, S.u.bwd[warp]);
+    }
+    if (!grid_barrier<DEG>(P, true, S)) return;
+    project_bwd_entry_part(P.pb, blockIdx.x, gridDim.x, S.tw);   // phase 3
+    if (!grid_barrier<DEG>(P, true, S)) return;
+    for (int64_t blk = blockIdx.x; blk * kPersistThreads < P.pb.n; blk += gridDim.x) {   // phase 4
+        project_bwd_rows<DEG, true, kPersistThreads>(P.pb, blk, S.tw, S.u.rows);
+        __syncthreads();
+    }
+}
+
+template <int DEG>
+static cudaError_t launch_persistent_d(const PersistentArgs& P, cudaStream_t st, int* grid_out) {
+    const size_t smem = sizeof(PersistSmem<DEG>);
+    static bool attr_set[kMaxDevices] = {};
+    cudaError_t e = once_per_device(attr_set, [&] {
+        return cudaFuncSetAttribute(step_persistent_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    });
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_persistent_kernel<DEG>, kPersistThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const int grid = per_sm * device_sms();
+    if (grid_out) *grid_out = grid;
+    if ((e = cudaMemsetAsync(P.sync, 0, sizeof(GridSync), st)) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kPersistThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step_persistent_kernel<DEG>, P);
+}
+
+cudaError_t launch_step_persistent(const FwdArgs& fwd, const BwdArgs& bwd, const ProjectBwdArgs& pb, int deg,
+                                   int total_tiles, float lambda_rgb, float lambda_depth, int has_depth,
+                                   float* loss_out, float b1, float b2, long long spin_limit, int skip_block,
+                                   cudaStream_t st, int* grid_out) {
+    PersistentArgs P;
+    P.fwd = fwd;
+    P.bwd = bwd;
+    P.pb = pb;
+    P.counters = fwd.counters;
+    P.sync = reinterpret_cast<GridSync*>(reinterpret_cast<char*>(fwd.counters) + 128);
+    P.total_tiles = total_tiles;
+    P.lambda_rgb = lambda_rgb;
+    P.lambda_depth = lambda_depth;
+    P.has_depth = has_depth;
+    P.loss_out = loss_out;
+    P.b1 = b1;
+    P.b2 = b2;
+    P.spin_limit = spin_limit > 0 ? (unsigned long long)spin_limit : 10000000ull;
+    P.skip_block = skip_block;
+    switch (deg) {
+        case 0: return launch_persistent_d<0>(P, st, grid_out);
+        case 1: return launch_persistent_d<1>(P, st, grid_out);
+        case 2: return launch_persistent_d<2>(P, st, grid_out);
+        default: return launch_persistent_d<3>(P, st, grid_out);
+    }
 }
 
 }  // namespace gs

@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 import synth
@@ -102,3 +103,17 @@ def test_stage_calls_reject_bad_arguments_without_launching(native):
                             None) == 1
     assert lib.gs_adam_step(C.byref(g2), C.byref(g2), C.byref(g2), C.byref(g2), None, None, lr, 1.5, 0.999, 1e-15, 1,
                             None) == 1
+
+
+def test_nonfinite_camera_rejected_on_the_host(native):
+    import paper_2604_12942_gb300 as gs
+    o = gs.default_opts()
+    L = native.WsLayout()
+    cam = synth.camera(64, 48, 60.0)
+    for key, idx in (("t", 1), ("R", 4)):
+        bad = dict(cam)
+        arr = np.array(bad[key], dtype=np.float64).copy()
+        arr.flat[idx] = np.nan
+        bad[key] = arr
+        assert native.lib().gs_workspace_layout(10, 1, gs.camera_array([bad]), C.byref(o), 100, C.byref(L)) == 5
+        assert b"not finite" in native.lib().gs_last_error()

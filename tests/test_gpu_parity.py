@@ -384,6 +384,45 @@ def test_capacity_overflow_reports_and_skips():
     assert c2.status == 0 and c2.n_pairs == c.n_pairs
 
 
+def _failed_step_changes_nothing(step, trgb, status):
+    before = [t.clone() for t in (step.planes, step.m, step.v)]
+    step(trgb)
+    torch.cuda.synchronize()
+    c = step.ws.counters()
+    assert c.status == status and c.adam_step == 0
+    for a, b in zip(before, (step.planes, step.m, step.v)):
+        assert torch.equal(a.view(torch.int32), b.view(torch.int32))   # bit for bit (a planted NaN included)
+
+
+def test_capacity_overflow_skips_the_whole_step():
+    """Pair capacity exceeded inside an optimising step: no gradient, no Adam update."""
+    sc = _scene_c1(3000, 0)
+    cams = [synth.camera(160, 120, 150.0)]
+    tg = synth.random_targets(5, cams)
+    step = gs.MappingStep(planes_of(sc), 0, cams, max_pairs=100)
+    _failed_step_changes_nothing(step, gs.pack_rgb([tg[0]["rgb"]]), 3)
+
+
+@pytest.mark.parametrize("plane,what", [(0, "nan"), (5, "inf"), (8, "nan"), (12, "nan")])
+def test_nonfinite_parameter_sets_status_and_skips_the_step(plane, what):
+    """A NaN or infinite mean, log-scale, quaternion or SH coefficient of a row some view sees
+    makes the projection set GS_ERR_NONFINITE; the step then changes nothing."""
+    sc = _scene_c1(3000, 1)
+    cams = [synth.camera(160, 120, 150.0)]
+    tg = synth.random_targets(6, cams)
+    planes = planes_of(sc)
+    ws, *_ = gpu_forward(sc, cams)
+    row = int(torch.nonzero(ws.visible())[0])
+    planes[plane, row] = float("nan") if what == "nan" else float("inf")
+    step = gs.MappingStep(planes, 1, cams)
+    _failed_step_changes_nothing(step, gs.pack_rgb([tg[0]["rgb"]]), 5)
+    # a finite map on the same workspace steps normally again
+    step.planes.copy_(planes_of(sc))
+    step(gs.pack_rgb([tg[0]["rgb"]]))
+    torch.cuda.synchronize()
+    assert step.ws.counters().status == 0 and step.ws.counters().adam_step == 1
+
+
 def test_mapping_step_reduces_loss():
     sc = _scene_c1(5000, 0, seed=21)
     gt = synth.perturbed(sc, 22)
