@@ -76,8 +76,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--learned", action="store_true",
                     help="secs-to-PSNR of learned init + batched views vs plain init + one view per step")
-    ap.add_argument("--learned-n", type=int, default=150_000)
+    ap.add_argument("--learned-n", type=int, default=400_000,
+                    help="Gaussians per training scene (8 scenes: about 2M training pairs)")
+    ap.add_argument("--learned-eval-n", type=int, default=200_000, help="new Gaussians per held-out scene")
     ap.add_argument("--ref-iters", type=int, default=3000)
+    ap.add_argument("--no-learned", action="store_true", help="leave the secs-to-PSNR experiment out of the line")
     return ap.parse_args()
 
 
@@ -403,48 +406,26 @@ def run_gpu(args, rank, world):
     f1 = f1_measure(args, step, cams, trgb, tdep, planes0, cap, st, dev)
     f23 = f23_measure(step, cams, dev)
     a9 = a9_measure(args, planes0, cams, trgb, tdep, cap, st, total_ms / args.steps)
-    # End to end through the public API: every step's targets are uploaded from pinned host
-    # memory and its loss is read back before the next step starts.  The upload of step k + 1
-    # runs on a copy stream into a staging buffer while step k computes (double buffering, as
-    # a mapping loop receiving keyframes would); the compute stream then moves the targets into
-    # the captured graph's input buffers (device copy) and replays the graph.
+    # End to end through the C ABI with host buffers: the step is captured with its targets in
+    # pinned host memory and a pinned host loss buffer (gs_step_io host_* pointers), so every
+    # replay uploads the step's targets (on a graph branch overlapped with the projection and
+    # the binning, which do not read them), runs the step and copies the loss back; the host
+    # synchronises and reads the loss after every step.
     h_rgb = trgb.cpu().pin_memory()
     h_dep = tdep.cpu().pin_memory()
     h_loss = torch.empty(len(cams) + 1).pin_memory()
-    s_rgb = [torch.empty_like(trgb) for _ in range(2)]
-    s_dep = [torch.empty_like(tdep) for _ in range(2)]
-    cs = torch.cuda.Stream(device=dev)
-    copied = [torch.cuda.Event() for _ in range(2)]
-    free = [torch.cuda.Event() for _ in range(2)]
+    d_rgb, d_dep = torch.empty_like(trgb), torch.empty_like(tdep)
     e_steps = max(3, args.steps // 2)
-
-    def upload(b):
-        with torch.cuda.stream(cs):
-            cs.wait_event(free[b])
-            s_rgb[b].copy_(h_rgb, non_blocking=True)
-            s_dep[b].copy_(h_dep, non_blocking=True)
-            copied[b].record(cs)
-
-    def e2e_step(k):
-        b = k & 1
-        upload(b ^ 1)   # the next step's targets, while this one computes
-        st.wait_event(copied[b])
-        trgb.copy_(s_rgb[b], non_blocking=True)
-        tdep.copy_(s_dep[b], non_blocking=True)
-        free[b].record(st)
+    step.capture(d_rgb, d_dep, host=(h_rgb, h_dep, None, h_loss))
+    for _ in range(2):
         step.replay()
-        h_loss.copy_(step.loss, non_blocking=True)
         st.synchronize()
-
-    for b in range(2):
-        free[b].record(st)
-    upload(0)
-    for k in range(2):
-        e2e_step(k)
-    torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for k in range(2, 2 + e_steps):
-        e2e_step(k)
+    host_losses = []
+    for _ in range(e_steps):
+        step.replay()
+        st.synchronize()
+        host_losses.append(float(h_loss[-1]))
     e_dt = (time.perf_counter() - e0) / e_steps
     torch.cuda.synchronize()
     # what the end-to-end time is made of: the eager step on the device, the target upload
@@ -456,8 +437,8 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     eager_ms = ea.elapsed_time(eb) / e_steps
     ea.record(st)
-    s_rgb[0].copy_(h_rgb, non_blocking=True)
-    s_dep[0].copy_(h_dep, non_blocking=True)
+    d_rgb.copy_(h_rgb, non_blocking=True)
+    d_dep.copy_(h_dep, non_blocking=True)
     eb.record(st)
     torch.cuda.synchronize()
     h2d_ms = ea.elapsed_time(eb)
@@ -740,45 +721,67 @@ def composite_fraction(table, ms_step):
     return {"t_star_ms": round(t_star, 4), "t_ms": round(ms_step, 4), "frac": round(t_star / ms_step, 4)}
 
 
-def run_learned(args):
-    """Train the initialiser on pairs from the plain loop (scenes 10-12), then on held-out
-    scenes (20, 21) measure wall seconds to the held-out PSNR that plain init + one view per
-    step reaches after --ref-iters iterations, for plain init + 1 view and learned init + 8
-    views per step."""
+def learned_experiment(n_train, n_eval, ref_iters, train_seeds=tuple(range(10, 18)), eval_seeds=(20, 21, 22, 23)):
+    """Secs-to-PSNR of the learned initialiser (§III-B cascade with the MLP, trained on the
+    plain loop's own (initial, optimised after 200 iterations) pairs of the training scenes)
+    against the plain voxel-PCA initialisation, on held-out scenes: wall seconds (CUDA-
+    synchronised, evaluations excluded) and iterations to the held-out PSNR that plain init +
+    one view per step reaches after ref_iters iterations, for plain + 1 view, learned + 8
+    views, and the two ablation arms plain + 8 views and learned + 1 view."""
     import torch
 
     from paper_2604_12942_gb300 import learned_init as li
-    torch.cuda.set_device(0)
     t0 = time.perf_counter()
-    x, y = li.training_pairs([10, 11, 12], args.learned_n, iters=200, views=8)
+    x, y = li.training_pairs(list(train_seeds), n_train, iters=200, views=8)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
     mlp, losses = li.train_mlp(x, y, epochs=40)
-    train_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
     rows = []
-    for s in (20, 21):
-        sd = li.make_scene(s, args.learned_n)
+    for s in eval_seeds:
+        sd = li.make_scene(s, n_eval)
         plain0, _, _ = li.initial_map(sd, None)
-        target = li.final_psnr(plain0.clone(), sd, 1, args.ref_iters, seed=s)
-        sp, ip, _ = li.seconds_to_psnr(plain0.clone(), sd, 1, target, args.ref_iters + 500, seed=s)
         learned0, _, branch = li.initial_map(sd, mlp)
-        sl, il, curve = li.seconds_to_psnr(learned0.clone(), sd, 8, target, args.ref_iters, seed=s)
-        # the two factors separately: plain init batched, learned init one view per step
-        spb, ipb, _ = li.seconds_to_psnr(plain0.clone(), sd, 8, target, args.ref_iters, seed=s)
-        sl1, il1, _ = li.seconds_to_psnr(learned0.clone(), sd, 1, target, args.ref_iters + 500, seed=s)
-        rows.append(dict(scene=s, target_psnr=round(target, 3), plain_s=round(sp, 3), plain_iters=ip,
-                         learned_s=round(sl, 3), learned_iters=il, plain_batched_s=round(spb, 3),
-                         plain_batched_iters=ipb, learned_single_s=round(sl1, 3), learned_single_iters=il1,
-                         model_branch_frac=round(float((branch == 2).float().mean()), 3)))
-    plain = float(np.mean([r["plain_s"] for r in rows]))
-    lrn = float(np.mean([r["learned_s"] for r in rows]))
-    print(json.dumps({
-        "metric": "secs-to-PSNR learned vs plain", "value": round(lrn, 3), "unit": "s", "higher_is_better": False,
-        "plain_value": round(plain, 3), "speedup": round(plain / lrn, 3) if lrn > 0 else None, "n_gpus": 1,
-        "dtype": "f32 (MLP bf16/f32-acc)", "data": "synthetic",
-        "config": {"workload": f"LiDAR line scenes, {args.learned_n} Gaussians SH1, 28 train + 4 held-out keyframes "
-                               f"320x240; MLP trained on 200-iteration pairs of scenes 10-12",
-                   "ref_iters": args.ref_iters, "train_pairs": int(x.shape[0]),
-                   "mlp_loss_first_last": [round(losses[0], 5), round(losses[-1], 5)], "train_s": round(train_s, 2)},
-        "scenes": rows}), flush=True)
+        target = li.final_psnr(plain0.clone(), sd, 1, ref_iters, seed=s)
+        row = {"scene": s, "target_psnr": round(target, 3), "model_branch_frac": round(float((branch == 2).float().mean()), 3)}
+        for name, p0, views, cap in (("plain_1view", plain0, 1, ref_iters + 500), ("learned_8view", learned0, 8, ref_iters),
+                                     ("plain_8view", plain0, 8, ref_iters), ("learned_1view", learned0, 1, ref_iters + 500)):
+            sec, it, _ = li.seconds_to_psnr(p0.clone(), sd, views, target, cap, seed=s)
+            row[name] = {"s": None if math.isinf(sec) else round(sec, 3), "iters": None if math.isinf(sec) else it}
+        rows.append(row)
+
+    def mean_s(arm):
+        v = [r[arm]["s"] for r in rows]
+        return None if any(x is None for x in v) else round(float(np.mean(v)), 3)
+    plain, lrn = mean_s("plain_1view"), mean_s("learned_8view")
+    gains = []
+    for r in rows:
+        a, b = r["plain_1view"]["iters"], r["learned_1view"]["iters"]
+        gains.append(None if a is None or b is None else round(a / b, 3))
+    return {"metric": "secs to the held-out PSNR of plain init + 1 view after ref_iters iterations",
+            "plain_1view_s": plain, "learned_8view_s": lrn,
+            "speedup": round(plain / lrn, 3) if plain and lrn else None,
+            "plain_8view_s": mean_s("plain_8view"), "learned_1view_s": mean_s("learned_1view"),
+            "learned_only_iter_gain_per_scene": gains,
+            "scenes": rows,
+            "config": {"scenes": "LiDAR line scenes SH1, 32 keyframes 320x240 (every 8th held out)",
+                       "train_scenes": list(train_seeds), "train_gaussians_per_scene": n_train,
+                       "train_pairs": int(x.shape[0]), "eval_scenes": list(eval_seeds),
+                       "new_gaussians_per_batch": n_eval, "ref_iters": ref_iters,
+                       "mlp_loss_first_last": [round(losses[0], 5), round(losses[-1], 5)],
+                       "pair_generation_s": round(gen_s, 2), "train_s": round(train_s, 2)}}
+
+
+def run_learned(args):
+    """--learned: the secs-to-PSNR experiment alone, as its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    r = learned_experiment(args.learned_n, args.learned_eval_n, args.ref_iters)
+    print(json.dumps({"metric": "secs-to-PSNR learned vs plain", "value": r["learned_8view_s"], "unit": "s",
+                      "higher_is_better": False, "n_gpus": 1, "dtype": "f32 (MLP bf16/f32-acc)", "data": "synthetic",
+                      **r}), flush=True)
 
 
 def max_over_ranks(ms, world, device):
@@ -850,13 +853,16 @@ def main():
                 "value": round(r["px"] / r["e2e_s"] / 1e6, 2), "unit": "Mpix/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"], "ms_per_step": round(1e3 * r["e2e_s"], 3),
                 "eager_device_ms_per_step": round(r["eager_ms"], 3), "h2d_ms_per_step": round(r["h2d_ms"], 3),
-                "path": "pinned host targets -> copy stream (next step's upload overlaps this step) -> graph "
-                        "input buffers -> gs_step graph replay -> loss read back, every step"},
+                "path": "C ABI (gs_graph_launch of a gs_step captured with host target and loss buffers): "
+                        "pinned host targets -> device (graph branch overlapped with projection and binning) -> "
+                        "step -> loss -> pinned host, stream synchronised and the loss read every step"},
         "gpu_launches": r["kernels"] * args.steps, "timed": "CUDA-graph replay of gs_step",
         "f1_ssim_and_mask": r["f1"], "f2_f3_calls": r["f23"], "a9_persistent": r["a9"],
         "kernel_shape": {"tile": args.tile, "chunk": args.chunk},
         "autotune": r["tune"],
     }
+    if not args.no_learned and not args.core_only and world == 1:
+        line["secs_to_psnr"] = learned_experiment(args.learned_n, args.learned_eval_n, args.ref_iters)
     if not args.no_cpu_baseline and not args.core_only and world == 1:
         tg = [{"rgb": t[0].cpu().numpy(), "depth": t[1].cpu().numpy()} for t in
               zip(__import__("paper_2604_12942_gb300").unpack_rgb(r["trgb"], r["cams"]),

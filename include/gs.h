@@ -197,6 +197,16 @@ typedef struct {
     float lr[6];                /* means, log-scales, quats, opacity, SH DC, SH rest */
     float b1, b2, eps;
     int32_t optimize;           /* 0: stop after the backward (gradients left in grads) */
+    /* Optional HOST buffers (pinned memory; NULL = not used) for a step fed from the host: the
+     * step starts by copying host_target_rgb [3*P], host_target_depth [P] and host_mask [P]
+     * into target_rgb, target_depth and mask (which must then be given: the device buffers the
+     * step reads) and ends by copying loss_out [n_views + 1] into host_loss_out.  In a graph of
+     * gs_graph_create the upload runs on a second branch, overlapped with the projection and
+     * the binning (which do not read the targets); gs_step copies in stream order.  The host
+     * buffers must stay valid until the step has completed on the stream. */
+    const float *host_target_rgb, *host_target_depth;
+    const uint8_t *host_mask;
+    float *host_loss_out;
 } gs_step_io;
 
 typedef struct gs_graph_s *gs_graph;

@@ -61,7 +61,8 @@ class StepIO(C.Structure):
                 ("out_rgb", C.c_void_p), ("out_depth", C.c_void_p), ("dl_drgb", C.c_void_p), ("dl_ddepth", C.c_void_p),
                 ("loss_out", C.c_void_p), ("grad_twist", C.c_void_p), ("update_mask", C.c_void_p),
                 ("lr", C.c_float * 6), ("b1", C.c_float), ("b2", C.c_float), ("eps", C.c_float),
-                ("optimize", C.c_int32)]
+                ("optimize", C.c_int32), ("host_target_rgb", C.c_void_p), ("host_target_depth", C.c_void_p),
+                ("host_mask", C.c_void_p), ("host_loss_out", C.c_void_p)]
 
 
 class PcaOpts(C.Structure):

@@ -343,8 +343,15 @@ class MappingStep:
         self.graph = None
         self._graph_io = None
 
-    def _io(self, target_rgb, target_depth, mask, update_mask, optimize, with_twist):
+    def _io(self, target_rgb, target_depth, mask, update_mask, optimize, with_twist, host=None):
         io = N.StepIO()
+        if host is not None:
+            # pinned host buffers (rgb, depth, mask, loss), each may be None: the step copies the
+            # targets from them into the device buffers above and the loss back
+            for name, t in zip(("host_target_rgb", "host_target_depth", "host_mask", "host_loss_out"), host):
+                if t is not None:
+                    assert not t.is_cuda and t.is_pinned() and t.is_contiguous(), name
+                    setattr(io, name, t.data_ptr())
         io.target_rgb, io.target_depth = target_rgb.data_ptr(), (target_depth.data_ptr() if target_depth is not None else None)
         io.mask = mask.data_ptr() if mask is not None else None
         io.out_rgb, io.out_depth = self.rgb.data_ptr(), self.depth.data_ptr()
@@ -358,19 +365,23 @@ class MappingStep:
         return io
 
     def __call__(self, target_rgb, target_depth=None, mask=None, update_mask=None, optimize=True,
-                 with_twist=False) -> StepResult:
-        io = self._io(target_rgb, target_depth, mask, update_mask, optimize, with_twist)
+                 with_twist=False, host=None) -> StepResult:
+        io = self._io(target_rgb, target_depth, mask, update_mask, optimize, with_twist, host)
         gp, gg, gm, gv = self._structs
         N.check(N.lib().gs_step(C.byref(gp), C.byref(gg), C.byref(gm), C.byref(gv), self.ws.cams_c,
                                 C.byref(self.opts), C.byref(self.ws.layout), _ptr(self.ws.buf), C.byref(io), _stream()),
                 "gs_step")
         return StepResult(self.loss, self.rgb, self.depth)
 
-    def capture(self, target_rgb, target_depth=None, mask=None, update_mask=None, optimize=True, with_twist=False):
-        """Record one step as a CUDA graph (inputs are read from these buffers at replay)."""
+    def capture(self, target_rgb, target_depth=None, mask=None, update_mask=None, optimize=True, with_twist=False,
+                host=None):
+        """Record one step as a CUDA graph (inputs are read from these buffers at replay).  With
+        host = (pinned rgb, depth, mask, loss) tensors (any may be None) every replay uploads
+        the targets from host memory (overlapped with the projection and binning) and copies
+        the loss back to host memory."""
         self.release()
-        io = self._io(target_rgb, target_depth, mask, update_mask, optimize, with_twist)
-        self._graph_io = (io, target_rgb, target_depth, mask, update_mask)
+        io = self._io(target_rgb, target_depth, mask, update_mask, optimize, with_twist, host)
+        self._graph_io = (io, target_rgb, target_depth, mask, update_mask, host)
         side = torch.cuda.Stream(device=self.planes.device)
         side.wait_stream(torch.cuda.current_stream())
         h = C.c_void_p()

@@ -576,17 +576,66 @@ static gs_status check_step_io(const gs_step_io* io) {
     if (!io->target_rgb || !io->out_rgb || !io->out_depth || !io->dl_drgb || !io->loss_out)
         return fail(GS_ERR_INVALID_ARG, "target_rgb, out_rgb, out_depth, dl_drgb and loss_out are required");
     if (io->target_depth && !io->dl_ddepth) return fail(GS_ERR_INVALID_ARG, "the depth loss needs dl_ddepth");
+    if ((io->host_target_depth && !io->target_depth) || (io->host_mask && !io->mask))
+        return fail(GS_ERR_INVALID_ARG, "host targets need the device buffers they are copied into");
     return GS_OK;
 }
+
+// Copies the step's host targets into its device buffers on stream `st`.
+static cudaError_t upload_targets(const gs_step_io* io, const gs_ws_layout* L, cudaStream_t st) {
+    const size_t P = (size_t)L->total_pixels;
+    cudaError_t e = cudaSuccess;
+    if (io->host_target_rgb)
+        e = cudaMemcpyAsync(const_cast<float*>(io->target_rgb), io->host_target_rgb, sizeof(float) * 3 * P,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && io->host_target_depth)
+        e = cudaMemcpyAsync(const_cast<float*>(io->target_depth), io->host_target_depth, sizeof(float) * P,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && io->host_mask)
+        e = cudaMemcpyAsync(const_cast<uint8_t*>(io->mask), io->host_mask, P, cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+// A second stream and fork / join events: the upload branch of a captured step.
+struct CopyBranch {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static gs_status run_step_tail(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
+                               const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
+                               const gs_step_io* io, cudaStream_t st);
 
 // The whole step on one stream (no host synchronisation, capturable).
 static gs_status run_step(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
                           const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
-                          const gs_step_io* io, cudaStream_t st) {
+                          const gs_step_io* io, cudaStream_t st, const CopyBranch* cb = nullptr) {
     gs_status s;
+    const bool host_in = io->host_target_rgb || io->host_target_depth || io->host_mask;
+    const bool branch = host_in && cb && cb->st;
+    if (branch) {
+        GS_CUDA(cudaEventRecord(cb->fork, st));
+        GS_CUDA(cudaStreamWaitEvent(cb->st, cb->fork, 0));
+        GS_CUDA(upload_targets(io, L, cb->st));
+        GS_CUDA(cudaEventRecord(cb->join, cb->st));
+    } else if (host_in) {
+        GS_CUDA(upload_targets(io, L, st));
+    }
     if ((s = upload_views(ws, *L, G, L->n_views, st)) != GS_OK) return s;
     GS_CUDA(run_project(params, opts, L, ws, st));
     GS_CUDA(run_bin_sort(opts, L, ws, st));
+    if (branch) GS_CUDA(cudaStreamWaitEvent(st, cb->join, 0));   // targets needed from here on
+    s = run_step_tail(params, grads, m, v, opts, L, G, ws, io, st);
+    if (s == GS_OK && io->host_loss_out)
+        GS_CUDA(cudaMemcpyAsync(io->host_loss_out, io->loss_out, sizeof(float) * (L->n_views + 1),
+                                cudaMemcpyDeviceToHost, st));
+    return s;
+}
+
+// The step after the binning: compositing with the loss, backward and update.
+static gs_status run_step_tail(gs_gaussians* params, gs_gaussians* grads, gs_gaussians* m, gs_gaussians* v,
+                               const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
+                               const gs_step_io* io, cudaStream_t st) {
     if (opts->persistent) {
         // loss normalisers first (the forward's epilogue reads them), then one persistent
         // kernel for forward, backward, projection backward and Adam
@@ -649,7 +698,15 @@ struct GraphState {
     gs_render_opts opts;
     gs_ws_layout layout;
     void* ws = nullptr;
+    CopyBranch copy;   // the host-target upload branch (created only when the step has one)
 };
+
+static void release_copy_branch(CopyBranch& c) {
+    if (c.fork) cudaEventDestroy(c.fork);
+    if (c.join) cudaEventDestroy(c.join);
+    if (c.st) cudaStreamDestroy(c.st);
+    c = CopyBranch();
+}
 
 // Error recording for entry points defined in other translation units.
 gs_status record_error(gs_status s, const char* msg) { return fail(s, "%s", msg); }
@@ -896,12 +953,30 @@ gs_status gs_graph_create(gs_graph* out, gs_gaussians* params, gs_gaussians* gra
     gst->opts = *opts;
     gst->layout = *L;
     gst->ws = ws;
-    GS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    s = run_step(params, grads, m, v, opts, L, G, ws, io, st);
+    if (io->host_target_rgb || io->host_target_depth || io->host_mask) {
+        cudaError_t e = cudaStreamCreateWithFlags(&gst->copy.st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&gst->copy.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&gst->copy.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            release_copy_branch(gst->copy);
+            delete gst;
+            return fail(GS_ERR_CUDA, "copy branch: %s", cudaGetErrorString(e));
+        }
+    }
+    {
+        const cudaError_t eb = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (eb != cudaSuccess) {
+            release_copy_branch(gst->copy);
+            delete gst;
+            return fail(GS_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(eb));
+        }
+    }
+    s = run_step(params, grads, m, v, opts, L, G, ws, io, st, &gst->copy);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(st, &graph);
     if (s != GS_OK || ec != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
+        release_copy_branch(gst->copy);
         delete gst;
         return s != GS_OK ? s : fail(GS_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ec));
     }
@@ -924,6 +999,7 @@ gs_status gs_graph_create(gs_graph* out, gs_gaussians* params, gs_gaussians* gra
     const cudaError_t ei = cudaGraphInstantiate(&gst->exec, graph, 0);
     if (ei != cudaSuccess || !gst->views_node) {
         cudaGraphDestroy(graph);
+        release_copy_branch(gst->copy);
         delete gst;
         return fail(GS_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
     }
@@ -962,6 +1038,7 @@ gs_status gs_graph_destroy(gs_graph g) {
     GraphState* gst = reinterpret_cast<GraphState*>(g);
     if (gst->exec) cudaGraphExecDestroy(gst->exec);
     if (gst->graph) cudaGraphDestroy(gst->graph);
+    release_copy_branch(gst->copy);
     delete gst;
     return GS_OK;
 }

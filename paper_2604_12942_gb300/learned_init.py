@@ -169,6 +169,48 @@ def seconds_to_psnr(planes, sd: SceneData, views, target_psnr, max_iters, eval_e
     return math.inf, max_iters, curve
 
 
+class HeldOutLoss:
+    """The mapping objective (L1 colour + depth, gs_render_fwd's fused loss) of a map on the
+    scene's held-out keyframes, with one workspace kept across evaluations."""
+
+    def __init__(self, sd: SceneData, n):
+        self.target_rgb, self.target_dep = render(sd.gt, sd.sh_degree, sd.test_cams)
+        self.ws = Workspace(n, sd.test_cams, default_opts(tile=16, chunk=64), max(1 << 20, 64 * n * len(sd.test_cams)),
+                            sd.gt.device)
+        P = self.ws.layout.total_pixels
+        dev = sd.gt.device
+        self.rgb, self.dep = torch.empty(3 * P, device=dev), torch.empty(P, device=dev)
+        self.dl, self.dld = torch.empty(3 * P, device=dev), torch.empty(P, device=dev)
+        self.loss = torch.empty(len(sd.test_cams) + 1, device=dev)
+        self.sh_degree = sd.sh_degree
+
+    def __call__(self, planes) -> float:
+        self.ws.project(planes, self.sh_degree)
+        self.ws.bin_sort()
+        self.ws.render_fwd(self.rgb, self.dep, None, self.target_rgb, self.target_dep, None, self.dl, self.dld,
+                           self.loss)
+        if self.ws.counters().status != 0:
+            raise RuntimeError("held-out render failed")
+        return float(self.loss[-1])
+
+
+def iterations_to_loss(planes, sd: SceneData, views, target_loss, max_iters, eval_every=25, seed=0):
+    """Iterations of the plain optimiser (`views` keyframes per step) until the held-out loss
+    falls to target_loss (None if it does not within max_iters), and the loss curve."""
+    ev = HeldOutLoss(sd, planes.shape[1])
+    opt = Optimizer(planes, sd, views, seed=seed)
+    curve = []
+    it = 0
+    while it < max_iters:
+        opt.run(eval_every)
+        it += eval_every
+        lval = ev(opt.step.planes)
+        curve.append((it, lval))
+        if lval <= target_loss:
+            return it, curve
+    return None, curve
+
+
 def final_psnr(planes, sd: SceneData, views, iters, seed=0):
     test_rgb, _ = render(sd.gt, sd.sh_degree, sd.test_cams)
     opt = Optimizer(planes, sd, views, seed=seed)

@@ -143,3 +143,32 @@ def test_optimizing_step_equals_staged_step():
     assert float(d.max()) <= 2.05 * max(lr)
     assert float((d > 1e-6 * float(planes.abs().max())).float().mean()) < 1e-3
     assert float(step.grads.abs().sum()) == 0.0   # the fused step does not touch the gradients
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_step_fed_from_host_buffers(graph):
+    """The step with its targets in pinned host memory (copied in by the step itself, in a graph
+    on a branch overlapped with the projection and binning) and its loss copied back to host
+    memory: the same results as the step on device targets."""
+    sc, cams, trgb, td = _setup(seed=43)
+    dev = gs.MappingStep(planes_of(sc), 3, cams)
+    host = gs.MappingStep(planes_of(sc), 3, cams)
+    h_rgb, h_dep = trgb.cpu().pin_memory(), td.cpu().pin_memory()
+    h_loss = torch.zeros(len(cams) + 1).pin_memory()
+    # the host step's device target buffers start as garbage: everything must come from the host
+    d_rgb, d_dep = torch.full_like(trgb, 7.0), torch.full_like(td, -3.0)
+    if graph:
+        dev.capture(trgb, td)
+        host.capture(d_rgb, d_dep, host=(h_rgb, h_dep, None, h_loss))
+    for k in range(3):
+        if graph:
+            dev.replay()
+            host.replay()
+        else:
+            dev(trgb, td)
+            host(d_rgb, d_dep, host=(h_rgb, h_dep, None, h_loss))
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(h_loss.numpy(), dev.loss.cpu().numpy(), rtol=1e-6)
+    assert torch.equal(d_rgb, trgb) and torch.equal(d_dep, td)
+    assert float(((host.planes - dev.planes).abs() > 1e-6).float().mean()) < 1e-3
+    assert host.ws.counters().adam_step == 3
