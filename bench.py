@@ -34,7 +34,10 @@ METRIC = "fwd+bwd render Mpix/s and iters/s at 2M Gaussians; secs-to-PSNR learne
 # below.  `digest` is the SHA-256 of the library's CUDA sources when the figures were taken:
 # once any kernel source changes the figures no longer describe the build, and every stage
 # reports traffic null until they are captured again.
-TRAFFIC = {"digest": None, "n": 2_000_000, "tile": 16, "chunk": 256, "bytes": {}}
+TRAFFIC = {"digest": "a90a94112a77152f171285172b387ee2e147c3a2ac771d76867e0cbdad8eaf5f", "n": 2_000_000, "tile": 16,
+           "chunk": 256,
+           "bytes": {"project": 490992896, "bin_sort": 742902528, "render_fwd": 448159488,
+                     "composite_bwd": 414814464, "project_bwd_adam": 2278777088}}
 
 
 def source_digest():
@@ -70,6 +73,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="32, 64, 128 or 256; 0 = autotune")
     ap.add_argument("--retune", action="store_true", help="ignore the autotune cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", type=int, default=0, metavar="K",
+                    help="set up the workload, run K eager steps (gs_step) and exit: the last kernels of the "
+                         "program are one whole step, for profilers")
     ap.add_argument("--core-only", action="store_true",
                     help="only the timed step and its stage breakdown (no f1/f2/f3 calls, end-to-end run or CPU "
                          "baseline): a short command for profilers")
@@ -326,6 +332,14 @@ def run_gpu(args, rank, world):
         tune = {"tile": ch.tile, "chunk": ch.chunk, "ms_per_step": round(ch.ms, 4), "table": ch.table, "key": key}
     opts = gs.default_opts(tile=args.tile, chunk=args.chunk)
     step = gs.MappingStep(planes0, 3, cams, opts, max_pairs=cap)
+    if args.profile_step:
+        for _ in range(args.profile_step):
+            step(trgb, tdep)
+        torch.cuda.synchronize()
+        c = step.ws.counters()
+        print(json.dumps({"profile_step": args.profile_step, "status": int(c.status), "pairs": int(c.n_pairs),
+                          "kernels_per_step": kernels_per_step(step.ws.layout)}), flush=True)
+        sys.exit(0 if c.status == 0 else 1)
     stages = ["project", "bin_sort", "render_fwd", "composite_bwd", "project_bwd_adam"]
     st = torch.cuda.current_stream()
 
@@ -647,10 +661,11 @@ def tile_sort_passes(L):
 def kernels_per_step(L):
     """Kernels one gs_step launches (the graph replays exactly these)."""
     # view table, project, entry count / scan / compaction, 4 depth-sort passes of 3
-    # kernels, pair count / scan / emission, 3 per tile-sort pass, ranges, 3 tile-order
-    # kernels, loss count + composite + loss finalize, gradient-record clear + composite
-    # backward + projection backward, Adam counter + Adam
-    return 1 + 1 + 3 + 3 * 4 + 3 + 3 * tile_sort_passes(L) + 1 + 3 + 3 + 3 + 2
+    # kernels, pair count / scan / offsets / emission, 3 per tile-sort pass, ranges, 3
+    # tile-order kernels, loss count + composite + loss finalize, gradient-record clear +
+    # composite backward + Adam counter, projection backward entry and row (+ Adam) parts
+    # (39 with two tile-sort passes, as the ncu launch list of one step shows)
+    return 1 + 1 + 3 + 3 * 4 + 4 + 3 * tile_sort_passes(L) + 1 + 3 + 3 + 3 + 2
 
 
 # Algorithmic FP32 work per evaluated fragment, (pixel, Gaussian) pairs tested: 20 operations in

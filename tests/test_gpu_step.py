@@ -172,3 +172,50 @@ def test_step_fed_from_host_buffers(graph):
     assert torch.equal(d_rgb, trgb) and torch.equal(d_dep, td)
     assert float(((host.planes - dev.planes).abs() > 1e-6).float().mean()) < 1e-3
     assert host.ws.counters().adam_step == 3
+
+
+def test_step_with_nothing_visible():
+    """Every Gaussian behind the camera: the image is the background, the loss is the L1 of the
+    black image against the targets (oracle), no row is updated, and the step reports no error."""
+    import oracle
+    sc = synth.uniform_box_scene(45, 500, sh_degree=3, box=((-3, 3), (-3, 3), (-9, -2)))
+    cams = [synth.camera(64, 48, 60.0), synth.camera(40, 30, 40.0)]
+    tg = synth.random_targets(46, cams)
+    planes = planes_of(sc)
+    step = gs.MappingStep(planes.clone(), 3, cams)
+    r = step(gs.pack_rgb([t["rgb"] for t in tg]), gs.pack_plane([t["depth"] for t in tg]))
+    torch.cuda.synchronize()
+    c = step.ws.counters()
+    assert c.status == 0 and c.n_pairs == 0 and c.n_entries == 0
+    assert float(r.rgb.abs().max()) == 0.0 and float(r.depth.abs().max()) == 0.0
+    ref = oracle.loss_and_grads(sc, cams, tg)
+    assert abs(float(r.loss[-1]) - ref["loss"]) < 1e-5 * ref["loss"]
+    assert torch.equal(step.planes, planes) and float(step.m.abs().max()) == 0.0
+
+
+def test_single_gaussian_and_the_maximum_view_count():
+    """One Gaussian seen by GS_MAX_VIEWS = 32 small views of different poses and sizes: images,
+    parameter gradients and all 32 twists against the oracle."""
+    import oracle
+    from tests.gpu_helpers import rel_l2
+    rng = np.random.default_rng(47)
+    sc = synth.uniform_box_scene(48, 1, sh_degree=3, box=((-0.2, 0.2), (-0.2, 0.2), (3, 4)))
+    sc.log_scales[:] = -1.0
+    cams = []
+    for v in range(32):
+        w, h = int(rng.integers(9, 40)), int(rng.integers(7, 30))
+        cams.append(synth.camera(w, h, 0.8 * w, t=rng.uniform(-0.15, 0.15, 3)))
+    tg = synth.random_targets(49, cams)
+    step = gs.MappingStep(planes_of(sc), 3, cams)
+    r = step(gs.pack_rgb([t["rgb"] for t in tg]), gs.pack_plane([t["depth"] for t in tg]), optimize=False,
+             with_twist=True)
+    torch.cuda.synchronize()
+    assert step.ws.counters().status == 0
+    ref = oracle.loss_and_grads(sc, cams, tg)
+    for v, C_ in enumerate(gs.unpack_rgb(r.rgb, cams)):
+        img = ref["fwd"][v][1]
+        ok = ~img["fragile"]
+        assert np.abs(C_.cpu().numpy() - img["C"])[:, ok].max() < 1e-4, v
+    assert abs(float(r.loss[-1]) - ref["loss"]) < 1e-4 * max(1.0, ref["loss"])
+    assert rel_l2(step.grads.cpu().numpy(), ref["grads"]) < 1e-3
+    assert rel_l2(step.twist.cpu().numpy(), ref["twists"]) < 1e-3
