@@ -152,6 +152,8 @@ typedef struct {
                             gs_composite_bwd); only the records of visible entries are defined */
     size_t geo2d;        /* [n_views*n] records of 12 floats: per visible entry, the gradients
                             w.r.t. the mean and the world covariance (projection backward) */
+    size_t dirgrad;      /* float [3][n]: per visible row, the gradient of the mean through the SH
+                            view directions (projection backward: SH part -> geometry part) */
     size_t visible;      /* uint8 [n]: 1 if the Gaussian covers a tile of any view */
     size_t entries;      /* uint32 [n_views*n]: the visible entries in (view, Gaussian) order */
     size_t erect;        /* uint32 [n_views*n][2]: per visible entry, in the order of `entries`,

@@ -44,7 +44,7 @@ class GicpResult(C.Structure):
 class WsLayout(C.Structure):
     _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "touched", "scan_tmp",
                                           "ekeys0", "ekeys1", "evals0", "evals1", "keys0", "keys1", "vals0", "vals1", "pair_mask", "emit_tmp", "sort_tmp", "ranges", "T_final",
-                                          "n_contrib", "grad2d", "geo2d", "visible", "entries", "erect", "tile_order", "render_mask",
+                                          "n_contrib", "grad2d", "geo2d", "dirgrad", "visible", "entries", "erect", "tile_order", "render_mask",
                                           "ssim_tmp", "total")] + \
                [("has_ssim", C.c_int32), ("sorted_buf", C.c_int32), ("total_tiles", C.c_int32), ("total_pixels", C.c_int64),
                 ("max_pairs", C.c_int64), ("n", C.c_int64), ("n_views", C.c_int32), ("tile", C.c_int32)]

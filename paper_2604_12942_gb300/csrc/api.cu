@@ -158,6 +158,7 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.n_contrib = take(sizeof(uint32_t) * (size_t)G.total_pixels);
     L.grad2d = take(sizeof(float) * 12 * (size_t)VN);
     L.geo2d = take(sizeof(float) * 12 * (size_t)VN);
+    L.dirgrad = take(sizeof(float) * 3 * (size_t)n);
     L.entries = take(sizeof(uint32_t) * (size_t)VN);
     L.erect = take(sizeof(uint32_t) * 2 * (size_t)VN);
     L.visible = take((size_t)n);
@@ -490,6 +491,7 @@ static ProjectBwdArgs pbwd_args(const gs_gaussians* g, const gs_render_opts* opt
     p.counters = at<Counters>(ws, L->counters);
     p.grad2d = at<float4>(ws, L->grad2d);
     p.geo2d = at<float4>(ws, L->geo2d);
+    p.dirgrad = at<float>(ws, L->dirgrad);
     if (grads) {
         p.g_means = grads->means; p.g_log_scales = grads->log_scales; p.g_quats = grads->quats;
         p.g_logits = grads->opacity_logits; p.g_sh = grads->sh;

@@ -29,6 +29,7 @@ struct ProjectBwdArgs {
     const Counters* counters; // n_entries
     const float4* grad2d;  // [V*n][3] screen-space sums
     float4* geo2d;         // [V*n][3] per-entry geometry gradients (entry part -> row part)
+    float* dirgrad;        // [3][n] view-direction gradient of the mean (SH part -> geometry part)
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
     float* grad_twist;     // [V][6] or null
     // fused Adam (fused_adam != 0): parameters updated in place, gradients not stored

@@ -106,11 +106,19 @@ __global__ void __launch_bounds__(kEntryThreads) project_bwd_entry_kernel(Projec
     project_bwd_entry_part(a, blockIdx.x, gridDim.x, s_tw);
 }
 
+// The row part as two kernels (SH part, then geometry part; see project_bwd.cuh).
+constexpr int kRowThreads = 128;
+
 template <int DEG, bool FUSED_ADAM>
-__global__ void __launch_bounds__(kProjBwdThreads, 4) project_bwd_kernel(ProjectBwdArgs a) {
+__global__ void __launch_bounds__(kRowThreads, 5) project_bwd_sh_kernel(ProjectBwdArgs a) {
     __shared__ float s_tw[GS_MAX_VIEWS * 6];
-    extern __shared__ float s_dyn[];
-    project_bwd_rows<DEG, FUSED_ADAM, kProjBwdThreads>(a, blockIdx.x, s_tw, s_dyn);
+    __shared__ float s_mv[FUSED_ADAM ? sh_mv_floats<DEG, kRowThreads>() : 1];
+    project_bwd_sh_rows<DEG, FUSED_ADAM, kRowThreads>(a, blockIdx.x, s_tw, s_mv);
+}
+
+template <int DEG, bool FUSED_ADAM>
+__global__ void __launch_bounds__(kRowThreads, 8) project_bwd_geo_kernel(ProjectBwdArgs a) {
+    project_bwd_geo_rows<DEG, FUSED_ADAM, kRowThreads>(a, blockIdx.x);
 }
 
 
@@ -129,20 +137,14 @@ cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st) {
 
 template <int DEG, bool FUSED_ADAM>
 static cudaError_t launch_project_bwd_d(const ProjectBwdArgs& a, unsigned blocks, cudaStream_t st) {
-    constexpr size_t smem = sizeof(float) * 2 * 3 * (DEG + 1) * (DEG + 1) * kProjBwdThreads;
-    static bool attr_set[kMaxDevices] = {};
-    cudaError_t e = once_per_device(attr_set, [&] {
-        return cudaFuncSetAttribute(project_bwd_kernel<DEG, FUSED_ADAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem);
-    });
-    if (e != cudaSuccess) return e;
-    project_bwd_kernel<DEG, FUSED_ADAM><<<blocks, kProjBwdThreads, smem, st>>>(a);
+    project_bwd_sh_kernel<DEG, FUSED_ADAM><<<blocks, kRowThreads, 0, st>>>(a);
+    project_bwd_geo_kernel<DEG, FUSED_ADAM><<<blocks, kRowThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <bool FUSED_ADAM>
 static cudaError_t launch_project_bwd_t(const ProjectBwdArgs& a, int deg, cudaStream_t st) {
-    const unsigned blocks = (unsigned)((a.n + kProjBwdThreads - 1) / kProjBwdThreads);
+    const unsigned blocks = (unsigned)((a.n + kRowThreads - 1) / kRowThreads);
     if (blocks == 0) return cudaSuccess;
     switch (deg) {
         case 0: return launch_project_bwd_d<0, FUSED_ADAM>(a, blocks, st);
@@ -153,7 +155,8 @@ static cudaError_t launch_project_bwd_t(const ProjectBwdArgs& a, int deg, cudaSt
 }
 
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st) {
-    // entry part (persistent grid over the device-side entry count), then the row part
+    // entry part (persistent grid over the device-side entry count), then the row part's SH
+    // and geometry kernels
     project_bwd_entry_kernel<<<sort_grid() * 4, kEntryThreads, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -182,230 +182,267 @@ __device__ __forceinline__ void project_bwd_entry_part(const ProjectBwdArgs& a, 
     }
 }
 
-// a7, row part, and a8 when fused.
-// One thread per Gaussian, kProjBwdThreads per block.  The 3K SH coefficients and their
-// gradient sums live in shared memory (one column per thread) rather than registers, which
-// keeps the kernel within 128 registers at SH degree 3.
-constexpr int kProjBwdThreads = 128;   // row block of the standalone kernel
+// ----------------------------------------------------------------------------------------
+// The row part in two kernels, each with fewer live registers than the combined row part (so
+// more resident warps for their memory latency):
+//   SH part        one colour channel at a time: the channel's K coefficients and their
+//                  gradient sums in registers (no shared memory), the row's views walked once
+//                  per channel; the SH planes' gradient (or, fused, their Adam step), the
+//                  view-direction gradient of the mean into dirgrad [3][n] and the
+//                  view-direction twist (rho) of every view
+//   geometry part  the entry part's geometry gradients and the opacity sums over the row's
+//                  views, plus dirgrad; the covariance -> scale and rotation chain; the 11
+//                  geometry planes' gradient (or, fused, their Adam step)
+// ----------------------------------------------------------------------------------------
+// Fused: each thread's Adam moments of a channel's K planes are copied asynchronously (cp.async,
+// 4 bytes each, no registers held while in flight) into s_mv [2 buffers][m, v][K][T] of shared
+// memory while the thread walks the previous channel's views, so the moment loads of a row are
+// in flight together with its other work; a thread reads only the slots it copied itself.
+template <int DEG, int T>
+constexpr int sh_mv_floats() { return 2 * 2 * (DEG + 1) * (DEG + 1) * T; }
 
-// FUSED_ADAM: apply the masked Adam step of a8 to the row with its finished gradient instead
-// of adding the gradient to the gradient planes (same arithmetic as adam_kernel).
-// Row block `blk` (rows blk * T .. blk * T + T - 1, T threads): s_tw is the block's
-// GS_MAX_VIEWS * 6 floats, s_dyn its 2 * 3K * T floats of shared memory.
 template <int DEG, bool FUSED_ADAM, int T>
-__device__ __forceinline__ void project_bwd_rows(const ProjectBwdArgs& a, int64_t blk, float* s_tw, float* s_dyn) {
+__device__ __forceinline__ void project_bwd_sh_rows(const ProjectBwdArgs& a, int64_t blk, float* s_tw, float* s_mv) {
     if (a.counters->status != 0) return;   // no gradient (and no Adam update) after a failed stage
     constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int kProjBwdThreads = T;   // the row-block size within this function
-    // dynamic shared memory: SH gradient sums [3K][threads], then SH coefficients [3K][threads]
     for (int t = threadIdx.x; t < a.n_views * 6; t += T) s_tw[t] = 0.f;
-    float* g_sh = s_dyn + threadIdx.x;                           // g_sh[k * kProjBwdThreads]
-    float* sh = s_dyn + 3 * K * kProjBwdThreads + threadIdx.x;   // sh[k * kProjBwdThreads]
-#pragma unroll
-    for (int k = 0; k < 3 * K; k++) g_sh[k * kProjBwdThreads] = 0.f;
     __syncthreads();
     const int64_t n = a.n;
     const int64_t i = blk * T + threadIdx.x;
-    // Rows that cover no tile of any view have no gradient: they read and write nothing.
     const bool live = i < n && a.visible[i] != 0;
     const int64_t ii = live ? i : 0;
-    // views whose tiles the row covers, loaded together
     uint64_t vmask = 0;
     if (live) {
 #pragma unroll 8
         for (int v = 0; v < a.n_views; v++)
             if (__ldg(a.touched + (int64_t)v * n + ii) != 0u) vmask |= 1ull << v;
     }
-    if (__all_sync(0xffffffffu, !live)) {
-        if (a.grad_twist == nullptr) return;
-    }
-    float mu[3], ls[3], q[4];
+    if (__all_sync(0xffffffffu, !live) && a.grad_twist == nullptr) return;
+    float mu[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        mu[k] = live ? __ldg(a.means + k * n + ii) : 0.f;
-        ls[k] = live ? __ldg(a.log_scales + k * n + ii) : 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++) q[k] = live ? __ldg(a.quats + k * n + ii) : (k == 0 ? 1.f : 0.f);
-    const float logit = live ? __ldg(a.logits + ii) : 0.f;
-#pragma unroll
-    for (int k = 0; k < 3 * K; k++) sh[k * kProjBwdThreads] = live ? __ldg(a.sh + k * n + ii) : 0.f;
-    Cov3 cv;
-    cov3_forward(q, ls, cv);
-    float g_mu[3] = {0, 0, 0};
-    float gS[6] = {0, 0, 0, 0, 0, 0};   // dL/dSigma as a symmetric matrix: xx xy xz yy yz zz
-    float g_o = 0.f;
+    for (int k = 0; k < 3; k++) mu[k] = live ? __ldg(a.means + k * n + ii) : 0.f;
     const int lane = threadIdx.x & 31;
-    // Each lane walks its own views in increasing order, so the warp iterates as often as its
-    // busiest Gaussian has views, not once per view any of its Gaussians has.
-    uint64_t todo = vmask;
-    while (__any_sync(0xffffffffu, todo != 0)) {
-        const bool act = todo != 0;
-        const int v = act ? __ffsll((long long)todo) - 1 : 0;
-        todo &= todo - 1;
-        const View& V = a.views[v];
-        const int64_t idx = (int64_t)v * n + ii;
-        float tw[6] = {0, 0, 0, 0, 0, 0};
-        if (act) {
-            // geometry gradients of the entry (entry part), opacity and colour sums
-            const float4* geo = a.geo2d + 3 * idx;
-            const float4 q0 = geo[0], q1 = geo[1], q2 = geo[2];
-            const float4* gr = a.grad2d + 3 * idx;
-            const float o_sum = reinterpret_cast<const float*>(gr + 1)[1];
-            const float4 r2 = gr[2];
-            g_mu[0] += q0.x; g_mu[1] += q0.y; g_mu[2] += q0.z;
-            gS[0] += q0.w; gS[1] += q1.x; gS[2] += q1.y; gS[3] += q1.z; gS[4] += q1.w; gS[5] += q2.x;
-            g_o += o_sum;
-            const float* W = V.R;
-            // SH colour: rgb_c = max(0, sum_k sh_kc Y_k(dir) + 0.5), dir = (mu - cw)/|mu - cw|
-            float d[3] = {mu[0] - V.cw[0], mu[1] - V.cw[1], mu[2] - V.cw[2]};
-            const float rn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            const float dir[3] = {d[0] * rn, d[1] * rn, d[2] * rn};
-            float Y[16];
-            sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
-            const float grgb[3] = {r2.x, r2.y, r2.z};
-            float wk[16];
+    const bool upd = live && (!FUSED_ADAM || !a.update_mask || a.update_mask[i]);
+    // moments of channel c into buffer c & 1 (an empty commit group when there is nothing to copy)
+    auto prefetch = [&](int c) {
+        if (FUSED_ADAM && upd) {
+            float* dst = s_mv + (c & 1) * 2 * K * T + threadIdx.x;
 #pragma unroll
-            for (int k = 0; k < K; k++) wk[k] = 0.f;
+            for (int k = 0; k < K; k++) {
+                cp_async4(dst + k * T, a.m[4] + (int64_t)(k * 3 + c) * n + i);
+                cp_async4(dst + (K + k) * T, a.v[4] + (int64_t)(k * 3 + c) * n + i);
+            }
+        }
+        cp_async_commit();
+    };
+    if (FUSED_ADAM) prefetch(0);
+    float gdir[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int c = 0; c < 3; c++) {
+        if (FUSED_ADAM) {
+            if (c < 2) prefetch(c + 1);
+            else cp_async_commit();
+        }
+        float shc[K], gc[K];
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
+        for (int k = 0; k < K; k++) {
+            shc[k] = live ? __ldg(a.sh + (int64_t)(k * 3 + c) * n + ii) : 0.f;
+            gc[k] = 0.f;
+        }
+        uint64_t todo = vmask;
+        while (__any_sync(0xffffffffu, todo != 0)) {
+            const bool act = todo != 0;
+            const int v = act ? __ffsll((long long)todo) - 1 : 0;
+            todo &= todo - 1;
+            float tw[3] = {0.f, 0.f, 0.f};
+            if (act) {
+                const View& V = a.views[v];
+                const int64_t idx = (int64_t)v * n + ii;
+                const float g = reinterpret_cast<const float*>(a.grad2d + 3 * idx + 2)[c];   // dL/d colour c
+                // rgb_c = max(0, sum_k sh_kc Y_k(dir) + 0.5), dir = (mu - cw)/|mu - cw|
+                const float d[3] = {mu[0] - V.cw[0], mu[1] - V.cw[1], mu[2] - V.cw[2]};
+                const float rn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                const float dir[3] = {d[0] * rn, d[1] * rn, d[2] * rn};
+                float Y[16];
+                sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
                 float s = 0.5f;
 #pragma unroll
-                for (int k = 0; k < K; k++) s += sh[(k * 3 + c) * kProjBwdThreads] * Y[k];
-                if (s < 0.f) continue;   // clamped channel: no gradient
+                for (int k = 0; k < K; k++) s += shc[k] * Y[k];
+                if (!(s < 0.f)) {   // a clamped channel has no gradient
 #pragma unroll
-                for (int k = 0; k < K; k++) {
-                    g_sh[(k * 3 + c) * kProjBwdThreads] += grgb[c] * Y[k];
-                    wk[k] += grgb[c] * sh[(k * 3 + c) * kProjBwdThreads];
+                    for (int k = 0; k < K; k++) gc[k] += g * Y[k];
+                    if (DEG > 0) {
+                        float gd[3] = {0.f, 0.f, 0.f};
+                        sh_basis_grad_acc<DEG>(dir[0], dir[1], dir[2], shc, gd[0], gd[1], gd[2]);
+                        const float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
+#pragma unroll
+                        for (int k = 0; k < 3; k++) gd[k] = g * (gd[k] - dir[k] * dd) * rn;
+#pragma unroll
+                        for (int k = 0; k < 3; k++) gdir[k] += gd[k];
+                        const float* W = V.R;
+#pragma unroll
+                        for (int r = 0; r < 3; r++) tw[r] = W[3 * r] * gd[0] + W[3 * r + 1] * gd[1] + W[3 * r + 2] * gd[2];
+                    }
                 }
             }
-            if (DEG > 0) {
-                float gd[3] = {0.f, 0.f, 0.f};
-                sh_basis_grad_acc<DEG>(dir[0], dir[1], dir[2], wk, gd[0], gd[1], gd[2]);
-                const float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
+            if (DEG > 0 && a.grad_twist) {
+                // the view-direction term moves only rho: one warp sum per view among the lanes
+                uint32_t pending = __ballot_sync(0xffffffffu, act);
+                while (pending) {
+                    const int leader = __ffs(pending) - 1;
+                    const int vl = __shfl_sync(0xffffffffu, v, leader);
+                    const uint32_t grp = __ballot_sync(0xffffffffu, act && v == vl);
 #pragma unroll
-                for (int k = 0; k < 3; k++) gd[k] = (gd[k] - dir[k] * dd) * rn;
-#pragma unroll
-                for (int k = 0; k < 3; k++) g_mu[k] += gd[k];
-#pragma unroll
-                for (int r = 0; r < 3; r++) tw[r] += W[3 * r] * gd[0] + W[3 * r + 1] * gd[1] + W[3 * r + 2] * gd[2];
+                    for (int k = 0; k < 3; k++) {
+                        const float x = warp_sum(((grp >> lane) & 1u) ? tw[k] : 0.f);
+                        if (lane == leader) atomicAdd(&s_tw[vl * 6 + k], x);
+                    }
+                    pending &= ~grp;
+                }
             }
         }
-        if (DEG > 0 && a.grad_twist) {
-            // the view-direction term moves only rho (the geometric twist came from the entry
-            // part): one warp sum per view present among the active lanes
-            uint32_t pending = __ballot_sync(0xffffffffu, act);
-            while (pending) {
-                const int leader = __ffs(pending) - 1;
-                const int vl = __shfl_sync(0xffffffffu, v, leader);
-                const uint32_t grp = __ballot_sync(0xffffffffu, act && v == vl);
+        if (upd) {
+            if constexpr (FUSED_ADAM) {
+                // a8 on the channel's planes: the gradient goes straight into Adam
+                const float bc1 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc1 : a.bc1);
+                const float bc2 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc2 : a.bc2);
+                cp_async_wait_prior();   // this channel's moments have landed (the next may be in flight)
+                const float* mv = s_mv + (c & 1) * 2 * K * T + threadIdx.x;
 #pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float x = warp_sum(((grp >> lane) & 1u) ? tw[k] : 0.f);
-                    if (lane == leader) atomicAdd(&s_tw[vl * 6 + k], x);
+                for (int k = 0; k < K; k++) {
+                    float p = shc[k], mm = mv[k * T], vv = mv[(K + k) * T];
+                    adam_update(p, gc[k], mm, vv, k == 0 ? a.lr[4] : a.lr[5], a.b1, a.b2, a.eps, bc1, bc2);
+                    a.p_sh[(int64_t)(k * 3 + c) * n + i] = p;
+                    a.m[4][(int64_t)(k * 3 + c) * n + i] = mm;
+                    a.v[4][(int64_t)(k * 3 + c) * n + i] = vv;
                 }
-                pending &= ~grp;
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    float* gp = a.g_sh + (int64_t)(k * 3 + c) * n + i;
+                    *gp = __fadd_rn(*gp, gc[k]);
+                }
             }
         }
     }
-    if (live) {
-        // Sigma = M M^T -> g_M = 2 gSigma M (symmetric gSigma); M = Rq diag(s)
-        const float Gs[9] = {gS[0], gS[1], gS[2], gS[1], gS[3], gS[4], gS[2], gS[4], gS[5]};
-        float gM[9];
+    if (FUSED_ADAM) cp_async_wait_all();
+    if (live && DEG > 0) {
 #pragma unroll
-        for (int r = 0; r < 3; r++)
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-                gM[3 * r + c] = 2.f * (Gs[3 * r] * cv.M[c] + Gs[3 * r + 1] * cv.M[3 + c] + Gs[3 * r + 2] * cv.M[6 + c]);
-        float gls[3], gR[9];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            gls[c] = (cv.Rq[c] * gM[c] + cv.Rq[3 + c] * gM[3 + c] + cv.Rq[6 + c] * gM[6 + c]) * cv.s[c];
-#pragma unroll
-            for (int r = 0; r < 3; r++) gR[3 * r + c] = gM[3 * r + c] * cv.s[c];
-        }
-        const float w = cv.qn[0], x = cv.qn[1], y = cv.qn[2], z = cv.qn[3];
-        float gq[4];
-        gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
-        gq[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.f * x * gR[8]);
-        gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.f * y * gR[8]);
-        gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
-        const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
-        const float qn[4] = {w, x, y, z};
-        const float o = 1.0f / (1.0f + expf(-logit));
-        if constexpr (FUSED_ADAM) {
-            // a8 on this row: the gradient goes straight into Adam (never stored)
-            if (!a.update_mask || a.update_mask[i]) {
-                const float bc1 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc1 : a.bc1);   // inverse bias corrections
-                const float bc2 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc2 : a.bc2);
-                // Moments are loaded a group of planes at a time, all loads of a group before
-                // its stores, so that a row waits for a few memory round trips, not 11 + 3K.
-                {
-                    float p[11], g[11], mm[11], vv[11];
-                    // element i of geometry plane k (means 0-2, log-scales 3-5, quats 6-9, logit 10)
-                    auto at = [&](float* const* grp, int k) -> float& {
-                        return k < 3 ? grp[0][k * n + i] : k < 6 ? grp[1][(k - 3) * n + i]
-                             : k < 10 ? grp[2][(k - 6) * n + i] : grp[3][i];
-                    };
-                    float* const pg[4] = {a.p_means, a.p_log_scales, a.p_quats, a.p_logits};
-#pragma unroll
-                    for (int k = 0; k < 11; k++) { mm[k] = at(a.m, k); vv[k] = at(a.v, k); }
-#pragma unroll
-                    for (int k = 0; k < 3; k++) { p[k] = mu[k]; g[k] = g_mu[k]; p[3 + k] = ls[k]; g[3 + k] = gls[k]; }
-#pragma unroll
-                    for (int k = 0; k < 4; k++) { p[6 + k] = q[k]; g[6 + k] = (gq[k] - qn[k] * dq) * cv.qinv; }
-                    p[10] = logit;
-                    g[10] = g_o * o * (1.f - o);
-#pragma unroll
-                    for (int k = 0; k < 11; k++) {
-                        const float lr = k < 3 ? a.lr[0] : k < 6 ? a.lr[1] : k < 10 ? a.lr[2] : a.lr[3];
-                        adam_update(p[k], g[k], mm[k], vv[k], lr, a.b1, a.b2, a.eps, bc1, bc2);
-                        at(pg, k) = p[k];
-                        at(a.m, k) = mm[k];
-                        at(a.v, k) = vv[k];
-                    }
-                }
-                constexpr int GS = 3 * K < 16 ? 3 * K : 16;
-                // (the group loop stays rolled: an unrolled tail of 3K planes would crowd the
-                // instruction cache of this already long kernel)
-#pragma unroll 1
-                for (int k0 = 0; k0 < 3 * K; k0 += GS) {
-                    float mm[GS], vv[GS];
-#pragma unroll
-                    for (int k = 0; k < GS; k++) {
-                        mm[k] = a.m[4][(k0 + k) * n + i];
-                        vv[k] = a.v[4][(k0 + k) * n + i];
-                    }
-#pragma unroll
-                    for (int k = 0; k < GS; k++) {
-                        float p = sh[(k0 + k) * kProjBwdThreads];
-                        adam_update(p, g_sh[(k0 + k) * kProjBwdThreads], mm[k], vv[k], k0 + k < 3 ? a.lr[4] : a.lr[5],
-                                    a.b1, a.b2, a.eps, bc1, bc2);
-                        a.p_sh[(k0 + k) * n + i] = p;
-                        a.m[4][(k0 + k) * n + i] = mm[k];
-                        a.v[4][(k0 + k) * n + i] = vv[k];
-                    }
-                }
-            }
-        } else {
-            // (explicit adds: the accumulation is never contracted into the last product of
-            // the gradient, which keeps it equal to the value the fused variant feeds to Adam)
-#pragma unroll
-            for (int k = 0; k < 3; k++) a.g_means[k * n + i] = __fadd_rn(a.g_means[k * n + i], g_mu[k]);
-#pragma unroll
-            for (int k = 0; k < 3; k++) a.g_log_scales[k * n + i] = __fadd_rn(a.g_log_scales[k * n + i], gls[k]);
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                a.g_quats[k * n + i] = __fadd_rn(a.g_quats[k * n + i], (gq[k] - qn[k] * dq) * cv.qinv);
-            a.g_logits[i] = __fadd_rn(a.g_logits[i], g_o * o * (1.f - o));
-#pragma unroll
-            for (int k = 0; k < 3 * K; k++) a.g_sh[k * n + i] = __fadd_rn(a.g_sh[k * n + i], g_sh[k * kProjBwdThreads]);
-        }
+        for (int k = 0; k < 3; k++) a.dirgrad[k * n + i] = gdir[k];
     }
     if (a.grad_twist) {
         __syncthreads();
         for (int t = threadIdx.x; t < a.n_views * 6; t += T)
             if (s_tw[t] != 0.f) atomicAdd(&a.grad_twist[t], s_tw[t]);
+    }
+}
+
+// Masked Adam on NP consecutive planes of one parameter group at row i (planes k n + i).
+template <int NP>
+__device__ __forceinline__ void adam_planes(float* P, float* M, float* V, int64_t n, int64_t i, const float* p0,
+                                            const float* g, float lr, const ProjectBwdArgs& a, float bc1, float bc2) {
+    float mm[NP], vv[NP];
+#pragma unroll
+    for (int k = 0; k < NP; k++) { mm[k] = M[k * n + i]; vv[k] = V[k * n + i]; }
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+        float p = p0[k];
+        adam_update(p, g[k], mm[k], vv[k], lr, a.b1, a.b2, a.eps, bc1, bc2);
+        P[k * n + i] = p;
+        M[k * n + i] = mm[k];
+        V[k * n + i] = vv[k];
+    }
+}
+
+template <int DEG, bool FUSED_ADAM, int T>
+__device__ __forceinline__ void project_bwd_geo_rows(const ProjectBwdArgs& a, int64_t blk) {
+    if (a.counters->status != 0) return;
+    const int64_t n = a.n;
+    const int64_t i = blk * T + threadIdx.x;
+    const bool live = i < n && a.visible[i] != 0;
+    if (!live) return;   // no block-wide synchronisation below
+    uint64_t vmask = 0;
+#pragma unroll 8
+    for (int v = 0; v < a.n_views; v++)
+        if (__ldg(a.touched + (int64_t)v * n + i) != 0u) vmask |= 1ull << v;
+    float mu[3], ls[3], q[4];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        mu[k] = __ldg(a.means + k * n + i);
+        ls[k] = __ldg(a.log_scales + k * n + i);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) q[k] = __ldg(a.quats + k * n + i);
+    const float logit = __ldg(a.logits + i);
+    float g_mu[3] = {0.f, 0.f, 0.f};
+    if (DEG > 0) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) g_mu[k] = a.dirgrad[k * n + i];
+    }
+    float gS[6] = {0, 0, 0, 0, 0, 0};   // dL/dSigma as a symmetric matrix: xx xy xz yy yz zz
+    float g_o = 0.f;
+    for (uint64_t todo = vmask; todo; todo &= todo - 1) {
+        const int v = __ffsll((long long)todo) - 1;
+        const int64_t idx = (int64_t)v * n + i;
+        const float4* geo = a.geo2d + 3 * idx;
+        const float4 q0 = geo[0], q1 = geo[1], q2 = geo[2];
+        g_o += reinterpret_cast<const float*>(a.grad2d + 3 * idx + 1)[1];
+        g_mu[0] += q0.x; g_mu[1] += q0.y; g_mu[2] += q0.z;
+        gS[0] += q0.w; gS[1] += q1.x; gS[2] += q1.y; gS[3] += q1.z; gS[4] += q1.w; gS[5] += q2.x;
+    }
+    Cov3 cv;
+    cov3_forward(q, ls, cv);
+    // Sigma = M M^T -> g_M = 2 gSigma M (symmetric gSigma); M = Rq diag(s)
+    const float Gs[9] = {gS[0], gS[1], gS[2], gS[1], gS[3], gS[4], gS[2], gS[4], gS[5]};
+    float gM[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            gM[3 * r + c] = 2.f * (Gs[3 * r] * cv.M[c] + Gs[3 * r + 1] * cv.M[3 + c] + Gs[3 * r + 2] * cv.M[6 + c]);
+    float gls[3], gR[9];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        gls[c] = (cv.Rq[c] * gM[c] + cv.Rq[3 + c] * gM[3 + c] + cv.Rq[6 + c] * gM[6 + c]) * cv.s[c];
+#pragma unroll
+        for (int r = 0; r < 3; r++) gR[3 * r + c] = gM[3 * r + c] * cv.s[c];
+    }
+    const float w = cv.qn[0], x = cv.qn[1], y = cv.qn[2], z = cv.qn[3];
+    float gq[4];
+    gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gq[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.f * x * gR[8]);
+    gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.f * y * gR[8]);
+    gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
+    const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    const float qn[4] = {w, x, y, z};
+    const float o = 1.0f / (1.0f + expf(-logit));
+    float g[11];
+#pragma unroll
+    for (int k = 0; k < 3; k++) { g[k] = g_mu[k]; g[3 + k] = gls[k]; }
+#pragma unroll
+    for (int k = 0; k < 4; k++) g[6 + k] = (gq[k] - qn[k] * dq) * cv.qinv;
+    g[10] = g_o * o * (1.f - o);
+    // element i of geometry plane k (means 0-2, log-scales 3-5, quats 6-9, logit 10)
+    auto at = [&](float* const* grp, int k) -> float& {
+        return k < 3 ? grp[0][k * n + i] : k < 6 ? grp[1][(k - 3) * n + i] : k < 10 ? grp[2][(k - 6) * n + i]
+                                                                                     : grp[3][i];
+    };
+    if constexpr (FUSED_ADAM) {
+        if (a.update_mask && !a.update_mask[i]) return;
+        const float bc1 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc1 : a.bc1);   // inverse bias corrections
+        const float bc2 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc2 : a.bc2);
+        // by parameter group (means, log-scales, quaternion, logit), all loads of a group before
+        // its stores
+        adam_planes<3>(a.p_means, a.m[0], a.v[0], n, i, mu, g, a.lr[0], a, bc1, bc2);
+        adam_planes<3>(a.p_log_scales, a.m[1], a.v[1], n, i, ls, g + 3, a.lr[1], a, bc1, bc2);
+        adam_planes<4>(a.p_quats, a.m[2], a.v[2], n, i, q, g + 6, a.lr[2], a, bc1, bc2);
+        adam_planes<1>(a.p_logits, a.m[3], a.v[3], n, i, &logit, g + 10, a.lr[3], a, bc1, bc2);
+    } else {
+        // (explicit adds: the accumulation is never contracted into the last product of the
+        // gradient, which keeps it equal to the value the fused variant feeds to Adam)
+        float* const gg[4] = {a.g_means, a.g_log_scales, a.g_quats, a.g_logits};
+#pragma unroll
+        for (int k = 0; k < 11; k++) at(gg, k) = __fadd_rn(at(gg, k), g[k]);
     }
 }
 

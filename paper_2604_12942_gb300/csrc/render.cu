@@ -809,38 +809,48 @@ __device__ __forceinline__ void render_bwd_region(const BwdArgs& a, int item, Bw
                 n_add += c0 + c1;
             }
             if (!__any_sync(0xffffffffu, contrib)) continue;
+            const float dxs[2] = {dx.x, dx.y}, dys[2] = {dy.x, dy.y}, hxs[2] = {fe.hx.x, fe.hx.y}, hys[2] = {fe.hy.x, fe.hy.y};
+            const float Gs[2] = {G.x, G.y}, a0s[2] = {a0.x, a0.y}, als[2] = {al.x, al.y};
+            // back to front, each pixel of the lane in turn: T in front of the fragment from the
+            // one behind it, weight, the colour / depth adjoint and dL/dalpha; pixels that do not
+            // add it keep T and S (scalar arithmetic: packing these pairs measured slower)
             const float4 r2 = s_rec[b][t][2];
-            // back to front: T in front of the fragment from the one behind it, weight, the
-            // colour / depth adjoint and dL/dalpha; pixels that do not add it keep T and S
-            const float2 om = __fadd2_rn(dup2(1.f), make_float2(-al.x, -al.y));
-            const float2 rom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-            const float2 Tn = __fmul2_rn(T2, rom);
-            const float2 wgt = __fmul2_rn(al, Tn);
-            const float2 gcz = __ffma2_rn(gd2, dup2(r0.z),
-                                          __ffma2_rn(g2, dup2(r2.z), __ffma2_rn(g1, dup2(r2.y), __fmul2_rn(g0, dup2(r2.x)))));
-            const float2 dLda = __ffma2_rn(Tn, gcz, __fmul2_rn(make_float2(-S2.x, -S2.y), rom));
-            const float2 Sn = __ffma2_rn(gcz, wgt, S2);
-            S2 = make_float2(c0 ? Sn.x : S2.x, c1 ? Sn.y : S2.y);
-            T2 = make_float2(c0 ? Tn.x : T2.x, c1 ? Tn.y : T2.y);
-            const float2 wc = make_float2(c0 ? wgt.x : 0.f, c1 ? wgt.y : 0.f);
-            // the 0.99 clamp stops the gradient through the exponent and the opacity
-            const float2 gl = make_float2((c0 && a0.x < amax) ? dLda.x : 0.f, (c1 && a0.y < amax) ? dLda.y : 0.f);
-            const float2 h = __fmul2_rn(gl, a0);
-            const float2 hdx = __fmul2_rn(h, dx);
-            float2 v2[10];
-            v2[0] = __fmul2_rn(h, fe.hx);
-            v2[1] = __fmul2_rn(h, fe.hy);
-            v2[2] = __fmul2_rn(hdx, dx);
-            v2[3] = __fmul2_rn(hdx, dy);
-            v2[4] = __fmul2_rn(__fmul2_rn(h, dy), dy);
-            v2[5] = __fmul2_rn(gl, G);
-            v2[6] = __fmul2_rn(gd2, wc);
-            v2[7] = __fmul2_rn(g0, wc);
-            v2[8] = __fmul2_rn(g1, wc);
-            v2[9] = __fmul2_rn(g2, wc);
+            const float4 cz = make_float4(r2.x, r2.y, r2.z, r0.z);
             float val[10];
 #pragma unroll
-            for (int q = 0; q < 10; q++) val[q] = v2[q].x + v2[q].y;
+            for (int q = 0; q < 10; q++) val[q] = 0.f;
+            const float Ts[2] = {T2.x, T2.y}, Ss[2] = {S2.x, S2.y};
+            const float g0s[2] = {g0.x, g0.y}, g1s[2] = {g1.x, g1.y}, g2s[2] = {g2.x, g2.y}, gds[2] = {gd2.x, gd2.y};
+            float Tn_[2], Sn_[2];
+            const bool cq[2] = {c0, c1};
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const float dxv = dxs[q], dyv = dys[q], Gv = Gs[q], a0v = a0s[q], alpha = als[q];
+                const bool c = cq[q];
+                const float rom = rcp_approx(1.f - alpha);
+                const float Tn = Ts[q] * rom;
+                const float wgt = alpha * Tn;
+                const float gcz = g0s[q] * cz.x + g1s[q] * cz.y + g2s[q] * cz.z + gds[q] * cz.w;
+                const float dLda = Tn * gcz - Ss[q] * rom;
+                Sn_[q] = c ? fmaf(gcz, wgt, Ss[q]) : Ss[q];
+                Tn_[q] = c ? Tn : Ts[q];
+                const float wc = c ? wgt : 0.f;
+                val[7] = fmaf(g0s[q], wc, val[7]);
+                val[8] = fmaf(g1s[q], wc, val[8]);
+                val[9] = fmaf(g2s[q], wc, val[9]);
+                val[6] = fmaf(gds[q], wc, val[6]);
+                const float gl = (c && a0v < amax) ? dLda : 0.f;   // the 0.99 clamp stops the gradient
+                const float h = gl * a0v;
+                const float hdx = h * dxv;
+                val[0] = fmaf(h, hxs[q], val[0]);
+                val[1] = fmaf(h, hys[q], val[1]);
+                val[2] = fmaf(hdx, dxv, val[2]);
+                val[3] = fmaf(hdx, dyv, val[3]);
+                val[4] = fmaf(h * dyv, dyv, val[4]);
+                val[5] = fmaf(gl, Gv, val[5]);
+            }
+            S2 = make_float2(Sn_[0], Sn_[1]);
+            T2 = make_float2(Tn_[0], Tn_[1]);
             const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
             if (cmask) {
                 float4* rec4 = a.grad2d + 3 * (size_t)s_id[b][t];
@@ -957,11 +967,13 @@ cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st
 //   -- barrier --
 //   phase 3  projection backward, entry part (grid-stride over the visible entries)
 //   -- barrier --
-//   phase 4  projection backward, row part, with the masked Adam update
+//   phase 4a projection backward, row part: SH planes (with their Adam update)
+//   -- barrier --
+//   phase 4b projection backward, row part: geometry planes (with their Adam update)
 // Every wait at a barrier is bounded: after `spin_limit` polls the block sets GS_ERR_TIMEOUT
 // in the status word and returns, and so does every block that then finds the status set, so
 // the kernel always ends.  The phases are the same device code as the stage kernels; the
-// register budget of the kernel is that of its heaviest phase (the row part).
+// register budget of the kernel is that of its heaviest phase.
 // ----------------------------------------------------------------------------------------
 struct GridSync {
     unsigned int count;   // blocks arrived at the current barrier
@@ -996,7 +1008,7 @@ struct PersistSmem {
     union {
         FwdSmem<16, 256> fwd;
         BwdWarpSmem bwd[kPersistWarps];
-        float rows[2 * 3 * (DEG + 1) * (DEG + 1) * kPersistThreads];
+        float mv[sh_mv_floats<DEG, kPersistThreads>()];
     } u;
     float tw[GS_MAX_VIEWS * 6];
     unsigned int item;
@@ -1079,10 +1091,13 @@ __global__ void __launch_bounds__(kPersistThreads, 2) step_persistent_kernel(Per
     if (!grid_barrier<DEG>(P, true, S)) return;
     project_bwd_entry_part(P.pb, blockIdx.x, gridDim.x, S.tw);   // phase 3
     if (!grid_barrier<DEG>(P, true, S)) return;
-    for (int64_t blk = blockIdx.x; blk * kPersistThreads < P.pb.n; blk += gridDim.x) {   // phase 4
-        project_bwd_rows<DEG, true, kPersistThreads>(P.pb, blk, S.tw, S.u.rows);
+    for (int64_t blk = blockIdx.x; blk * kPersistThreads < P.pb.n; blk += gridDim.x) {   // phase 4a
+        project_bwd_sh_rows<DEG, true, kPersistThreads>(P.pb, blk, S.tw, S.u.mv);
         __syncthreads();
     }
+    if (!grid_barrier<DEG>(P, true, S)) return;
+    for (int64_t blk = blockIdx.x; blk * kPersistThreads < P.pb.n; blk += gridDim.x)   // phase 4b
+        project_bwd_geo_rows<DEG, true, kPersistThreads>(P.pb, blk);
 }
 
 template <int DEG>
