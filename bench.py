@@ -34,10 +34,10 @@ METRIC = "fwd+bwd render Mpix/s and iters/s at 2M Gaussians; secs-to-PSNR learne
 # below.  `digest` is the SHA-256 of the library's CUDA sources when the figures were taken:
 # once any kernel source changes the figures no longer describe the build, and every stage
 # reports traffic null until they are captured again.
-TRAFFIC = {"digest": "a90a94112a77152f171285172b387ee2e147c3a2ac771d76867e0cbdad8eaf5f", "n": 2_000_000, "tile": 16,
+TRAFFIC = {"digest": "5387850d3d20685af70e9bb3991bfe04ae773fd690afe59fa84061889410518b", "n": 2_000_000, "tile": 16,
            "chunk": 256,
-           "bytes": {"project": 490992896, "bin_sort": 742902528, "render_fwd": 448159488,
-                     "composite_bwd": 414814464, "project_bwd_adam": 2278777088}}
+           "bytes": {"project": 490725632, "bin_sort": 742576896, "render_fwd": 447328768,
+                     "composite_bwd": 414784000, "project_bwd_adam": 2399926784}}
 
 
 def source_digest():
@@ -663,9 +663,9 @@ def kernels_per_step(L):
     # view table, project, entry count / scan / compaction, 4 depth-sort passes of 3
     # kernels, pair count / scan / offsets / emission, 3 per tile-sort pass, ranges, 3
     # tile-order kernels, loss count + composite + loss finalize, gradient-record clear +
-    # composite backward + Adam counter, projection backward entry and row (+ Adam) parts
-    # (39 with two tile-sort passes, as the ncu launch list of one step shows)
-    return 1 + 1 + 3 + 3 * 4 + 4 + 3 * tile_sort_passes(L) + 1 + 3 + 3 + 3 + 2
+    # composite backward + Adam counter, projection backward entry, SH and geometry (+ Adam)
+    # parts (40 with two tile-sort passes, as the ncu launch list of one step shows)
+    return 1 + 1 + 3 + 3 * 4 + 4 + 3 * tile_sort_passes(L) + 1 + 3 + 3 + 3 + 3
 
 
 # Algorithmic FP32 work per evaluated fragment, (pixel, Gaussian) pairs tested: 20 operations in
@@ -849,7 +849,7 @@ def main():
     roof = dict(table[dom])
     roof.update({"kernel": {"composite_bwd": "render_bwd_warp_kernel" if args.tile == 16 else "render_bwd_kernel",
                             "render_fwd": "render_fwd_kernel",
-                            "project_bwd_adam": "project_bwd_kernel (fused Adam)", "project": "project_kernel",
+                            "project_bwd_adam": "project_bwd_{entry,sh,geo}_kernel (fused Adam)", "project": "project_kernel",
                             "bin_sort": "scan/emit/radix/ranges kernels"}[dom],
                  "traffic": stage_traffic(dom, args.tile, args.chunk, args.n),
                  "peak_kind": (pk_kind + " HBM copy") if roof["bound"] == "hbm" else

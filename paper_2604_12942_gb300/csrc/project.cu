@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(kRowThreads, 5) project_bwd_sh_kernel(ProjectB
 
 template <int DEG, bool FUSED_ADAM>
 __global__ void __launch_bounds__(kRowThreads, 8) project_bwd_geo_kernel(ProjectBwdArgs a) {
-    project_bwd_geo_rows<DEG, FUSED_ADAM, kRowThreads>(a, blockIdx.x);
+    __shared__ float s_mv[FUSED_ADAM ? geo_mv_floats<kRowThreads>() : 1];
+    project_bwd_geo_rows<DEG, FUSED_ADAM, kRowThreads>(a, blockIdx.x, s_mv);
 }
 
 

@@ -337,13 +337,15 @@ __device__ __forceinline__ void project_bwd_sh_rows(const ProjectBwdArgs& a, int
     }
 }
 
-// Masked Adam on NP consecutive planes of one parameter group at row i (planes k n + i).
+// Adam on NP consecutive planes of one parameter group at row i (planes k n + i), the moments
+// read from shared memory (sm[k * stride], sv[k * stride]) and written back to global memory.
 template <int NP>
 __device__ __forceinline__ void adam_planes(float* P, float* M, float* V, int64_t n, int64_t i, const float* p0,
-                                            const float* g, float lr, const ProjectBwdArgs& a, float bc1, float bc2) {
+                                            const float* g, const float* sm, const float* sv, int stride, float lr,
+                                            const ProjectBwdArgs& a, float bc1, float bc2) {
     float mm[NP], vv[NP];
 #pragma unroll
-    for (int k = 0; k < NP; k++) { mm[k] = M[k * n + i]; vv[k] = V[k * n + i]; }
+    for (int k = 0; k < NP; k++) { mm[k] = sm[k * stride]; vv[k] = sv[k * stride]; }
 #pragma unroll
     for (int k = 0; k < NP; k++) {
         float p = p0[k];
@@ -354,13 +356,34 @@ __device__ __forceinline__ void adam_planes(float* P, float* M, float* V, int64_
     }
 }
 
+// Fused: the row's 22 Adam moments of the geometry planes are copied asynchronously into
+// s_mv [2][11][T] of shared memory when the thread starts, so they are in flight during the
+// walk over its views and the covariance chain; a thread reads only its own slots.
+template <int T>
+constexpr int geo_mv_floats() { return 2 * 11 * T; }
+
 template <int DEG, bool FUSED_ADAM, int T>
-__device__ __forceinline__ void project_bwd_geo_rows(const ProjectBwdArgs& a, int64_t blk) {
+__device__ __forceinline__ void project_bwd_geo_rows(const ProjectBwdArgs& a, int64_t blk, float* s_mv) {
     if (a.counters->status != 0) return;
     const int64_t n = a.n;
     const int64_t i = blk * T + threadIdx.x;
     const bool live = i < n && a.visible[i] != 0;
     if (!live) return;   // no block-wide synchronisation below
+    const bool upd = !FUSED_ADAM || !a.update_mask || a.update_mask[i];
+    if (FUSED_ADAM && upd) {
+        float* dst = s_mv + threadIdx.x;
+        const float* const mg[2][4] = {{a.m[0], a.m[1], a.m[2], a.m[3]}, {a.v[0], a.v[1], a.v[2], a.v[3]}};
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+#pragma unroll
+            for (int k = 0; k < 11; k++) {
+                const float* src = k < 3 ? mg[h][0] + k * n : k < 6 ? mg[h][1] + (k - 3) * n
+                                 : k < 10 ? mg[h][2] + (k - 6) * n : mg[h][3];
+                cp_async4(dst + (h * 11 + k) * T, src + i);
+            }
+        }
+        cp_async_commit();
+    }
     uint64_t vmask = 0;
 #pragma unroll 8
     for (int v = 0; v < a.n_views; v++)
@@ -428,15 +451,18 @@ __device__ __forceinline__ void project_bwd_geo_rows(const ProjectBwdArgs& a, in
                                                                                      : grp[3][i];
     };
     if constexpr (FUSED_ADAM) {
-        if (a.update_mask && !a.update_mask[i]) return;
+        if (!upd) return;
         const float bc1 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc1 : a.bc1);   // inverse bias corrections
         const float bc2 = __frcp_rn(a.step_dev ? a.step_dev->adam_bc2 : a.bc2);
-        // by parameter group (means, log-scales, quaternion, logit), all loads of a group before
-        // its stores
-        adam_planes<3>(a.p_means, a.m[0], a.v[0], n, i, mu, g, a.lr[0], a, bc1, bc2);
-        adam_planes<3>(a.p_log_scales, a.m[1], a.v[1], n, i, ls, g + 3, a.lr[1], a, bc1, bc2);
-        adam_planes<4>(a.p_quats, a.m[2], a.v[2], n, i, q, g + 6, a.lr[2], a, bc1, bc2);
-        adam_planes<1>(a.p_logits, a.m[3], a.v[3], n, i, &logit, g + 10, a.lr[3], a, bc1, bc2);
+        cp_async_wait_all();
+        const float* mv = s_mv + threadIdx.x;
+        // by parameter group (means, log-scales, quaternion, logit)
+        adam_planes<3>(a.p_means, a.m[0], a.v[0], n, i, mu, g, mv, mv + 11 * T, T, a.lr[0], a, bc1, bc2);
+        adam_planes<3>(a.p_log_scales, a.m[1], a.v[1], n, i, ls, g + 3, mv + 3 * T, mv + 14 * T, T, a.lr[1], a, bc1,
+                       bc2);
+        adam_planes<4>(a.p_quats, a.m[2], a.v[2], n, i, q, g + 6, mv + 6 * T, mv + 17 * T, T, a.lr[2], a, bc1, bc2);
+        adam_planes<1>(a.p_logits, a.m[3], a.v[3], n, i, &logit, g + 10, mv + 10 * T, mv + 21 * T, T, a.lr[3], a, bc1,
+                       bc2);
     } else {
         // (explicit adds: the accumulation is never contracted into the last product of the
         // gradient, which keeps it equal to the value the fused variant feeds to Adam)

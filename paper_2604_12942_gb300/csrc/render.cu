@@ -1009,6 +1009,7 @@ struct PersistSmem {
         FwdSmem<16, 256> fwd;
         BwdWarpSmem bwd[kPersistWarps];
         float mv[sh_mv_floats<DEG, kPersistThreads>()];
+        float gmv[geo_mv_floats<kPersistThreads>()];
     } u;
     float tw[GS_MAX_VIEWS * 6];
     unsigned int item;
@@ -1097,7 +1098,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) step_persistent_kernel(Per
     }
     if (!grid_barrier<DEG>(P, true, S)) return;
     for (int64_t blk = blockIdx.x; blk * kPersistThreads < P.pb.n; blk += gridDim.x)   // phase 4b
-        project_bwd_geo_rows<DEG, true, kPersistThreads>(P.pb, blk);
+        project_bwd_geo_rows<DEG, true, kPersistThreads>(P.pb, blk, S.u.gmv);
 }
 
 template <int DEG>
