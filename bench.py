@@ -554,7 +554,7 @@ def a9_measure(args, planes0, cams, trgb, tdep, cap, st, graph_ms):
     ps.release()
     return {"persistent_step_ms": round(ms, 4), "graph_step_ms": round(graph_ms, 4), "status_ok": ok,
             "kernels_replaced": "render_fwd, loss finalize, grad-record clear, render_bwd, Adam counter, "
-                                "projection backward entry and row (+Adam) -> 1 cooperative kernel"}
+                                "projection backward entry, SH and geometry parts (+Adam) -> 1 cooperative kernel"}
 
 
 def _se3_exp(xi):
