@@ -112,8 +112,9 @@ constexpr int kRowThreads = 128;
 template <int DEG, bool FUSED_ADAM>
 __global__ void __launch_bounds__(kRowThreads, 5) project_bwd_sh_kernel(ProjectBwdArgs a) {
     __shared__ float s_tw[GS_MAX_VIEWS * 6];
+    __shared__ float s_cam[GS_MAX_VIEWS * 12];
     __shared__ float s_mv[FUSED_ADAM ? sh_mv_floats<DEG, kRowThreads>() : 1];
-    project_bwd_sh_rows<DEG, FUSED_ADAM, kRowThreads>(a, blockIdx.x, s_tw, s_mv);
+    project_bwd_sh_rows<DEG, FUSED_ADAM, kRowThreads>(a, blockIdx.x, s_tw, s_mv, s_cam);
 }
 
 template <int DEG, bool FUSED_ADAM>

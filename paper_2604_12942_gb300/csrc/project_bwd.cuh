@@ -201,11 +201,20 @@ __device__ __forceinline__ void project_bwd_entry_part(const ProjectBwdArgs& a, 
 template <int DEG, int T>
 constexpr int sh_mv_floats() { return 2 * 2 * (DEG + 1) * (DEG + 1) * T; }
 
+// s_cam: GS_MAX_VIEWS * 12 floats of shared memory, each view's camera centre and rotation
+// (cw, R) copied there when the block starts, so the walk over a row's views reads them without
+// a trip to L2 (the streamed planes keep little of the view table in L1).
 template <int DEG, bool FUSED_ADAM, int T>
-__device__ __forceinline__ void project_bwd_sh_rows(const ProjectBwdArgs& a, int64_t blk, float* s_tw, float* s_mv) {
+__device__ __forceinline__ void project_bwd_sh_rows(const ProjectBwdArgs& a, int64_t blk, float* s_tw, float* s_mv,
+                                                    float* s_cam) {
     if (a.counters->status != 0) return;   // no gradient (and no Adam update) after a failed stage
     constexpr int K = (DEG + 1) * (DEG + 1);
     for (int t = threadIdx.x; t < a.n_views * 6; t += T) s_tw[t] = 0.f;
+    for (int t = threadIdx.x; t < a.n_views * 12; t += T) {
+        const View& V = a.views[t / 12];
+        const int f = t % 12;
+        s_cam[t] = f < 3 ? V.cw[f] : V.R[f - 3];
+    }
     __syncthreads();
     const int64_t n = a.n;
     const int64_t i = blk * T + threadIdx.x;
@@ -249,18 +258,26 @@ __device__ __forceinline__ void project_bwd_sh_rows(const ProjectBwdArgs& a, int
             shc[k] = live ? __ldg(a.sh + (int64_t)(k * 3 + c) * n + ii) : 0.f;
             gc[k] = 0.f;
         }
+        // the walk over the row's views loads the next view's dL/d colour c while it evaluates
+        // the current one
+        auto colour_grad = [&](int v) {
+            return __ldg(reinterpret_cast<const float*>(a.grad2d + 3 * ((int64_t)v * n + ii) + 2) + c);
+        };
         uint64_t todo = vmask;
-        while (__any_sync(0xffffffffu, todo != 0)) {
-            const bool act = todo != 0;
-            const int v = act ? __ffsll((long long)todo) - 1 : 0;
+        int v_nx = todo != 0 ? __ffsll((long long)todo) - 1 : -1;
+        float g_nx = v_nx >= 0 ? colour_grad(v_nx) : 0.f;
+        while (__any_sync(0xffffffffu, v_nx >= 0)) {
+            const bool act = v_nx >= 0;
+            const int v = act ? v_nx : 0;
+            const float g = g_nx;   // dL/d colour c in view v
             todo &= todo - 1;
+            v_nx = todo != 0 ? __ffsll((long long)todo) - 1 : -1;
+            if (v_nx >= 0) g_nx = colour_grad(v_nx);
             float tw[3] = {0.f, 0.f, 0.f};
             if (act) {
-                const View& V = a.views[v];
-                const int64_t idx = (int64_t)v * n + ii;
-                const float g = reinterpret_cast<const float*>(a.grad2d + 3 * idx + 2)[c];   // dL/d colour c
+                const float* cam = s_cam + v * 12;   // cw, then R row-major
                 // rgb_c = max(0, sum_k sh_kc Y_k(dir) + 0.5), dir = (mu - cw)/|mu - cw|
-                const float d[3] = {mu[0] - V.cw[0], mu[1] - V.cw[1], mu[2] - V.cw[2]};
+                const float d[3] = {mu[0] - cam[0], mu[1] - cam[1], mu[2] - cam[2]};
                 const float rn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
                 const float dir[3] = {d[0] * rn, d[1] * rn, d[2] * rn};
                 float Y[16];
@@ -279,7 +296,7 @@ __device__ __forceinline__ void project_bwd_sh_rows(const ProjectBwdArgs& a, int
                         for (int k = 0; k < 3; k++) gd[k] = g * (gd[k] - dir[k] * dd) * rn;
 #pragma unroll
                         for (int k = 0; k < 3; k++) gdir[k] += gd[k];
-                        const float* W = V.R;
+                        const float* W = cam + 3;
 #pragma unroll
                         for (int r = 0; r < 3; r++) tw[r] = W[3 * r] * gd[0] + W[3 * r + 1] * gd[1] + W[3 * r + 2] * gd[2];
                     }

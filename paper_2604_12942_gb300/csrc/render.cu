@@ -1012,6 +1012,7 @@ struct PersistSmem {
         float gmv[geo_mv_floats<kPersistThreads>()];
     } u;
     float tw[GS_MAX_VIEWS * 6];
+    float cam[GS_MAX_VIEWS * 12];
     unsigned int item;
     int ok;
 };
@@ -1093,7 +1094,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) step_persistent_kernel(Per
     project_bwd_entry_part(P.pb, blockIdx.x, gridDim.x, S.tw);   // phase 3
     if (!grid_barrier<DEG>(P, true, S)) return;
     for (int64_t blk = blockIdx.x; blk * kPersistThreads < P.pb.n; blk += gridDim.x) {   // phase 4a
-        project_bwd_sh_rows<DEG, true, kPersistThreads>(P.pb, blk, S.tw, S.u.mv);
+        project_bwd_sh_rows<DEG, true, kPersistThreads>(P.pb, blk, S.tw, S.u.mv, S.cam);
         __syncthreads();
     }
     if (!grid_barrier<DEG>(P, true, S)) return;
