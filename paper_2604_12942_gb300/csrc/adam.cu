@@ -12,17 +12,6 @@ __device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v,
     if (vis) g = 0.f;
 }
 
-// Advances the device-side Adam step counter and stores the bias corrections of that step
-// (one thread; lets a captured graph run many steps without host-side parameters).
-__global__ void adam_step_counter_kernel(Counters* c, float b1, float b2) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) adam_step_advance(c, b1, b2);
-}
-
-cudaError_t launch_adam_step_counter(Counters* c, float b1, float b2, cudaStream_t st) {
-    adam_step_counter_kernel<<<1, 32, 0, st>>>(c, b1, b2);
-    return cudaGetLastError();
-}
-
 // grid: (blocks over n in steps of 4*256, total planes).  Plane k of the packed layout
 // (means 3, log-scales 3, quats 4, opacity 1, SH 3K) maps to group pointer and row.
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {

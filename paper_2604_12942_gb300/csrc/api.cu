@@ -462,8 +462,9 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
 }
 
 static cudaError_t run_composite_bwd(const gs_render_opts* opts, const gs_ws_layout* L, void* ws, const float* dl_drgb,
-                                     const float* dl_ddepth, cudaStream_t st) {
-    return launch_render_bwd(bwd_args(opts, L, ws, dl_drgb, dl_ddepth), L->total_tiles, st);
+                                     const float* dl_ddepth, cudaStream_t st, Counters* adam_ctr = nullptr,
+                                     float b1 = 0.f, float b2 = 0.f) {
+    return launch_render_bwd(bwd_args(opts, L, ws, dl_drgb, dl_ddepth), L->total_tiles, st, adam_ctr, b1, b2);
 }
 
 // Adam settings of the fused projection backward (a7 + a8).
@@ -664,8 +665,8 @@ static gs_status run_step_tail(gs_gaussians* params, gs_gaussians* grads, gs_gau
     const float* dl_dd = io->target_depth ? io->dl_ddepth : nullptr;
     if (io->optimize) {
         Counters* c = at<Counters>(ws, L->counters);
-        GS_CUDA(run_composite_bwd(opts, L, ws, io->dl_drgb, dl_dd, st));
-        GS_CUDA(launch_adam_step_counter(c, io->b1, io->b2, st));
+        // (the record clear before the compositing also advances the Adam step counter)
+        GS_CUDA(run_composite_bwd(opts, L, ws, io->dl_drgb, dl_dd, st, c, io->b1, io->b2));
         FusedAdam fa{params, m, v, io->update_mask, io->lr, io->b1, io->b2, io->eps, 0, c};
         GS_CUDA(run_project_bwd(params, opts, L, ws, nullptr, io->grad_twist, st, &fa));
     } else {

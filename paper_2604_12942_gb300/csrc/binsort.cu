@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
     __shared__ uint16_t s_wx[kEmitChunk + 1], s_tx[kEmitChunk + 1];
     __shared__ __align__(16) uint16_t s_own[kEmitChunk];   // slot -> local entry index
     __shared__ uint32_t s_wmax[kEmitThreads / 32];
+    __shared__ uint16_t s_view_tx[GS_MAX_VIEWS];   // tiles per row of each view
     if (a.counters->status != 0) return;
+    for (int v = threadIdx.x; v < a.n_views; v += blockDim.x) s_view_tx[v] = (uint16_t)a.views[v].tiles_x;
     const uint64_t P = a.counters->n_pairs;
     const int64_t E = (int64_t)a.counters->n_entries;
     const uint64_t n_chunks = (P + kEmitChunk - 1) / kEmitChunk;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
             s_t0[j] = r.x;
             s_id[j] = idx;
             s_wx[j] = (uint16_t)(r.y & 0xFFFFu);
-            s_tx[j] = (uint16_t)a.views[idx / (uint32_t)a.n].tiles_x;
+            s_tx[j] = s_view_tx[idx / (uint32_t)a.n];
             // the entry's first pair slot in this chunk (entry 0 starts at or before p0)
             if (j > 0 && off < p1) s_own[off - p0] = (uint16_t)j;
         }

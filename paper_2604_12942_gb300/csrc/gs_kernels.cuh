@@ -234,9 +234,11 @@ cudaError_t launch_render_fwd(const FwdArgs& a, int total_tiles, cudaStream_t st
 cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
                                  float lambda_depth, float lambda_ssim, int has_depth, float* loss_out,
                                  cudaStream_t st);
-cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st);
+// Clears the gradient records of the visible entries (and, with adam_ctr, advances the fused
+// step's Adam counter with adam_step_advance), then the backward compositing.
+cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st, Counters* adam_ctr = nullptr,
+                              float b1 = 0.f, float b2 = 0.f);
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t st);
-cudaError_t launch_adam_step_counter(Counters* c, float b1, float b2, cudaStream_t st);
 // The persistent form of forward -> backward -> projection backward + Adam (render.cu); the
 // grid state lives 128 bytes into the counters' 256-byte slot of the workspace.
 cudaError_t launch_step_persistent(const FwdArgs& fwd, const BwdArgs& bwd, const ProjectBwdArgs& pb, int deg,

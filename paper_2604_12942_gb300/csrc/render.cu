@@ -28,11 +28,23 @@ __global__ void __launch_bounds__(256) loss_count_kernel(const View* views, cons
     const View& V = views[v];
     const int64_t P = (int64_t)V.W * V.H;
     uint32_t cm = 0, cd = 0;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = V.pix_off + p;
-        const bool in = mask ? mask[g] != 0 : true;
-        cm += in;
-        cd += (in && tgt_depth && tgt_depth[g] > 0.f);
+    // four independent pixels per iteration, so that their loads are in flight together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < P; p0 += 4 * stride) {
+        bool in[4];
+        float d[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t p = p0 + u * stride;
+            const int64_t g = V.pix_off + p;
+            in[u] = p < P && (mask ? mask[g] != 0 : true);
+            d[u] = (p < P && tgt_depth) ? tgt_depth[g] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            cm += in[u];
+            cd += (in[u] && d[u] > 0.f);
+        }
     }
     cm = warp_sum(cm);
     cd = warp_sum(cd);
@@ -934,16 +946,23 @@ cudaError_t launch_render_fwd(const FwdArgs& a, int total_tiles, cudaStream_t st
 
 // Zeroes the screen-space gradient records of the visible entries -- the only records the
 // backward compositing adds to and the projection backward reads.
-__global__ void __launch_bounds__(256) clear_grad2d_kernel(BwdArgs a) {
+// Also advances the Adam step counter of the fused step (adam_ctr non-null), one thread.
+__global__ void __launch_bounds__(256) clear_grad2d_kernel(BwdArgs a, Counters* adam_ctr, float b1, float b2) {
     if (a.counters->status != 0) return;
+    if (adam_ctr && blockIdx.x == 0 && threadIdx.x == 0) adam_step_advance(adam_ctr, b1, b2);
     const int64_t E = (int64_t)a.counters->n_entries;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * E; e += (int64_t)gridDim.x * blockDim.x)
-        a.grad2d[3 * (size_t)a.entries[e / 3] + (size_t)(e % 3)] = z;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        float4* rec = a.grad2d + 3 * (size_t)a.entries[e];
+        rec[0] = z;
+        rec[1] = z;
+        rec[2] = z;
+    }
 }
 
-cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st) {
-    clear_grad2d_kernel<<<sort_grid() * 4, 256, 0, st>>>(a);
+cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st, Counters* adam_ctr, float b1,
+                              float b2) {
+    clear_grad2d_kernel<<<sort_grid() * 4, 256, 0, st>>>(a, adam_ctr, b1, b2);
     if (total_tiles <= 0) return cudaGetLastError();
     // 16 x 16 tiles: one independent warp per 8 x 8 region (8 x 8 tiles are one warp already)
     if (a.op.tile == 16) {
@@ -1064,9 +1083,13 @@ __global__ void __launch_bounds__(kPersistThreads, 2) step_persistent_kernel(Per
     {   // phase 0
         const int64_t E = (int64_t)P.counters->n_entries;
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t e = (int64_t)blockIdx.x * kPersistThreads + threadIdx.x; e < 3 * E;
-             e += (int64_t)gridDim.x * kPersistThreads)
-            P.bwd.grad2d[3 * (size_t)P.bwd.entries[e / 3] + (size_t)(e % 3)] = z;
+        for (int64_t e = (int64_t)blockIdx.x * kPersistThreads + threadIdx.x; e < E;
+             e += (int64_t)gridDim.x * kPersistThreads) {
+            float4* rec = P.bwd.grad2d + 3 * (size_t)P.bwd.entries[e];
+            rec[0] = z;
+            rec[1] = z;
+            rec[2] = z;
+        }
     }
     for (;;) {   // phase 1
         if (threadIdx.x == 0) S.item = atomicAdd(&P.sync->q_fwd, 1u);
