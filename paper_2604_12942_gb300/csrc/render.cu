@@ -103,44 +103,33 @@ struct TileMap {
     static constexpr int RH = 4 * PPT;              // warp region height
 };
 
-// Least value over the rectangle [x0, x1] x [y0, y1] of Q(d) = A dx^2 + 2 B dx dy + C dy^2
-// (positive definite): 0 if the rectangle holds the origin, else the least of its four edge
-// minima, each a 1-D quadratic minimised at its stationary point clamped to the edge.
-__device__ __forceinline__ float rect_min_quadratic(float A, float B, float C, float iA, float iC, float x0, float x1,
-                                                    float y0, float y1) {
-    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return 0.f;
-    float m = INFINITY;
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-        const float X = s ? x1 : x0;
-        const float dy = fminf(fmaxf(-B * X * iC, y0), y1);
-        m = fminf(m, (A * X + 2.f * B * dy) * X + C * dy * dy);
-        const float Y = s ? y1 : y0;
-        const float dx = fminf(fmaxf(-B * Y * iA, x0), x1);
-        m = fminf(m, (C * Y + 2.f * B * dx) * Y + A * dx * dx);
-    }
-    return m;
-}
-
 // Bit r of the result is set when warp region r of the tile whose top-left pixel is (X0, Y0)
 // may hold a fragment of the record with alpha >= alpha_min.  Regions are first tested
 // against the record's alpha box, then exactly: alpha = o 2^e >= alpha_min needs
-// Q = -e <= thr = log2(o / alpha_min), so a region is dropped when the least Q over the
-// rectangle spanned by its pixel centres exceeds thr by more than a margin that covers the
-// FP32 rounding of e in the compositing loops (well above 10 ulp of the largest term).
-// Computed once per staged record; warps then test one bit per fragment.
+// Q = -e <= thr = log2(o / alpha_min) with Q(d) = A dx^2 + 2 B dx dy + C dy^2 (positive
+// definite), so a region is dropped when the least Q over the rectangle spanned by its pixel
+// centres exceeds thr by more than a margin that covers the FP32 rounding of e in the
+// compositing loops (well above 10 ulp of the largest term).  The least Q is 0 when the
+// rectangle holds the mean; otherwise it lies on an edge that faces the mean (at the
+// minimiser the gradient of Q points into the rectangle, so the mean is on the outer side of
+// that edge's line): at most one vertical edge (x = x0 if x0 > 0, x = x1 if x1 < 0) and one
+// horizontal edge, each minimised at its stationary point clamped to the edge.  The
+// stationary points and the margin's terms depend on the column or the row only and are
+// computed once per column and row.  Computed once per staged record; warps then test one
+// bit per fragment.
 template <int TILE, int PPT>
 __device__ __forceinline__ uint32_t region_mask(float u, float v, float rx, float ry, float a, float b, float c,
                                                 float o, float alpha_min, float X0, float Y0) {
     using TM = TileMap<TILE, PPT>;
+    constexpr int NC = TM::WX, NR = TILE / TM::RH;
     uint32_t cols = 0, rows = 0;
 #pragma unroll
-    for (int cc = 0; cc < TM::WX; cc++) {
+    for (int cc = 0; cc < NC; cc++) {
         const float x0 = X0 + 8.f * cc;
         if (u - rx <= x0 + 7.5f && u + rx >= x0 + 0.5f) cols |= 1u << cc;
     }
 #pragma unroll
-    for (int r = 0; r < TILE / TM::RH; r++) {
+    for (int r = 0; r < NR; r++) {
         const float y0 = Y0 + (float)(TM::RH * r);
         if (v - ry <= y0 + ((float)TM::RH - 0.5f) && v + ry >= y0 + 0.5f) rows |= 1u << r;
     }
@@ -148,22 +137,59 @@ __device__ __forceinline__ uint32_t region_mask(float u, float v, float rx, floa
     const float A = -a, B = -b, C = -c;   // e = -(A dx^2 + 2 B dx dy + C dy^2)
     const float iA = 1.f / A, iC = 1.f / C;
     const float thr = __log2f(o / alpha_min);
+    const float B2 = 2.f * B, aB2 = 2.f * fabsf(B);
+    // per column: its edges, the facing vertical edge X (if any) with A X and the stationary
+    // dy of Q on x = X, and A Xm^2 for the margin (Xm the farther edge)
+    float cx0[NC], cx1[NC], cX[NC], cAX[NC], cDy[NC], cXm[NC], cM[NC];
+    bool cF[NC];
+#pragma unroll
+    for (int cc = 0; cc < NC; cc++) {
+        const float x0 = X0 + 8.f * cc + 0.5f - u, x1 = x0 + 7.f;
+        cx0[cc] = x0;
+        cx1[cc] = x1;
+        cF[cc] = x0 > 0.f || x1 < 0.f;
+        const float X = x0 > 0.f ? x0 : x1;
+        cX[cc] = X;
+        cAX[cc] = A * X;
+        cDy[cc] = -B * X * iC;
+        const float Xm = fmaxf(fabsf(x0), fabsf(x1));
+        cXm[cc] = Xm;
+        cM[cc] = A * Xm * Xm;
+    }
     uint32_t m = 0;
 #pragma unroll
-    for (int r = 0; r < TILE / TM::RH; r++) {
-        if (!(rows & (1u << r))) continue;
+    for (int r = 0; r < NR; r++) {
         const float y0 = Y0 + (float)(TM::RH * r) + 0.5f - v, y1 = y0 + (float)(TM::RH - 1);
+        const bool rF = y0 > 0.f || y1 < 0.f;
+        const float Y = y0 > 0.f ? y0 : y1;
+        const float CY = C * Y, dxs = -B * Y * iA;
+        const float Ym = fmaxf(fabsf(y0), fabsf(y1));
+        const float rM = C * Ym * Ym;
 #pragma unroll
-        for (int cc = 0; cc < TM::WX; cc++) {
-            if (!(cols & (1u << cc))) continue;
-            const float x0 = X0 + 8.f * cc + 0.5f - u, x1 = x0 + 7.f;
-            const float q = rect_min_quadratic(A, B, C, iA, iC, x0, x1, y0, y1);
-            const float X = fmaxf(fabsf(x0), fabsf(x1)), Y = fmaxf(fabsf(y0), fabsf(y1));
-            const float margin = 1e-5f * (A * X * X + 2.f * fabsf(B) * X * Y + C * Y * Y) + 1e-3f;
-            if (!(q > thr + margin)) m |= 1u << (r * TM::WX + cc);
+        for (int cc = 0; cc < NC; cc++) {
+            float q = 0.f;   // the rectangle holds the mean
+            if (cF[cc] || rF) {
+                float qv = INFINITY, qh = INFINITY;
+                if (cF[cc]) {
+                    const float dy = fminf(fmaxf(cDy[cc], y0), y1);
+                    qv = (cAX[cc] + B2 * dy) * cX[cc] + C * dy * dy;
+                }
+                if (rF) {
+                    const float dx = fminf(fmaxf(dxs, cx0[cc]), cx1[cc]);
+                    qh = (CY + B2 * dx) * Y + A * dx * dx;
+                }
+                q = fminf(qv, qh);
+            }
+            const float margin = 1e-5f * (cM[cc] + aB2 * cXm[cc] * Ym + rM) + 1e-3f;
+            if (!(q > thr + margin)) m |= 1u << (r * NC + cc);
         }
     }
-    return m;
+    // regions outside the alpha box hold no fragment with alpha >= alpha_min
+    uint32_t box = 0;
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+        if (rows & (1u << r)) box |= cols << (r * NC);
+    return m & box;
 }
 
 // Backward warp regions (8 x 8) from the forward ones (8 x 4): region (c, r) is the union of
