@@ -662,10 +662,10 @@ def kernels_per_step(L):
     """Kernels one gs_step launches (the graph replays exactly these)."""
     # view table, project, entry count / scan / compaction, 4 depth-sort passes of 3
     # kernels, pair count / scan / offsets / emission, 3 per tile-sort pass, ranges, 3
-    # tile-order kernels, loss count + composite + loss finalize, gradient-record clear (with
-    # the Adam counter) + composite backward, projection backward entry, SH and geometry
-    # (+ Adam) parts (39 with two tile-sort passes, as the ncu launch list of one step shows)
-    return 1 + 1 + 3 + 3 * 4 + 4 + 3 * tile_sort_passes(L) + 1 + 3 + 3 + 2 + 3
+    # tile-order kernels, loss count + composite, gradient-record clear (with the loss terms
+    # and the Adam counter) + composite backward, projection backward entry, SH and geometry
+    # (+ Adam) parts (38 with two tile-sort passes, as the ncu launch list of one step shows)
+    return 1 + 1 + 3 + 3 * 4 + 4 + 3 * tile_sort_passes(L) + 1 + 3 + 2 + 2 + 3
 
 
 # Algorithmic FP32 work per evaluated fragment, (pixel, Gaussian) pairs tested: 20 operations in

@@ -429,7 +429,7 @@ static BwdArgs bwd_args(const gs_render_opts* opts, const gs_ws_layout* L, void*
 static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, const Geometry& G, void* ws,
                            float* out_rgb, float* out_depth, float* out_T, const float* target_rgb,
                            const float* target_depth, const uint8_t* mask, float* dl_drgb, float* dl_ddepth,
-                           float* loss_out, cudaStream_t st) {
+                           float* loss_out, cudaStream_t st, LossFinal* defer = nullptr) {
     double* sums = at<double>(ws, L->loss_acc);
     uint32_t* counts = reinterpret_cast<uint32_t*>(sums + 3 * GS_MAX_VIEWS);
     const bool separate = target_rgb && (opts->lambda_ssim > 0.f || opts->mask_erode >= 0);
@@ -445,6 +445,11 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
                                fused ? target_depth : nullptr, fused ? mask : nullptr, fused ? dl_drgb : nullptr,
                                fused ? dl_ddepth : nullptr);
     if ((e = launch_render_fwd(a, L->total_tiles, st)) != cudaSuccess) return e;
+    if (fused && defer) {   // the caller's next kernel writes the loss terms
+        *defer = LossFinal{sums, counts, L->n_views, opts->lambda_rgb, opts->lambda_depth, target_depth != nullptr,
+                           loss_out};
+        return cudaSuccess;
+    }
     if (fused)
         return launch_loss_finalize(sums, counts, L->n_views, opts->lambda_rgb, opts->lambda_depth, 0.f,
                                     target_depth != nullptr, loss_out, st);
@@ -463,8 +468,8 @@ static cudaError_t run_fwd(const gs_render_opts* opts, const gs_ws_layout* L, co
 
 static cudaError_t run_composite_bwd(const gs_render_opts* opts, const gs_ws_layout* L, void* ws, const float* dl_drgb,
                                      const float* dl_ddepth, cudaStream_t st, Counters* adam_ctr = nullptr,
-                                     float b1 = 0.f, float b2 = 0.f) {
-    return launch_render_bwd(bwd_args(opts, L, ws, dl_drgb, dl_ddepth), L->total_tiles, st, adam_ctr, b1, b2);
+                                     float b1 = 0.f, float b2 = 0.f, const LossFinal& lf = LossFinal()) {
+    return launch_render_bwd(bwd_args(opts, L, ws, dl_drgb, dl_ddepth), L->total_tiles, st, adam_ctr, b1, b2, lf);
 }
 
 // Adam settings of the fused projection backward (a7 + a8).
@@ -659,14 +664,18 @@ static gs_status run_step_tail(gs_gaussians* params, gs_gaussians* grads, gs_gau
                                        nullptr));
         return GS_OK;
     }
+    // with the update, the fused loss's terms are written by the record clear that starts the
+    // backward (one kernel fewer)
+    LossFinal lf;
     GS_CUDA(run_fwd(opts, L, G, ws, io->out_rgb, io->out_depth, nullptr, io->target_rgb, io->target_depth, io->mask,
-                    io->dl_drgb, io->target_depth ? io->dl_ddepth : nullptr, io->loss_out, st));
+                    io->dl_drgb, io->target_depth ? io->dl_ddepth : nullptr, io->loss_out, st,
+                    io->optimize ? &lf : nullptr));
     if (io->grad_twist) GS_CUDA(cudaMemsetAsync(io->grad_twist, 0, sizeof(float) * 6 * L->n_views, st));
     const float* dl_dd = io->target_depth ? io->dl_ddepth : nullptr;
     if (io->optimize) {
         Counters* c = at<Counters>(ws, L->counters);
         // (the record clear before the compositing also advances the Adam step counter)
-        GS_CUDA(run_composite_bwd(opts, L, ws, io->dl_drgb, dl_dd, st, c, io->b1, io->b2));
+        GS_CUDA(run_composite_bwd(opts, L, ws, io->dl_drgb, dl_dd, st, c, io->b1, io->b2, lf));
         FusedAdam fa{params, m, v, io->update_mask, io->lr, io->b1, io->b2, io->eps, 0, c};
         GS_CUDA(run_project_bwd(params, opts, L, ws, nullptr, io->grad_twist, st, &fa));
     } else {

@@ -234,10 +234,20 @@ cudaError_t launch_render_fwd(const FwdArgs& a, int total_tiles, cudaStream_t st
 cudaError_t launch_loss_finalize(const double* sums, const uint32_t* counts, int n_views, float lambda_rgb,
                                  float lambda_depth, float lambda_ssim, int has_depth, float* loss_out,
                                  cudaStream_t st);
+// The loss terms of the fused L1 loss (loss_finalize_one's arguments); loss_out null: none.
+struct LossFinal {
+    const double* sums = nullptr;
+    const uint32_t* counts = nullptr;
+    int n_views = 0;
+    float lambda_rgb = 0.f, lambda_depth = 0.f;
+    int has_depth = 0;
+    float* loss_out = nullptr;
+};
 // Clears the gradient records of the visible entries (and, with adam_ctr, advances the fused
-// step's Adam counter with adam_step_advance), then the backward compositing.
+// step's Adam counter with adam_step_advance; with lf.loss_out, writes the loss terms as
+// launch_loss_finalize does), then the backward compositing.
 cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st, Counters* adam_ctr = nullptr,
-                              float b1 = 0.f, float b2 = 0.f);
+                              float b1 = 0.f, float b2 = 0.f, const LossFinal& lf = LossFinal());
 cudaError_t launch_adam(const AdamArgs& a, cudaStream_t st);
 // The persistent form of forward -> backward -> projection backward + Adam (render.cu); the
 // grid state lives 128 bytes into the counters' 256-byte slot of the workspace.

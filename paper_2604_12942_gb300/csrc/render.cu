@@ -46,11 +46,25 @@ __global__ void __launch_bounds__(256) loss_count_kernel(const View* views, cons
             cd += (in[u] && d[u] > 0.f);
         }
     }
+    // block sums first: the counters of a view take one atomic per block, not one per warp
+    // (same-address atomics are applied one after another)
+    __shared__ uint32_t s_c[2][8];
     cm = warp_sum(cm);
     cd = warp_sum(cd);
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        if (cm) atomicAdd(&counts[2 * v], cm);
-        if (cd) atomicAdd(&counts[2 * v + 1], cd);
+        s_c[0][w] = cm;
+        s_c[1][w] = cd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tm = 0, td = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+            tm += s_c[0][k];
+            td += s_c[1][k];
+        }
+        if (tm) atomicAdd(&counts[2 * v], tm);
+        if (td) atomicAdd(&counts[2 * v + 1], td);
     }
 }
 
@@ -972,23 +986,34 @@ cudaError_t launch_render_fwd(const FwdArgs& a, int total_tiles, cudaStream_t st
 
 // Zeroes the screen-space gradient records of the visible entries -- the only records the
 // backward compositing adds to and the projection backward reads.
-// Also advances the Adam step counter of the fused step (adam_ctr non-null), one thread.
-__global__ void __launch_bounds__(256) clear_grad2d_kernel(BwdArgs a, Counters* adam_ctr, float b1, float b2) {
+// Also, one thread each: the fused step's loss terms (lf.loss_out non-null; whatever the status,
+// as the separate loss kernel) and its Adam step counter (adam_ctr non-null).
+__global__ void __launch_bounds__(256) clear_grad2d_kernel(BwdArgs a, Counters* adam_ctr, float b1, float b2,
+                                                           LossFinal lf) {
+    if (lf.loss_out && blockIdx.x == 0 && threadIdx.x == 0)
+        loss_finalize_one(lf.sums, lf.counts, lf.n_views, lf.lambda_rgb, lf.lambda_depth, 0.f, lf.has_depth,
+                          lf.loss_out);
     if (a.counters->status != 0) return;
     if (adam_ctr && blockIdx.x == 0 && threadIdx.x == 0) adam_step_advance(adam_ctr, b1, b2);
     const int64_t E = (int64_t)a.counters->n_entries;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-        float4* rec = a.grad2d + 3 * (size_t)a.entries[e];
-        rec[0] = z;
-        rec[1] = z;
-        rec[2] = z;
+    // three threads per entry, one 16-byte word each (a warp's stores then cover about 11 whole
+    // records); 32-bit index arithmetic while 3 E fits
+    if (3 * E <= (int64_t)0xFFFFFFFFu) {
+        const uint32_t n3 = (uint32_t)(3 * E);
+        for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += gridDim.x * blockDim.x) {
+            const uint32_t ent = e / 3u;
+            a.grad2d[3 * (size_t)a.entries[ent] + (e - 3u * ent)] = z;
+        }
+    } else {
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * E; e += (int64_t)gridDim.x * blockDim.x)
+            a.grad2d[3 * (size_t)a.entries[e / 3] + (size_t)(e % 3)] = z;
     }
 }
 
 cudaError_t launch_render_bwd(const BwdArgs& a, int total_tiles, cudaStream_t st, Counters* adam_ctr, float b1,
-                              float b2) {
-    clear_grad2d_kernel<<<sort_grid() * 4, 256, 0, st>>>(a, adam_ctr, b1, b2);
+                              float b2, const LossFinal& lf) {
+    clear_grad2d_kernel<<<sort_grid() * 4, 256, 0, st>>>(a, adam_ctr, b1, b2, lf);
     if (total_tiles <= 0) return cudaGetLastError();
     // 16 x 16 tiles: one independent warp per 8 x 8 region (8 x 8 tiles are one warp already)
     if (a.op.tile == 16) {
