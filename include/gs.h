@@ -151,7 +151,9 @@ typedef struct {
     size_t grad2d;       /* [n_views*n] records of 12 floats (screen-space gradient sums of
                             gs_composite_bwd); only the records of visible entries are defined */
     size_t geo2d;        /* [n_views*n] records of 12 floats: per visible entry, the gradients
-                            w.r.t. the mean and the world covariance (projection backward) */
+                            w.r.t. the mean and the world covariance (projection backward);
+                            before that, the binning's scratch (the depth-sorted entries' tile
+                            rectangles and indices) */
     size_t dirgrad;      /* float [3][n]: per visible row, the gradient of the mean through the SH
                             view directions (projection backward: SH part -> geometry part) */
     size_t visible;      /* uint8 [n]: 1 if the Gaussian covers a tile of any view */

@@ -281,6 +281,7 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     b.vis_bits = at<uint32_t>(ws, L->ekeys1);       // free until the entry sort
     b.poff = at<uint32_t>(ws, L->ekeys1);           // free once the entries are sorted
     b.chunk_first = at<uint32_t>(ws, L->emit_tmp);
+    b.srt = at<uint32_t>(ws, L->geo2d);              // free until the projection backward
     b.counters = cnt;
     cudaError_t e = launch_entries(b, st);
     if (e != cudaSuccess) return e;

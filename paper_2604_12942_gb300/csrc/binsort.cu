@@ -176,16 +176,26 @@ cudaError_t launch_entries(const BinArgs& a, cudaStream_t st) {
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t rect_count(uint2 r) { return (r.y & 0xFFFFu) * (r.y >> 16); }
 
+// Also writes, in depth order, each entry's tile rectangle and index (srt), which the offsets
+// and the emission then read without the gather through the sorted compact indices.
 __global__ void __launch_bounds__(kScanThreads) pair_count_kernel(BinArgs a) {
     __shared__ uint32_t s[33];
     const int64_t E = (int64_t)a.counters->n_entries;
+    const int64_t VN = (int64_t)a.n_views * a.n;
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     uint32_t sum = 0;
     if (base < E) {
 #pragma unroll
         for (int k = 0; k < kScanItems; k++) {
             const int64_t j = base + (int64_t)k * kScanThreads + threadIdx.x;
-            if (j < E) sum += rect_count(a.erect[a.sorted_evals[j]]);
+            if (j < E) {
+                const uint32_t c = a.sorted_evals[j];
+                const uint2 r = a.erect[c];
+                a.srt[j] = r.x;
+                a.srt[VN + j] = r.y;
+                a.srt[2 * VN + j] = a.entries[c];
+                sum += rect_count(r);
+            }
         }
     }
     sum = warp_sum(sum);
@@ -209,7 +219,7 @@ __global__ void __launch_bounds__(kScanThreads) pair_offsets_kernel(BinArgs a) {
     uint32_t t[kScanItems], sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
-        t[k] = base + k < E ? rect_count(a.erect[a.sorted_evals[base + k]]) : 0u;
+        t[k] = base + k < E ? rect_count(make_uint2(0u, a.srt[(int64_t)a.n_views * a.n + base + k])) : 0u;
         sum += t[k];
     }
     uint32_t tot;
@@ -252,11 +262,11 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
         const int ne = (int)(e1 - e0 + 1);   // <= kEmitChunk + 1: every entry has >= 1 pair
         for (int i = threadIdx.x; i < kEmitChunk; i += blockDim.x) s_own[i] = 0;
         __syncthreads();
+        const int64_t VN = (int64_t)a.n_views * a.n;
         for (int j = threadIdx.x; j < ne; j += blockDim.x) {
             const int64_t e = e0 + j;
-            const uint32_t c = a.sorted_evals[e];
-            const uint32_t idx = a.entries[c];
-            const uint2 r = a.erect[c];
+            const uint32_t idx = a.srt[2 * VN + e];
+            const uint2 r = make_uint2(a.srt[e], a.srt[VN + e]);
             const uint32_t off = a.poff[e];
             s_off[j] = off;
             s_t0[j] = r.x;

@@ -63,6 +63,8 @@ struct BinArgs {
     uint32_t* pvals;              //   and the entry's view * n + Gaussian index
     uint32_t* poff;               // [n_views * n] pair offset of each depth-sorted entry
     uint32_t* chunk_first;        // [max_pairs / kEmitChunk + 2] entry of each chunk's first pair
+    uint32_t* srt;                // [3][n_views * n] the depth-sorted entries' first tile ids,
+                                  //   tile spans (wx | wy << 16) and view * n + index (scratch)
     Counters* counters;
 };
 
