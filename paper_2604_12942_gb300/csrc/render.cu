@@ -841,40 +841,48 @@ __device__ __forceinline__ void render_bwd_region(const BwdArgs& a, int item, Bw
         cp_async_wait_prior();   // this window's copies (all lanes') have landed after the syncwarp
         __syncwarp();
         if constexpr (COUNT) n_visit += cnt;
-        for (int t = 0; t < cnt; t++) {
+        // the alphas of the lane's two pixels of record t, as one packed pair: a record that no
+        // pixel of the warp adds (all below alpha_min or past their pixels' last fragment)
+        // changes nothing and is skipped whole
+        struct Alphas {
+            float2 dx, dy, hx, hy, G, a0, al;
+            bool c0, c1;
+        };
+        auto alphas = [&](int t, Alphas& P) {
             const uint32_t j = (uint32_t)s_pos[b][t];
             const float4 r0 = s_rec[b][t][0], r1 = s_rec[b][t][1];
-            // the alphas of the lane's two pixels first, as one packed pair: a record that no
-            // pixel of the warp adds (all below alpha_min or past their pixels' last fragment)
-            // changes nothing and is skipped whole
-            const float2 dx = __fadd2_rn(px2, dup2(-r0.x));
-            const float2 dy = __fadd2_rn(py2, dup2(-r0.y));
-            const FragE2 fe = frag_exponent2(dx, dy, dup2(r1.x), dup2(r1.y), dup2(r1.z));
-            const float2 G = make_float2(ex2_approx(fe.e.x), ex2_approx(fe.e.y));
-            const float2 a0 = __fmul2_rn(dup2(r0.w), G);
-            const float2 al = make_float2(fminf(amax, a0.x), fminf(amax, a0.y));
-            const bool c0 = j < last[0] && !(al.x < amin);
-            const bool c1 = j < last[1] && !(al.y < amin);
-            const bool contrib = c0 || c1;
+            P.dx = __fadd2_rn(px2, dup2(-r0.x));
+            P.dy = __fadd2_rn(py2, dup2(-r0.y));
+            const FragE2 fe = frag_exponent2(P.dx, P.dy, dup2(r1.x), dup2(r1.y), dup2(r1.z));
+            P.hx = fe.hx;
+            P.hy = fe.hy;
+            P.G = make_float2(ex2_approx(fe.e.x), ex2_approx(fe.e.y));
+            P.a0 = __fmul2_rn(dup2(r0.w), P.G);
+            P.al = make_float2(fminf(amax, P.a0.x), fminf(amax, P.a0.y));
+            P.c0 = j < last[0] && !(P.al.x < amin);
+            P.c1 = j < last[1] && !(P.al.y < amin);
             if constexpr (COUNT) {
                 n_eval += (j < last[0]) + (j < last[1]);
-                n_add += c0 + c1;
+                n_add += P.c0 + P.c1;
             }
-            if (!__any_sync(0xffffffffu, contrib)) continue;
-            const float dxs[2] = {dx.x, dx.y}, dys[2] = {dy.x, dy.y}, hxs[2] = {fe.hx.x, fe.hx.y}, hys[2] = {fe.hy.x, fe.hy.y};
-            const float Gs[2] = {G.x, G.y}, a0s[2] = {a0.x, a0.y}, als[2] = {al.x, al.y};
-            // back to front, each pixel of the lane in turn: T in front of the fragment from the
-            // one behind it, weight, the colour / depth adjoint and dL/dalpha; pixels that do not
-            // add it keep T and S (scalar arithmetic: packing these pairs measured slower)
+        };
+        // back to front, each pixel of the lane in turn: T in front of the fragment from the one
+        // behind it, weight, the colour / depth adjoint and dL/dalpha; pixels that do not add it
+        // keep T and S (scalar arithmetic: packing these pairs measured slower)
+        auto adjoint = [&](int t, const Alphas& P) {
+            const bool contrib = P.c0 || P.c1;
+            const float dxs[2] = {P.dx.x, P.dx.y}, dys[2] = {P.dy.x, P.dy.y}, hxs[2] = {P.hx.x, P.hx.y},
+                        hys[2] = {P.hy.x, P.hy.y};
+            const float Gs[2] = {P.G.x, P.G.y}, a0s[2] = {P.a0.x, P.a0.y}, als[2] = {P.al.x, P.al.y};
             const float4 r2 = s_rec[b][t][2];
-            const float4 cz = make_float4(r2.x, r2.y, r2.z, r0.z);
+            const float4 cz = make_float4(r2.x, r2.y, r2.z, s_rec[b][t][0].z);
             float val[10];
 #pragma unroll
             for (int q = 0; q < 10; q++) val[q] = 0.f;
             const float Ts[2] = {T2.x, T2.y}, Ss[2] = {S2.x, S2.y};
             const float g0s[2] = {g0.x, g0.y}, g1s[2] = {g1.x, g1.y}, g2s[2] = {g2.x, g2.y}, gds[2] = {gd2.x, gd2.y};
             float Tn_[2], Sn_[2];
-            const bool cq[2] = {c0, c1};
+            const bool cq[2] = {P.c0, P.c1};
 #pragma unroll
             for (int q = 0; q < 2; q++) {
                 const float dxv = dxs[q], dyv = dys[q], Gv = Gs[q], a0v = a0s[q], alpha = als[q];
@@ -904,25 +912,37 @@ __device__ __forceinline__ void render_bwd_region(const BwdArgs& a, int item, Bw
             S2 = make_float2(Sn_[0], Sn_[1]);
             T2 = make_float2(Tn_[0], Tn_[1]);
             const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
-            if (cmask) {
-                float4* rec4 = a.grad2d + 3 * (size_t)s_id[b][t];
-                if (__popc(cmask) <= kBwdDirectLanes) {
-                    if (contrib) {
-                        atomicAdd(rec4, make_float4(val[0], val[1], val[2], val[3]));
-                        atomicAdd(rec4 + 1, make_float4(val[4], val[5], val[6], 0.f));
-                        atomicAdd(rec4 + 2, make_float4(val[7], val[8], val[9], 0.f));
-                    }
-                } else {
-                    float t8, t2;
-                    warp_reduce10(val, t8, t2);
-                    float* rec = reinterpret_cast<float*>(rec4);
-                    if ((lane & 3) == 0) {
-                        const int idx = lane >> 2;
-                        atomicAdd(rec + (idx < 7 ? idx : idx + 1), t8);
-                    }
-                    if ((lane & 15) == 0) atomicAdd(rec + 9 + (lane >> 4), t2);
+            float4* rec4 = a.grad2d + 3 * (size_t)s_id[b][t];
+            if (__popc(cmask) <= kBwdDirectLanes) {
+                if (contrib) {
+                    atomicAdd(rec4, make_float4(val[0], val[1], val[2], val[3]));
+                    atomicAdd(rec4 + 1, make_float4(val[4], val[5], val[6], 0.f));
+                    atomicAdd(rec4 + 2, make_float4(val[7], val[8], val[9], 0.f));
                 }
+            } else {
+                float t8, t2;
+                warp_reduce10(val, t8, t2);
+                float* rec = reinterpret_cast<float*>(rec4);
+                if ((lane & 3) == 0) {
+                    const int idx = lane >> 2;
+                    atomicAdd(rec + (idx < 7 ? idx : idx + 1), t8);
+                }
+                if ((lane & 15) == 0) atomicAdd(rec + 9 + (lane >> 4), t2);
             }
+        };
+        // two records per iteration: their alphas are independent (the adjoints are not)
+        int t = 0;
+        for (; t + 1 < cnt; t += 2) {
+            Alphas A, B;
+            alphas(t, A);
+            alphas(t + 1, B);
+            if (__any_sync(0xffffffffu, A.c0 || A.c1)) adjoint(t, A);
+            if (__any_sync(0xffffffffu, B.c0 || B.c1)) adjoint(t + 1, B);
+        }
+        if (t < cnt) {
+            Alphas A;
+            alphas(t, A);
+            if (__any_sync(0xffffffffu, A.c0 || A.c1)) adjoint(t, A);
         }
         __syncwarp();   // every lane is done with buffer b before it is refilled
         cnt = cnt_next;
