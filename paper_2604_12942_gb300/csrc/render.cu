@@ -386,8 +386,19 @@ __device__ __forceinline__ void render_fwd_tile(const FwdArgs& a, int item, FwdS
             }
             __syncwarp();
             if constexpr (COUNT) n_visit += cnt;
-            // two records per iteration: their alphas are independent, the compositing is not
+            // four, then two records per iteration: their alphas are independent, the
+            // compositing is not
             int t = 0;
+            for (; t + 3 < cnt; t += 4) {
+                if (__all_sync(0xffffffffu, done)) break;
+                const int ka = s_list[w][t], kb = s_list[w][t + 1], kc = s_list[w][t + 2], kd = s_list[w][t + 3];
+                const float alpha_a = alpha_of(ka), alpha_b = alpha_of(kb);
+                const float alpha_c = alpha_of(kc), alpha_d = alpha_of(kd);
+                add(alpha_a, ka, base);
+                add(alpha_b, kb, base);
+                add(alpha_c, kc, base);
+                add(alpha_d, kd, base);
+            }
             for (; t + 1 < cnt; t += 2) {
                 if (__all_sync(0xffffffffu, done)) break;
                 const int ka = s_list[w][t], kb = s_list[w][t + 1];
