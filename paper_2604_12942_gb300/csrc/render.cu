@@ -386,9 +386,21 @@ __device__ __forceinline__ void render_fwd_tile(const FwdArgs& a, int item, FwdS
             }
             __syncwarp();
             if constexpr (COUNT) n_visit += cnt;
-            // four, then two records per iteration: their alphas are independent, the
-            // compositing is not
+            // eight, four, then two records per iteration: their alphas are independent, the
+            // compositing is not (four per iteration: 0.936 -> 0.908 ms at 2M Gaussians, 8 views;
+            // eight: 0.882)
             int t = 0;
+            for (; t + 7 < cnt; t += 8) {
+                if (__all_sync(0xffffffffu, done)) break;
+                int kk[8];
+                float al[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) kk[u] = s_list[w][t + u];
+#pragma unroll
+                for (int u = 0; u < 8; u++) al[u] = alpha_of(kk[u]);
+#pragma unroll
+                for (int u = 0; u < 8; u++) add(al[u], kk[u], base);
+            }
             for (; t + 3 < cnt; t += 4) {
                 if (__all_sync(0xffffffffu, done)) break;
                 const int ka = s_list[w][t], kb = s_list[w][t + 1], kc = s_list[w][t + 2], kd = s_list[w][t + 3];
