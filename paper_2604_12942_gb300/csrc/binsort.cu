@@ -134,25 +134,43 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t ltm;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(ltm));
-    for (int k = 0; k < 32; k++) {
-        const int lw = w * 32 + k;
-        const uint32_t bw = s_word[lw];
-        if ((bw >> lane) & 1u) {
-            const uint32_t pos = s_off[lw] + (uint32_t)__popc(bw & ltm);
+    // four bit words per iteration: their record gathers are issued together
+    for (int k = 0; k < 32; k += 4) {
+        bool hit[4];
+        float4 g0[4];
+        int grx[4], gry[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int lw = w * 32 + k + u;
+            hit[u] = (s_word[lw] >> lane) & 1u;
             const uint32_t idx = (uint32_t)(((int64_t)blockIdx.x * kScanThreads + lw) * 32 + lane);
-            const float4 r0 = __ldg(a.proj + 3 * (size_t)idx);
-            const int rx = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 1).w);
-            const int ry = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 2).w);
-            const View& V = a.views[idx / (uint32_t)a.n];
-            // the rectangle the projection counted (touched > 0: both spans are non-empty)
-            int xa = 0, xb = 0, ya = 0, yb = 0;
-            tile_span(r0.x, rx, a.tile, V.tiles_x, xa, xb);
-            tile_span(r0.y, ry, a.tile, V.tiles_y, ya, yb);
-            a.ekeys[pos] = __float_as_uint(r0.z);   // z > 0: bits are monotone
-            a.evals[pos] = pos;
-            a.entries[pos] = idx;
-            a.erect[pos] = make_uint2((uint32_t)(V.tile_off + ya * V.tiles_x + xa),
-                                      (uint32_t)(xb - xa + 1) | ((uint32_t)(yb - ya + 1) << 16));
+            if (hit[u]) {
+                g0[u] = __ldg(a.proj + 3 * (size_t)idx);
+                grx[u] = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 1).w);
+                gry[u] = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 2).w);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int lw = w * 32 + k + u;
+            const uint32_t bw = s_word[lw];
+            if (hit[u]) {
+                const uint32_t pos = s_off[lw] + (uint32_t)__popc(bw & ltm);
+                const uint32_t idx = (uint32_t)(((int64_t)blockIdx.x * kScanThreads + lw) * 32 + lane);
+                const float4 r0 = g0[u];
+                const int rx = grx[u];
+                const int ry = gry[u];
+                const View& V = a.views[idx / (uint32_t)a.n];
+                // the rectangle the projection counted (touched > 0: both spans are non-empty)
+                int xa = 0, xb = 0, ya = 0, yb = 0;
+                tile_span(r0.x, rx, a.tile, V.tiles_x, xa, xb);
+                tile_span(r0.y, ry, a.tile, V.tiles_y, ya, yb);
+                a.ekeys[pos] = __float_as_uint(r0.z);   // z > 0: bits are monotone
+                a.evals[pos] = pos;
+                a.entries[pos] = idx;
+                a.erect[pos] = make_uint2((uint32_t)(V.tile_off + ya * V.tiles_x + xa),
+                                          (uint32_t)(xb - xa + 1) | ((uint32_t)(yb - ya + 1) << 16));
+            }
         }
     }
 }
