@@ -863,6 +863,10 @@ __device__ __forceinline__ void render_bwd_region(const BwdArgs& a, int item, Bw
         next -= kWin;
         cp_async_wait_prior();   // this window's copies (all lanes') have landed after the syncwarp
         __syncwarp();
+        // each record's depth into its colour word's last slot (r_y is not needed here), so that
+        // the adjoint reads colour and depth with one 16-byte load
+        if (lane < cnt) s_rec[b][lane][2].w = s_rec[b][lane][0].z;
+        __syncwarp();
         if constexpr (COUNT) n_visit += cnt;
         // the alphas of the lane's two pixels of record t, as one packed pair: a record that no
         // pixel of the warp adds (all below alpha_min or past their pixels' last fragment)
@@ -898,7 +902,7 @@ __device__ __forceinline__ void render_bwd_region(const BwdArgs& a, int item, Bw
                         hys[2] = {P.hy.x, P.hy.y};
             const float Gs[2] = {P.G.x, P.G.y}, a0s[2] = {P.a0.x, P.a0.y}, als[2] = {P.al.x, P.al.y};
             const float4 r2 = s_rec[b][t][2];
-            const float4 cz = make_float4(r2.x, r2.y, r2.z, s_rec[b][t][0].z);
+            const float4 cz = r2;   // colour and depth
             float val[10];
 #pragma unroll
             for (int q = 0; q < 10; q++) val[q] = 0.f;
