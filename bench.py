@@ -696,19 +696,20 @@ def roofline_table(stage, w, pk, sms):
     n, V, P, E = w["n"], w["views"], w["pairs"], w["visible_entries"]
     VN = V * n
     B = {
-        # geometry of every row, SH of the rows some view sees
-        "project": 44 * n + 192 * w["visible_gaussians"] + 4 * VN + 48 * E,
-        # entry count (touched once, bit words written) and compaction (bit words read; per
+        # geometry of every row, SH of the rows some view sees; records of the visible entries
+        # and one visibility bit per (view, row) written
+        "project": 44 * n + 192 * w["visible_gaussians"] + VN // 8 + 48 * E,
+        # entry count and compaction (visibility bit words read twice; per
         # entry 24 B of its record read, key, value, index and tile rectangle written: 20 B),
         # depth sort (20 B per entry per pass), pair count and offsets (sorted id and rectangle
         # twice, offset written: 28 B per entry), emission (sorted id, index, rectangle, offset:
         # 20 B per entry; 8 B per pair written), tile sort (20 B per pair per pass), ranges
-        "bin_sort": 4 * VN + VN // 4 + 44 * E + w["depth_sort_passes"] * 20 * E + 48 * E + 8 * P
+        "bin_sort": VN // 4 + 44 * E + w["depth_sort_passes"] * 20 * E + 48 * E + 8 * P
                     + w["tile_sort_passes"] * 20 * P + 4 * P,
         # fused projection backward + Adam, rows visible in some view: parameters, m and v
-        # read, parameters, m and v written (6 x 236 B); visibility and touched flags of every
-        # row; screen-space sums of the visible entries
-        "project_bwd_adam": 6 * 236 * w["visible_gaussians"] + n + 4 * VN + 48 * E,
+        # read, parameters, m and v written (6 x 236 B); visibility flag and per-view bits of
+        # every row; screen-space sums of the visible entries
+        "project_bwd_adam": 6 * 236 * w["visible_gaussians"] + n + VN // 8 + 48 * E,
     }
     F = {"render_fwd": FLOP_FWD * w["frag_fwd_eval"], "composite_bwd": FLOP_BWD * w["frag_bwd_eval"]}
     Fk = {"render_fwd": FLOP_EVAL * w["frag_fwd_eval"] + FLOP_FWD_ADD * w["frag_fwd_add"],

@@ -131,7 +131,9 @@ typedef struct {
                             (a, b, c, rx bits), (r, g, b, ry bits); (a, b, c) is the inverse
                             2-D covariance times -log2(e)/2, so alpha = o * 2^(a dx^2 +
                             2 b dx dy + c dy^2); rx, ry are the box half-extents (int32) */
-    size_t touched;      /* uint32 [n_views*n] tiles covered */
+    size_t vis_bits;     /* uint32 [n_views][ceil(n/32)]: bit i % 32 of word
+                            v * ceil(n/32) + i / 32 is set when Gaussian i covers a tile of
+                            view v (its record in proj is then valid); other bits are 0 */
     size_t scan_tmp;     /* uint32 scratch of the scans */
     size_t ekeys0, ekeys1; /* uint32 [n_views*n] ping-pong: bits(z) of the visible entries */
     size_t evals0, evals1; /* uint32 [n_views*n] ping-pong: their compact indices (positions
@@ -249,7 +251,7 @@ gs_status gs_workspace_init(const gs_ws_layout *L, void *ws, void *stream);
  * sigmoid(logit), culled if o < alpha_min; rgb = max(0, sum_k sh_k Y_k(dir) + 0.5),
  * dir = normalize(mu - camera centre); box half-extents rx = ceil(sqrt(tau Sigma'_xx)), ry = ceil(sqrt(tau
  * Sigma'_yy)), tau = 2 ln(o/alpha_min) (the bounding box of the ellipse outside which
- * alpha < alpha_min).  Writes the proj, touched and visible regions of the workspace. */
+ * alpha < alpha_min).  Writes the proj, vis_bits and visible regions of the workspace. */
 gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, const gs_render_opts *opts,
                      const gs_ws_layout *L, void *ws, void *stream);
 
@@ -262,7 +264,8 @@ gs_status gs_project(const gs_gaussians *g, const gs_camera *cams, const gs_rend
  * row-major tile order -- computed as a stable sort of the visible (v, i) entries by
  * float_bits(z) followed by a stable sort of their pairs by tile id.  If the pairs exceed
  * max_pairs the status word becomes GS_ERR_CAPACITY, n_pairs holds the required count and
- * the later stages of the step do nothing. */
+ * the later stages of the step do nothing.  Reads the proj and vis_bits regions that
+ * gs_project writes. */
 gs_status gs_bin_sort(const gs_camera *cams, const gs_render_opts *opts, const gs_ws_layout *L,
                       void *ws, void *stream);
 

@@ -42,7 +42,7 @@ class GicpResult(C.Structure):
 
 
 class WsLayout(C.Structure):
-    _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "touched", "scan_tmp",
+    _fields_ = [(k, C.c_size_t) for k in ("views", "counters", "loss_acc", "proj", "vis_bits", "scan_tmp",
                                           "ekeys0", "ekeys1", "evals0", "evals1", "keys0", "keys1", "vals0", "vals1", "pair_mask", "emit_tmp", "sort_tmp", "ranges", "T_final",
                                           "n_contrib", "grad2d", "geo2d", "dirgrad", "visible", "entries", "erect", "tile_order", "render_mask",
                                           "ssim_tmp", "total")] + \

@@ -140,7 +140,7 @@ static gs_status layout(int64_t n, int32_t n_views, const gs_camera* cams, const
     L.counters = take(sizeof(Counters));
     L.loss_acc = take(kLossAccBytes);
     L.proj = take(sizeof(float) * 12 * (size_t)VN);
-    L.touched = take(sizeof(uint32_t) * (size_t)VN);
+    L.vis_bits = take(sizeof(uint32_t) * (size_t)n_views * (size_t)((n + 31) / 32));
     L.scan_tmp = take(sizeof(uint32_t) * ((size_t)VN / kScanBlock + 2));
     L.ekeys0 = take(sizeof(uint32_t) * (size_t)VN);
     L.ekeys1 = take(sizeof(uint32_t) * (size_t)VN);
@@ -254,7 +254,7 @@ static cudaError_t run_project(const gs_gaussians* g, const gs_render_opts* opts
     a.op = to_opts(opts);
     a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats; a.logits = g->opacity_logits; a.sh = g->sh;
     a.proj = at<float4>(ws, L->proj);
-    a.touched = at<uint32_t>(ws, L->touched);
+    a.vis_bits = at<uint32_t>(ws, L->vis_bits);
     a.visible = at<uint8_t>(ws, L->visible);
     a.counters = at<Counters>(ws, L->counters);
     return launch_project(a, g->sh_degree, st);
@@ -269,7 +269,7 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     b.tile = opts->tile;
     b.max_pairs = L->max_pairs;
     b.proj = at<float4>(ws, L->proj);
-    b.touched = at<uint32_t>(ws, L->touched);
+    b.vis_bits = at<uint32_t>(ws, L->vis_bits);
     b.scan_tmp = at<uint32_t>(ws, L->scan_tmp);
     b.ekeys = at<uint32_t>(ws, L->ekeys0);
     b.evals = at<uint32_t>(ws, L->evals0);
@@ -278,7 +278,6 @@ static cudaError_t run_bin_sort(const gs_render_opts* opts, const gs_ws_layout* 
     b.sorted_evals = at<uint32_t>(ws, L->evals0);   // 4 passes: the entry sort ends in buffer 0
     b.pkeys = at<uint32_t>(ws, L->keys0);
     b.pvals = at<uint32_t>(ws, L->vals0);
-    b.vis_bits = at<uint32_t>(ws, L->ekeys1);       // free until the entry sort
     b.poff = at<uint32_t>(ws, L->ekeys1);           // free once the entries are sorted
     b.chunk_first = at<uint32_t>(ws, L->emit_tmp);
     b.srt = at<uint32_t>(ws, L->geo2d);              // free until the projection backward
@@ -492,7 +491,7 @@ static ProjectBwdArgs pbwd_args(const gs_gaussians* g, const gs_render_opts* opt
     p.views = at<View>(ws, L->views);
     p.op = to_opts(opts);
     p.means = g->means; p.log_scales = g->log_scales; p.quats = g->quats; p.logits = g->opacity_logits; p.sh = g->sh;
-    p.touched = at<uint32_t>(ws, L->touched);
+    p.vis_bits = at<uint32_t>(ws, L->vis_bits);
     p.visible = at<uint8_t>(ws, L->visible);
     p.entries = at<uint32_t>(ws, L->entries);
     p.counters = at<Counters>(ws, L->counters);

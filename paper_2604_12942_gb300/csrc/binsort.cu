@@ -77,40 +77,18 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t* __r
 }
 
 // ----------------------------------------------------------------------------------------
-// Entry compaction.  The (view, Gaussian) slots are taken 32 at a time as one bit word (bit
-// set: touched > 0).  A block of 1024 threads covers 1024 words (32768 slots): the count
-// kernel reads the touched counts once, writes the words and the block's entry total; the
-// totals are scanned; the compaction kernel then reads only the words, gives each its offset
-// by a block scan of the word counts, and each warp writes the entries of 32 words, one word
-// at a time with a lane per slot, so entries stay in (view, index) order.
+// Entry compaction.  The projection leaves one bit word per view and 32 Gaussians (vis_bits,
+// each view padded to whole words).  A block of 1024 threads covers 1024 words: the count
+// kernel writes the block's entry total; the totals are scanned; the compaction kernel gives
+// each word its offset by a block scan of the word counts, and each warp writes the entries of
+// 32 words, one word at a time with a lane per slot, so entries stay in (view, index) order.
 // ----------------------------------------------------------------------------------------
-constexpr int64_t kEntrySlotsPerBlock = (int64_t)kScanThreads * 32;
-
-__global__ void __launch_bounds__(kScanThreads) entry_count_kernel(const uint32_t* __restrict__ touched, int64_t total,
-                                                                  uint32_t* __restrict__ bits,
+__global__ void __launch_bounds__(kScanThreads) entry_count_kernel(const uint32_t* __restrict__ bits, int64_t n_words,
                                                                   uint32_t* __restrict__ bsum) {
     __shared__ uint32_t s[33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // the warp's 32 words are slots s0 .. s0 + 1023; word k of the warp ends up in lane k
-    const int64_t s0 = (int64_t)blockIdx.x * kEntrySlotsPerBlock + (int64_t)w * 1024;
-    uint32_t mine = 0;
-#pragma unroll
-    for (int k0 = 0; k0 < 32; k0 += 8) {
-        uint32_t t[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const int64_t j = s0 + (int64_t)(k0 + k) * 32 + lane;
-            t[k] = j < total ? touched[j] : 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const uint32_t b = __ballot_sync(0xffffffffu, t[k] != 0u);
-            if (lane == k0 + k) mine = b;
-        }
-    }
     const int64_t word = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
-    if (word * 32 < total) bits[word] = mine;
-    uint32_t sum = warp_sum((uint32_t)__popc(mine));
+    const uint32_t sum = warp_sum((uint32_t)__popc(word < n_words ? bits[word] : 0u));
     if (lane == 0) s[w] = sum;
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -120,12 +98,13 @@ __global__ void __launch_bounds__(kScanThreads) entry_count_kernel(const uint32_
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, int64_t total) {
+__global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, int64_t n_words) {
     __shared__ uint32_t s[33];
     __shared__ uint32_t s_off[kScanThreads], s_word[kScanThreads];
     if (a.counters->status != 0) return;
     const int64_t word = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
-    const uint32_t b = word * 32 < total ? a.vis_bits[word] : 0u;
+    const uint32_t b = word < n_words ? a.vis_bits[word] : 0u;
+    const uint32_t nw = (uint32_t)((a.n + 31) >> 5);   // words per view
     uint32_t tot;
     const uint32_t off = block_exclusive_scan_1024((uint32_t)__popc(b), s, tot) + a.scan_tmp[blockIdx.x];
     s_off[threadIdx.x] = off;
@@ -143,7 +122,9 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
         for (int u = 0; u < 4; u++) {
             const int lw = w * 32 + k + u;
             hit[u] = (s_word[lw] >> lane) & 1u;
-            const uint32_t idx = (uint32_t)(((int64_t)blockIdx.x * kScanThreads + lw) * 32 + lane);
+            const uint32_t gw = (uint32_t)blockIdx.x * kScanThreads + lw;   // < V * nw
+            const uint32_t v = gw / nw;
+            const uint32_t idx = v * (uint32_t)a.n + (gw - v * nw) * 32 + lane;
             if (hit[u]) {
                 g0[u] = __ldg(a.proj + 3 * (size_t)idx);
                 grx[u] = __float_as_int(__ldg(a.proj + 3 * (size_t)idx + 1).w);
@@ -156,12 +137,14 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
             const uint32_t bw = s_word[lw];
             if (hit[u]) {
                 const uint32_t pos = s_off[lw] + (uint32_t)__popc(bw & ltm);
-                const uint32_t idx = (uint32_t)(((int64_t)blockIdx.x * kScanThreads + lw) * 32 + lane);
+                const uint32_t gw = (uint32_t)blockIdx.x * kScanThreads + lw;
+                const uint32_t v = gw / nw;
+                const uint32_t idx = v * (uint32_t)a.n + (gw - v * nw) * 32 + lane;
                 const float4 r0 = g0[u];
                 const int rx = grx[u];
                 const int ry = gry[u];
-                const View& V = a.views[idx / (uint32_t)a.n];
-                // the rectangle the projection counted (touched > 0: both spans are non-empty)
+                const View& V = a.views[v];
+                // the rectangle the projection found non-empty
                 int xa = 0, xb = 0, ya = 0, yb = 0;
                 tile_span(r0.x, rx, a.tile, V.tiles_x, xa, xb);
                 tile_span(r0.y, ry, a.tile, V.tiles_y, ya, yb);
@@ -176,12 +159,12 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
 }
 
 cudaError_t launch_entries(const BinArgs& a, cudaStream_t st) {
-    const int64_t total = (int64_t)a.n_views * a.n;
-    const int nb = (int)((total + kEntrySlotsPerBlock - 1) / kEntrySlotsPerBlock);
-    if (nb > 0) entry_count_kernel<<<nb, kScanThreads, 0, st>>>(a.touched, total, a.vis_bits, a.scan_tmp);
+    const int64_t n_words = (int64_t)a.n_views * ((a.n + 31) >> 5);
+    const int nb = (int)((n_words + kScanThreads - 1) / kScanThreads);
+    if (nb > 0) entry_count_kernel<<<nb, kScanThreads, 0, st>>>(a.vis_bits, n_words, a.scan_tmp);
     scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(a.scan_tmp, nb, &a.counters->n_entries, &a.counters->n_entries32,
                                                    a.counters, -1);
-    if (nb > 0) entry_compact_kernel<<<nb, kScanThreads, 0, st>>>(a, total);
+    if (nb > 0) entry_compact_kernel<<<nb, kScanThreads, 0, st>>>(a, n_words);
     return cudaGetLastError();
 }
 

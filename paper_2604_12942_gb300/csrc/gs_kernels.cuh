@@ -12,7 +12,8 @@ struct ProjectArgs {
     Opts op;
     const float *means, *log_scales, *quats, *logits, *sh;
     float4* proj;          // [V*n][3]
-    uint32_t* touched;     // [V*n]
+    uint32_t* vis_bits;    // [V][ceil(n/32)] bit i % 32 of word v * ceil(n/32) + i / 32: view v
+                           //   covers a tile of Gaussian i
     uint8_t* visible;      // [n]
     Counters* counters;    // status word: GS_ERR_NONFINITE on a non-finite parameter
 };
@@ -23,7 +24,7 @@ struct ProjectBwdArgs {
     const View* views;
     Opts op;
     const float *means, *log_scales, *quats, *logits, *sh;
-    const uint32_t* touched;
+    const uint32_t* vis_bits; // [V][ceil(n/32)] per-view visibility words (ProjectArgs)
     const uint8_t* visible;   // [n] covers a tile of some view (rows without it are skipped)
     const uint32_t* entries;  // visible (view, Gaussian) entries in (view, Gaussian) order
     const Counters* counters; // n_entries
@@ -51,9 +52,8 @@ struct BinArgs {
     int tile;
     int64_t max_pairs;
     const float4* proj;
-    const uint32_t* touched;
+    const uint32_t* vis_bits;     // [V][ceil(n/32)] per-view visibility words (ProjectArgs)
     uint32_t* scan_tmp;           // block sums of the scans
-    uint32_t* vis_bits;           // [ceil(n_views * n / 32)] scratch: one bit per (view, Gaussian) slot
     uint32_t* ekeys;              // compaction output: bits(z) of each entry
     uint32_t* evals;              //   and its compact index (the value the depth sort carries)
     uint32_t* entries;            //   view * n + Gaussian index of each entry, (view, Gaussian) order
@@ -218,7 +218,7 @@ cudaError_t launch_gicp_normal_eq(const GicpMap& src, const uint8_t* src_flag, c
 
 cudaError_t launch_project(const ProjectArgs& a, int deg, cudaStream_t st);
 cudaError_t launch_project_bwd(const ProjectBwdArgs& a, int deg, cudaStream_t st);
-// Compaction of the visible entries (touched > 0) in (view, Gaussian) order with their
+// Compaction of the visible entries (their vis_bits set) in (view, Gaussian) order with their
 // depth keys; the count goes to c->n_entries.
 cudaError_t launch_entries(const BinArgs& a, cudaStream_t st);
 // Pair offsets over the depth-sorted entries (total to c->n_pairs, GS_ERR_CAPACITY above

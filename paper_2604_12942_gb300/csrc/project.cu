@@ -26,13 +26,17 @@ __global__ void __launch_bounds__(128, 8) project_kernel(ProjectArgs a) {
     __syncthreads();
     const int64_t n = a.n;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    // Every lane reaches the ballots after the view loop (they build the visibility words);
+    // lanes past n read row n - 1 and see nothing.  Blocks of 128 rows start on a word, so
+    // the 32 lanes of a warp are the 32 rows of word i / 32 of each view.
+    const bool in = i < n;
+    const int64_t ii = in ? i : n - 1;
     float mu[3], ls[3], q[4];
 #pragma unroll
-    for (int k = 0; k < 3; k++) { mu[k] = __ldg(a.means + k * n + i); ls[k] = __ldg(a.log_scales + k * n + i); }
+    for (int k = 0; k < 3; k++) { mu[k] = __ldg(a.means + k * n + ii); ls[k] = __ldg(a.log_scales + k * n + ii); }
 #pragma unroll
-    for (int k = 0; k < 4; k++) q[k] = __ldg(a.quats + k * n + i);
-    const float logit = __ldg(a.logits + i);
+    for (int k = 0; k < 4; k++) q[k] = __ldg(a.quats + k * n + ii);
+    const float logit = __ldg(a.logits + ii);
     // A non-finite parameter invalidates the step: the row is treated as unseen and the status
     // word becomes GS_ERR_NONFINITE, so the later stages of the step do nothing.
     bool finite = isfinite(logit);
@@ -40,42 +44,45 @@ __global__ void __launch_bounds__(128, 8) project_kernel(ProjectArgs a) {
     for (int k = 0; k < 3; k++) finite = finite && isfinite(mu[k]) && isfinite(ls[k]);
 #pragma unroll
     for (int k = 0; k < 4; k++) finite = finite && isfinite(q[k]);
-    if (!finite) {
-        set_status(a.counters, GS_ERR_NONFINITE);
-        for (int v = 0; v < a.n_views; v++) a.touched[(int64_t)v * n + i] = 0;
-        a.visible[i] = 0;
-        return;
-    }
-    Cov3 cv;
-    cov3_forward(q, ls, cv);
-    const Opts op = a.op;
+    if (in && !finite) set_status(a.counters, GS_ERR_NONFINITE);
     // geometry of every view first; the SH coefficients are then loaded only by rows that
     // some view sees (a row no view sees reads 11 of its 11 + 3K floats)
     uint32_t vis = 0;
-    for (int v = 0; v < a.n_views; v++) {
-        const View& V = s_views[v];
-        const int64_t idx = (int64_t)v * n + i;
-        ProjV P;
-        project_view(mu, cv, logit, V, op, P);
-        uint32_t touched = 0;
-        if (!P.culled) {
+    const Opts op = a.op;
+    if (in && finite) {
+        Cov3 cv;
+        cov3_forward(q, ls, cv);
+        for (int v = 0; v < a.n_views; v++) {
+            const View& V = s_views[v];
+            ProjV P;
+            project_view(mu, cv, logit, V, op, P);
+            if (P.culled) continue;
             int x0, x1, y0, y1;
-            if (tile_span(P.u, P.rx, op.tile, V.tiles_x, x0, x1) &&
-                tile_span(P.v, P.ry, op.tile, V.tiles_y, y0, y1))
-                touched = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-        }
-        if (touched) {
+            if (!tile_span(P.u, P.rx, op.tile, V.tiles_x, x0, x1) ||
+                !tile_span(P.v, P.ry, op.tile, V.tiles_y, y0, y1))
+                continue;
             const float idet = 1.0f / P.det;
             const float A = P.c * idet, B = -P.b * idet, C = P.a * idet;
-            float4* rec = a.proj + 3 * idx;
+            float4* rec = a.proj + 3 * ((int64_t)v * n + i);
             rec[0] = make_float4(P.u, P.v, P.pc[2], P.o);
             rec[1] = make_float4(kConicScale * A, kConicScale * B, kConicScale * C, __int_as_float(P.rx));
             rec[2].w = __int_as_float(P.ry);
             vis |= 1u << v;
         }
-        a.touched[idx] = touched;
     }
-    a.visible[i] = vis ? 1 : 0;
+    // view v's word of the warp's 32 rows goes to lane v, which stores it
+    {
+        const int lane = threadIdx.x & 31;
+        const int64_t nw = (n + 31) >> 5;   // words per view
+        const int64_t word = i >> 5;
+        uint32_t mine = 0;
+        for (int v = 0; v < a.n_views; v++) {
+            const uint32_t bits = __ballot_sync(0xffffffffu, (vis >> v) & 1u);
+            if (lane == v) mine = bits;
+        }
+        if (lane < a.n_views && word < nw) a.vis_bits[lane * nw + word] = mine;
+    }
+    if (in) a.visible[i] = vis ? 1 : 0;
     if (!vis) return;
     float sh[3 * K];
     bool sh_finite = true;

@@ -222,9 +222,11 @@ __device__ __forceinline__ void project_bwd_sh_rows(const ProjectBwdArgs& a, int
     const int64_t ii = live ? i : 0;
     uint64_t vmask = 0;
     if (live) {
+        // the row's bit of each view's visibility word (one word for the 32 rows of a warp)
+        const int64_t nw = (n + 31) >> 5;
 #pragma unroll 8
         for (int v = 0; v < a.n_views; v++)
-            if (__ldg(a.touched + (int64_t)v * n + ii) != 0u) vmask |= 1ull << v;
+            vmask |= (uint64_t)((__ldg(a.vis_bits + v * nw + (ii >> 5)) >> (ii & 31)) & 1u) << v;
     }
     if (__all_sync(0xffffffffu, !live) && a.grad_twist == nullptr) return;
     float mu[3];
@@ -402,9 +404,10 @@ __device__ __forceinline__ void project_bwd_geo_rows(const ProjectBwdArgs& a, in
         cp_async_commit();
     }
     uint64_t vmask = 0;
+    const int64_t nw = (n + 31) >> 5;
 #pragma unroll 8
     for (int v = 0; v < a.n_views; v++)
-        if (__ldg(a.touched + (int64_t)v * n + i) != 0u) vmask |= 1ull << v;
+        vmask |= (uint64_t)((__ldg(a.vis_bits + v * nw + (i >> 5)) >> (i & 31)) & 1u) << v;
     float mu[3], ls[3], q[4];
 #pragma unroll
     for (int k = 0; k < 3; k++) {

@@ -15,7 +15,7 @@ import torch
 import oracle
 import paper_2604_12942_gb300 as gs
 import synth
-from tests.gpu_helpers import GROUPS, gpu_forward, planes_of, rel_l2
+from tests.gpu_helpers import GROUPS, get_vis_bits, gpu_forward, planes_of, rel_l2, set_vis_bits
 
 pytestmark = pytest.mark.gpu
 
@@ -58,10 +58,10 @@ def test_project_matches_oracle(deg):
     ws, planes, *_ = gpu_forward(sc, cams)
     n = sc.n
     rec = ws.region("proj", torch.float32, 12 * len(cams) * n).view(len(cams), n, 12).cpu().numpy()
-    touched = ws.region("touched", torch.int32, len(cams) * n).view(len(cams), n).cpu().numpy()
+    seen = get_vis_bits(ws, len(cams), n)
     for v, cam in enumerate(cams):
         pr = oracle.project(sc, cam)
-        t = touched[v] > 0
+        t = seen[v]
         ok = pr["visible"].astype(bool) & ~pr["fragile"].astype(bool)
         # every GPU-kept Gaussian is visible for the oracle (up to fragile cull decisions)
         assert np.all(pr["visible"][t] | pr["fragile"][t])
@@ -101,7 +101,7 @@ def _bin_case(cams, n, tile, seed, radius_max=48):
         rec[v, :, 7] = it["rx"].view(np.float32)
         rec[v, :, 11] = it["ry"].view(np.float32)
     ws.region("proj", torch.float32, 12 * V * n).copy_(torch.as_tensor(rec.reshape(-1)))
-    ws.region("touched", torch.int32, V * n).copy_(torch.as_tensor(ref["touched"].astype(np.int32)))
+    set_vis_bits(ws, ref["touched"].reshape(V, n) > 0)
     ws.region("counters", torch.int32, 8).zero_()
     ws.bin_sort()
     c = ws.counters()
@@ -154,7 +154,7 @@ def test_bin_sort_single_tile():
 def test_bin_sort_empty():
     cams = [synth.camera(64, 48, 60.0)]
     ws = gs.Workspace(10, cams, gs.default_opts(), 128)
-    ws.region("touched", torch.int32, 10).zero_()
+    set_vis_bits(ws, np.zeros((1, 10), bool))
     ws.region("counters", torch.int32, 8).zero_()
     ws.bin_sort()
     c = ws.counters()

@@ -20,6 +20,7 @@ import oracle
 import paper_2604_12942_gb300 as gs
 import synth
 from paper_2604_12942_gb300 import _native as N
+from tests.gpu_helpers import set_vis_bits
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +42,7 @@ def _regular_sort(items, cams, tile):
         rec[v, :, 7] = it["rx"].view(np.float32)
         rec[v, :, 11] = it["ry"].view(np.float32)
     ws.region("proj", torch.float32, 12 * V * n).copy_(torch.as_tensor(rec.reshape(-1)))
-    ws.region("touched", torch.int32, V * n).copy_(torch.as_tensor(ref["touched"].astype(np.int32)))
+    set_vis_bits(ws, ref["touched"].reshape(V, n) > 0)
     ws.region("counters", torch.int32, 8).zero_()
     ws.bin_sort()
     c = ws.counters()
