@@ -78,31 +78,35 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(uint32_t* __r
 
 // ----------------------------------------------------------------------------------------
 // Entry compaction.  The projection leaves one bit word per view and 32 Gaussians (vis_bits,
-// each view padded to whole words).  A block of 1024 threads covers 1024 words: the count
-// kernel writes the block's entry total; the totals are scanned; the compaction kernel gives
-// each word its offset by a block scan of the word counts, and each warp writes the entries of
-// 32 words, one word at a time with a lane per slot, so entries stay in (view, index) order.
+// each view padded to whole words).  A block of kEntryThreads threads covers as many words:
+// the count kernel writes the block's entry total; the totals are scanned; the compaction
+// kernel gives each word its offset by a block scan of the word counts, and each warp writes
+// the entries of 32 words, one word at a time with a lane per slot, so entries stay in (view,
+// index) order.  Blocks of 256 (four resident per SM) rather than 1024 (one, at the
+// compaction's registers) shorten the ragged end of the grid.
 // ----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) entry_count_kernel(const uint32_t* __restrict__ bits, int64_t n_words,
-                                                                  uint32_t* __restrict__ bsum) {
-    __shared__ uint32_t s[33];
+constexpr int kEntryThreads = 256;
+
+__global__ void __launch_bounds__(kEntryThreads) entry_count_kernel(const uint32_t* __restrict__ bits, int64_t n_words,
+                                                                   uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t s[kEntryThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t word = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+    const int64_t word = (int64_t)blockIdx.x * kEntryThreads + threadIdx.x;
     const uint32_t sum = warp_sum((uint32_t)__popc(word < n_words ? bits[word] : 0u));
     if (lane == 0) s[w] = sum;
     __syncthreads();
     if (threadIdx.x < 32) {
-        uint32_t t = threadIdx.x < (kScanThreads >> 5) ? s[threadIdx.x] : 0u;
+        uint32_t t = threadIdx.x < (kEntryThreads >> 5) ? s[threadIdx.x] : 0u;
         t = warp_sum(t);
         if (threadIdx.x == 0) bsum[blockIdx.x] = t;
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, int64_t n_words) {
+__global__ void __launch_bounds__(kEntryThreads, 4) entry_compact_kernel(BinArgs a, int64_t n_words) {
     __shared__ uint32_t s[33];
-    __shared__ uint32_t s_off[kScanThreads], s_word[kScanThreads];
+    __shared__ uint32_t s_off[kEntryThreads], s_word[kEntryThreads];
     if (a.counters->status != 0) return;
-    const int64_t word = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+    const int64_t word = (int64_t)blockIdx.x * kEntryThreads + threadIdx.x;
     const uint32_t b = word < n_words ? a.vis_bits[word] : 0u;
     const uint32_t nw = (uint32_t)((a.n + 31) >> 5);   // words per view
     uint32_t tot;
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
         for (int u = 0; u < 4; u++) {
             const int lw = w * 32 + k + u;
             hit[u] = (s_word[lw] >> lane) & 1u;
-            const uint32_t gw = (uint32_t)blockIdx.x * kScanThreads + lw;   // < V * nw
+            const uint32_t gw = (uint32_t)blockIdx.x * kEntryThreads + lw;   // < V * nw
             const uint32_t v = gw / nw;
             const uint32_t idx = v * (uint32_t)a.n + (gw - v * nw) * 32 + lane;
             if (hit[u]) {
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
             const uint32_t bw = s_word[lw];
             if (hit[u]) {
                 const uint32_t pos = s_off[lw] + (uint32_t)__popc(bw & ltm);
-                const uint32_t gw = (uint32_t)blockIdx.x * kScanThreads + lw;
+                const uint32_t gw = (uint32_t)blockIdx.x * kEntryThreads + lw;
                 const uint32_t v = gw / nw;
                 const uint32_t idx = v * (uint32_t)a.n + (gw - v * nw) * 32 + lane;
                 const float4 r0 = g0[u];
@@ -160,11 +164,11 @@ __global__ void __launch_bounds__(kScanThreads) entry_compact_kernel(BinArgs a, 
 
 cudaError_t launch_entries(const BinArgs& a, cudaStream_t st) {
     const int64_t n_words = (int64_t)a.n_views * ((a.n + 31) >> 5);
-    const int nb = (int)((n_words + kScanThreads - 1) / kScanThreads);
-    if (nb > 0) entry_count_kernel<<<nb, kScanThreads, 0, st>>>(a.vis_bits, n_words, a.scan_tmp);
+    const int nb = (int)((n_words + kEntryThreads - 1) / kEntryThreads);
+    if (nb > 0) entry_count_kernel<<<nb, kEntryThreads, 0, st>>>(a.vis_bits, n_words, a.scan_tmp);
     scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(a.scan_tmp, nb, &a.counters->n_entries, &a.counters->n_entries32,
                                                    a.counters, -1);
-    if (nb > 0) entry_compact_kernel<<<nb, kScanThreads, 0, st>>>(a, n_words);
+    if (nb > 0) entry_compact_kernel<<<nb, kEntryThreads, 0, st>>>(a, n_words);
     return cudaGetLastError();
 }
 
