@@ -181,15 +181,24 @@ cudaError_t launch_entries(const BinArgs& a, cudaStream_t st) {
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t rect_count(uint2 r) { return (r.y & 0xFFFFu) * (r.y >> 16); }
 
-// Also writes, in depth order, each entry's tile rectangle and index (srt), which the offsets
-// and the emission then read without the gather through the sorted compact indices.
-__global__ void __launch_bounds__(kScanThreads) pair_count_kernel(BinArgs a) {
+// The entry count is known only on the device, so the scans over the depth-sorted entries
+// cover the capacity (n_views * n) in chunks of kScanBlock entries, taken in turn by a grid of
+// resident blocks: a chunk past the last entry costs one store, not a block launch.
+//
+// Pair count of each chunk.  Also writes, in depth order, each entry's tile rectangle and
+// index (srt), which the offsets and the emission then read without the gather through the
+// sorted compact indices.
+__global__ void __launch_bounds__(kScanThreads) pair_count_kernel(BinArgs a, int nb) {
     __shared__ uint32_t s[33];
     const int64_t E = (int64_t)a.counters->n_entries;
     const int64_t VN = (int64_t)a.n_views * a.n;
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
-    uint32_t sum = 0;
-    if (base < E) {
+    for (int ch = blockIdx.x; ch < nb; ch += gridDim.x) {
+        const int64_t base = (int64_t)ch * kScanBlock;
+        if (base >= E) {   // (the same for the whole block)
+            if (threadIdx.x == 0) a.scan_tmp[ch] = 0u;
+            continue;
+        }
+        uint32_t sum = 0;
 #pragma unroll
         for (int k = 0; k < kScanItems; k++) {
             const int64_t j = base + (int64_t)k * kScanThreads + threadIdx.x;
@@ -202,42 +211,45 @@ __global__ void __launch_bounds__(kScanThreads) pair_count_kernel(BinArgs a) {
                 sum += rect_count(r);
             }
         }
-    }
-    sum = warp_sum(sum);
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t t = threadIdx.x < (kScanThreads >> 5) ? s[threadIdx.x] : 0u;
-        t = warp_sum(t);
-        if (threadIdx.x == 0) a.scan_tmp[blockIdx.x] = t;
+        sum = warp_sum(sum);
+        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t t = threadIdx.x < (kScanThreads >> 5) ? s[threadIdx.x] : 0u;
+            t = warp_sum(t);
+            if (threadIdx.x == 0) a.scan_tmp[ch] = t;
+        }
+        __syncthreads();   // s is written again for the next chunk
     }
 }
 
 // Pair offsets of the depth-sorted entries (poff[e] = pairs of the entries before e), and
 // for every output chunk of kEmitChunk pairs the entry holding its first pair.
-__global__ void __launch_bounds__(kScanThreads) pair_offsets_kernel(BinArgs a) {
+__global__ void __launch_bounds__(kScanThreads) pair_offsets_kernel(BinArgs a, int nb) {
     __shared__ uint32_t s[33];
     if (a.counters->status != 0) return;
     const int64_t E = (int64_t)a.counters->n_entries;
-    if ((int64_t)blockIdx.x * kScanBlock >= E) return;
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
-    uint32_t t[kScanItems], sum = 0;
+    for (int ch = blockIdx.x; ch < nb && (int64_t)ch * kScanBlock < E; ch += gridDim.x) {
+        const int64_t base = (int64_t)ch * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+        uint32_t t[kScanItems], sum = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-        t[k] = base + k < E ? rect_count(make_uint2(0u, a.srt[(int64_t)a.n_views * a.n + base + k])) : 0u;
-        sum += t[k];
-    }
-    uint32_t tot;
-    uint32_t off = block_exclusive_scan_1024(sum, s, tot) + a.scan_tmp[blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-        if (base + k < E) {
-            a.poff[base + k] = off;
-            // chunk starts c * kEmitChunk inside [off, off + t)
-            for (uint32_t c = (off + kEmitChunk - 1) / kEmitChunk; c * (uint64_t)kEmitChunk < (uint64_t)off + t[k]; c++)
-                a.chunk_first[c] = (uint32_t)(base + k);
+        for (int k = 0; k < kScanItems; k++) {
+            t[k] = base + k < E ? rect_count(make_uint2(0u, a.srt[(int64_t)a.n_views * a.n + base + k])) : 0u;
+            sum += t[k];
         }
-        off += t[k];
+        uint32_t tot;
+        uint32_t off = block_exclusive_scan_1024(sum, s, tot) + a.scan_tmp[ch];   // (ends with a barrier)
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            if (base + k < E) {
+                a.poff[base + k] = off;
+                // chunk starts c * kEmitChunk inside [off, off + t)
+                for (uint32_t c = (off + kEmitChunk - 1) / kEmitChunk; c * (uint64_t)kEmitChunk < (uint64_t)off + t[k];
+                     c++)
+                    a.chunk_first[c] = (uint32_t)(base + k);
+            }
+            off += t[k];
+        }
     }
 }
 
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
     const int64_t E = (int64_t)a.counters->n_entries;
     const uint64_t n_chunks = (P + kEmitChunk - 1) / kEmitChunk;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // one chunk per block (the grid covers the pair capacity; blocks past the last chunk exit)
+    // the chunks in turn over the grid (a resident grid: the pair count is known only here)
     for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
         const uint64_t p0 = c * kEmitChunk, p1 = p0 + kEmitChunk < P ? p0 + kEmitChunk : P;
         const int64_t e0 = a.chunk_first[c];
@@ -323,16 +335,39 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(BinArgs a) {
     }
 }
 
+// Blocks of `kernel` resident on the device at once (occupancy times SMs), kept per device.
+template <class Kernel>
+static int resident_grid(int (&cache)[kMaxDevices], Kernel kernel, int threads) {
+    const int d = current_device();
+    if (d >= 0 && cache[d] > 0) return cache[d];
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int g = per_sm * device_sms();
+    if (d >= 0) cache[d] = g;
+    return g;
+}
+
 cudaError_t launch_emit(const BinArgs& a, cudaStream_t st) {
+    static int g_count[kMaxDevices] = {}, g_offsets[kMaxDevices] = {}, g_emit[kMaxDevices] = {};
     const int64_t total = (int64_t)a.n_views * a.n;   // upper bound of the entry count
     const int nb = (int)((total + kScanBlock - 1) / kScanBlock);
-    if (nb > 0) pair_count_kernel<<<nb, kScanThreads, 0, st>>>(a);
+    if (nb > 0) {
+        const int g = resident_grid(g_count, pair_count_kernel, kScanThreads);
+        pair_count_kernel<<<g < nb ? g : nb, kScanThreads, 0, st>>>(a, nb);
+    }
     scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(a.scan_tmp, nb, &a.counters->n_pairs, nullptr, a.counters,
                                                    a.max_pairs);
-    if (nb > 0) pair_offsets_kernel<<<nb, kScanThreads, 0, st>>>(a);
-    const int64_t emit_blocks = (a.max_pairs + kEmitChunk - 1) / kEmitChunk;
-    pair_emit_kernel<<<(unsigned)(emit_blocks > 0 ? (emit_blocks < (1 << 30) ? emit_blocks : (1 << 30)) : 1), kEmitThreads,
-                       0, st>>>(a);
+    if (nb > 0) {
+        const int g = resident_grid(g_offsets, pair_offsets_kernel, kScanThreads);
+        pair_offsets_kernel<<<g < nb ? g : nb, kScanThreads, 0, st>>>(a, nb);
+    }
+    // one chunk of kEmitChunk pairs per block and turn; the pair count is known only on the
+    // device, so the grid is the resident one (capped by the capacity's chunks)
+    const int64_t emit_chunks = (a.max_pairs + kEmitChunk - 1) / kEmitChunk;
+    const int64_t ge = resident_grid(g_emit, pair_emit_kernel, kEmitThreads);
+    const int64_t emit_grid = emit_chunks < ge ? emit_chunks : ge;
+    pair_emit_kernel<<<(unsigned)(emit_grid > 0 ? emit_grid : 1), kEmitThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
